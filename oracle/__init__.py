@@ -1,0 +1,171 @@
+"""Test oracle for the DFS spectral-interpolation step.
+
+Test infrastructure only: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import it; the library path never does, and
+it shares no code with the CUDA path.
+
+Contents, each following the passage it cites:
+
+* :func:`evaluate` -- the exact result the NUFFT approximates: plain FP64
+  direct summation of Eq. 5.3 (type-II NUDFT, Sec. 5) in C (``dfs_oracle.c``),
+  OpenMP over points, Neumaier-compensated sums.
+* :func:`nudft_matrix` -- the same sum written as a dense NumPy matrix product,
+  usable on tiny grids only (brute-force pin).
+* :func:`complex_from_cossin` -- the map of Eq. 5.4 from the standard DFS
+  cosine/sine coefficients (Eq. 4.6-4.7) to complex coefficients, with the
+  rows the paper leaves out derived from the same expansion (n = 0 with a sine
+  part, m = 0 with n >= 1).
+* :func:`eval_cossin` -- direct evaluation of the standard DFS real form
+  (Eq. 4.6-4.7), an independent route to the same field values.
+
+Every function here is pinned by the ``-m "not gpu"`` tests against closed
+forms, invariants and library special cases (see tests/test_oracle_pins.py).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dfs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libdfsoracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (host code only, portable flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+               "-std=c11", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        lib.dfs_oracle_eval.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int]
+        lib.dfs_oracle_eval.restype = ctypes.c_int
+        lib.dfs_oracle_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def max_threads() -> int:
+    return int(_load().dfs_oracle_max_threads())
+
+
+def evaluate(coeffs: np.ndarray, lon: np.ndarray, colat: np.ndarray,
+             nthreads: int = 0) -> np.ndarray:
+    """Eq. 5.3 at every point, FP64.  ``coeffs`` is (N2, N1) or (F, N2, N1)
+    complex in the centred layout (row n + N2/2, column m + N1/2).  Returns the
+    complex values, shape (P,) or (F, P)."""
+    lib = _load()
+    c = np.ascontiguousarray(coeffs, dtype=np.complex128)
+    single = c.ndim == 2
+    if single:
+        c = c[None]
+    lon = np.ascontiguousarray(lon, dtype=np.float64)
+    colat = np.ascontiguousarray(colat, dtype=np.float64)
+    if lon.shape != colat.shape or lon.ndim != 1:
+        raise ValueError("lon and colat must be 1-D of equal length")
+    f, n2, n1 = c.shape
+    out = np.empty((f, lon.size), dtype=np.complex128)
+    for i in range(f):
+        rc = lib.dfs_oracle_eval(n1, n2, c[i].ctypes.data, lon.size, lon.ctypes.data,
+                                 colat.ctypes.data, out[i].ctypes.data, int(nthreads))
+        if rc != 0:
+            raise RuntimeError("dfs_oracle_eval failed with code %d" % rc)
+    return out[0] if single else out
+
+
+def nudft_matrix(coeffs: np.ndarray, lon: np.ndarray, colat: np.ndarray) -> np.ndarray:
+    """Eq. 5.3 as a dense matrix-vector product (tiny grids only)."""
+    c = np.asarray(coeffs, dtype=np.complex128)
+    n2, n1 = c.shape
+    n = np.arange(n2) - n2 // 2
+    m = np.arange(n1) - n1 // 2
+    a = np.exp(1j * (np.asarray(colat)[:, None, None] * n[None, :, None]
+                     + np.asarray(lon)[:, None, None] * m[None, None, :]))
+    return np.tensordot(a, c, axes=([1, 2], [0, 1]))
+
+
+def complex_from_cossin(fc: np.ndarray, fs: np.ndarray, n_lon: int, n_lat: int) -> np.ndarray:
+    """Eq. 5.4: standard DFS coefficients (index [n, m], n = 0..N, m = 0..M) to the
+    centred complex array of shape (2 n_lat, n_lon).
+
+    Even m multiply cos(n theta) (n >= 0), odd m multiply sin(n theta) (n >= 1),
+    per Eq. 4.7.  Rows used exactly as printed: n >= 1 for every m >= 1 and
+    n = 0, m = 0.  Rows derived from the same cos/sin expansion where the paper
+    is silent or prints only part: f_{0,+-m} = (fc -+ i fs)/2 for even m >= 2,
+    and f_{+-n,0} = fc_{n,0}/2 for n >= 1.
+    """
+    n2, n1 = 2 * n_lat, n_lon
+    N, M = fc.shape[0] - 1, fc.shape[1] - 1
+    if N >= n2 // 2 or M >= n1 // 2:
+        raise ValueError("cos/sin truncation exceeds the complex array")
+    out = np.zeros((n2, n1), dtype=np.complex128)
+    r0, q0 = n2 // 2, n1 // 2
+
+    def put(n, m, val):
+        out[n + r0, m + q0] += val
+
+    put(0, 0, fc[0, 0])
+    for n in range(1, N + 1):
+        put(n, 0, 0.5 * fc[n, 0])
+        put(-n, 0, 0.5 * fc[n, 0])
+    for m in range(1, M + 1):
+        if m % 2 == 0:
+            put(0, m, 0.5 * (fc[0, m] - 1j * fs[0, m]))
+            put(0, -m, 0.5 * (fc[0, m] + 1j * fs[0, m]))
+            for n in range(1, N + 1):
+                for sn in (1, -1):
+                    put(sn * n, m, 0.25 * (fc[n, m] - 1j * fs[n, m]))
+                    put(sn * n, -m, 0.25 * (fc[n, m] + 1j * fs[n, m]))
+        else:
+            for n in range(1, N + 1):
+                for sn in (1, -1):
+                    put(sn * n, m, -sn * 0.25 * (1j * fc[n, m] + fs[n, m]))
+                    put(sn * n, -m, -sn * 0.25 * (1j * fc[n, m] - fs[n, m]))
+    return out
+
+
+def eval_cossin(fc: np.ndarray, fs: np.ndarray, lon: np.ndarray, colat: np.ndarray) -> np.ndarray:
+    """Eq. 4.6-4.7: f = sum_m [F^c_m(theta) cos m phi + F^s_m(theta) sin m phi] with
+    F_m = sum_n f_{n,m} cos(n theta) for even m and sum_{n>=1} f_{n,m} sin(n theta)
+    for odd m (the sine-in-phi part is absent for m = 0)."""
+    lon = np.asarray(lon, dtype=np.float64)
+    colat = np.asarray(colat, dtype=np.float64)
+    N, M = fc.shape[0] - 1, fc.shape[1] - 1
+    out = np.zeros(lon.shape, dtype=np.float64)
+    for m in range(M + 1):
+        if m % 2 == 0:
+            basis = [np.cos(n * colat) for n in range(N + 1)]
+            n_lo = 0
+        else:
+            basis = [np.sin(n * colat) for n in range(N + 1)]
+            n_lo = 1
+        fcm = sum(fc[n, m] * basis[n] for n in range(n_lo, N + 1))
+        out += fcm * np.cos(m * lon)
+        if m > 0:
+            fsm = sum(fs[n, m] * basis[n] for n in range(n_lo, N + 1))
+            out += fsm * np.sin(m * lon)
+    return out
+
+
+def rel_linf(values: np.ndarray, reference: np.ndarray) -> float:
+    """max |v - o| / max |o| over the checked points (the acceptance measure)."""
+    v = np.asarray(values)
+    o = np.asarray(reference)
+    den = np.max(np.abs(o))
+    return float(np.max(np.abs(v - o)) / (den if den > 0 else 1.0))
