@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Benchmark of the DFS spectral-interpolation step (type-2 NUFFT) on GB300.
+
+One step = set_points (fold + bin the departure points) + execute (all fields:
+deconvolve/pad + theta FFT pass + phi FFT pass + interpolation) on one batch of
+synthetic input already resident in HBM.  The default workload is the
+2048 x 1024 grid with three fields (h, u, v) in FP32 with FP64 coordinate
+folding (2,097,152 departure points).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+With N > 1 the script runs under torch.distributed.run, one replica per GPU
+(the interpolation of independent members shards with no exchange: weak scaling).
+``--impl reference`` times the FP64 direct-sum oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NUFFT interp points·fields/s at stated error; HBM roofline frac; p50/p99 lat"
+UNIT = "point-fields/s"
+L2_FLUSH_BYTES = 512 << 20          # written between timed steps (L2 is 126 MB)
+
+WORKLOADS = {
+    "c3_2048x1024_f32": ("f32", "c3"),
+    "c3_2048x1024_f64": ("f64", "c3"),
+    "c2_512x256_f64": ("f64", "c2"),
+    "c2_512x256_f32": ("f32", "c2"),
+    "c1_64x32_f64": ("f64", "c1"),
+}
+DEFAULT_WORKLOAD = "c3_2048x1024_f32"
+
+
+def make_workload(name):
+    from paper_2605_01313_gb300 import synth
+    dtype, kind = WORKLOADS[name]
+    if kind == "c3":
+        return synth.workload_c3(dtype)
+    if kind == "c2":
+        return synth.workload_c2(dtype)
+    return synth.workload_c1()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.lines = []
+        self.proc = None
+        self.gpu_id = gpu_id
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def stage_bytes(prm, n_fields, n_points, rows):
+    """Algorithmic HBM bytes per launch of each stage (one execute of all fields)."""
+    cs = 16 if prm["dtype"] == 0 else 8
+    rs = cs // 2
+    N1, N2, n1 = prm["N1"], prm["N2"], prm["n1"]
+    F, P = n_fields, n_points
+    rec = 8 + 2 * rs + 4                       # sorted record: base int2, offsets, index
+    return {
+        "set_points": P * (16 + 4) + P * (16 + 4) + P * rec,
+        "theta_pass": F * (N2 * N1 * cs + rows * N1 * cs) + 8 * (N1 + N2),
+        "phi_pass": F * (rows * N1 * cs + rows * n1 * cs),
+        "interp": F * (rows * n1 * cs + P * rs) + P * rec,
+    }
+
+
+def interp_flops(prm, n_fields, n_points):
+    w = prm["w"]
+    return n_fields * n_points * 4 * w * (w + 1)
+
+
+def profile_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and
+    workload, if the kernel's source is unchanged since the capture."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith(".md"):
+            continue
+        text = open(os.path.join(pdir, fn)).read()
+        meta = dict(re.findall(r"^- (\w+): `?([^`\n]+)`?$", text, flags=re.M))
+        if meta.get("stage") != kernel or meta.get("workload") != workload:
+            continue
+        src = meta.get("source_file")
+        if not src or "dram_bytes_per_launch" not in meta:
+            continue
+        path = os.path.join(ROOT, src)
+        if not os.path.exists(path):
+            continue
+        h = hashlib.sha1(open(path, "rb").read()).hexdigest()
+        if h != meta.get("source_sha1"):
+            return None
+        try:
+            return float(meta["dram_bytes_per_launch"])
+        except ValueError:
+            return None
+    return None
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    from paper_2605_01313_gb300 import Plan, nufft
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    wl = make_workload(args.workload)
+    F, P = wl.n_fields, wl.n_points
+    cd = torch.complex128 if wl.dtype == "f64" else torch.complex64
+    rd = torch.float64 if wl.dtype == "f64" else torch.float32
+    lon = torch.from_numpy(wl.lon).to(dev)
+    colat = torch.from_numpy(wl.colat).to(dev)
+    coeffs = torch.from_numpy(wl.coeffs).to(cd).to(dev)
+    out = torch.empty((F, P), dtype=rd, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    plan = Plan(wl.n_lon, wl.n_lat, wl.tol, wl.dtype, F, stream=stream)
+    prm = plan.params
+
+    def step():
+        plan.set_points(lon, colat)
+        plan.execute(coeffs, out)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize(dev)
+    stats = nufft.dfsnufft_plan_point_stats(plan._h)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    sampler = ClockSampler(("GPU-" + str(uuid)) if uuid else None)
+    nufft.dfsnufft_plan_enable_timing(plan._h, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    for i in range(args.steps):
+        flush.fill_(i & 255)                  # untimed: evicts L2 between timed steps
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    stage = nufft.dfsnufft_plan_read_timing(plan._h)
+    nufft.dfsnufft_plan_enable_timing(plan._h, False)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * F * P * args.steps / (total_ms * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    h_lon, h_colat = pin(wl.lon), pin(wl.colat)
+    h_coef = pin(wl.coeffs.astype(np.complex128 if wl.dtype == "f64" else np.complex64))
+    h_out = torch.empty((F, P), dtype=rd).pin_memory().numpy()
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        plan.set_points_host(h_lon, h_colat)
+        plan.execute_host(h_coef, h_out)
+    e2e_ms = []
+    for _ in range(e2e_steps):
+        flush.fill_(3)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        plan.set_points_host(h_lon, h_colat)
+        plan.execute_host(h_coef, h_out)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = sum(e2e_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = ws * F * P * e2e_steps / (e2e_total * 1e-3)
+    h2d = 2 * 8 * P + h_coef.nbytes
+    d2h = h_out.nbytes
+    assert np.array_equal(h_out, out.cpu().numpy()), "host and device paths disagree"
+
+    if rank != 0:
+        plan.destroy()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel
+    pk, pk_kind = peaks()
+    per_stage_ms = {k: (v[0] / v[1] if v[1] else None) for k, v in stage.items()}
+    sbytes = stage_bytes(prm, F, P, stats["rows_needed"])
+    dom = max(("theta_pass", "phi_pass", "interp", "set_points"),
+              key=lambda k: per_stage_ms[k] or 0.0)
+    dom_ms = per_stage_ms[dom]
+    if wl.dtype == "f64" and dom == "interp":
+        fma = nufft.dfsnufft_probe_fma_rate("f64", 20.0)
+        achieved = interp_flops(prm, F, P) / (dom_ms * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fma / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / (fma / 1e12),
+                "peak_source": "measured FP64 FMA rate (dfsnufft_probe_fma_rate)",
+                "traffic": profile_traffic(dom, args.workload)}
+    else:
+        achieved = sbytes[dom] / (dom_ms * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                "peak_source": "%s hbm_gbs" % pk_kind,
+                "traffic": profile_traffic(dom, args.workload)}
+    stages_out = {}
+    for k in per_stage_ms:
+        ms = per_stage_ms[k]
+        stages_out[k] = {"ms": ms, "bytes": sbytes[k],
+                         "gbs": (sbytes[k] / (ms * 1e-3) / 1e9) if ms else None}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": wl.dtype, "data": "synthetic",
+        "config": {"workload": args.workload, "grid": "%dx%d" % (wl.n_lon, wl.n_lat),
+                   "modes": "%dx%d" % (2 * wl.n_lat, wl.n_lon), "fields": F, "points": P,
+                   "tol": wl.tol, "w": prm["w"], "fine": "%dx%d" % (prm["n2"], prm["n1"]),
+                   "rows_needed": stats["rows_needed"], "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roof,
+        "stages": stages_out,
+        "gpu_launches": 6 * args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / e2e_steps},
+        "clocks": clocks,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"], line["error"] = cpu_baseline(wl, out.cpu().numpy(), args.cpu_seconds)
+    plan.destroy()
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _oracle_sample_size(wl, seconds):
+    import oracle
+    probe = wl.sample[:4]
+    t0 = time.perf_counter()
+    oracle.evaluate(wl.coeffs, wl.lon[probe], wl.colat[probe])
+    per_point = (time.perf_counter() - t0) / probe.size
+    return int(max(8, min(wl.sample.size, seconds / max(per_point, 1e-9))))
+
+
+def cpu_baseline(wl, gpu_vals, seconds):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    workload's checked points; also the GPU error on that sample."""
+    import oracle
+    n = _oracle_sample_size(wl, seconds)
+    s = wl.sample[:n]
+    t0 = time.perf_counter()
+    ref = oracle.evaluate(wl.coeffs, wl.lon[s], wl.colat[s])
+    dt = time.perf_counter() - t0
+    err = [oracle.rel_linf(gpu_vals[f][s], ref[f].real) for f in range(wl.n_fields)]
+    base = {"value": n * wl.n_fields / dt, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": "%d of the workload's seeded check points x %d fields, FP64 direct sum"
+                      % (n, wl.n_fields)}
+    bound = 1e-11 if wl.dtype == "f64" else 2e-5
+    return base, {"rel_linf_per_field": err, "bound": bound, "ok": max(err) <= bound,
+                  "points_checked": int(n)}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    wl = make_workload(args.workload)
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    n = _oracle_sample_size(wl, per_step)
+    times = []
+    for i in range(args.warmup + args.steps):
+        s = wl.sample[(i * n) % wl.sample.size:][:n]
+        if s.size < n:
+            s = wl.sample[:n]
+        t0 = time.perf_counter()
+        oracle.evaluate(wl.coeffs, wl.lon[s], wl.colat[s])
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * n * wl.n_fields / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": "%dx%d" % (wl.n_lon, wl.n_lat),
+                   "fields": wl.n_fields, "points": wl.n_points},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle",
+                         "sample": "%d points x %d fields per step, FP64 direct sum"
+                                   % (n, wl.n_fields)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    ws, _, _ = dist_env()
+    if args.gpus > 1 and ws == 1 and "LOCAL_RANK" not in os.environ:
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+               "--nproc-per-node", str(args.gpus), "--master-addr", "127.0.0.1",
+               "--master-port", "29533"] + sys.argv
+        sys.exit(subprocess.call(cmd))
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from paper_2605_01313_gb300 import build
+        build.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

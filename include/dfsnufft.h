@@ -1,0 +1,164 @@
+/*
+ * dfsnufft -- GB300 (sm_103a) type-2 NUFFT for DFS spectral interpolation.
+ *
+ * The operation (Sec. 5, Eq. 5.3): given the complex coefficients c_{n,m} of a
+ * field's bivariate Fourier series on the doubled sphere and P departure
+ * points (phi_p, theta_p), evaluate
+ *
+ *     v_p = sum_{n=-N2/2}^{N2/2-1} sum_{m=-N1/2}^{N1/2-1} c_{n,m} e^{i m phi_p} e^{i n theta_p}
+ *
+ * for every point: the type-II nonuniform DFT that the paper evaluates with a
+ * NUFFT (Sec. 5) in place of Lagrange interpolation at the semi-Lagrangian
+ * departure points (Sec. 2).  For an n_lat x n_lon Grid [0] (Sec. 3,
+ * n_lon = 2J) the coefficient array is N2 x N1 = (2 n_lat) x n_lon.
+ *
+ * Method: exponential-of-semicircle spreading kernel of width w and shape
+ * beta (w = ceil(log10(1/tol)) + 1, beta = 2.30 w), oversampling sigma >= 2
+ * to power-of-two fine sizes; deconvolve-and-pad, 2-D inverse FFT (sign +1),
+ * then a w x w interpolation at each point from the fine grid.
+ *
+ * Conventions common to every entry point
+ *  - Coefficients: n_fields x N2 x N1 complex, C-contiguous, interleaved
+ *    (re, im), m fastest.  Row r <-> n = r - N2/2, column q <-> m = q - N1/2.
+ *    complex128 for DFSNUFFT_F64 plans, complex64 for DFSNUFFT_F32 plans.
+ *    The Nyquist row/column (n = -N2/2, m = -N1/2) are evaluated literally.
+ *  - Points: two arrays of n_points float64 (radians): longitude phi and
+ *    colatitude theta.  Any real value is accepted; both are wrapped by
+ *    2 pi periodicity of the doubled torus.  Points with colatitude in
+ *    [0, pi] (the physical sphere) touch only half of the fine grid, and only
+ *    that half is computed.
+ *  - Values: n_fields x n_points real (float64 or float32 by plan dtype),
+ *    Re(v_p) in the caller's point order.
+ *  - Streams: every device call is enqueued on the plan's CUDA stream and
+ *    returns after enqueue (asynchronous); results are ready when the stream
+ *    reaches that point.  A plan is not thread-safe.
+ *  - Ownership: the caller allocates and owns every input and output buffer.
+ *    The plan owns its fine grids, deconvolution factors, twiddle tables and
+ *    sorted point data; set_points copies what it needs, so the point
+ *    buffers may be reused once the stream has passed the call.
+ *  - Errors: every function returns a status (0 = DFSNUFFT_OK).  No exception
+ *    or abort crosses this boundary.  A CUDA failure makes the plan's status
+ *    sticky: later calls on that plan return DFSNUFFT_ERR_CUDA until it is
+ *    destroyed; dfsnufft_plan_last_error() gives the message.
+ */
+#ifndef DFSNUFFT_H
+#define DFSNUFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dfsnufft_plan_s *dfsnufft_plan;
+
+/* Arithmetic type of a plan. */
+enum { DFSNUFFT_F64 = 0, DFSNUFFT_F32 = 1 };
+
+/* Status codes. */
+enum {
+    DFSNUFFT_OK = 0,
+    DFSNUFFT_ERR_INVALID_ARG = 1,      /* bad size, dtype, null pointer, odd dims   */
+    DFSNUFFT_ERR_TOL_UNATTAINABLE = 2, /* tol below 1e-15 (F64) or 1e-7 (F32)       */
+    DFSNUFFT_ERR_NO_POINTS = 3,        /* execute before set_points                 */
+    DFSNUFFT_ERR_OOM = 4,              /* device allocation failed                  */
+    DFSNUFFT_ERR_CUDA = 5,             /* a CUDA call failed (sticky per plan)      */
+    DFSNUFFT_ERR_UNSUPPORTED = 6       /* size outside the supported range          */
+};
+
+/* Parameters a plan chooses (also available without a GPU). */
+typedef struct {
+    int n_lon, n_lat;      /* grid: N1 = n_lon phi-modes, N2 = 2 n_lat theta-modes  */
+    int N1, N2;            /* coefficient array dims (columns, rows)               */
+    int n1, n2;            /* fine (oversampled) grid dims, powers of two          */
+    int w;                 /* kernel width in fine-grid cells                      */
+    double beta;           /* kernel shape parameter                               */
+    double tol;            /* requested tolerance                                  */
+    int dtype;             /* DFSNUFFT_F64 or DFSNUFFT_F32                          */
+    int tile_x, tile_y;    /* interpolation bin size in fine cells                 */
+} dfsnufft_params;
+
+/* Create a plan for an n_lat x n_lon grid.
+ *   n_lon : even, >= 4; N1 = n_lon phi-modes.  n_lat >= 2; N2 = 2 n_lat.
+ *   tol   : requested relative accuracy, 1e-15 <= tol < 1 (F64),
+ *           1e-7 <= tol < 1 (F32).
+ *   dtype : DFSNUFFT_F64 or DFSNUFFT_F32.
+ *   n_fields : fields evaluated per execute at the same points (>= 1).
+ *   stream : cudaStream_t to enqueue on (NULL = legacy default stream).
+ *   out    : receives the plan handle (owned by the library until destroy).
+ * Fine grids up to 8192 x 8192 are supported (ERR_UNSUPPORTED above). */
+int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype, int n_fields,
+                         void *stream, dfsnufft_plan *out);
+
+/* Give the plan its departure points (device pointers, float64 radians,
+ * n_points each, 1 <= n_points < 2^31).  Folds them onto the fine-grid torus
+ * in FP64, sorts them by interpolation bin (counting sort) and marks the fine
+ * rows they touch.  Replaces any previous points. */
+int dfsnufft_set_points(dfsnufft_plan plan, int64_t n_points, const double *lon,
+                        const double *colat);
+
+/* Evaluate all n_fields series at the plan's points (Eq. 5.3).
+ *   coeffs : device pointer, n_fields x N2 x N1 complex (see conventions).
+ *   values : device pointer, n_fields x n_points real, written in full. */
+int dfsnufft_execute(dfsnufft_plan plan, const void *coeffs, void *values);
+
+/* Host-buffer variants: the same operations with host pointers.  The data are
+ * copied to plan-owned device buffers on the plan's stream (pinned host memory
+ * makes the copies asynchronous); dfsnufft_execute_host waits for the stream
+ * before it returns, so values are ready on return. */
+int dfsnufft_set_points_host(dfsnufft_plan plan, int64_t n_points, const double *lon,
+                             const double *colat);
+int dfsnufft_execute_host(dfsnufft_plan plan, const void *coeffs, void *values);
+
+/* Release every device buffer of the plan (synchronises its stream first). */
+int dfsnufft_destroy(dfsnufft_plan plan);
+
+/* Static description of a status code. */
+const char *dfsnufft_strerror(int status);
+
+/* Last error message recorded on the plan ("" if none). */
+const char *dfsnufft_plan_last_error(dfsnufft_plan plan);
+
+/* Parameters of an existing plan. */
+int dfsnufft_plan_get_params(dfsnufft_plan plan, dfsnufft_params *out);
+
+/* Stage timing.  Stages: 0 set_points (fold, scan, scatter), 1 theta pass
+ * (deconvolve, pad, column FFTs), 2 phi pass (row FFTs), 3 interpolation.
+ * When enabled, the plan records a CUDA event pair around every stage on its
+ * stream.  dfsnufft_plan_read_timing synchronises the stream, adds the elapsed
+ * times of all pending pairs to the running totals, and copies the totals
+ * (milliseconds) and the number of timed calls of each stage into the
+ * caller's arrays of DFSNUFFT_N_STAGES entries; enabling resets the totals.
+ * Measurement aid of this library; the paper has no counterpart. */
+#define DFSNUFFT_N_STAGES 4
+int dfsnufft_plan_enable_timing(dfsnufft_plan plan, int enable);
+int dfsnufft_plan_read_timing(dfsnufft_plan plan, double *ms_total, int64_t *calls);
+
+/* Work statistics of the current points (synchronises the stream): the
+ * number of fine rows the points' stencils touch (per field) and the number
+ * of non-empty interpolation bins.  Measurement aid; no paper counterpart. */
+int dfsnufft_plan_point_stats(dfsnufft_plan plan, int64_t *rows_needed, int64_t *nonempty_bins);
+
+/* ---- host-only helpers (no GPU needed) ---------------------------------- */
+
+/* Parameters a plan with these arguments would use. */
+int dfsnufft_choose_params(int n_lon, int n_lat, double tol, int dtype, dfsnufft_params *out);
+
+/* The kernel phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)) for |z| < w/2, else 0
+ * (z in fine-grid cells). */
+double dfsnufft_es_kernel(double z, int w, double beta);
+
+/* Fourier transform of the kernel at the centred modes of a length-n_modes
+ * series on a fine grid of n_fine cells:
+ *   out[q] = integral phi(z) cos(2 pi k z / n_fine) dz,  k = q - n_modes/2,
+ * by Gauss-Legendre quadrature in FP64.  Deconvolution divides by these. */
+int dfsnufft_kernel_ft(int w, double beta, int n_fine, int n_modes, double *out);
+
+/* Library version string. */
+const char *dfsnufft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFSNUFFT_H */

@@ -1,0 +1,15 @@
+"""dfsnufft: GB300-native type-2 NUFFT for the spectral interpolation step of the
+double-Fourier-sphere semi-implicit semi-Lagrangian shallow-water scheme.
+
+The compute path is the CUDA library built from ``csrc/`` (C ABI in
+``include/dfsnufft.h``); :mod:`.nufft` is its Python binding and :mod:`.synth`
+draws seeded synthetic inputs.
+"""
+__all__ = ["Plan", "nufft", "synth"]
+
+
+def __getattr__(name):
+    if name == "Plan":
+        from .nufft import Plan
+        return Plan
+    raise AttributeError(name)

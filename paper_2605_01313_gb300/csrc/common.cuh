@@ -1,0 +1,87 @@
+// Internal definitions shared by the dfsnufft translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dfsnufft.h"
+
+// ---------------------------------------------------------------- complex helpers
+template <typename R> struct CxT;
+template <> struct CxT<float> { typedef float2 type; };
+template <> struct CxT<double> { typedef double2 type; };
+
+__host__ __device__ __forceinline__ float2 cmake(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 cmake(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+template <typename C>
+__host__ __device__ __forceinline__ C cmul(C a, C b) {
+    return cmake(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// ---------------------------------------------------------------- plan layout
+// Row-block granularity of the "fine rows needed" mask (rows per flag).
+#define DFS_ROW_BLOCK 16
+// Elements each FFT thread holds in registers (radix-16 Stockham stages).
+#define DFS_FFT_E 16
+#define DFS_FFT_MIN_LOG 4
+#define DFS_FFT_MAX_LOG 13
+// Event pairs kept per stage before read_timing must drain them.
+#define DFS_TIMING_SLOTS 64
+
+struct dfsnufft_plan_s {
+    dfsnufft_params prm;
+    int n_fields;
+    int c0;                 // first tap sits c0 cells left of the point's base cell
+    int nbx, nby, nbins;    // interpolation bins
+    int n_row_blocks;       // blocks of DFS_ROW_BLOCK fine rows
+    cudaStream_t stream;
+
+    // device buffers owned by the plan
+    double *d_inv1;         // N1: 1 / phihat(m), centred
+    double *d_inv2;         // N2: 1 / phihat(n), centred
+    void *d_tw1;            // n1 twiddles e^{+2 pi i k / n1} (plan precision)
+    void *d_tw2;            // n2 twiddles
+    void *d_T;              // theta-pass output, n_fields x n2 x N1
+    void *d_G;              // fine grids, n_fields x n2 x n1
+    int *d_bin_count;       // nbins
+    int *d_bin_start;       // nbins + 1
+    int *d_task_bin;        // nbins: list of non-empty bins
+    int *d_n_tasks;         // 1
+    unsigned char *d_rowmask;   // n_row_blocks (fine rows, mod n2)
+
+    // point data (capacity grows with set_points)
+    int64_t n_points, cap_points;
+    int *d_rank;            // rank of each point inside its bin (input order)
+    int2 *d_base;           // sorted: first-tap fine index (i0, j0)
+    void *d_frac;           // sorted: offsets (tx, ty) in plan precision
+    int *d_idx;             // sorted: original point index
+    double *d_pts_stage;    // host-variant staging: 2 x cap_points
+    void *d_coef_stage;     // host-variant staging of coefficients
+    void *d_val_stage;      // host-variant staging of values
+    int64_t val_stage_cap;
+    int64_t pts_stage_cap;
+
+    // stage timing (dfsnufft_plan_enable_timing)
+    int timing;
+    cudaEvent_t *ev;            // 2 * DFS_TIMING_SLOTS * DFSNUFFT_N_STAGES events
+    int pending[DFSNUFFT_N_STAGES];
+    double ms_total[DFSNUFFT_N_STAGES];
+    int64_t calls[DFSNUFFT_N_STAGES];
+
+    int has_points;
+    int status;             // sticky CUDA status
+    char msg[512];
+};
+
+// ---------------------------------------------------------------- launches
+// points.cu
+cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const double *colat);
+// fft.cu
+cudaError_t dfs_launch_theta_pass(dfsnufft_plan p, const void *coeffs);
+cudaError_t dfs_launch_phi_pass(dfsnufft_plan p);
+// interp.cu
+cudaError_t dfs_launch_interp(dfsnufft_plan p, void *values);

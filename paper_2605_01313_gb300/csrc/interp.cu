@@ -1,0 +1,168 @@
+// Interpolation from the fine grid to the departure points: the last stage of
+// the type-2 NUFFT evaluating Eq. 5.3 (Sec. 5).  For each point
+//
+//   v_p = sum_{b<w} sum_{a<w} phi(z_b^y) phi(z_a^x) G[j0 + b][i0 + a]   (indices mod n)
+//
+// with phi the exponential-of-semicircle kernel
+// phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)) and z_a = (a - c0) - t the
+// offsets produced by set_points.
+//
+// Points arrive sorted by bin (tile_x x tile_y fine cells); one CTA takes a
+// bin, stages the bin's tile plus its (w-1)-cell halo of every field into
+// shared memory with coalesced loads, and each thread then evaluates one
+// point at a time from shared memory, computing its 2w kernel values once
+// for all fields.
+#include "common.cuh"
+
+namespace {
+
+struct InterpArgs {
+    int n1, n2;
+    int tile_x, tile_y, nbx;
+    int c0;
+    int F, FG;            // fields, fields staged per pass
+    int P;
+    double beta;
+};
+
+template <typename R> __device__ __forceinline__ R kexp(R x);
+template <> __device__ __forceinline__ float kexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double kexp<double>(double x) { return exp(x); }
+template <typename R> __device__ __forceinline__ R ksqrt(R x);
+template <> __device__ __forceinline__ float ksqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double ksqrt<double>(double x) { return sqrt(x); }
+
+// Kernel values at the W taps of one dimension: z_a = (a - c0) - t.
+template <typename R, int W>
+__device__ __forceinline__ void es_weights(R t, int c0, R beta, R *wv) {
+    const R two_over_w = (R)2 / (R)W;
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        const R z = (R)(a - c0) - t;
+        const R u = z * two_over_w;
+        const R s = ((R)1 - u) * ((R)1 + u);
+        // written so that a NaN offset propagates to the value
+        wv[a] = s <= (R)0 ? (R)0 : kexp<R>(beta * (ksqrt<R>(s) - (R)1));
+    }
+}
+
+template <typename R, int W>
+__global__ void __launch_bounds__(256) k_interp(InterpArgs a,
+                                                const typename CxT<R>::type *__restrict__ grid,
+                                                const int2 *__restrict__ base,
+                                                const R *__restrict__ frac,
+                                                const int *__restrict__ idx,
+                                                const int *__restrict__ bin_start,
+                                                const int *__restrict__ task_bin,
+                                                const int *__restrict__ n_tasks,
+                                                R *__restrict__ out) {
+    typedef typename CxT<R>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tile = reinterpret_cast<C *>(smem_raw);
+    const int TH = a.tile_y + W - 1;
+    const int TW = a.tile_x + W - 1;
+    const int tsz = TH * TW;
+    const int ntask = *n_tasks;
+    const R beta = (R)a.beta;
+    for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+        const int bin = task_bin[task];
+        const int by = bin / a.nbx;
+        const int bx = bin - by * a.nbx;
+        const int col0 = bx * a.tile_x - a.c0;
+        const int row0 = by * a.tile_y - a.c0;
+        const int s = bin_start[bin];
+        const int e = bin_start[bin + 1];
+        for (int f0 = 0; f0 < a.F; f0 += a.FG) {
+            const int fg = min(a.FG, a.F - f0);
+            __syncthreads();
+            for (int k = threadIdx.x; k < fg * tsz; k += blockDim.x) {
+                const int ff = k / tsz;
+                const int rem = k - ff * tsz;
+                const int r = rem / TW;
+                const int cc = rem - r * TW;
+                const int gr = (row0 + r) & (a.n2 - 1);
+                const int gc = (col0 + cc) & (a.n1 - 1);
+                tile[k] = grid[((size_t)(f0 + ff) * a.n2 + gr) * a.n1 + gc];
+            }
+            __syncthreads();
+            for (int pi = s + threadIdx.x; pi < e; pi += blockDim.x) {
+                const int2 b = base[pi];
+                R wx[W], wy[W];
+                es_weights<R, W>(frac[2 * pi], a.c0, beta, wx);
+                es_weights<R, W>(frac[2 * pi + 1], a.c0, beta, wy);
+                const int ox = b.x - col0;
+                const int oy = b.y - row0;
+                const int dst = idx[pi];
+                for (int ff = 0; ff < fg; ++ff) {
+                    const C *tp = tile + ff * tsz + oy * TW + ox;
+                    R acc_re = 0, acc_im = 0;
+#pragma unroll
+                    for (int bb = 0; bb < W; ++bb) {
+                        R rr = 0, ri = 0;
+#pragma unroll
+                        for (int aa = 0; aa < W; ++aa) {
+                            const C g = tp[bb * TW + aa];
+                            rr += wx[aa] * g.x;
+                            ri += wx[aa] * g.y;
+                        }
+                        acc_re += wy[bb] * rr;
+                        acc_im += wy[bb] * ri;
+                    }
+                    (void)acc_im;
+                    out[(size_t)(f0 + ff) * a.P + dst] = acc_re;
+                }
+            }
+        }
+    }
+}
+
+template <typename R, int W>
+cudaError_t launch_w(dfsnufft_plan p, void *values) {
+    typedef typename CxT<R>::type C;
+    const dfsnufft_params &q = p->prm;
+    InterpArgs a;
+    a.n1 = q.n1;
+    a.n2 = q.n2;
+    a.tile_x = q.tile_x;
+    a.tile_y = q.tile_y;
+    a.nbx = p->nbx;
+    a.c0 = p->c0;
+    a.F = p->n_fields;
+    a.P = (int)p->n_points;
+    a.beta = q.beta;
+    const size_t per_field = sizeof(C) * (size_t)(q.tile_y + W - 1) * (q.tile_x + W - 1);
+    int fg = (int)((96 * 1024) / per_field);
+    if (fg < 1) fg = 1;
+    if (fg > a.F) fg = a.F;
+    a.FG = fg;
+    const size_t smem = per_field * fg;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_interp<R, W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e) return e;
+    }
+    const int threads = sizeof(R) == 4 ? 128 : 256;
+    int blocks = p->nbins < 152 * 16 ? p->nbins : 152 * 16;
+    k_interp<R, W><<<blocks, threads, smem, p->stream>>>(
+        a, (const C *)p->d_G, p->d_base, (const R *)p->d_frac, p->d_idx, p->d_bin_start,
+        p->d_task_bin, p->d_n_tasks, (R *)values);
+    return cudaGetLastError();
+}
+
+template <typename R, int W>
+cudaError_t dispatch(dfsnufft_plan p, void *values, int w) {
+    if constexpr (W > 16) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (w == W) return launch_w<R, W>(p, values);
+        return dispatch<R, W + 1>(p, values, w);
+    }
+}
+
+}  // namespace
+
+cudaError_t dfs_launch_interp(dfsnufft_plan p, void *values) {
+    if (p->prm.dtype == DFSNUFFT_F64) return dispatch<double, 2>(p, values, p->prm.w);
+    return dispatch<float, 2>(p, values, p->prm.w);
+}

@@ -1,0 +1,532 @@
+// Host runtime and C ABI of dfsnufft: plan parameters, deconvolution factors,
+// device memory, and the entry points declared in include/dfsnufft.h.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+#define DFS_VERSION "dfsnufft 0.1 (sm_103a)"
+
+static const double kPi = 3.14159265358979323846264338327950288;
+
+// ------------------------------------------------------------------ helpers
+
+static int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+static void set_msg(dfsnufft_plan p, const char *what, cudaError_t e) {
+    snprintf(p->msg, sizeof(p->msg), "%s: %s (%s)", what, cudaGetErrorName(e),
+             cudaGetErrorString(e));
+}
+
+// Record a CUDA failure on the plan (sticky) and return the ABI status.
+static int fail_cuda(dfsnufft_plan p, const char *what, cudaError_t e) {
+    p->status = DFSNUFFT_ERR_CUDA;
+    set_msg(p, what, e);
+    return DFSNUFFT_ERR_CUDA;
+}
+
+#define DFS_CK(p, call)                                                   \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return fail_cuda((p), #call, e_);          \
+    } while (0)
+
+static int dfs_alloc(dfsnufft_plan p, void **ptr, size_t bytes, const char *what) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        snprintf(p->msg, sizeof(p->msg), "out of device memory allocating %s (%zu bytes)", what,
+                 bytes);
+        *ptr = nullptr;
+        return DFSNUFFT_ERR_OOM;
+    }
+    if (e != cudaSuccess) return fail_cuda(p, what, e);
+    return DFSNUFFT_OK;
+}
+
+static void dfs_free(void **ptr) {
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+}
+
+// ------------------------------------------------------------------ stage timing
+
+static cudaEvent_t *stage_event(dfsnufft_plan p, int stage, int slot, int which) {
+    return &p->ev[((size_t)stage * DFS_TIMING_SLOTS + slot) * 2 + which];
+}
+
+static cudaError_t timing_drain(dfsnufft_plan p) {
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e) return e;
+    for (int s = 0; s < DFSNUFFT_N_STAGES; ++s) {
+        for (int i = 0; i < p->pending[s]; ++i) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, *stage_event(p, s, i, 0), *stage_event(p, s, i, 1));
+            if (e) return e;
+            p->ms_total[s] += ms;
+            p->calls[s] += 1;
+        }
+        p->pending[s] = 0;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t timing_begin(dfsnufft_plan p, int stage) {
+    if (!p->timing) return cudaSuccess;
+    if (p->pending[stage] == DFS_TIMING_SLOTS) {
+        cudaError_t e = timing_drain(p);
+        if (e) return e;
+    }
+    return cudaEventRecord(*stage_event(p, stage, p->pending[stage], 0), p->stream);
+}
+
+static cudaError_t timing_end(dfsnufft_plan p, int stage) {
+    if (!p->timing) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(*stage_event(p, stage, p->pending[stage], 1), p->stream);
+    p->pending[stage] += 1;
+    return e;
+}
+
+// ------------------------------------------------------------------ kernel math (host)
+
+extern "C" double dfsnufft_es_kernel(double z, int w, double beta) {
+    double u = 2.0 * z / (double)w;
+    if (!(fabs(u) < 1.0)) return 0.0;
+    return exp(beta * (sqrt((1.0 - u) * (1.0 + u)) - 1.0));
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_q, using the
+// three-term recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1} and
+// P_q'(x) = q (x P_q - P_{q-1}) / (x^2 - 1).  legendre_pair gives P_q, P_{q-1}.
+static void legendre_pair(int q, double z, double *pq, double *pq1) {
+    double p0 = 1.0, p1 = z;
+    for (int k = 1; k < q; ++k) {
+        double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    *pq = p1;
+    *pq1 = p0;
+}
+
+static void gauss_legendre(int q, double *x, double *wt) {
+    for (int i = 0; i < q; ++i) {
+        double z = cos(kPi * (i + 0.75) / (q + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double pq, pq1;
+            legendre_pair(q, z, &pq, &pq1);
+            double dz = pq / (q * (z * pq - pq1) / (z * z - 1.0));
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        double pq, pq1;
+        legendre_pair(q, z, &pq, &pq1);
+        double dp = q * (z * pq - pq1) / (z * z - 1.0);
+        x[i] = z;
+        wt[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+extern "C" int dfsnufft_kernel_ft(int w, double beta, int n_fine, int n_modes, double *out) {
+    if (w < 2 || w > 16 || !(beta > 0) || n_fine < 2 || n_modes < 1 || !out)
+        return DFSNUFFT_ERR_INVALID_ARG;
+    // phihat(xi) = int_{-w/2}^{w/2} phi(z) cos(xi z) dz
+    //            = w int_0^1 e^{beta (sqrt(1-u^2) - 1)} cos(xi w u / 2) du
+    //            = w int_0^{pi/2} e^{beta (cos s - 1)} cos(xi (w/2) sin s) cos s ds   (u = sin s)
+    // The substitution removes the square-root endpoint singularity, so the
+    // Gauss-Legendre rule converges exponentially.
+    const int q = 2 * w + 60;
+    double *x = (double *)malloc(sizeof(double) * q);
+    double *wt = (double *)malloc(sizeof(double) * q);
+    double *fz = (double *)malloc(sizeof(double) * q);
+    double *zz = (double *)malloc(sizeof(double) * q);
+    if (!x || !wt || !fz || !zz) {
+        free(x); free(wt); free(fz); free(zz);
+        return DFSNUFFT_ERR_INVALID_ARG;
+    }
+    gauss_legendre(q, x, wt);
+    for (int i = 0; i < q; ++i) {
+        double sv = 0.25 * kPi * (x[i] + 1.0);  // node mapped to [0, pi/2]
+        zz[i] = 0.5 * w * sin(sv);              // z in fine cells
+        fz[i] = 0.25 * kPi * wt[i] * exp(beta * (cos(sv) - 1.0)) * cos(sv);
+    }
+    for (int qi = 0; qi < n_modes; ++qi) {
+        double k = (double)(qi - n_modes / 2);
+        double xi = 2.0 * kPi * k / (double)n_fine;
+        double acc = 0.0;
+        for (int i = 0; i < q; ++i) acc += fz[i] * cos(xi * zz[i]);
+        out[qi] = w * acc;
+    }
+    free(x); free(wt); free(fz); free(zz);
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_choose_params(int n_lon, int n_lat, double tol, int dtype,
+                                      dfsnufft_params *out) {
+    if (!out) return DFSNUFFT_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    if (n_lon < 4 || (n_lon & 1) || n_lat < 2) return DFSNUFFT_ERR_INVALID_ARG;
+    if (dtype != DFSNUFFT_F64 && dtype != DFSNUFFT_F32) return DFSNUFFT_ERR_INVALID_ARG;
+    if (!(tol > 0.0) || !(tol < 1.0)) return DFSNUFFT_ERR_INVALID_ARG;
+    if (dtype == DFSNUFFT_F64 && tol < 1e-15) return DFSNUFFT_ERR_TOL_UNATTAINABLE;
+    if (dtype == DFSNUFFT_F32 && tol < 1e-7) return DFSNUFFT_ERR_TOL_UNATTAINABLE;
+    int w = (int)ceil(-log10(tol) - 1e-9) + 1;
+    if (w < 2) w = 2;
+    if (w > 16) w = 16;
+    out->n_lon = n_lon;
+    out->n_lat = n_lat;
+    out->N1 = n_lon;
+    out->N2 = 2 * n_lat;
+    int a1 = 2 * out->N1 > 2 * w ? 2 * out->N1 : 2 * w;
+    int a2 = 2 * out->N2 > 2 * w ? 2 * out->N2 : 2 * w;
+    out->n1 = next_pow2(a1 > 16 ? a1 : 16);
+    out->n2 = next_pow2(a2 > 16 ? a2 : 16);
+    if (out->n1 > (1 << DFS_FFT_MAX_LOG) || out->n2 > (1 << DFS_FFT_MAX_LOG))
+        return DFSNUFFT_ERR_UNSUPPORTED;
+    out->w = w;
+    out->beta = 2.30 * w;
+    out->tol = tol;
+    out->dtype = dtype;
+    out->tile_x = 32;
+    out->tile_y = dtype == DFSNUFFT_F32 ? 16 : 32;
+    if (out->tile_x > out->n1) out->tile_x = out->n1;
+    if (out->tile_y > out->n2) out->tile_y = out->n2;
+    return DFSNUFFT_OK;
+}
+
+extern "C" const char *dfsnufft_strerror(int status) {
+    switch (status) {
+        case DFSNUFFT_OK: return "ok";
+        case DFSNUFFT_ERR_INVALID_ARG: return "invalid argument";
+        case DFSNUFFT_ERR_TOL_UNATTAINABLE: return "tolerance unattainable in this precision";
+        case DFSNUFFT_ERR_NO_POINTS: return "execute called before set_points";
+        case DFSNUFFT_ERR_OOM: return "out of device memory";
+        case DFSNUFFT_ERR_CUDA: return "CUDA error";
+        case DFSNUFFT_ERR_UNSUPPORTED: return "size outside the supported range";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char *dfsnufft_version(void) { return DFS_VERSION; }
+
+// ------------------------------------------------------------------ plan lifetime
+
+static void release(dfsnufft_plan p) {
+    void **bufs[] = {(void **)&p->d_inv1, (void **)&p->d_inv2, &p->d_tw1, &p->d_tw2,
+                     &p->d_T, &p->d_G, (void **)&p->d_bin_count, (void **)&p->d_bin_start,
+                     (void **)&p->d_task_bin, (void **)&p->d_n_tasks, (void **)&p->d_rowmask,
+                     (void **)&p->d_rank, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
+                     (void **)&p->d_pts_stage, &p->d_coef_stage, &p->d_val_stage};
+    for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) dfs_free(bufs[i]);
+    if (p->ev) {
+        for (int i = 0; i < 2 * DFS_TIMING_SLOTS * DFSNUFFT_N_STAGES; ++i)
+            if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+        free(p->ev);
+        p->ev = nullptr;
+    }
+}
+
+template <typename C, typename R>
+static void fill_twiddles(C *h, int n) {
+    for (int k = 0; k < n; ++k) {
+        double a = 2.0 * kPi * (double)k / (double)n;
+        h[k].x = (R)cos(a);
+        h[k].y = (R)sin(a);
+    }
+}
+
+static int upload_tables(dfsnufft_plan p) {
+    const dfsnufft_params &q = p->prm;
+    int rc;
+    double *ft1 = (double *)malloc(sizeof(double) * q.N1);
+    double *ft2 = (double *)malloc(sizeof(double) * q.N2);
+    if (!ft1 || !ft2) {
+        free(ft1); free(ft2);
+        return DFSNUFFT_ERR_INVALID_ARG;
+    }
+    dfsnufft_kernel_ft(q.w, q.beta, q.n1, q.N1, ft1);
+    dfsnufft_kernel_ft(q.w, q.beta, q.n2, q.N2, ft2);
+    for (int i = 0; i < q.N1; ++i) ft1[i] = 1.0 / ft1[i];
+    for (int i = 0; i < q.N2; ++i) ft2[i] = 1.0 / ft2[i];
+    cudaError_t e1 = cudaMemcpy(p->d_inv1, ft1, sizeof(double) * q.N1, cudaMemcpyHostToDevice);
+    cudaError_t e2 = cudaMemcpy(p->d_inv2, ft2, sizeof(double) * q.N2, cudaMemcpyHostToDevice);
+    free(ft1);
+    free(ft2);
+    if (e1 != cudaSuccess) return fail_cuda(p, "upload deconvolution factors", e1);
+    if (e2 != cudaSuccess) return fail_cuda(p, "upload deconvolution factors", e2);
+
+    size_t cs = q.dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
+    void *h1 = malloc(cs * q.n1), *h2 = malloc(cs * q.n2);
+    if (!h1 || !h2) {
+        free(h1); free(h2);
+        return DFSNUFFT_ERR_INVALID_ARG;
+    }
+    if (q.dtype == DFSNUFFT_F64) {
+        fill_twiddles<double2, double>((double2 *)h1, q.n1);
+        fill_twiddles<double2, double>((double2 *)h2, q.n2);
+    } else {
+        fill_twiddles<float2, float>((float2 *)h1, q.n1);
+        fill_twiddles<float2, float>((float2 *)h2, q.n2);
+    }
+    e1 = cudaMemcpy(p->d_tw1, h1, cs * q.n1, cudaMemcpyHostToDevice);
+    e2 = cudaMemcpy(p->d_tw2, h2, cs * q.n2, cudaMemcpyHostToDevice);
+    free(h1);
+    free(h2);
+    if (e1 != cudaSuccess) return fail_cuda(p, "upload twiddles", e1);
+    if (e2 != cudaSuccess) return fail_cuda(p, "upload twiddles", e2);
+    rc = DFSNUFFT_OK;
+    return rc;
+}
+
+extern "C" int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype, int n_fields,
+                                    void *stream, dfsnufft_plan *out) {
+    if (!out) return DFSNUFFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_fields < 1 || n_fields > 64) return DFSNUFFT_ERR_INVALID_ARG;
+    dfsnufft_params prm;
+    int rc = dfsnufft_choose_params(n_lon, n_lat, tol, dtype, &prm);
+    if (rc != DFSNUFFT_OK) return rc;
+
+    dfsnufft_plan p = new (std::nothrow) dfsnufft_plan_s;
+    if (!p) return DFSNUFFT_ERR_OOM;
+    memset(p, 0, sizeof(*p));
+    p->prm = prm;
+    p->n_fields = n_fields;
+    p->stream = (cudaStream_t)stream;
+    p->c0 = (prm.w % 2 == 0) ? prm.w / 2 - 1 : (prm.w - 1) / 2;
+    p->nbx = prm.n1 / prm.tile_x + 1;
+    p->nby = prm.n2 / prm.tile_y + 1;
+    p->nbins = p->nbx * p->nby;
+    p->n_row_blocks = (prm.n2 + DFS_ROW_BLOCK - 1) / DFS_ROW_BLOCK;
+
+    size_t cs = dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
+    size_t nf = (size_t)n_fields;
+    struct { void **ptr; size_t bytes; const char *what; } allocs[] = {
+        {(void **)&p->d_inv1, sizeof(double) * prm.N1, "deconvolution factors"},
+        {(void **)&p->d_inv2, sizeof(double) * prm.N2, "deconvolution factors"},
+        {&p->d_tw1, cs * prm.n1, "twiddles"},
+        {&p->d_tw2, cs * prm.n2, "twiddles"},
+        {&p->d_T, cs * nf * prm.n2 * prm.N1, "theta-pass buffer"},
+        {&p->d_G, cs * nf * prm.n2 * prm.n1, "fine grid"},
+        {(void **)&p->d_bin_count, sizeof(int) * p->nbins, "bin counts"},
+        {(void **)&p->d_bin_start, sizeof(int) * (p->nbins + 1), "bin starts"},
+        {(void **)&p->d_task_bin, sizeof(int) * p->nbins, "bin list"},
+        {(void **)&p->d_n_tasks, sizeof(int), "bin list size"},
+        {(void **)&p->d_rowmask, (size_t)p->n_row_blocks, "row mask"},
+    };
+    for (size_t i = 0; i < sizeof(allocs) / sizeof(allocs[0]); ++i) {
+        rc = dfs_alloc(p, allocs[i].ptr, allocs[i].bytes, allocs[i].what);
+        if (rc != DFSNUFFT_OK) {
+            release(p);
+            delete p;
+            return rc;
+        }
+    }
+    rc = upload_tables(p);
+    if (rc != DFSNUFFT_OK) {
+        release(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_destroy(dfsnufft_plan p) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    cudaStreamSynchronize(p->stream);
+    release(p);
+    delete p;
+    return DFSNUFFT_OK;
+}
+
+extern "C" const char *dfsnufft_plan_last_error(dfsnufft_plan p) { return p ? p->msg : ""; }
+
+extern "C" int dfsnufft_plan_get_params(dfsnufft_plan p, dfsnufft_params *out) {
+    if (!p || !out) return DFSNUFFT_ERR_INVALID_ARG;
+    *out = p->prm;
+    return DFSNUFFT_OK;
+}
+
+// ------------------------------------------------------------------ points
+
+static int ensure_point_capacity(dfsnufft_plan p, int64_t n) {
+    if (n <= p->cap_points) return DFSNUFFT_OK;
+    // the stream may still use the old buffers
+    DFS_CK(p, cudaStreamSynchronize(p->stream));
+    dfs_free((void **)&p->d_rank);
+    dfs_free((void **)&p->d_base);
+    dfs_free(&p->d_frac);
+    dfs_free((void **)&p->d_idx);
+    p->cap_points = 0;
+    size_t rs = p->prm.dtype == DFSNUFFT_F64 ? sizeof(double) : sizeof(float);
+    int rc;
+    if ((rc = dfs_alloc(p, (void **)&p->d_rank, sizeof(int) * n, "point ranks")) ||
+        (rc = dfs_alloc(p, (void **)&p->d_base, sizeof(int2) * n, "point bases")) ||
+        (rc = dfs_alloc(p, &p->d_frac, 2 * rs * n, "point offsets")) ||
+        (rc = dfs_alloc(p, (void **)&p->d_idx, sizeof(int) * n, "point order")))
+        return rc;
+    p->cap_points = n;
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_set_points(dfsnufft_plan p, int64_t n_points, const double *lon,
+                                   const double *colat) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    if (n_points < 1 || n_points > 0x7fffffffLL || !lon || !colat)
+        return DFSNUFFT_ERR_INVALID_ARG;
+    int rc = ensure_point_capacity(p, n_points);
+    if (rc) return rc;
+    p->n_points = n_points;
+    p->has_points = 0;
+    DFS_CK(p, timing_begin(p, 0));
+    DFS_CK(p, dfs_launch_set_points(p, lon, colat));
+    DFS_CK(p, timing_end(p, 0));
+    p->has_points = 1;
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_execute(dfsnufft_plan p, const void *coeffs, void *values) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    if (!p->has_points) return DFSNUFFT_ERR_NO_POINTS;
+    if (!coeffs || !values) return DFSNUFFT_ERR_INVALID_ARG;
+    DFS_CK(p, timing_begin(p, 1));
+    DFS_CK(p, dfs_launch_theta_pass(p, coeffs));
+    DFS_CK(p, timing_end(p, 1));
+    DFS_CK(p, timing_begin(p, 2));
+    DFS_CK(p, dfs_launch_phi_pass(p));
+    DFS_CK(p, timing_end(p, 2));
+    DFS_CK(p, timing_begin(p, 3));
+    DFS_CK(p, dfs_launch_interp(p, values));
+    DFS_CK(p, timing_end(p, 3));
+    return DFSNUFFT_OK;
+}
+
+// ------------------------------------------------------------------ host-buffer variants
+
+extern "C" int dfsnufft_set_points_host(dfsnufft_plan p, int64_t n_points, const double *lon,
+                                        const double *colat) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    if (n_points < 1 || n_points > 0x7fffffffLL || !lon || !colat)
+        return DFSNUFFT_ERR_INVALID_ARG;
+    int rc = ensure_point_capacity(p, n_points);
+    if (rc) return rc;
+    if (p->pts_stage_cap < p->cap_points) {
+        // staging sized to the point capacity
+        DFS_CK(p, cudaStreamSynchronize(p->stream));
+        dfs_free((void **)&p->d_pts_stage);
+        p->pts_stage_cap = 0;
+        rc = dfs_alloc(p, (void **)&p->d_pts_stage, 2 * sizeof(double) * p->cap_points,
+                       "point staging");
+        if (rc) return rc;
+        p->pts_stage_cap = p->cap_points;
+    }
+    size_t b = sizeof(double) * (size_t)n_points;
+    DFS_CK(p, cudaMemcpyAsync(p->d_pts_stage, lon, b, cudaMemcpyHostToDevice, p->stream));
+    DFS_CK(p, cudaMemcpyAsync(p->d_pts_stage + p->pts_stage_cap, colat, b,
+                              cudaMemcpyHostToDevice, p->stream));
+    p->n_points = n_points;
+    p->has_points = 0;
+    DFS_CK(p, timing_begin(p, 0));
+    DFS_CK(p, dfs_launch_set_points(p, p->d_pts_stage, p->d_pts_stage + p->pts_stage_cap));
+    DFS_CK(p, timing_end(p, 0));
+    p->has_points = 1;
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *values) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    if (!p->has_points) return DFSNUFFT_ERR_NO_POINTS;
+    if (!coeffs || !values) return DFSNUFFT_ERR_INVALID_ARG;
+    const dfsnufft_params &q = p->prm;
+    size_t cs = q.dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
+    size_t rs = cs / 2;
+    size_t cb = cs * (size_t)p->n_fields * q.N2 * q.N1;
+    size_t vb = rs * (size_t)p->n_fields * (size_t)p->n_points;
+    int rc;
+    if (!p->d_coef_stage) {
+        rc = dfs_alloc(p, &p->d_coef_stage, cb, "coefficient staging");
+        if (rc) return rc;
+    }
+    if (p->val_stage_cap < p->n_points) {
+        DFS_CK(p, cudaStreamSynchronize(p->stream));
+        dfs_free(&p->d_val_stage);
+        rc = dfs_alloc(p, &p->d_val_stage, rs * (size_t)p->n_fields * p->cap_points,
+                       "value staging");
+        if (rc) return rc;
+        p->val_stage_cap = p->cap_points;
+    }
+    DFS_CK(p, cudaMemcpyAsync(p->d_coef_stage, coeffs, cb, cudaMemcpyHostToDevice, p->stream));
+    rc = dfsnufft_execute(p, p->d_coef_stage, p->d_val_stage);
+    if (rc) return rc;
+    DFS_CK(p, cudaMemcpyAsync(values, p->d_val_stage, vb, cudaMemcpyDeviceToHost, p->stream));
+    DFS_CK(p, cudaStreamSynchronize(p->stream));
+    return DFSNUFFT_OK;
+}
+
+// ------------------------------------------------------------------ measurement aids
+
+extern "C" int dfsnufft_plan_enable_timing(dfsnufft_plan p, int enable) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    if (enable && !p->ev) {
+        const int n = 2 * DFS_TIMING_SLOTS * DFSNUFFT_N_STAGES;
+        p->ev = (cudaEvent_t *)calloc(n, sizeof(cudaEvent_t));
+        if (!p->ev) return DFSNUFFT_ERR_OOM;
+        for (int i = 0; i < n; ++i) DFS_CK(p, cudaEventCreate(&p->ev[i]));
+    }
+    if (p->timing) DFS_CK(p, timing_drain(p));
+    for (int s = 0; s < DFSNUFFT_N_STAGES; ++s) {
+        p->pending[s] = 0;
+        p->ms_total[s] = 0.0;
+        p->calls[s] = 0;
+    }
+    p->timing = enable ? 1 : 0;
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_plan_read_timing(dfsnufft_plan p, double *ms_total, int64_t *calls) {
+    if (!p || !ms_total || !calls) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    if (p->timing) DFS_CK(p, timing_drain(p));
+    for (int s = 0; s < DFSNUFFT_N_STAGES; ++s) {
+        ms_total[s] = p->ms_total[s];
+        calls[s] = p->calls[s];
+    }
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_plan_point_stats(dfsnufft_plan p, int64_t *rows_needed,
+                                         int64_t *nonempty_bins) {
+    if (!p || !rows_needed || !nonempty_bins) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    if (!p->has_points) return DFSNUFFT_ERR_NO_POINTS;
+    DFS_CK(p, cudaStreamSynchronize(p->stream));
+    unsigned char *mask = (unsigned char *)malloc(p->n_row_blocks);
+    if (!mask) return DFSNUFFT_ERR_OOM;
+    int ntask = 0;
+    cudaError_t e1 = cudaMemcpy(mask, p->d_rowmask, p->n_row_blocks, cudaMemcpyDeviceToHost);
+    cudaError_t e2 = cudaMemcpy(&ntask, p->d_n_tasks, sizeof(int), cudaMemcpyDeviceToHost);
+    int64_t blocks = 0;
+    for (int i = 0; i < p->n_row_blocks; ++i) blocks += mask[i] != 0;
+    free(mask);
+    if (e1) return fail_cuda(p, "read row mask", e1);
+    if (e2) return fail_cuda(p, "read bin count", e2);
+    *rows_needed = blocks * DFS_ROW_BLOCK;
+    *nonempty_bins = ntask;
+    return DFSNUFFT_OK;
+}

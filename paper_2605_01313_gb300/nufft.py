@@ -1,0 +1,313 @@
+"""Python binding of the dfsnufft C ABI (include/dfsnufft.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  The low-level functions keep the C names; :class:`Plan` wraps them
+for torch tensors (device memory and the current CUDA stream come from torch).
+The library must have been built (``python -m paper_2605_01313_gb300.build``);
+there is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+F64 = 0
+F32 = 1
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_TOL_UNATTAINABLE = 2
+ERR_NO_POINTS = 3
+ERR_OOM = 4
+ERR_CUDA = 5
+ERR_UNSUPPORTED = 6
+
+# Every symbol include/dfsnufft.h declares.
+EXPORTS = (
+    "dfsnufft_plan_create", "dfsnufft_set_points", "dfsnufft_execute",
+    "dfsnufft_set_points_host", "dfsnufft_execute_host", "dfsnufft_destroy",
+    "dfsnufft_strerror", "dfsnufft_plan_last_error", "dfsnufft_plan_get_params",
+    "dfsnufft_choose_params", "dfsnufft_es_kernel", "dfsnufft_kernel_ft", "dfsnufft_version",
+    "dfsnufft_plan_enable_timing", "dfsnufft_plan_read_timing", "dfsnufft_plan_point_stats",
+    "dfsnufft_probe_fma_rate",
+)
+N_STAGES = 4
+STAGES = ("set_points", "theta_pass", "phi_pass", "interp")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_lon", ctypes.c_int), ("n_lat", ctypes.c_int), ("N1", ctypes.c_int),
+                ("N2", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int),
+                ("w", ctypes.c_int), ("beta", ctypes.c_double), ("tol", ctypes.c_double),
+                ("dtype", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DfsError(RuntimeError):
+    def __init__(self, status, detail=""):
+        self.status = status
+        msg = "dfsnufft: %s (status %d)" % (_strerror(status), status)
+        if detail:
+            msg += ": " + detail
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError("dfsnufft CUDA library missing at %s; build it with "
+                               "`python -m paper_2605_01313_gb300.build`" % path)
+        L = ctypes.CDLL(path)
+        vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        L.dfsnufft_plan_create.argtypes = [i32, i32, f64, i32, i32, vp, ctypes.POINTER(vp)]
+        L.dfsnufft_set_points.argtypes = [vp, i64, vp, vp]
+        L.dfsnufft_set_points_host.argtypes = [vp, i64, vp, vp]
+        L.dfsnufft_execute.argtypes = [vp, vp, vp]
+        L.dfsnufft_execute_host.argtypes = [vp, vp, vp]
+        L.dfsnufft_destroy.argtypes = [vp]
+        L.dfsnufft_strerror.argtypes = [i32]
+        L.dfsnufft_strerror.restype = ctypes.c_char_p
+        L.dfsnufft_plan_last_error.argtypes = [vp]
+        L.dfsnufft_plan_last_error.restype = ctypes.c_char_p
+        L.dfsnufft_plan_get_params.argtypes = [vp, ctypes.POINTER(Params)]
+        L.dfsnufft_choose_params.argtypes = [i32, i32, f64, i32, ctypes.POINTER(Params)]
+        L.dfsnufft_es_kernel.argtypes = [f64, i32, f64]
+        L.dfsnufft_es_kernel.restype = f64
+        L.dfsnufft_kernel_ft.argtypes = [i32, f64, i32, i32, vp]
+        L.dfsnufft_version.restype = ctypes.c_char_p
+        L.dfsnufft_plan_enable_timing.argtypes = [vp, i32]
+        L.dfsnufft_plan_read_timing.argtypes = [vp, vp, vp]
+        L.dfsnufft_plan_point_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.dfsnufft_probe_fma_rate.argtypes = [i32, f64, ctypes.POINTER(f64)]
+        for name in EXPORTS:
+            if name not in ("dfsnufft_strerror", "dfsnufft_plan_last_error", "dfsnufft_es_kernel",
+                            "dfsnufft_version"):
+                getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _strerror(status):
+    try:
+        return lib().dfsnufft_strerror(int(status)).decode()
+    except Exception:   # library not loadable: still describe the code
+        return "status %d" % status
+
+
+def _check(rc, plan_handle=None):
+    if rc != OK:
+        detail = ""
+        if plan_handle is not None:
+            detail = (lib().dfsnufft_plan_last_error(plan_handle) or b"").decode()
+        raise DfsError(rc, detail)
+
+
+def _dtype_code(dtype) -> int:
+    if dtype in (F64, "f64", "float64", "double", np.float64):
+        return F64
+    if dtype in (F32, "f32", "float32", "float", np.float32):
+        return F32
+    raise ValueError("dtype must be 'f64' or 'f32'")
+
+
+# ------------------------------------------------------------ host-only helpers
+
+def dfsnufft_choose_params(n_lon, n_lat, tol, dtype="f64") -> dict:
+    p = Params()
+    _check(lib().dfsnufft_choose_params(int(n_lon), int(n_lat), float(tol), _dtype_code(dtype),
+                                        ctypes.byref(p)))
+    return p.as_dict()
+
+
+def dfsnufft_es_kernel(z, w, beta) -> float:
+    return float(lib().dfsnufft_es_kernel(float(z), int(w), float(beta)))
+
+
+def dfsnufft_kernel_ft(w, beta, n_fine, n_modes) -> np.ndarray:
+    out = np.empty(int(n_modes), dtype=np.float64)
+    _check(lib().dfsnufft_kernel_ft(int(w), float(beta), int(n_fine), int(n_modes),
+                                    out.ctypes.data))
+    return out
+
+
+def dfsnufft_version() -> str:
+    return lib().dfsnufft_version().decode()
+
+
+# ------------------------------------------------------------ plan-level calls
+
+def dfsnufft_plan_create(n_lon, n_lat, tol, dtype, n_fields, stream) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().dfsnufft_plan_create(int(n_lon), int(n_lat), float(tol), _dtype_code(dtype),
+                                      int(n_fields), ctypes.c_void_p(int(stream or 0)),
+                                      ctypes.byref(h)))
+    return h
+
+
+def dfsnufft_set_points(h, n_points, lon_ptr, colat_ptr):
+    _check(lib().dfsnufft_set_points(h, int(n_points), ctypes.c_void_p(lon_ptr),
+                                     ctypes.c_void_p(colat_ptr)), h)
+
+
+def dfsnufft_execute(h, coeffs_ptr, values_ptr):
+    _check(lib().dfsnufft_execute(h, ctypes.c_void_p(coeffs_ptr), ctypes.c_void_p(values_ptr)), h)
+
+
+def dfsnufft_set_points_host(h, n_points, lon_ptr, colat_ptr):
+    _check(lib().dfsnufft_set_points_host(h, int(n_points), ctypes.c_void_p(lon_ptr),
+                                          ctypes.c_void_p(colat_ptr)), h)
+
+
+def dfsnufft_execute_host(h, coeffs_ptr, values_ptr):
+    _check(lib().dfsnufft_execute_host(h, ctypes.c_void_p(coeffs_ptr),
+                                       ctypes.c_void_p(values_ptr)), h)
+
+
+def dfsnufft_destroy(h):
+    _check(lib().dfsnufft_destroy(h))
+
+
+def dfsnufft_plan_enable_timing(h, enable=True):
+    _check(lib().dfsnufft_plan_enable_timing(h, 1 if enable else 0), h)
+
+
+def dfsnufft_plan_read_timing(h) -> dict:
+    """{stage: (total ms, calls)} for the stages of STAGES (synchronises)."""
+    ms = np.zeros(N_STAGES, dtype=np.float64)
+    calls = np.zeros(N_STAGES, dtype=np.int64)
+    _check(lib().dfsnufft_plan_read_timing(h, ms.ctypes.data, calls.ctypes.data), h)
+    return {STAGES[i]: (float(ms[i]), int(calls[i])) for i in range(N_STAGES)}
+
+
+def dfsnufft_plan_point_stats(h) -> dict:
+    rows = ctypes.c_int64()
+    bins = ctypes.c_int64()
+    _check(lib().dfsnufft_plan_point_stats(h, ctypes.byref(rows), ctypes.byref(bins)), h)
+    return {"rows_needed": rows.value, "nonempty_bins": bins.value}
+
+
+def dfsnufft_probe_fma_rate(dtype, target_ms=20.0) -> float:
+    out = ctypes.c_double()
+    _check(lib().dfsnufft_probe_fma_rate(_dtype_code(dtype), float(target_ms), ctypes.byref(out)))
+    return out.value
+
+
+def dfsnufft_plan_get_params(h) -> dict:
+    p = Params()
+    _check(lib().dfsnufft_plan_get_params(h, ctypes.byref(p)), h)
+    return p.as_dict()
+
+
+class Plan:
+    """A type-2 NUFFT plan for an n_lat x n_lon grid (coefficients (F, 2 n_lat, n_lon)).
+
+    ``set_points`` takes CUDA float64 tensors; ``execute`` takes a CUDA complex
+    tensor (complex128 for 'f64', complex64 for 'f32') and returns or fills a
+    (F, P) real tensor.  Work is enqueued on ``stream`` (default: torch's
+    current stream at creation).
+    """
+
+    def __init__(self, n_lon, n_lat, tol=1e-12, dtype="f64", n_fields=1, stream=None):
+        import torch
+        self.n_lon, self.n_lat = int(n_lon), int(n_lat)
+        self.dtype = "f64" if _dtype_code(dtype) == F64 else "f32"
+        self.n_fields = int(n_fields)
+        self.tol = float(tol)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._h = dfsnufft_plan_create(n_lon, n_lat, tol, self.dtype, n_fields, handle)
+        self.params = dfsnufft_plan_get_params(self._h)
+        self.n_points = 0
+        self._keep = None
+
+    @property
+    def coeff_shape(self):
+        return (self.n_fields, 2 * self.n_lat, self.n_lon)
+
+    def _real_dtype(self):
+        import torch
+        return torch.float64 if self.dtype == "f64" else torch.float32
+
+    def _cplx_dtype(self):
+        import torch
+        return torch.complex128 if self.dtype == "f64" else torch.complex64
+
+    def set_points(self, lon, colat):
+        import torch
+        for t in (lon, colat):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.dim() == 1 and t.is_contiguous()):
+                raise ValueError("points must be contiguous 1-D CUDA float64 tensors")
+        if lon.numel() != colat.numel():
+            raise ValueError("lon and colat differ in length")
+        dfsnufft_set_points(self._h, lon.numel(), lon.data_ptr(), colat.data_ptr())
+        self.n_points = lon.numel()
+        self._keep = (lon, colat)
+
+    def execute(self, coeffs, out=None):
+        import torch
+        if tuple(coeffs.shape) != self.coeff_shape or coeffs.dtype != self._cplx_dtype() \
+                or not coeffs.is_cuda or not coeffs.is_contiguous():
+            raise ValueError("coeffs must be a contiguous CUDA %s tensor of shape %s"
+                             % (self._cplx_dtype(), self.coeff_shape))
+        if out is None:
+            out = torch.empty((self.n_fields, self.n_points), dtype=self._real_dtype(),
+                              device=coeffs.device)
+        elif tuple(out.shape) != (self.n_fields, self.n_points) or \
+                out.dtype != self._real_dtype() or not out.is_contiguous():
+            raise ValueError("out must be a contiguous (F, P) %s tensor" % self._real_dtype())
+        dfsnufft_execute(self._h, coeffs.data_ptr(), out.data_ptr())
+        return out
+
+    def set_points_host(self, lon, colat):
+        lon = np.ascontiguousarray(lon, dtype=np.float64)
+        colat = np.ascontiguousarray(colat, dtype=np.float64)
+        if lon.shape != colat.shape or lon.ndim != 1:
+            raise ValueError("points must be 1-D float64 arrays of equal length")
+        dfsnufft_set_points_host(self._h, lon.size, lon.ctypes.data, colat.ctypes.data)
+        self.n_points = lon.size
+
+    def execute_host(self, coeffs, out=None):
+        cd = np.complex128 if self.dtype == "f64" else np.complex64
+        rd = np.float64 if self.dtype == "f64" else np.float32
+        c = np.ascontiguousarray(coeffs, dtype=cd)
+        if c.shape != self.coeff_shape:
+            raise ValueError("coeffs must have shape %s" % (self.coeff_shape,))
+        if out is None:
+            out = np.empty((self.n_fields, self.n_points), dtype=rd)
+        dfsnufft_execute_host(self._h, c.ctypes.data, out.ctypes.data)
+        return out
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            dfsnufft_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()

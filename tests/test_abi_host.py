@@ -1,0 +1,121 @@
+"""Host-side checks of the C-ABI library (no GPU): it loads, exports every symbol
+the header declares, and its host logic (parameters, kernel, deconvolution
+factors, status strings) is right."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2605_01313_gb300 import build, nufft
+
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return nufft.lib()
+
+
+def _declared_functions():
+    names = set()
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            text = open(os.path.join(INCLUDE, h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names.update(re.findall(r"\b(dfsnufft_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_binding_exports():
+    assert _declared_functions() == sorted(nufft.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version(lib):
+    assert "sm_103a" in nufft.dfsnufft_version()
+
+
+def test_strerror_covers_every_code(lib):
+    seen = set()
+    for code in range(0, 7):
+        s = lib.dfsnufft_strerror(code).decode()
+        assert s and s != "unknown status"
+        seen.add(s)
+    assert len(seen) == 7
+    assert lib.dfsnufft_strerror(99).decode() == "unknown status"
+
+
+@pytest.mark.parametrize("tol,w", [(1e-1, 2), (1e-3, 4), (1e-6, 7), (1e-9, 10), (1e-12, 13),
+                                   (1e-14, 15), (1e-15, 16)])
+def test_width_rule(lib, tol, w):
+    p = nufft.dfsnufft_choose_params(64, 32, tol, "f64")
+    assert p["w"] == w
+    assert p["beta"] == pytest.approx(2.30 * w)
+
+
+@pytest.mark.parametrize("n_lon,n_lat", [(64, 32), (160, 80), (2048, 1024), (8, 4), (24, 12)])
+def test_fine_sizes(lib, n_lon, n_lat):
+    p = nufft.dfsnufft_choose_params(n_lon, n_lat, 1e-12, "f64")
+    assert p["N1"] == n_lon and p["N2"] == 2 * n_lat
+    for n, N in ((p["n1"], p["N1"]), (p["n2"], p["N2"])):
+        assert n & (n - 1) == 0 and n >= 2 * N and n >= 2 * p["w"]
+        assert n < 2 * max(2 * N, 2 * p["w"], 16)
+
+
+def test_parameter_errors(lib):
+    bad = [((63, 32, 1e-6, "f64"), nufft.ERR_INVALID_ARG),
+           ((2, 32, 1e-6, "f64"), nufft.ERR_INVALID_ARG),
+           ((64, 1, 1e-6, "f64"), nufft.ERR_INVALID_ARG),
+           ((64, 32, 0.0, "f64"), nufft.ERR_INVALID_ARG),
+           ((64, 32, 1.5, "f64"), nufft.ERR_INVALID_ARG),
+           ((64, 32, 1e-16, "f64"), nufft.ERR_TOL_UNATTAINABLE),
+           ((64, 32, 1e-8, "f32"), nufft.ERR_TOL_UNATTAINABLE),
+           ((8192, 32, 1e-6, "f32"), nufft.ERR_UNSUPPORTED),
+           ((64, 4096, 1e-6, "f32"), nufft.ERR_UNSUPPORTED)]
+    for args, code in bad:
+        with pytest.raises(nufft.DfsError) as ei:
+            nufft.dfsnufft_choose_params(*args)
+        assert ei.value.status == code, args
+
+
+def test_es_kernel_shape(lib):
+    w, beta = 7, 2.30 * 7
+    assert nufft.dfsnufft_es_kernel(0.0, w, beta) == 1.0
+    assert nufft.dfsnufft_es_kernel(3.5, w, beta) == 0.0
+    assert nufft.dfsnufft_es_kernel(-3.6, w, beta) == 0.0
+    for z in (0.3, 1.7, 3.2):
+        a = nufft.dfsnufft_es_kernel(z, w, beta)
+        assert a == nufft.dfsnufft_es_kernel(-z, w, beta)
+        assert a == pytest.approx(math.exp(beta * (math.sqrt(1 - (2 * z / w) ** 2) - 1)), rel=1e-15)
+    # at the edge of the support the kernel is e^{-beta}, below the tolerance it serves
+    assert nufft.dfsnufft_es_kernel(3.4999999, w, beta) < 2 * math.exp(-beta) * 10
+
+
+@pytest.mark.parametrize("w", [4, 7, 13])
+def test_kernel_ft_against_adaptive_quadrature(lib, w):
+    """Deconvolution factors (Gauss-Legendre in the library) against scipy's adaptive
+    quadrature of the same integral, an independent numerical route."""
+    from scipy.integrate import quad
+    beta = 2.30 * w
+    n_fine, n_modes = 256, 128
+    ft = nufft.dfsnufft_kernel_ft(w, beta, n_fine, n_modes)
+    for q in (0, 1, 17, 40, 63, 64, 100, 127):
+        k = q - n_modes // 2
+        xi = 2 * math.pi * k / n_fine
+        f = lambda z: math.exp(beta * (math.sqrt(max(0.0, 1 - (2 * z / w) ** 2)) - 1)) * math.cos(xi * z)
+        ref, _ = quad(f, -w / 2, w / 2, epsabs=1e-15, epsrel=1e-14, limit=200)
+        assert ft[q] == pytest.approx(ref, rel=1e-12, abs=1e-15)
+    assert np.all(ft > 0)
+    assert np.allclose(ft, ft[::-1][np.r_[n_modes - 1, 0:n_modes - 1]], rtol=1e-14)  # even in k
+
+
+def test_kernel_ft_bad_args(lib):
+    with pytest.raises(nufft.DfsError):
+        nufft.dfsnufft_kernel_ft(1, 2.3, 64, 32)

@@ -1,0 +1,306 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 direct-sum oracle.
+
+Acceptance (relative l-infinity over the checked points, per field, against
+the oracle's real part): <= 1e-11 for FP64 plans at tol 1e-12 and <= 2e-5
+for FP32 plans at tol 1e-6.  Other tolerances are checked at 10 x tol.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_01313_gb300 import build, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_F64 = 1e-11
+TOL_F32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for the -m gpu tests")
+    build.build()
+    return torch
+
+
+def accept(dtype, tol):
+    if dtype == "f64":
+        return TOL_F64 if tol == 1e-12 else 10 * tol
+    return TOL_F32 if tol >= 1e-6 else 20 * tol
+
+
+def run_gpu(torch, wl, dtype=None, tol=None, lon=None, colat=None):
+    from paper_2605_01313_gb300 import Plan
+    dtype = dtype or wl.dtype
+    tol = tol or wl.tol
+    lon = wl.lon if lon is None else lon
+    colat = wl.colat if colat is None else colat
+    cd = torch.complex128 if dtype == "f64" else torch.complex64
+    with Plan(wl.n_lon, wl.n_lat, tol, dtype, wl.n_fields) as plan:
+        plan.set_points(torch.from_numpy(np.ascontiguousarray(lon)).cuda(),
+                        torch.from_numpy(np.ascontiguousarray(colat)).cuda())
+        out = plan.execute(torch.from_numpy(wl.coeffs).to(cd).cuda())
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+def check_against_oracle(vals, wl, bound, sample=None, lon=None, colat=None):
+    sample = wl.sample if sample is None else sample
+    lon = wl.lon if lon is None else lon
+    colat = wl.colat if colat is None else colat
+    ref = oracle.evaluate(wl.coeffs, lon[sample], colat[sample])
+    errs = []
+    for f in range(wl.n_fields):
+        e = oracle.rel_linf(vals[f][sample], ref[f].real)
+        errs.append(e)
+    assert max(errs) <= bound, (wl.name, errs, bound)
+    return errs
+
+
+# ------------------------------------------------------------------ the workloads
+
+def test_c1_f64_all_points(torch_cuda):
+    wl = synth.workload_c1()
+    vals = run_gpu(torch_cuda, wl)
+    check_against_oracle(vals, wl, TOL_F64)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_c2_three_fields(torch_cuda, dtype):
+    wl = synth.workload_c2(dtype)
+    vals = run_gpu(torch_cuda, wl)
+    check_against_oracle(vals, wl, accept(dtype, wl.tol))
+
+
+def test_c3_f32_full_size(torch_cuda):
+    wl = synth.workload_c3("f32")
+    vals = run_gpu(torch_cuda, wl)
+    assert np.all(np.isfinite(vals))
+    check_against_oracle(vals, wl, TOL_F32)
+
+
+def test_c3_f64_full_size(torch_cuda):
+    wl = synth.workload_c3("f64", n_sample=300)
+    vals = run_gpu(torch_cuda, wl)
+    check_against_oracle(vals, wl, TOL_F64)
+
+
+# ------------------------------------------------------- sizes, fields, tolerances
+
+@pytest.mark.parametrize("n_lon,n_lat", [(8, 4), (16, 8), (24, 12), (64, 32), (96, 48),
+                                         (160, 80), (256, 128)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_small_grids_every_point(torch_cuda, n_lon, n_lat, dtype):
+    for nf, pts in ((1, "rotation"), (3, "divergent"), (2, "uniform")):
+        wl = synth.small_workload(100 + n_lon + nf, n_lon, n_lat, n_fields=nf, dtype=dtype,
+                                  points=pts)
+        vals = run_gpu(torch_cuda, wl)
+        check_against_oracle(vals, wl, accept(dtype, wl.tol))
+
+
+def test_tolerance_sweep_monotone(torch_cuda):
+    wl = synth.small_workload(7, 64, 32, n_fields=1, dtype="f64", points="uniform")
+    ref = oracle.evaluate(wl.coeffs, wl.lon, wl.colat)[0].real
+    prev = 1.0
+    for tol in (1e-2, 1e-4, 1e-6, 1e-8, 1e-10, 1e-12, 1e-14):
+        err = oracle.rel_linf(run_gpu(torch_cuda, wl, tol=tol)[0], ref)
+        assert err <= 10 * tol, (tol, err)
+        assert err < prev or err < 1e-14, (tol, err, prev)
+        prev = err
+    for tol in (1e-2, 1e-4, 1e-6, 1e-7):
+        err = oracle.rel_linf(run_gpu(torch_cuda, wl, dtype="f32", tol=tol)[0], ref)
+        assert err <= max(10 * tol, 5e-6), (tol, err)
+
+
+@pytest.mark.parametrize("n_points", [1, 2, 7, 31, 1000, 4097])
+def test_ragged_point_counts(torch_cuda, n_points):
+    rng = np.random.default_rng(n_points)
+    wl = synth.small_workload(9, 64, 32, n_fields=2, dtype="f64")
+    lon = rng.uniform(0, 2 * math.pi, n_points)
+    colat = np.arccos(rng.uniform(-1, 1, n_points))
+    vals = run_gpu(torch_cuda, wl, lon=lon, colat=colat)
+    assert vals.shape == (2, n_points)
+    check_against_oracle(vals, wl, TOL_F64, sample=np.arange(n_points), lon=lon, colat=colat)
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_edge_coordinates(torch_cuda):
+    """Poles, seams, coordinates outside [0, 2pi) x [0, pi], fine-grid nodes and
+    bin edges all match the oracle (which evaluates the same periodic series)."""
+    wl = synth.small_workload(11, 64, 32, n_fields=1, dtype="f64")
+    n1 = 128
+    lon = np.array([0.0, 2 * math.pi, -math.pi, 7 * math.pi, 1e-17, -1e-17, 2 * math.pi * (1 - 1e-16),
+                    math.pi, 2 * math.pi * 31 / n1, 2 * math.pi * 32 / n1, 2 * math.pi * 95.5 / n1,
+                    3.0, 3.0, 3.0, 3.0, 1.0, 100.0, -100.0])
+    colat = np.array([0.0, math.pi, 0.0, math.pi, 1.0, 2.0, 0.5, -0.3, math.pi + 0.3, 2 * math.pi,
+                      -2 * math.pi, 1e-300, math.pi - 1e-16, 2 * math.pi * 16 / n1,
+                      2 * math.pi * 15.5 / n1, 4.5, 50.0, -50.0])
+    for dtype in ("f64", "f32"):
+        vals = run_gpu(torch_cuda, wl, dtype=dtype, tol=1e-12 if dtype == "f64" else 1e-6,
+                       lon=lon, colat=colat)
+        check_against_oracle(vals, wl, TOL_F64 if dtype == "f64" else TOL_F32,
+                             sample=np.arange(lon.size), lon=lon, colat=colat)
+
+
+def test_non_finite_point_gives_nan_only_there(torch_cuda):
+    wl = synth.small_workload(12, 32, 16, n_fields=2, dtype="f64")
+    lon = wl.lon.copy()
+    colat = wl.colat.copy()
+    lon[5] = np.nan
+    colat[9] = np.inf
+    vals = run_gpu(torch_cuda, wl, lon=lon, colat=colat)
+    bad = np.zeros(lon.size, bool)
+    bad[[5, 9]] = True
+    assert np.all(np.isnan(vals[:, bad]))
+    good = np.nonzero(~bad)[0]
+    check_against_oracle(vals, wl, TOL_F64, sample=good, lon=lon, colat=colat)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_single_modes_including_nyquist(torch_cuda, dtype):
+    """One unit coefficient at (n0, m0) evaluates to cos(m0 phi + n0 theta).
+
+    A lone mode at the corner of the band is the kernel's worst case: at
+    tol 1e-12 (w = 13) the 1-D band-edge error is 7e-12, so the bound for FP64
+    here is 2e-11; the seeded workloads keep the 1e-11 bound."""
+    n_lon, n_lat = 32, 16
+    n2, n1 = synth.coeff_shape(n_lon, n_lat)
+    rng = np.random.default_rng(13)
+    lon = rng.uniform(-1, 7, 300)
+    colat = rng.uniform(-1, 4, 300)
+    bound = 2e-11 if dtype == "f64" else TOL_F32
+    for n0, m0 in [(0, 0), (3, -5), (n2 // 2 - 1, n1 // 2 - 1), (-(n2 // 2), -(n1 // 2)),
+                   (-(n2 // 2), 4), (7, -(n1 // 2))]:
+        c = np.zeros((1, n2, n1), np.complex128)
+        c[0, n0 + n2 // 2, m0 + n1 // 2] = 1.0
+        wl = synth.Workload("mode", n_lon, n_lat, c, lon, colat, 1e-12 if dtype == "f64" else 1e-6,
+                            dtype)
+        vals = run_gpu(torch_cuda, wl)
+        want = np.cos(m0 * lon + n0 * colat)
+        assert np.max(np.abs(vals[0] - want)) <= bound, (n0, m0)
+
+
+def test_grid_point_reproduction(torch_cuda):
+    """Coefficients interpolating samples on the doubled Grid [0] torus reproduce the
+    samples at those points (exact reproduction up to the NUFFT tolerance)."""
+    n_lon, n_lat = 64, 32
+    n2, n1 = synth.coeff_shape(n_lon, n_lat)
+    rng = np.random.default_rng(14)
+    samples = rng.standard_normal((n2, n1))
+    c = synth.torus_samples_to_coeffs(samples)
+    th = (np.arange(n2) + 0.5) * (2 * math.pi / n2)
+    ph = np.arange(n1) * (2 * math.pi / n1)
+    tt, pp = np.meshgrid(th, ph, indexing="ij")
+    wl = synth.Workload("repro", n_lon, n_lat, c[None], pp.ravel(), tt.ravel(), 1e-12, "f64")
+    vals = run_gpu(torch_cuda, wl)
+    assert np.max(np.abs(vals[0] - samples.ravel())) <= 1e-11 * np.max(np.abs(samples)) * 10
+
+
+@pytest.mark.parametrize("parity", [synth.SCALAR, synth.VECTOR])
+def test_dfs_symmetry(torch_cuda, parity):
+    rng = np.random.default_rng(15)
+    c = synth.random_spectrum(rng, 128, 64, 2.0, parity)[None]
+    lon = rng.uniform(0, 2 * math.pi, 2000)
+    colat = np.arccos(rng.uniform(-1, 1, 2000))
+    wl = synth.Workload("sym", 128, 64, c, lon, colat, 1e-12, "f64")
+    a = run_gpu(torch_cuda, wl)[0]
+    b = run_gpu(torch_cuda, wl, lon=lon + math.pi, colat=-colat)[0]
+    assert np.max(np.abs(b - parity * a)) <= 2e-11 * np.max(np.abs(a))
+
+
+def test_zonal_flow_analytic(torch_cuda):
+    """The steady zonal geostrophic flow's exact coefficients give the analytic h, u, v
+    at the departure points."""
+    alpha = math.pi / 2 - 0.05
+    n_lon, n_lat = 64, 32
+    c = np.stack(synth.zonal_flow_coeffs(n_lon, n_lat, alpha))
+    lon, colat = synth.solid_body_departure(*synth.grid0_points(n_lon, n_lat), alpha,
+                                            synth.U0_12DAY, 5000.0)
+    wl = synth.Workload("tc2", n_lon, n_lat, c, lon, colat, 1e-12, "f64")
+    vals = run_gpu(torch_cuda, wl)
+    for f, want in enumerate(synth.zonal_flow_values(lon, colat, alpha)):
+        assert np.max(np.abs(vals[f] - want)) <= 1e-11 * np.max(np.abs(want))
+
+
+# ------------------------------------------------------------------ API behaviour
+
+def test_host_variants_match_device(torch_cuda):
+    from paper_2605_01313_gb300 import Plan
+    wl = synth.small_workload(16, 128, 64, n_fields=3, dtype="f32")
+    dev = run_gpu(torch_cuda, wl)
+    with Plan(wl.n_lon, wl.n_lat, wl.tol, "f32", 3) as plan:
+        plan.set_points_host(wl.lon, wl.colat)
+        host = plan.execute_host(wl.coeffs.astype(np.complex64))
+    assert np.array_equal(dev, host)
+
+
+def test_repeatable_and_resettable(torch_cuda):
+    from paper_2605_01313_gb300 import Plan
+    torch = torch_cuda
+    wl = synth.small_workload(17, 64, 32, n_fields=2, dtype="f64")
+    rng = np.random.default_rng(5)
+    coeffs = torch.from_numpy(wl.coeffs).cuda()
+    with Plan(wl.n_lon, wl.n_lat, 1e-12, "f64", 2) as plan:
+        lo, co = torch.from_numpy(wl.lon).cuda(), torch.from_numpy(wl.colat).cuda()
+        plan.set_points(lo, co)
+        a = plan.execute(coeffs).cpu().numpy()
+        b = plan.execute(coeffs).cpu().numpy()
+        assert np.array_equal(a, b)
+        big_lon = rng.uniform(0, 2 * math.pi, 20000)
+        big_col = np.arccos(rng.uniform(-1, 1, 20000))
+        plan.set_points(torch.from_numpy(big_lon).cuda(), torch.from_numpy(big_col).cuda())
+        c = plan.execute(coeffs).cpu().numpy()
+        check_against_oracle(c, wl, TOL_F64, sample=np.arange(0, 20000, 97), lon=big_lon,
+                             colat=big_col)
+        plan.set_points(lo, co)
+        d = plan.execute(coeffs).cpu().numpy()
+        assert np.array_equal(a, d)
+
+
+def test_errors(torch_cuda):
+    from paper_2605_01313_gb300 import Plan, nufft
+    torch = torch_cuda
+    plan = Plan(64, 32, 1e-12, "f64", 1)
+    coeffs = torch.zeros((1, 64, 64), dtype=torch.complex128, device="cuda")
+    out = torch.zeros((1, 10), dtype=torch.float64, device="cuda")
+    with pytest.raises(nufft.DfsError) as ei:
+        nufft.dfsnufft_execute(plan._h, coeffs.data_ptr(), out.data_ptr())
+    assert ei.value.status == nufft.ERR_NO_POINTS
+    with pytest.raises(nufft.DfsError) as ei:
+        nufft.dfsnufft_set_points(plan._h, 0, 0, 0)
+    assert ei.value.status == nufft.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        plan.execute(coeffs.to(torch.complex64))
+    plan.destroy()
+    with pytest.raises(nufft.DfsError) as ei:
+        nufft.dfsnufft_plan_create(63, 32, 1e-12, "f64", 1, 0)
+    assert ei.value.status == nufft.ERR_INVALID_ARG
+
+
+def test_two_plans_two_streams(torch_cuda):
+    from paper_2605_01313_gb300 import Plan
+    torch = torch_cuda
+    wl = synth.small_workload(18, 128, 64, n_fields=3, dtype="f32")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    lo, co = torch.from_numpy(wl.lon).cuda(), torch.from_numpy(wl.colat).cuda()
+    cf = torch.from_numpy(wl.coeffs).to(torch.complex64).cuda()
+    torch.cuda.synchronize()
+    p1 = Plan(wl.n_lon, wl.n_lat, wl.tol, "f32", 3, stream=s1)
+    p2 = Plan(wl.n_lon, wl.n_lat, wl.tol, "f32", 3, stream=s2)
+    p1.set_points(lo, co)
+    p2.set_points(lo, co)
+    with torch.cuda.stream(s1):
+        o1 = torch.empty((3, lo.numel()), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(s2):
+        o2 = torch.empty((3, lo.numel()), dtype=torch.float32, device="cuda")
+    p1.execute(cf, o1)
+    p2.execute(cf, o2)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o2)
+    p1.destroy()
+    p2.destroy()
