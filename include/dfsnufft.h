@@ -139,6 +139,42 @@ int dfsnufft_plan_read_timing(dfsnufft_plan plan, double *ms_total, int64_t *cal
  * of non-empty interpolation bins.  Measurement aid; no paper counterpart. */
 int dfsnufft_plan_point_stats(dfsnufft_plan plan, int64_t *rows_needed, int64_t *nonempty_bins);
 
+/* ---- allocation-free one-shot call -------------------------------------- */
+
+/* Bytes of the library's static device scratch used by dfsnufft_execute_noalloc. */
+#define DFSNUFFT_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* One-shot evaluation (the work of set_points followed by execute) that
+ * allocates no device memory: for callers that cannot call cudaMalloc, such as
+ * a model time step that runs inside another framework's memory pool, or a
+ * latency-critical loop that must not take the device-wide synchronisation
+ * that cudaMalloc/cudaFree imply.  The paper has no counterpart; this is an
+ * interface of this library.
+ *
+ * All working memory (fine grids, theta-pass buffer, kernel tables, bins and
+ * sorted points) lives in one static device array of
+ * DFSNUFFT_NOALLOC_SCRATCH_BYTES that every GPU which loads this library's
+ * module holds until the process exits (under CUDA's default lazy module
+ * loading, from the first call on that GPU).  Arguments are those of dfsnufft_plan_create,
+ * dfsnufft_set_points and dfsnufft_execute (device pointers; the caller owns
+ * inputs and outputs), with stream = cudaStream_t (NULL = legacy default).
+ *   - A problem whose working memory exceeds the scratch, or whose fine grid
+ *     exceeds 2048 cells in a dimension, is rejected with
+ *     DFSNUFFT_ERR_UNSUPPORTED before anything is enqueued.
+ *   - The first call on a device resolves the scratch's device address
+ *     (cudaGetSymbolAddress, which may load the module); make that first call
+ *     before any stream capture on that device.
+ *   - Every call on a device shares the same scratch, which keeps the last
+ *     call's contents (the kernel tables are reused when the grid, tolerance
+ *     and precision repeat; counters are cleared on every call).  Calls that
+ *     overlap on the GPU (other streams, other host threads) race on it:
+ *     order them on one stream or synchronise between them.
+ *   - Kernel tables are uploaded from host memory with cudaMemcpyAsync when
+ *     the configuration changes. */
+int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dtype, int n_fields,
+                             int64_t n_points, const double *lon, const double *colat,
+                             const void *coeffs, void *values, void *stream);
+
 /* ---- host-only helpers (no GPU needed) ---------------------------------- */
 
 /* Parameters a plan with these arguments would use. */

@@ -33,7 +33,7 @@ EXPORTS = (
     "dfsnufft_strerror", "dfsnufft_plan_last_error", "dfsnufft_plan_get_params",
     "dfsnufft_choose_params", "dfsnufft_es_kernel", "dfsnufft_kernel_ft", "dfsnufft_version",
     "dfsnufft_plan_enable_timing", "dfsnufft_plan_read_timing", "dfsnufft_plan_point_stats",
-    "dfsnufft_probe_fma_rate",
+    "dfsnufft_probe_fma_rate", "dfsnufft_execute_noalloc",
 )
 N_STAGES = 4
 STAGES = ("set_points", "theta_pass", "phi_pass", "interp")
@@ -95,6 +95,7 @@ def lib():
         L.dfsnufft_plan_read_timing.argtypes = [vp, vp, vp]
         L.dfsnufft_plan_point_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.dfsnufft_probe_fma_rate.argtypes = [i32, f64, ctypes.POINTER(f64)]
+        L.dfsnufft_execute_noalloc.argtypes = [i32, i32, f64, i32, i32, i64, vp, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("dfsnufft_strerror", "dfsnufft_plan_last_error", "dfsnufft_es_kernel",
                             "dfsnufft_version"):
@@ -206,6 +207,17 @@ def dfsnufft_probe_fma_rate(dtype, target_ms=20.0) -> float:
     out = ctypes.c_double()
     _check(lib().dfsnufft_probe_fma_rate(_dtype_code(dtype), float(target_ms), ctypes.byref(out)))
     return out.value
+
+
+def dfsnufft_execute_noalloc(n_lon, n_lat, tol, dtype, n_fields, n_points, lon_ptr, colat_ptr,
+                             coeffs_ptr, values_ptr, stream=0):
+    """One-shot evaluation on the library's static device scratch: no device
+    memory is allocated (for callers that cannot call cudaMalloc)."""
+    _check(lib().dfsnufft_execute_noalloc(int(n_lon), int(n_lat), float(tol), _dtype_code(dtype),
+                                          int(n_fields), int(n_points), ctypes.c_void_p(lon_ptr),
+                                          ctypes.c_void_p(colat_ptr), ctypes.c_void_p(coeffs_ptr),
+                                          ctypes.c_void_p(values_ptr),
+                                          ctypes.c_void_p(int(stream or 0))))
 
 
 def dfsnufft_plan_get_params(h) -> dict:
