@@ -146,8 +146,8 @@ def stage_bytes(prm, n_fields, n_points, rows):
     return {
         "set_points": P * (16 + 4) + P * (16 + 4) + P * rec,
         "theta_pass": F * (N2 * N1 * cs + rows * N1 * cs) + 8 * (N1 + N2),
-        "phi_pass": F * (rows * N1 * cs + rows * n1 * cs),
-        "interp": F * (rows * n1 * cs + P * rs) + P * rec,
+        "phi_pass": F * (rows * N1 * cs + rows * n1 * rs),     # writes the real part only
+        "interp": F * (rows * n1 * rs + P * rs) + P * rec,
     }
 
 

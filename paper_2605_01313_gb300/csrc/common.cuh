@@ -41,12 +41,12 @@ struct dfsnufft_plan_s {
     cudaStream_t stream;
 
     // device buffers owned by the plan
-    double *d_inv1;         // N1: 1 / phihat(m), centred
-    double *d_inv2;         // N2: 1 / phihat(n), centred
+    void *d_inv1;           // N1: 1 / phihat(m), centred, plan precision
+    void *d_inv2;           // N2: 1 / phihat(n), centred, plan precision
     void *d_tw1;            // n1 twiddles e^{+2 pi i k / n1} (plan precision)
     void *d_tw2;            // n2 twiddles
     void *d_T;              // theta-pass output, n_fields x n2 x N1
-    void *d_G;              // fine grids, n_fields x n2 x n1
+    void *d_G;              // fine grids (real part), n_fields x n2 x n1, plan precision
     int *d_bin_count;       // nbins
     int *d_bin_start;       // nbins + 1
     int *d_task_bin;        // nbins: list of non-empty bins

@@ -1,17 +1,18 @@
 // Interpolation from the fine grid to the departure points: the last stage of
 // the type-2 NUFFT evaluating Eq. 5.3 (Sec. 5).  For each point
 //
-//   v_p = sum_{b<w} sum_{a<w} phi(z_b^y) phi(z_a^x) G[j0 + b][i0 + a]   (indices mod n)
+//   Re v_p = sum_{b<w} sum_{a<w} phi(z_b^y) phi(z_a^x) Re G[j0 + b][i0 + a]   (indices mod n)
 //
 // with phi the exponential-of-semicircle kernel
 // phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)) and z_a = (a - c0) - t the
 // offsets produced by set_points.
 //
-// Points arrive sorted by bin (tile_x x tile_y fine cells); one CTA takes a
-// bin, stages the bin's tile plus its (w-1)-cell halo of every field into
-// shared memory with coalesced loads, and each thread then evaluates one
-// point at a time from shared memory, computing its 2w kernel values once
-// for all fields.
+// The weights are real, so only the real part of the fine grid is read (the
+// phi pass stores nothing else).  Points arrive sorted by bin (tile_x x tile_y
+// fine cells); one CTA takes a bin, stages the bin's tile plus its halo of
+// every field into shared memory with coalesced loads, and each thread then
+// evaluates one point at a time from shared memory, computing its 2w kernel
+// values once for all fields.
 #include "common.cuh"
 
 namespace {
@@ -47,8 +48,7 @@ __device__ __forceinline__ void es_weights(R t, int c0, R beta, R *wv) {
 }
 
 template <typename R, int W>
-__global__ void __launch_bounds__(256) k_interp(InterpArgs a,
-                                                const typename CxT<R>::type *__restrict__ grid,
+__global__ void __launch_bounds__(256) k_interp(InterpArgs a, const R *__restrict__ grid,
                                                 const int2 *__restrict__ base,
                                                 const R *__restrict__ frac,
                                                 const int *__restrict__ idx,
@@ -56,9 +56,8 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a,
                                                 const int *__restrict__ task_bin,
                                                 const int *__restrict__ n_tasks,
                                                 R *__restrict__ out) {
-    typedef typename CxT<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *tile = reinterpret_cast<C *>(smem_raw);
+    R *tile = reinterpret_cast<R *>(smem_raw);
     const int TH = a.tile_y + W - 1;
     const int TW = a.tile_x + W - 1;
     const int tsz = TH * TW;
@@ -75,14 +74,15 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a,
         for (int f0 = 0; f0 < a.F; f0 += a.FG) {
             const int fg = min(a.FG, a.F - f0);
             __syncthreads();
-            for (int k = threadIdx.x; k < fg * tsz; k += blockDim.x) {
-                const int ff = k / tsz;
-                const int rem = k - ff * tsz;
-                const int r = rem / TW;
-                const int cc = rem - r * TW;
+            // one warp per tile row: coalesced reads of TW consecutive cells
+            for (int rr = threadIdx.x >> 5; rr < fg * TH; rr += blockDim.x >> 5) {
+                const int ff = rr / TH;
+                const int r = rr - ff * TH;
                 const int gr = (row0 + r) & (a.n2 - 1);
-                const int gc = (col0 + cc) & (a.n1 - 1);
-                tile[k] = grid[((size_t)(f0 + ff) * a.n2 + gr) * a.n1 + gc];
+                const R *src = grid + ((size_t)(f0 + ff) * a.n2 + gr) * a.n1;
+                R *dst = tile + ff * tsz + r * TW;
+                for (int cc = threadIdx.x & 31; cc < TW; cc += 32)
+                    dst[cc] = src[(col0 + cc) & (a.n1 - 1)];
             }
             __syncthreads();
             for (int pi = s + threadIdx.x; pi < e; pi += blockDim.x) {
@@ -94,22 +94,99 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a,
                 const int oy = b.y - row0;
                 const int dst = idx[pi];
                 for (int ff = 0; ff < fg; ++ff) {
-                    const C *tp = tile + ff * tsz + oy * TW + ox;
-                    R acc_re = 0, acc_im = 0;
+                    const R *tp = tile + ff * tsz + oy * TW + ox;
+                    R acc = 0;
 #pragma unroll
                     for (int bb = 0; bb < W; ++bb) {
-                        R rr = 0, ri = 0;
+                        R rr = 0;
 #pragma unroll
-                        for (int aa = 0; aa < W; ++aa) {
-                            const C g = tp[bb * TW + aa];
-                            rr += wx[aa] * g.x;
-                            ri += wx[aa] * g.y;
-                        }
-                        acc_re += wy[bb] * rr;
-                        acc_im += wy[bb] * ri;
+                        for (int aa = 0; aa < W; ++aa) rr += wx[aa] * tp[bb * TW + aa];
+                        acc += wy[bb] * rr;
                     }
-                    (void)acc_im;
-                    out[(size_t)(f0 + ff) * a.P + dst] = acc_re;
+                    out[(size_t)(f0 + ff) * a.P + dst] = acc;
+                }
+            }
+        }
+    }
+}
+
+// FP32 form: the tile starts at an even column and each stencil row is read as
+// WP/2 aligned pairs of cells (8-byte shared loads).  Neighbouring points of
+// the departure grid sit about two cells apart, so a warp's loads fall on
+// consecutive 8-byte words and do not conflict in the shared-memory banks.
+// The point's parity within its pair shifts its w weights into a zero-padded
+// vector of WP weights.
+template <int W>
+__global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a, const float *__restrict__ grid,
+                                                    const int2 *__restrict__ base,
+                                                    const float *__restrict__ frac,
+                                                    const int *__restrict__ idx,
+                                                    const int *__restrict__ bin_start,
+                                                    const int *__restrict__ task_bin,
+                                                    const int *__restrict__ n_tasks,
+                                                    float *__restrict__ out) {
+    constexpr int WP = (W + 2) & ~1;          // taps read per row, even
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tile = reinterpret_cast<float *>(smem_raw);
+    const int TH = a.tile_y + W - 1;
+    const int TW = a.tile_x + WP;             // even: rows stay 8-byte aligned
+    const int Q = TW / 2;                     // pairs per tile row
+    const int tsz = TH * TW;
+    const int ntask = *n_tasks;
+    const float beta = (float)a.beta;
+    for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+        const int bin = task_bin[task];
+        const int by = bin / a.nbx;
+        const int bx = bin - by * a.nbx;
+        const int col0 = (bx * a.tile_x - a.c0) & ~1;
+        const int row0 = by * a.tile_y - a.c0;
+        const int s = bin_start[bin];
+        const int e = bin_start[bin + 1];
+        for (int f0 = 0; f0 < a.F; f0 += a.FG) {
+            const int fg = min(a.FG, a.F - f0);
+            __syncthreads();
+            for (int k = threadIdx.x; k < fg * TH * Q; k += blockDim.x) {
+                const int rr = k / Q;
+                const int qd = k - rr * Q;
+                const int ff = rr / TH;
+                const int r = rr - ff * TH;
+                const int gr = (row0 + r) & (a.n2 - 1);
+                const int gc = (col0 + 2 * qd) & (a.n1 - 1);
+                const float2 v = *reinterpret_cast<const float2 *>(
+                    grid + ((size_t)(f0 + ff) * a.n2 + gr) * a.n1 + gc);
+                *reinterpret_cast<float2 *>(tile + ff * tsz + r * TW + 2 * qd) = v;
+            }
+            __syncthreads();
+            for (int pi = s + threadIdx.x; pi < e; pi += blockDim.x) {
+                const int2 b = base[pi];
+                float wx[W], wy[W], w8[WP];
+                es_weights<float, W>(frac[2 * pi], a.c0, beta, wx);
+                es_weights<float, W>(frac[2 * pi + 1], a.c0, beta, wy);
+                const int ox = b.x - col0;
+                const int odd = ox & 1;
+#pragma unroll
+                for (int k = 0; k < WP; ++k) {
+                    const float lo = k < W ? wx[k] : 0.f;
+                    const float hi = (k >= 1 && k - 1 < W) ? wx[k - 1] : 0.f;
+                    w8[k] = odd ? hi : lo;
+                }
+                const int oy = b.y - row0;
+                const int dst = idx[pi];
+                for (int ff = 0; ff < fg; ++ff) {
+                    const float2 *tp = reinterpret_cast<const float2 *>(
+                        tile + ff * tsz + oy * TW + (ox - odd));
+                    float acc = 0.f;
+#pragma unroll
+                    for (int bb = 0; bb < W; ++bb) {
+                        float rr = 0.f;
+#pragma unroll
+                        for (int k = 0; k < WP / 2; ++k) {
+                            const float2 g = tp[bb * Q + k];
+                            rr += w8[2 * k] * g.x + w8[2 * k + 1] * g.y;
+                        }
+                        acc += wy[bb] * rr;
+                    }
+                    out[(size_t)(f0 + ff) * a.P + dst] = acc;
                 }
             }
         }
@@ -130,23 +207,37 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
     a.F = p->n_fields;
     a.P = (int)p->n_points;
     a.beta = q.beta;
-    const size_t per_field = sizeof(C) * (size_t)(q.tile_y + W - 1) * (q.tile_x + W - 1);
+    constexpr bool pair = sizeof(R) == 4 && W <= 8;   // FP32: paired loads
+    const int tw = pair ? q.tile_x + ((W + 2) & ~1) : q.tile_x + W - 1;
+    const size_t per_field = sizeof(R) * (size_t)(q.tile_y + W - 1) * tw;
     int fg = (int)((96 * 1024) / per_field);
     if (fg < 1) fg = 1;
     if (fg > a.F) fg = a.F;
     a.FG = fg;
     const size_t smem = per_field * fg;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_interp<R, W>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e) return e;
-    }
-    const int threads = sizeof(R) == 4 ? 128 : 256;
     int blocks = p->nbins < 152 * 16 ? p->nbins : 152 * 16;
-    k_interp<R, W><<<blocks, threads, smem, p->stream>>>(
-        a, (const C *)p->d_G, p->d_base, (const R *)p->d_frac, p->d_idx, p->d_bin_start,
-        p->d_task_bin, p->d_n_tasks, (R *)values);
+    if constexpr (pair) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_interp_f32<W>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e) return e;
+        }
+        k_interp_f32<W><<<blocks, 128, smem, p->stream>>>(
+            a, (const float *)p->d_G, p->d_base, (const float *)p->d_frac, p->d_idx,
+            p->d_bin_start, p->d_task_bin, p->d_n_tasks, (float *)values);
+    } else {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_interp<R, W>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e) return e;
+        }
+        const int threads = sizeof(R) == 4 ? 128 : 256;
+        k_interp<R, W><<<blocks, threads, smem, p->stream>>>(
+            a, (const R *)p->d_G, p->d_base, (const R *)p->d_frac, p->d_idx, p->d_bin_start,
+            p->d_task_bin, p->d_n_tasks, (R *)values);
+    }
     return cudaGetLastError();
 }
 

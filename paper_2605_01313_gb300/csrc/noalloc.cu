@@ -79,6 +79,19 @@ void inverse_kernel_ft(int w, double beta, int n_fine, int n_modes, double *out)
     }
 }
 
+// Deconvolution factors in plan precision (FP64 values rounded once for FP32).
+cudaError_t upload_factors(const dfsnufft_params &prm, int dtype, int n_fine, int n_modes,
+                           void *dst, cudaStream_t st) {
+    inverse_kernel_ft(prm.w, prm.beta, n_fine, n_modes, g_ft_stage);
+    size_t bytes = sizeof(double) * n_modes;
+    if (dtype == DFSNUFFT_F32) {
+        float *f = reinterpret_cast<float *>(g_ft_stage);
+        for (int i = 0; i < n_modes; ++i) f[i] = (float)g_ft_stage[i];
+        bytes = sizeof(float) * n_modes;
+    }
+    return cudaMemcpyAsync(dst, g_ft_stage, bytes, cudaMemcpyHostToDevice, st);
+}
+
 template <typename C, typename R>
 cudaError_t upload_twiddles(int n, void *dst, cudaStream_t st) {
     C *h = reinterpret_cast<C *>(g_tw_stage);
@@ -120,11 +133,11 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     p.cap_points = n_points;
     p.has_points = 1;
     const size_t cs = dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
-    const size_t rs = cs / 2;
+    const size_t rs = cs / 2;                    // factor tables are in plan precision
     const size_t nf = (size_t)n_fields, P = (size_t)n_points;
     size_t off[16], total = 0;
-    const size_t sizes[] = {sizeof(double) * prm.N1, sizeof(double) * prm.N2, cs * prm.n1,
-                            cs * prm.n2, cs * nf * prm.n2 * prm.N1, cs * nf * prm.n2 * prm.n1,
+    const size_t sizes[] = {rs * prm.N1, rs * prm.N2, cs * prm.n1,
+                            cs * prm.n2, cs * nf * prm.n2 * prm.N1, rs * nf * prm.n2 * prm.n1,
                             sizeof(int) * p.nbins, sizeof(int) * (p.nbins + 1),
                             sizeof(int) * p.nbins, sizeof(int), (size_t)p.n_row_blocks,
                             sizeof(int) * P, sizeof(int2) * P, 2 * rs * P, sizeof(int) * P};
@@ -148,8 +161,8 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
         ds.base = (unsigned char *)ptr;
     }
     unsigned char *b = ds.base;
-    p.d_inv1 = (double *)(b + off[0]);
-    p.d_inv2 = (double *)(b + off[1]);
+    p.d_inv1 = b + off[0];
+    p.d_inv2 = b + off[1];
     p.d_tw1 = b + off[2];
     p.d_tw2 = b + off[3];
     p.d_T = b + off[4];
@@ -172,13 +185,8 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     if (!same) {
         ds.have_tables = 0;
         cudaError_t e;
-        inverse_kernel_ft(prm.w, prm.beta, prm.n1, prm.N1, g_ft_stage);
-        if ((e = cudaMemcpyAsync(p.d_inv1, g_ft_stage, sizeof(double) * prm.N1,
-                                 cudaMemcpyHostToDevice, p.stream)))
-            return DFSNUFFT_ERR_CUDA;
-        inverse_kernel_ft(prm.w, prm.beta, prm.n2, prm.N2, g_ft_stage);
-        if ((e = cudaMemcpyAsync(p.d_inv2, g_ft_stage, sizeof(double) * prm.N2,
-                                 cudaMemcpyHostToDevice, p.stream)))
+        if ((e = upload_factors(prm, dtype, prm.n1, prm.N1, p.d_inv1, p.stream)) ||
+            (e = upload_factors(prm, dtype, prm.n2, prm.N2, p.d_inv2, p.stream)))
             return DFSNUFFT_ERR_CUDA;
         if (dtype == DFSNUFFT_F64) {
             if ((e = upload_twiddles<double2, double>(prm.n1, p.d_tw1, p.stream)) ||

@@ -222,7 +222,7 @@ extern "C" const char *dfsnufft_version(void) { return DFS_VERSION; }
 // ------------------------------------------------------------------ plan lifetime
 
 static void release(dfsnufft_plan p) {
-    void **bufs[] = {(void **)&p->d_inv1, (void **)&p->d_inv2, &p->d_tw1, &p->d_tw2,
+    void **bufs[] = {&p->d_inv1, &p->d_inv2, &p->d_tw1, &p->d_tw2,
                      &p->d_T, &p->d_G, (void **)&p->d_bin_count, (void **)&p->d_bin_start,
                      (void **)&p->d_task_bin, (void **)&p->d_n_tasks, (void **)&p->d_rowmask,
                      (void **)&p->d_rank, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
@@ -258,8 +258,16 @@ static int upload_tables(dfsnufft_plan p) {
     dfsnufft_kernel_ft(q.w, q.beta, q.n2, q.N2, ft2);
     for (int i = 0; i < q.N1; ++i) ft1[i] = 1.0 / ft1[i];
     for (int i = 0; i < q.N2; ++i) ft2[i] = 1.0 / ft2[i];
-    cudaError_t e1 = cudaMemcpy(p->d_inv1, ft1, sizeof(double) * q.N1, cudaMemcpyHostToDevice);
-    cudaError_t e2 = cudaMemcpy(p->d_inv2, ft2, sizeof(double) * q.N2, cudaMemcpyHostToDevice);
+    // factors in plan precision: FP64 values rounded once for FP32 plans
+    size_t fs = sizeof(double);
+    if (q.dtype == DFSNUFFT_F32) {
+        float *f1 = (float *)ft1, *f2 = (float *)ft2;
+        for (int i = 0; i < q.N1; ++i) f1[i] = (float)ft1[i];
+        for (int i = 0; i < q.N2; ++i) f2[i] = (float)ft2[i];
+        fs = sizeof(float);
+    }
+    cudaError_t e1 = cudaMemcpy(p->d_inv1, ft1, fs * q.N1, cudaMemcpyHostToDevice);
+    cudaError_t e2 = cudaMemcpy(p->d_inv2, ft2, fs * q.N2, cudaMemcpyHostToDevice);
     free(ft1);
     free(ft2);
     if (e1 != cudaSuccess) return fail_cuda(p, "upload deconvolution factors", e1);
@@ -312,12 +320,12 @@ extern "C" int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype,
     size_t cs = dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
     size_t nf = (size_t)n_fields;
     struct { void **ptr; size_t bytes; const char *what; } allocs[] = {
-        {(void **)&p->d_inv1, sizeof(double) * prm.N1, "deconvolution factors"},
-        {(void **)&p->d_inv2, sizeof(double) * prm.N2, "deconvolution factors"},
+        {&p->d_inv1, cs / 2 * prm.N1, "deconvolution factors"},
+        {&p->d_inv2, cs / 2 * prm.N2, "deconvolution factors"},
         {&p->d_tw1, cs * prm.n1, "twiddles"},
         {&p->d_tw2, cs * prm.n2, "twiddles"},
         {&p->d_T, cs * nf * prm.n2 * prm.N1, "theta-pass buffer"},
-        {&p->d_G, cs * nf * prm.n2 * prm.n1, "fine grid"},
+        {&p->d_G, cs / 2 * nf * prm.n2 * prm.n1, "fine grid (real part)"},
         {(void **)&p->d_bin_count, sizeof(int) * p->nbins, "bin counts"},
         {(void **)&p->d_bin_start, sizeof(int) * (p->nbins + 1), "bin starts"},
         {(void **)&p->d_task_bin, sizeof(int) * p->nbins, "bin list"},

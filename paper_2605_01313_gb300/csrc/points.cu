@@ -1,196 +1,258 @@
-// set_points: fold the departure points onto the fine-grid torus (FP64), sort
-// them by interpolation bin with a counting sort, and mark the fine rows their
-// stencils touch.
+// set_points: fold the departure points onto the fine-grid torus, sort them by
+// interpolation bin with a counting sort, and mark the fine rows their stencils
+// touch.
 //
-// Every point gets, in FP64, its fine-grid coordinates x = phi n1 / 2pi and
-// y = theta n2 / 2pi wrapped to [0, n) (the doubled torus is 2pi-periodic in
-// both angles, Sec. 4-5), an integer base cell b and an offset t = x - b:
+// The doubled torus is 2 pi periodic in both angles (Sec. 4-5), so a coordinate
+// only matters as a fraction of a turn.  That fraction is computed exactly in
+// integer arithmetic from the FP64 bit pattern: Y = floor(v / (2 pi) 2^64)
+// mod 2^64 (Q0.64 turns), from the 53-bit significand times 1/(2 pi) held to
+// 128 bits.  GB300 runs FP64 at a small fraction of its integer rate, and the
+// fixed-point result is also more accurate (one unit in 2^-64 turns) than an
+// FP64 product would be.  For a fine grid of n = 2^L cells the point sits at
+// x = Y / 2^(64-L) cells; it gets an integer base cell b and an offset t = x - b:
 //   even w: b = floor(x),       t in [0, 1)
 //   odd  w: b = floor(x + 1/2), t in [-1/2, 1/2)
 // The w taps sit at cells b - c0 .. b - c0 + w - 1 (c0 = w/2 - 1 or (w-1)/2),
 // at kernel arguments z_a = (a - c0) - t, all inside [-w/2, w/2].  Only the
-// small offset t leaves this file in plan precision, so the FP32 form keeps
-// its kernel arguments accurate to ~3e-8 cells whatever the grid size.
+// offset t leaves this file in plan precision (FP32 or FP64), so the FP32 form
+// keeps its kernel arguments accurate to ~1e-9 cells at any grid size.
 #include "common.cuh"
 
 namespace {
 
+// 1/(2 pi) as an unsigned Q0.128 number, floor(2^128 / (2 pi)) (Machin's formula).
+#define DFS_INV_2PI_HI 0x28be60db9391054aULL
+#define DFS_INV_2PI_LO 0x7f09d5f47d4d3770ULL
+
 struct FoldParams {
-    double sx, sy;      // n / (2 pi)
-    int n1, n2;
+    int L1, L2;         // log2 of the fine sizes
     int odd_w;
     int c0, w;
     int tile_x, tile_y, nbx;
-    int n_row_blocks;
 };
 
-__device__ __forceinline__ double wrap(double v, int n) {
-    double dn = (double)n;
-    double t = v - dn * floor(v / dn);
-    if (t >= dn) t -= dn;
-    if (t < 0.0) t += dn;
-    return t;
+// Fraction of a turn of v in Q0.64.  False for inf/nan and for |v| >= 2^53,
+// where FP64 no longer resolves a position within a turn.
+__device__ __forceinline__ bool turns_q64(double v, unsigned long long &Y) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    int e = (int)((bits >> 52) & 0x7ff);
+    if (e == 0x7ff) return false;
+    unsigned long long m = bits & 0xfffffffffffffULL;
+    if (e == 0) e = 1;                      // subnormal: m * 2^(1 - 1075)
+    else m |= 1ULL << 52;                   // |v| = m * 2^(e - 1075)
+    const int sh = 1139 - e;                // Y = floor(m * K * 2^-sh), K = 2^128 / (2 pi)
+    if (sh < 64) return false;
+    unsigned long long y = 0;
+    if (sh < 192) {
+        const unsigned long long hi0 = __umul64hi(m, DFS_INV_2PI_LO);
+        const unsigned long long lo1 = m * DFS_INV_2PI_HI;
+        const unsigned long long hi1 = __umul64hi(m, DFS_INV_2PI_HI);
+        const unsigned long long p1 = hi0 + lo1;          // product bits 64..127
+        const unsigned long long p2 = hi1 + (p1 < hi0);   // product bits 128..
+        if (sh >= 128) {
+            y = p2 >> (sh - 128);
+        } else {
+            const int s = sh - 64;
+            y = s ? ((p1 >> s) | (p2 << (64 - s))) : p1;
+        }
+    }
+    Y = (bits >> 63) ? 0ULL - y : y;
+    return true;
 }
 
-// A non-finite coordinate is placed at cell 0 with a NaN offset: its stencil
-// stays inside the grid and its value comes out NaN.
-__device__ __forceinline__ void fold_point(const FoldParams &f, double lon, double colat,
-                                           int &bx, int &by, double &tx, double &ty) {
-    double x = wrap(lon * f.sx, f.n1);
-    double y = wrap(colat * f.sy, f.n2);
-    bool ok = (x >= 0.0 && x < (double)f.n1) && (y >= 0.0 && y < (double)f.n2);
-    if (!ok) {
-        x = 0.0;
-        y = 0.0;
+// Base cell and offset of one coordinate on a fine grid of 2^L cells.  tq is the
+// offset t in units of 2^-64 cells (signed for odd w).
+__device__ __forceinline__ void split_cell(unsigned long long Y, int L, int odd_w, int &b,
+                                           long long &tq) {
+    if (odd_w) {
+        const unsigned long long yr = Y + (1ULL << (63 - L));
+        b = (int)(yr >> (64 - L));
+        tq = (long long)((yr << L) ^ (1ULL << 63));
+    } else {
+        b = (int)(Y >> (64 - L));
+        tq = (long long)(Y << L);           // unsigned fraction, read back as such
     }
-    double fx = f.odd_w ? floor(x + 0.5) : floor(x);
-    double fy = f.odd_w ? floor(y + 0.5) : floor(y);
-    bx = (int)fx;
-    by = (int)fy;
-    tx = ok ? x - fx : __longlong_as_double(0x7ff8000000000000LL);
-    ty = ok ? y - fy : tx;
+}
+
+template <typename R> __device__ __forceinline__ R offset_value(long long tq, int odd_w);
+template <> __device__ __forceinline__ float offset_value<float>(long long tq, int odd_w) {
+    return odd_w ? (float)(int)(tq >> 32) * 0x1p-32f
+                 : (float)(unsigned)((unsigned long long)tq >> 32) * 0x1p-32f;
+}
+template <> __device__ __forceinline__ double offset_value<double>(long long tq, int odd_w) {
+    return odd_w ? (double)(tq >> 11) * 0x1p-53
+                 : (double)(long long)((unsigned long long)tq >> 11) * 0x1p-53;
+}
+
+// A coordinate that cannot be folded (non-finite, or beyond 2^53 rad) is placed
+// at cell 0; its offset becomes NaN so that its value comes out NaN.
+__device__ __forceinline__ bool fold_point(const FoldParams &f, double lon, double colat,
+                                           int &bx, int &by, long long &tx, long long &ty) {
+    unsigned long long yx = 0, yy = 0;
+    const bool ok = turns_q64(lon, yx) & turns_q64(colat, yy);
+    split_cell(ok ? yx : 0ULL, f.L1, f.odd_w, bx, tx);
+    split_cell(ok ? yy : 0ULL, f.L2, f.odd_w, by, ty);
+    return ok;
 }
 
 __device__ __forceinline__ int bin_of(const FoldParams &f, int bx, int by) {
     return (by / f.tile_y) * f.nbx + bx / f.tile_x;
 }
 
-__global__ void k_fold_count(int n, const double *__restrict__ lon,
-                             const double *__restrict__ colat, FoldParams f,
-                             int *__restrict__ bin_count, int *__restrict__ rank,
-                             unsigned char *__restrict__ rowmask) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    bool live = p < n;
-    int bin = -1;
-    int j0 = 0;
+__global__ void __launch_bounds__(256) k_fold_count(int n, const double *__restrict__ lon,
+                                                    const double *__restrict__ colat,
+                                                    FoldParams f, int *__restrict__ bin_count,
+                                                    int *__restrict__ rank,
+                                                    unsigned char *__restrict__ rowmask) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = p < n;
+    int bin = -1, by = 0;
     if (live) {
-        int bx, by;
-        double tx, ty;
+        int bx;
+        long long tx, ty;
         fold_point(f, lon[p], colat[p], bx, by, tx, ty);
         bin = bin_of(f, bx, by);
-        j0 = by - f.c0;
     }
     // warp-aggregated increment: lanes sharing a bin take consecutive ranks
-    unsigned live_mask = __ballot_sync(0xffffffffu, live);
+    const unsigned live_mask = __ballot_sync(0xffffffffu, live);
     if (!live) return;
-    unsigned peers = __match_any_sync(live_mask, bin);
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(peers) - 1;
+    const unsigned peers = __match_any_sync(live_mask, bin);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
     int base = 0;
     if (lane == leader) base = atomicAdd(&bin_count[bin], __popc(peers));
     base = __shfl_sync(peers, base, leader);
     rank[p] = base + __popc(peers & ((1u << lane) - 1u));
     // fine rows j0 .. j0 + w - 1 (mod n2) span at most two row blocks (w <= 16)
-    int r_lo = j0 & (f.n2 - 1);
-    int r_hi = (j0 + f.w - 1) & (f.n2 - 1);
-    rowmask[r_lo / DFS_ROW_BLOCK] = 1;
-    rowmask[r_hi / DFS_ROW_BLOCK] = 1;
+    const int j0 = by - f.c0;
+    const int nmask = (1 << f.L2) - 1;
+    rowmask[(j0 & nmask) / DFS_ROW_BLOCK] = 1;
+    rowmask[((j0 + f.w - 1) & nmask) / DFS_ROW_BLOCK] = 1;
 }
 
-// One CTA: exclusive scan of the bin counts and the list of non-empty bins.
+// One CTA: exclusive scan of the bin counts and the list of non-empty bins, in
+// chunks of 4 * blockDim bins (each thread four consecutive bins).
 __global__ void __launch_bounds__(1024) k_scan_bins(int nbins, const int *__restrict__ count,
                                                     int *__restrict__ start,
                                                     int *__restrict__ task_bin,
                                                     int *__restrict__ n_tasks) {
-    __shared__ int s_cnt[32], s_ne[32];
-    const int tid = threadIdx.x;
-    const int per = (nbins + blockDim.x - 1) / blockDim.x;
-    const int lo = tid * per;
-    const int hi = min(lo + per, nbins);
-    int sum = 0, ne = 0;
-    for (int i = lo; i < hi; ++i) {
-        int c = count[i];
-        sum += c;
-        ne += c > 0;
-    }
-    // block-wide exclusive scan of (sum, ne)
-    int lane = tid & 31, wid = tid >> 5;
-    int xs = sum, xn = ne;
-    for (int o = 1; o < 32; o <<= 1) {
-        int ys = __shfl_up_sync(0xffffffffu, xs, o);
-        int yn = __shfl_up_sync(0xffffffffu, xn, o);
-        if (lane >= o) {
-            xs += ys;
-            xn += yn;
+    __shared__ int s_sum[32], s_ne[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    int carry = 0, carry_n = 0;
+    for (int base = 0; base < nbins; base += 4 * blockDim.x) {
+        const int i0 = base + 4 * tid;
+        int c[4];
+        if (i0 + 3 < nbins) {
+            const int4 v = *reinterpret_cast<const int4 *>(count + i0);
+            c[0] = v.x;
+            c[1] = v.y;
+            c[2] = v.z;
+            c[3] = v.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c[k] = i0 + k < nbins ? count[i0 + k] : 0;
         }
-    }
-    if (lane == 31) {
-        s_cnt[wid] = xs;
-        s_ne[wid] = xn;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        int nw = blockDim.x >> 5;
-        int vs = lane < nw ? s_cnt[lane] : 0;
-        int vn = lane < nw ? s_ne[lane] : 0;
+        const int sum = c[0] + c[1] + c[2] + c[3];
+        const int ne = (c[0] > 0) + (c[1] > 0) + (c[2] > 0) + (c[3] > 0);
+        int xs = sum, xn = ne;
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int ys = __shfl_up_sync(0xffffffffu, vs, o);
-            int yn = __shfl_up_sync(0xffffffffu, vn, o);
+            const int ys = __shfl_up_sync(0xffffffffu, xs, o);
+            const int yn = __shfl_up_sync(0xffffffffu, xn, o);
             if (lane >= o) {
-                vs += ys;
-                vn += yn;
+                xs += ys;
+                xn += yn;
             }
         }
-        if (lane < nw) {
-            s_cnt[lane] = vs;
-            s_ne[lane] = vn;
+        if (lane == 31) {
+            s_sum[wid] = xs;
+            s_ne[wid] = xn;
         }
+        __syncthreads();
+        if (wid == 0) {
+            int vs = lane < nw ? s_sum[lane] : 0;
+            int vn = lane < nw ? s_ne[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int ys = __shfl_up_sync(0xffffffffu, vs, o);
+                const int yn = __shfl_up_sync(0xffffffffu, vn, o);
+                if (lane >= o) {
+                    vs += ys;
+                    vn += yn;
+                }
+            }
+            if (lane < nw) {
+                s_sum[lane] = vs;
+                s_ne[lane] = vn;
+            }
+        }
+        __syncthreads();
+        int off_s = carry + xs - sum + (wid > 0 ? s_sum[wid - 1] : 0);
+        int off_n = carry_n + xn - ne + (wid > 0 ? s_ne[wid - 1] : 0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < nbins) {
+                start[i0 + k] = off_s;
+                if (c[k] > 0) task_bin[off_n++] = i0 + k;
+            }
+            off_s += c[k];
+        }
+        carry += s_sum[nw - 1];
+        carry_n += s_ne[nw - 1];
+        __syncthreads();
     }
-    __syncthreads();
-    int off_s = xs - sum + (wid > 0 ? s_cnt[wid - 1] : 0);
-    int off_n = xn - ne + (wid > 0 ? s_ne[wid - 1] : 0);
-    for (int i = lo; i < hi; ++i) {
-        int c = count[i];
-        start[i] = off_s;
-        off_s += c;
-        if (c > 0) task_bin[off_n++] = i;
-    }
-    if (tid == blockDim.x - 1) {
-        start[nbins] = off_s;
-        *n_tasks = off_n;
+    if (tid == 0) {
+        start[nbins] = carry;
+        *n_tasks = carry_n;
     }
 }
 
 template <typename R>
-__global__ void k_scatter(int n, const double *__restrict__ lon, const double *__restrict__ colat,
-                          FoldParams f, const int *__restrict__ start,
-                          const int *__restrict__ rank, int2 *__restrict__ base,
-                          R *__restrict__ frac, int *__restrict__ idx) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_scatter(int n, const double *__restrict__ lon,
+                                                 const double *__restrict__ colat, FoldParams f,
+                                                 const int *__restrict__ start,
+                                                 const int *__restrict__ rank,
+                                                 int2 *__restrict__ base, R *__restrict__ frac,
+                                                 int *__restrict__ idx) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     int bx, by;
-    double tx, ty;
-    fold_point(f, lon[p], colat[p], bx, by, tx, ty);
-    int pos = start[bin_of(f, bx, by)] + rank[p];
+    long long tx, ty;
+    const bool ok = fold_point(f, lon[p], colat[p], bx, by, tx, ty);
+    const int pos = start[bin_of(f, bx, by)] + rank[p];
     base[pos] = make_int2(bx - f.c0, by - f.c0);
-    frac[2 * pos] = (R)tx;
-    frac[2 * pos + 1] = (R)ty;
+    R ox = offset_value<R>(tx, f.odd_w), oy = offset_value<R>(ty, f.odd_w);
+    if (!ok) ox = oy = (R)__int_as_float(0x7fc00000);
+    frac[2 * pos] = ox;
+    frac[2 * pos + 1] = oy;
     idx[pos] = p;
+}
+
+int ilog2(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
 }
 
 }  // namespace
 
 cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const double *colat) {
     const dfsnufft_params &q = p->prm;
-    const double two_pi = 6.283185307179586476925286766559;
     FoldParams f;
-    f.sx = (double)q.n1 / two_pi;
-    f.sy = (double)q.n2 / two_pi;
-    f.n1 = q.n1;
-    f.n2 = q.n2;
+    f.L1 = ilog2(q.n1);
+    f.L2 = ilog2(q.n2);
     f.odd_w = q.w & 1;
     f.c0 = p->c0;
     f.w = q.w;
     f.tile_x = q.tile_x;
     f.tile_y = q.tile_y;
     f.nbx = p->nbx;
-    f.n_row_blocks = p->n_row_blocks;
-    int n = (int)p->n_points;
+    const int n = (int)p->n_points;
     cudaError_t e;
     if ((e = cudaMemsetAsync(p->d_bin_count, 0, sizeof(int) * p->nbins, p->stream))) return e;
     if ((e = cudaMemsetAsync(p->d_rowmask, 0, p->n_row_blocks, p->stream))) return e;
     const int tpb = 256;
-    int blocks = (n + tpb - 1) / tpb;
+    const int blocks = (n + tpb - 1) / tpb;
     k_fold_count<<<blocks, tpb, 0, p->stream>>>(n, lon, colat, f, p->d_bin_count, p->d_rank,
                                                p->d_rowmask);
     k_scan_bins<<<1, 1024, 0, p->stream>>>(p->nbins, p->d_bin_count, p->d_bin_start,
