@@ -63,7 +63,8 @@ enum {
     DFSNUFFT_ERR_NO_POINTS = 3,        /* execute before set_points                 */
     DFSNUFFT_ERR_OOM = 4,              /* device allocation failed                  */
     DFSNUFFT_ERR_CUDA = 5,             /* a CUDA call failed (sticky per plan)      */
-    DFSNUFFT_ERR_UNSUPPORTED = 6       /* size outside the supported range          */
+    DFSNUFFT_ERR_UNSUPPORTED = 6,      /* size outside the supported range          */
+    DFSNUFFT_ERR_TIMEOUT = 7           /* a kernel gave up waiting on an async copy */
 };
 
 /* Parameters a plan chooses (also available without a GPU). */
@@ -119,6 +120,13 @@ const char *dfsnufft_strerror(int status);
 /* Last error message recorded on the plan ("" if none). */
 const char *dfsnufft_plan_last_error(dfsnufft_plan plan);
 
+/* Synchronise the plan's stream and read its device status word.  Kernels that
+ * wait on asynchronous (TMA) copies give up after about one second and record
+ * a timeout there instead of hanging; this call then returns
+ * DFSNUFFT_ERR_TIMEOUT (sticky for the plan).  Otherwise it returns the plan's
+ * status (DFSNUFFT_OK when healthy). */
+int dfsnufft_plan_check(dfsnufft_plan plan);
+
 /* Parameters of an existing plan. */
 int dfsnufft_plan_get_params(dfsnufft_plan plan, dfsnufft_params *out);
 
@@ -135,8 +143,9 @@ int dfsnufft_plan_enable_timing(dfsnufft_plan plan, int enable);
 int dfsnufft_plan_read_timing(dfsnufft_plan plan, double *ms_total, int64_t *calls);
 
 /* Work statistics of the current points (synchronises the stream): the
- * number of fine rows the points' stencils touch (per field) and the number
- * of non-empty interpolation bins.  Measurement aid; no paper counterpart. */
+ * number of fine rows computed per field (one circular range, in blocks of 16
+ * rows, covering every row the points' stencils touch) and the number of
+ * non-empty interpolation bins.  Measurement aid; no paper counterpart. */
 int dfsnufft_plan_point_stats(dfsnufft_plan plan, int64_t *rows_needed, int64_t *nonempty_bins);
 
 /* ---- allocation-free one-shot call -------------------------------------- */

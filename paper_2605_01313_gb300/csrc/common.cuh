@@ -23,10 +23,11 @@ __host__ __device__ __forceinline__ C cmul(C a, C b) {
 }
 
 // ---------------------------------------------------------------- plan layout
+// Elements per thread of the FFT kernels (both passes, both precisions).
+#define DFS_FFT_E 8
 // Row-block granularity of the "fine rows needed" mask (rows per flag).
 #define DFS_ROW_BLOCK 16
-// Elements each FFT thread holds in registers (radix-16 Stockham stages).
-#define DFS_FFT_E 16
+#define DFS_MAX_ROW_BLOCKS (8192 / DFS_ROW_BLOCK)
 #define DFS_FFT_MIN_LOG 4
 #define DFS_FFT_MAX_LOG 13
 // Event pairs kept per stage before read_timing must drain them.
@@ -37,7 +38,6 @@ struct dfsnufft_plan_s {
     int n_fields;
     int c0;                 // first tap sits c0 cells left of the point's base cell
     int nbx, nby, nbins;    // interpolation bins
-    int n_row_blocks;       // blocks of DFS_ROW_BLOCK fine rows
     cudaStream_t stream;
 
     // device buffers owned by the plan
@@ -45,13 +45,17 @@ struct dfsnufft_plan_s {
     void *d_inv2;           // N2: 1 / phihat(n), centred, plan precision
     void *d_tw1;            // n1 twiddles e^{+2 pi i k / n1} (plan precision)
     void *d_tw2;            // n2 twiddles
+    void *d_stw_theta;      // stage-ordered twiddles of the length-n2/2 theta transforms
+    void *d_stw_phi;        // stage-ordered twiddles of the length-n1/2 phi transforms
     void *d_T;              // theta-pass output, n_fields x n2 x N1
     void *d_G;              // fine grids (real part), n_fields x n2 x n1, plan precision
     int *d_bin_count;       // nbins
     int *d_bin_start;       // nbins + 1
     int *d_task_bin;        // nbins: list of non-empty bins
     int *d_n_tasks;         // 1
-    unsigned char *d_rowmask;   // n_row_blocks (fine rows, mod n2)
+    int2 *d_rowrange;           // circular range of needed fine rows: (first, count)
+    int *d_status;              // device status word (DFS_STATUS_*), zero when healthy
+    int num_sms;                // multiprocessors of the plan's device
 
     // point data (capacity grows with set_points)
     int64_t n_points, cap_points;

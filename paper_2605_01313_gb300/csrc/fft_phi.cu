@@ -1,0 +1,124 @@
+// phi pass: the row FFTs of the oversampled 2-D inverse FFT (sign +1), the
+// last FFT stage of the type-2 NUFFT evaluating Eq. 5.3 (Sec. 5).
+//
+// Only the real part of the fine grid is needed (the interpolation weights are
+// real and the values are Re v), so each row is a complex-to-real transform:
+// Re g(j) = sum_k H_k e^{2 pi i k j / n1} with H_k = (T_k + conj T_{-k}) / 2
+// Hermitian.  With M = n1 / 2 and Z_k = (H_k + H_{k+M}) + i e^{2 pi i k / n1}
+// (H_k - H_{k+M}), the length-M inverse FFT z of Z gives
+// Re g(2j) = Re z_j and Re g(2j+1) = Im z_j.  T_k is the theta-pass value at
+// phi-mode k mod n1 (zero outside the N1 modes).  Each CTA handles CB rows
+// inside the plan's needed row range; the row's N1 values are staged in
+// shared memory first, since every one of them enters two Z_k.
+#include "fft_core.cuh"
+
+using namespace dfs_fft;
+
+namespace {
+
+struct PhiArgs {
+    int N1, n1, logm, n2;     // logm = log2(n1 / 2)
+    int CB;                   // rows per CTA (divides DFS_ROW_BLOCK)
+};
+
+// grid (n2 / CB, n_fields); block CB * M/E threads, thread = (t, c) with t fastest.
+// LOGM > 0 fixes the transform length at compile time; 0 takes it from a.logm.
+template <typename R, int E, int MAXT, int MINB, int LOGM>
+__global__ void __launch_bounds__(MAXT, MINB)
+    k_phi_pass(PhiArgs a, const typename CxT<R>::type *__restrict__ in,
+               const typename CxT<R>::type *__restrict__ tw,
+               const typename CxT<R>::type *__restrict__ stw, const int2 *__restrict__ rowrange,
+               R *__restrict__ grid) {
+    typedef typename CxT<R>::type C;
+    const int row0 = blockIdx.x * a.CB;
+    const int2 rr = *rowrange;
+    // whole CTA (within one row block): no stencil touches these rows
+    if (((row0 - rr.x) & (a.n2 - 1)) >= rr.y) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *smem = reinterpret_cast<C *>(smem_raw);
+    const int M = LOGM ? (1 << LOGM) : (1 << a.logm);
+    const int T = M / E;
+    const int t = threadIdx.x % T;
+    const int c = threadIdx.x / T;
+    const int row = row0 + c;
+    const int f = blockIdx.y;
+    const C *src = in + ((size_t)f * a.n2 + row) * a.N1;
+    R *dst = grid + ((size_t)f * a.n2 + row) * a.n1;
+    const int half = a.N1 / 2;
+    const int nmask = a.n1 - 1;
+    C *sm = smem + (size_t)c * region_len<C>(M);
+    C *srow = smem + (size_t)a.CB * region_len<C>(M) + (size_t)c * a.N1;
+    for (int i = t; i < a.N1; i += T) srow[i] = src[i];
+    __syncthreads();
+    auto tval = [&](int k) -> C {              // T_k, k taken mod n1
+        k &= nmask;
+        int m;
+        if (k < half) m = k;
+        else if (k >= a.n1 - half) m = k - a.n1;
+        else return cmake((R)0, (R)0);
+        return srow[m + half];
+    };
+    auto ld = [&](int k) -> C {
+        const C t0 = tval(k), t1 = tval(-k), t2 = tval(k + M), t3 = tval(M - k);
+        // 2 H_k = T_k + conj T_{-k},  2 H_{k+M} = T_{k+M} + conj T_{M-k}
+        const C h0 = cmake(t0.x + t1.x, t0.y - t1.y);
+        const C h1 = cmake(t2.x + t3.x, t2.y - t3.y);
+        const C d = cmul(cmake(h0.x - h1.x, h0.y - h1.y), __ldg(&tw[k]));
+        // (h0 + h1 + i d) / 2
+        return cmake((R)0.5 * (h0.x + h1.x - d.y), (R)0.5 * (h0.y + h1.y + d.x));
+    };
+    auto st = [&](int j, C z) { reinterpret_cast<C *>(dst)[j] = z; };
+    if constexpr (LOGM > 0) line_fft_ct<LOGM, E>(stw, sm, t, ld, st);
+    else line_fft<E>(a.logm, tw, 1, sm, t, ld, st);
+}
+
+template <typename R> struct PhiCfg;
+template <> struct PhiCfg<float> { static const int E = DFS_FFT_E, MAXT = 256, MINB = 3; };
+template <> struct PhiCfg<double> { static const int E = DFS_FFT_E, MAXT = 512, MINB = 1; };
+
+template <typename R, int LOGM>
+cudaError_t run_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
+    typedef typename CxT<R>::type C;
+    constexpr int E = PhiCfg<R>::E, MAXT = PhiCfg<R>::MAXT, MINB = PhiCfg<R>::MINB;
+    cudaError_t e = allow_smem(k_phi_pass<R, E, MAXT, MINB, LOGM>, smem);
+    if (e) return e;
+    k_phi_pass<R, E, MAXT, MINB, LOGM><<<grid, threads, smem, p->stream>>>(
+        a, (const C *)p->d_T, (const C *)p->d_tw1, (const C *)p->d_stw_phi, p->d_rowrange,
+        (R *)p->d_G);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_phi(dfsnufft_plan p) {
+    typedef typename CxT<R>::type C;
+    constexpr int E = PhiCfg<R>::E, MAXT = PhiCfg<R>::MAXT;
+    const dfsnufft_params &q = p->prm;
+    PhiArgs a;
+    a.N1 = q.N1;
+    a.n1 = q.n1;
+    a.logm = ilog2(q.n1) - 1;
+    a.n2 = q.n2;
+    const int M = q.n1 / 2;
+    const int T = M / E;
+    int cb = MAXT / T;
+    if (cb < 1) cb = 1;
+    if (cb > DFS_ROW_BLOCK) cb = DFS_ROW_BLOCK;
+    const size_t per_row = sizeof(C) * (size_t)(region_len<C>(M) + q.N1);
+    while (cb > 1 && per_row * cb > 160 * 1024) cb >>= 1;
+    a.CB = cb;
+    const size_t smem = per_row * cb;
+    const dim3 grid(q.n2 / cb, p->n_fields);
+    if (!p->d_stw_phi) return run_phi<R, 0>(p, a, smem, grid, cb * T);
+    switch (a.logm) {
+        case 9: return run_phi<R, 9>(p, a, smem, grid, cb * T);
+        case 10: return run_phi<R, 10>(p, a, smem, grid, cb * T);
+        case 11: return run_phi<R, 11>(p, a, smem, grid, cb * T);
+        default: return run_phi<R, 0>(p, a, smem, grid, cb * T);
+    }
+}
+
+}  // namespace
+
+cudaError_t dfs_launch_phi_pass(dfsnufft_plan p) {
+    return p->prm.dtype == DFSNUFFT_F64 ? launch_phi<double>(p) : launch_phi<float>(p);
+}

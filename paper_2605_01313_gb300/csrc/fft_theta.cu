@@ -1,0 +1,280 @@
+// theta pass: deconvolve-and-pad fused with the column FFTs of the oversampled
+// 2-D inverse FFT (sign +1, unnormalised), a middle stage of the type-2 NUFFT
+// evaluating Eq. 5.3 (Sec. 5).  For each phi-mode column q (m = q - N1/2), the
+// N2 theta modes, each divided by phihat2(n) phihat1(m), are placed at fine
+// index n mod n2 (zeros elsewhere) and transformed along the column; only the
+// fine rows inside the plan's needed row range are stored: T[f][row][q].
+//
+// Main kernel (k_theta_tma): persistent CTAs take blocks of CB columns (32-byte
+// row segments).  The block's N2 coefficient rows arrive in shared memory by
+// 2-D TMA boxes, double-buffered so that the next block streams in while this
+// one is transformed.  Each column's length-n2 transform is done as two
+// length-n2/2 transforms: output row 2q + s = sum_n c_n e^{2 pi i n s / n2}
+// e^{2 pi i n q / (n2/2)}, s = 0, 1 (the N2 modes fit in n2/2 without aliasing).
+// k_theta_pass is the plain-load version for shapes the TMA kernel does not
+// take (unaligned coefficient pointer, CTA or shared-memory limits).
+#include "fft_core.cuh"
+#include "tma.cuh"
+
+using namespace dfs_fft;
+
+namespace {
+
+struct ThetaArgs {
+    int N1, N2, n2, logn2;
+    int CB;                   // columns per CTA
+};
+
+// grid (ceil(N1 / CB), n_fields); block CB * n2/E threads, thread = (t, c) with c fastest.
+template <typename R, int E, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
+    k_theta_pass(ThetaArgs a, const typename CxT<R>::type *__restrict__ coef,
+                 const R *__restrict__ inv1, const R *__restrict__ inv2,
+                 const typename CxT<R>::type *__restrict__ tw,
+                 const int2 *__restrict__ rowrange, typename CxT<R>::type *__restrict__ out) {
+    typedef typename CxT<R>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *smem = reinterpret_cast<C *>(smem_raw);
+    const int2 rr = *rowrange;
+    const int c = threadIdx.x % a.CB;
+    const int t = threadIdx.x / a.CB;
+    const int q = blockIdx.x * a.CB + c;
+    const int f = blockIdx.y;
+    const bool col_ok = q < a.N1;
+    const C *src = coef + (size_t)f * a.N2 * a.N1 + q;
+    C *dst = out + (size_t)f * a.n2 * a.N1 + q;
+    const int half = a.N2 / 2;
+    const R sq = col_ok ? inv1[q] : (R)0;
+    C *sm = smem + (size_t)c * region_len<C>(a.n2);
+    auto ld = [&](int i) -> C {
+        int n;
+        if (i < half) n = i;
+        else if (i >= a.n2 - half) n = i - a.n2;
+        else return cmake((R)0, (R)0);
+        if (!col_ok) return cmake((R)0, (R)0);
+        const int r = n + half;
+        const C v = src[(size_t)r * a.N1];
+        const R s = sq * inv2[r];
+        return cmake(v.x * s, v.y * s);
+    };
+    auto st = [&](int i, C v) {
+        if (col_ok && ((i - rr.x) & (a.n2 - 1)) < rr.y) dst[(size_t)i * a.N1] = v;
+    };
+    line_fft<E>(a.logn2, tw, 0, sm, t, ld, st);
+}
+
+struct ThetaTmaArgs {
+    int N1, N2, n2, logh;     // logh = log2(n2 / 2)
+    int nbq;                  // column blocks per field, ceil(N1 / CB)
+    int total;                // nbq * n_fields
+    int nbox, box_rows;       // TMA boxes per block and rows per box
+    int in_elems;             // complex elements delivered per block
+    int nbuf;                 // input buffers (2: prefetch the next block)
+    unsigned tx_bytes;        // bytes delivered per block
+};
+
+// LOGH > 0: half length 2^LOGH fixed at compile time (unrolled transform);
+// LOGH == 0: taken from the arguments.
+template <typename R, int E, int CB, int MAXT, int LOGH>
+__global__ void __launch_bounds__(MAXT, 1)
+    k_theta_tma(ThetaTmaArgs a, const __grid_constant__ CUtensorMap tmap,
+                const R *__restrict__ inv1, const R *__restrict__ inv2,
+                const typename CxT<R>::type *__restrict__ tw,
+                const typename CxT<R>::type *__restrict__ stw, const int2 *__restrict__ rowrange,
+                typename CxT<R>::type *__restrict__ out, int *__restrict__ status) {
+    typedef typename CxT<R>::type C;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations start on 128-byte boundaries (base rounded up here;
+    // buffer and box sizes are multiples of 128 bytes by construction)
+    unsigned char *base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base);
+    C *inb = reinterpret_cast<C *>(base + 128);
+    C *ex = inb + (size_t)a.nbuf * a.in_elems;
+    const int H = LOGH ? (1 << LOGH) : (a.n2 >> 1);
+    const int T = H / E;
+    R *f2 = reinterpret_cast<R *>(ex + (size_t)CB * region_len<C>(H));   // 1 / phihat2, N2 rows
+    const int c = threadIdx.x % CB;
+    const int t = threadIdx.x / CB;
+    const int half = a.N2 / 2;
+    const int2 rr = *rowrange;
+    C *sm = ex + (size_t)c * region_len<C>(H);
+    for (int i = threadIdx.x; i < a.N2; i += blockDim.x) f2[i] = inv2[i];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int blk, int b) {
+        const int f = blk / a.nbq;
+        const int qb = blk - f * a.nbq;
+        C *dst = inb + (size_t)b * a.in_elems;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar[b], a.tx_bytes);
+        const int x = qb * CB * (int)(sizeof(C) / 8);
+        for (int i = 0; i < a.nbox; ++i)
+            tma_load_2d(dst + (size_t)i * a.box_rows * CB, &tmap, x, f * a.N2 + i * a.box_rows,
+                        &bar[b]);
+    };
+    uint32_t phase0 = 0, phase1 = 0;
+    int it = 0;
+    if (threadIdx.x == 0 && (int)blockIdx.x < a.total) issue(blockIdx.x, 0);
+    for (int blk = blockIdx.x; blk < a.total; blk += gridDim.x, ++it) {
+        const int cur = a.nbuf == 2 ? (it & 1) : 0;
+        const int nxt = blk + gridDim.x;
+        const bool pre = a.nbuf == 2 && nxt < a.total;
+        if (pre && threadIdx.x == 0) issue(nxt, cur ^ 1);
+        const bool ok = mbar_wait_bounded(&bar[cur], cur ? phase1 : phase0);
+        if (cur) phase1 ^= 1;
+        else phase0 ^= 1;
+        if (__syncthreads_or(!ok)) {
+            // give up on this launch; let copies still in flight land first
+            if (threadIdx.x == 0) {
+                atomicExch(status, DFS_STATUS_TIMEOUT);
+                mbar_wait_bounded(&bar[cur], cur ? phase1 ^ 1 : phase0 ^ 1);
+                if (pre) mbar_wait_bounded(&bar[cur ^ 1], cur ? phase0 : phase1);
+            }
+            __syncthreads();
+            return;
+        }
+        const int f = blk / a.nbq;
+        const int q = (blk - f * a.nbq) * CB + c;
+        const bool col_ok = q < a.N1;
+        const R sq = col_ok ? inv1[q] : (R)0;
+        const C *in = inb + (size_t)cur * a.in_elems;
+        C *dst = out + (size_t)f * a.n2 * a.N1 + q;
+#pragma unroll 1
+        for (int s = 0; s < 2; ++s) {
+            auto ld = [&](int i) -> C {
+                int n;
+                if (i < half) n = i;
+                else if (i >= H - half) n = i - H;
+                else return cmake((R)0, (R)0);
+                const int r = n + half;
+                const C v = in[r * CB + c];
+                const R sc = sq * f2[r];
+                C y = cmake(v.x * sc, v.y * sc);
+                if (s) y = cmul(y, __ldg(&tw[n & (a.n2 - 1)]));
+                return y;
+            };
+            auto st = [&](int qq, C v) {
+                const int row = 2 * qq + s;
+                if (col_ok && ((row - rr.x) & (a.n2 - 1)) < rr.y) dst[(size_t)row * a.N1] = v;
+            };
+            if constexpr (LOGH > 0) line_fft_ct<LOGH, E>(stw, sm, t, ld, st);
+            else line_fft<E>(a.logh, tw, 1, sm, t, ld, st);
+            __syncthreads();
+        }
+        if (a.nbuf == 1 && threadIdx.x == 0 && nxt < a.total) issue(nxt, 0);
+    }
+}
+
+// Per precision: elements per thread E, threads per CTA at most MAXT, resident
+// CTAs MINB the register budget is set for (plain kernel); columns per block CB.
+template <typename R> struct ThetaCfg;
+template <> struct ThetaCfg<float> { static const int E = DFS_FFT_E, MAXT = 1024, MINB = 1, CB = 4; };
+template <> struct ThetaCfg<double> { static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, CB = 2; };
+
+template <typename R, int LOGH>
+cudaError_t run_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUtensorMap &tmap,
+                          size_t smem, int grid, int threads) {
+    typedef typename CxT<R>::type C;
+    constexpr int E = ThetaCfg<R>::E, CB = ThetaCfg<R>::CB, MAXT = ThetaCfg<R>::MAXT;
+    cudaError_t e = cudaFuncSetAttribute(k_theta_tma<R, E, CB, MAXT, LOGH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    k_theta_tma<R, E, CB, MAXT, LOGH><<<grid, threads, smem, p->stream>>>(
+        a, tmap, (const R *)p->d_inv1, (const R *)p->d_inv2, (const C *)p->d_tw2,
+        (const C *)p->d_stw_theta, p->d_rowrange, (C *)p->d_T, p->d_status);
+    return cudaGetLastError();
+}
+
+// Launch the TMA theta pass; returns cudaErrorNotSupported (without launching)
+// when the shape or the coefficient pointer does not suit it.
+template <typename R>
+cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
+    typedef typename CxT<R>::type C;
+    constexpr int E = ThetaCfg<R>::E, CB = ThetaCfg<R>::CB, MAXT = ThetaCfg<R>::MAXT;
+    const dfsnufft_params &q = p->prm;
+    if (((uintptr_t)coeffs & 15) != 0 || !p->d_status) return cudaErrorNotSupported;
+    const int H = q.n2 / 2;
+    if (H < E || CB * (H / E) > MAXT) return cudaErrorNotSupported;
+    ThetaTmaArgs a;
+    a.N1 = q.N1;
+    a.N2 = q.N2;
+    a.n2 = q.n2;
+    a.logh = ilog2(H);
+    a.nbq = (q.N1 + CB - 1) / CB;
+    a.total = a.nbq * p->n_fields;
+    // boxes of CB columns x box_rows rows, each a multiple of 128 bytes
+    // (CB * sizeof(C) = 32 bytes a row, box_rows a multiple of 4)
+    a.box_rows = q.N2 < 256 ? ((q.N2 + 3) & ~3) : 256;
+    a.nbox = (q.N2 + a.box_rows - 1) / a.box_rows;
+    a.in_elems = a.nbox * a.box_rows * CB;
+    a.tx_bytes = (unsigned)(sizeof(C) * a.in_elems);
+    const size_t ex_bytes = sizeof(C) * (size_t)CB * region_len<C>(H);
+    const size_t f2_bytes = sizeof(R) * (size_t)q.N2;
+    const size_t limit = 220 * 1024;
+    const size_t in_bytes = sizeof(C) * (size_t)a.in_elems;
+    a.nbuf = 256 + 2 * in_bytes + ex_bytes + f2_bytes <= limit ? 2 : 1;
+    const size_t smem = 256 + a.nbuf * in_bytes + ex_bytes + f2_bytes;
+    if (smem > limit) return cudaErrorNotSupported;
+    CUtensorMap tmap;
+    cudaError_t e = dfs_encode_tensor_map_2d(&tmap, coeffs, (uint64_t)q.N1 * (sizeof(C) / 8),
+                                             (uint64_t)q.N2 * p->n_fields,
+                                             sizeof(C) * (uint64_t)q.N1,
+                                             (uint32_t)(CB * (sizeof(C) / 8)),
+                                             (uint32_t)a.box_rows);
+    if (e) return e;
+    int grid = p->num_sms > 0 ? p->num_sms : 1;
+    if (grid > a.total) grid = a.total;
+    const int threads = CB * (H / E);
+    if (!p->d_stw_theta) return run_theta_tma<R, 0>(p, a, tmap, smem, grid, threads);
+    switch (a.logh) {
+        case 9: return run_theta_tma<R, 9>(p, a, tmap, smem, grid, threads);
+        case 10: return run_theta_tma<R, 10>(p, a, tmap, smem, grid, threads);
+        case 11: return run_theta_tma<R, 11>(p, a, tmap, smem, grid, threads);
+        default: return run_theta_tma<R, 0>(p, a, tmap, smem, grid, threads);
+    }
+}
+
+template <typename R>
+cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs) {
+    typedef typename CxT<R>::type C;
+    {
+        cudaError_t e = launch_theta_tma<R>(p, coeffs);
+        if (e != cudaErrorNotSupported) return e;
+        cudaGetLastError();
+    }
+    constexpr int E = ThetaCfg<R>::E, MAXT = ThetaCfg<R>::MAXT, MINB = ThetaCfg<R>::MINB;
+    const dfsnufft_params &q = p->prm;
+    ThetaArgs a;
+    a.N1 = q.N1;
+    a.N2 = q.N2;
+    a.n2 = q.n2;
+    a.logn2 = ilog2(q.n2);
+    const int T = q.n2 / E;
+    int cb = MAXT / T;
+    if (cb < 1) cb = 1;
+    int n1p = 1;
+    while (n1p < q.N1) n1p <<= 1;
+    if (cb > n1p) cb = n1p;
+    const size_t per_col = sizeof(C) * (size_t)region_len<C>(q.n2);
+    while (cb > 1 && per_col * cb > 160 * 1024) cb >>= 1;
+    a.CB = cb;
+    const size_t smem = per_col * cb;
+    cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB>, smem);
+    if (e) return e;
+    dim3 grid((q.N1 + cb - 1) / cb, p->n_fields);
+    k_theta_pass<R, E, MAXT, MINB><<<grid, cb * T, smem, p->stream>>>(
+        a, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2, (const C *)p->d_tw2,
+        p->d_rowrange, (C *)p->d_T);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t dfs_launch_theta_pass(dfsnufft_plan p, const void *coeffs) {
+    return p->prm.dtype == DFSNUFFT_F64 ? launch_theta<double>(p, coeffs)
+                                        : launch_theta<float>(p, coeffs);
+}

@@ -26,8 +26,11 @@ struct InterpArgs {
     double beta;
 };
 
+// FP32: the hardware exponential (exp2 of x log2 e); for arguments in
+// [-beta, 0] its relative error stays near 1e-7, far below the FP32 form's
+// tolerance.  FP64 keeps the correctly rounded library exp.
 template <typename R> __device__ __forceinline__ R kexp(R x);
-template <> __device__ __forceinline__ float kexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ float kexp<float>(float x) { return __expf(x); }
 template <> __device__ __forceinline__ double kexp<double>(double x) { return exp(x); }
 template <typename R> __device__ __forceinline__ R ksqrt(R x);
 template <> __device__ __forceinline__ float ksqrt<float>(float x) { return sqrtf(x); }
@@ -145,16 +148,34 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a, const float *_
         for (int f0 = 0; f0 < a.F; f0 += a.FG) {
             const int fg = min(a.FG, a.F - f0);
             __syncthreads();
-            for (int k = threadIdx.x; k < fg * TH * Q; k += blockDim.x) {
-                const int rr = k / Q;
-                const int qd = k - rr * Q;
-                const int ff = rr / TH;
-                const int r = rr - ff * TH;
-                const int gr = (row0 + r) & (a.n2 - 1);
-                const int gc = (col0 + 2 * qd) & (a.n1 - 1);
-                const float2 v = *reinterpret_cast<const float2 *>(
-                    grid + ((size_t)(f0 + ff) * a.n2 + gr) * a.n1 + gc);
-                *reinterpret_cast<float2 *>(tile + ff * tsz + r * TW + 2 * qd) = v;
+            // one warp per tile row, a lane per pair of cells (Q <= 32); each warp
+            // issues the loads of 4 rows before storing any, to keep them in flight
+            {
+                const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+                const int nrows = fg * TH;
+                const int gc = (col0 + 2 * lane) & (a.n1 - 1);
+                for (int r0 = threadIdx.x >> 5; r0 < nrows; r0 += 4 * nwarp) {
+                    float2 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int rr = r0 + u * nwarp;
+                        if (rr < nrows && lane < Q) {
+                            const int ff = rr / TH;
+                            const int gr = (row0 + rr - ff * TH) & (a.n2 - 1);
+                            v[u] = *reinterpret_cast<const float2 *>(
+                                grid + ((size_t)(f0 + ff) * a.n2 + gr) * a.n1 + gc);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int rr = r0 + u * nwarp;
+                        if (rr < nrows && lane < Q) {
+                            const int ff = rr / TH;
+                            *reinterpret_cast<float2 *>(tile + ff * tsz + (rr - ff * TH) * TW +
+                                                        2 * lane) = v[u];
+                        }
+                    }
+                }
             }
             __syncthreads();
             for (int pi = s + threadIdx.x; pi < e; pi += blockDim.x) {
@@ -207,7 +228,8 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
     a.F = p->n_fields;
     a.P = (int)p->n_points;
     a.beta = q.beta;
-    constexpr bool pair = sizeof(R) == 4 && W <= 8;   // FP32: paired loads
+    // FP32: paired loads, tile rows of at most 32 pairs
+    const bool pair = sizeof(R) == 4 && W <= 8 && (q.tile_x + ((W + 2) & ~1)) / 2 <= 32;
     const int tw = pair ? q.tile_x + ((W + 2) & ~1) : q.tile_x + W - 1;
     const size_t per_field = sizeof(R) * (size_t)(q.tile_y + W - 1) * tw;
     int fg = (int)((96 * 1024) / per_field);
@@ -216,7 +238,7 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
     a.FG = fg;
     const size_t smem = per_field * fg;
     int blocks = p->nbins < 152 * 16 ? p->nbins : 152 * 16;
-    if constexpr (pair) {
+    if (pair) {
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(k_interp_f32<W>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -128,19 +128,19 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     p.nbx = prm.n1 / prm.tile_x + 1;
     p.nby = prm.n2 / prm.tile_y + 1;
     p.nbins = p.nbx * p.nby;
-    p.n_row_blocks = (prm.n2 + DFS_ROW_BLOCK - 1) / DFS_ROW_BLOCK;
     p.n_points = n_points;
     p.cap_points = n_points;
     p.has_points = 1;
     const size_t cs = dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
     const size_t rs = cs / 2;                    // factor tables are in plan precision
     const size_t nf = (size_t)n_fields, P = (size_t)n_points;
-    size_t off[16], total = 0;
+    size_t off[20], total = 0;
     const size_t sizes[] = {rs * prm.N1, rs * prm.N2, cs * prm.n1,
                             cs * prm.n2, cs * nf * prm.n2 * prm.N1, rs * nf * prm.n2 * prm.n1,
                             sizeof(int) * p.nbins, sizeof(int) * (p.nbins + 1),
-                            sizeof(int) * p.nbins, sizeof(int), (size_t)p.n_row_blocks,
-                            sizeof(int) * P, sizeof(int2) * P, 2 * rs * P, sizeof(int) * P};
+                            sizeof(int) * p.nbins, sizeof(int), (size_t)0 /* unused */,
+                            sizeof(int) * P, sizeof(int2) * P, 2 * rs * P, sizeof(int) * P,
+                            sizeof(int2)};
     const int nbuf = (int)(sizeof(sizes) / sizeof(sizes[0]));
     for (int i = 0; i < nbuf; ++i) {
         off[i] = total;
@@ -171,11 +171,11 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     p.d_bin_start = (int *)(b + off[7]);
     p.d_task_bin = (int *)(b + off[8]);
     p.d_n_tasks = (int *)(b + off[9]);
-    p.d_rowmask = b + off[10];
     p.d_rank = (int *)(b + off[11]);
     p.d_base = (int2 *)(b + off[12]);
     p.d_frac = b + off[13];
     p.d_idx = (int *)(b + off[14]);
+    p.d_rowrange = (int2 *)(b + off[15]);
 
     // kernel tables: uploaded only when the configuration differs from the
     // one whose tables the scratch holds (their offsets depend only on it)

@@ -8,6 +8,7 @@
 #include <new>
 
 #include "common.cuh"
+#include "fft_core.cuh"
 
 #define DFS_VERSION "dfsnufft 0.1 (sm_103a)"
 
@@ -213,6 +214,7 @@ extern "C" const char *dfsnufft_strerror(int status) {
         case DFSNUFFT_ERR_OOM: return "out of device memory";
         case DFSNUFFT_ERR_CUDA: return "CUDA error";
         case DFSNUFFT_ERR_UNSUPPORTED: return "size outside the supported range";
+        case DFSNUFFT_ERR_TIMEOUT: return "a kernel timed out waiting on an asynchronous copy";
         default: return "unknown status";
     }
 }
@@ -222,9 +224,10 @@ extern "C" const char *dfsnufft_version(void) { return DFS_VERSION; }
 // ------------------------------------------------------------------ plan lifetime
 
 static void release(dfsnufft_plan p) {
-    void **bufs[] = {&p->d_inv1, &p->d_inv2, &p->d_tw1, &p->d_tw2,
+    void **bufs[] = {&p->d_inv1, &p->d_inv2, &p->d_tw1, &p->d_tw2, &p->d_stw_theta, &p->d_stw_phi,
                      &p->d_T, &p->d_G, (void **)&p->d_bin_count, (void **)&p->d_bin_start,
-                     (void **)&p->d_task_bin, (void **)&p->d_n_tasks, (void **)&p->d_rowmask,
+                     (void **)&p->d_task_bin, (void **)&p->d_n_tasks,
+                     (void **)&p->d_status, (void **)&p->d_rowrange,
                      (void **)&p->d_rank, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
                      (void **)&p->d_pts_stage, &p->d_coef_stage, &p->d_val_stage};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) dfs_free(bufs[i]);
@@ -243,6 +246,56 @@ static void fill_twiddles(C *h, int n) {
         h[k].x = (R)cos(a);
         h[k].y = (R)sin(a);
     }
+}
+
+// Stage-ordered twiddles of a length-2^logn transform with e elements per
+// thread (layout of dfs_fft::line_fft_ct): per stage after the first, entry
+// (r - 1) Ns + jm = e^{+2 pi i r jm / (Ns R)}.
+template <typename C, typename R>
+static void fill_stage_twiddles(C *h, int logn, int e) {
+    const int le = e == 16 ? 4 : e == 8 ? 3 : 2;
+    int l = 0, off = 0;
+    while (l < logn) {
+        const int lr = logn - l < le ? logn - l : le;
+        if (l > 0) {
+            const int ns = 1 << l, radix = 1 << lr;
+            for (int r = 1; r < radix; ++r)
+                for (int jm = 0; jm < ns; ++jm) {
+                    const double a = 2.0 * kPi * (double)(r * jm) / (double)(ns * radix);
+                    h[off + (r - 1) * ns + jm].x = (R)cos(a);
+                    h[off + (r - 1) * ns + jm].y = (R)sin(a);
+                }
+            off += (radix - 1) << l;
+        }
+        l += lr;
+    }
+}
+
+static int stage_table_len(int n) {
+    int logn = 0;
+    while ((1 << logn) < n) ++logn;
+    const int sz = dfs_fft::stage_table_size(logn, DFS_FFT_E);
+    return sz > 0 ? sz : 1;
+}
+
+static int upload_stage_tables(dfsnufft_plan p) {
+    const dfsnufft_params &q = p->prm;
+    const size_t cs = q.dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
+    const int lens[2] = {q.n2 / 2, q.n1 / 2};
+    void *dst[2] = {p->d_stw_theta, p->d_stw_phi};
+    for (int k = 0; k < 2; ++k) {
+        int logn = 0;
+        while ((1 << logn) < lens[k]) ++logn;
+        const int sz = stage_table_len(lens[k]);
+        void *h = calloc((size_t)sz, cs);
+        if (!h) return DFSNUFFT_ERR_OOM;
+        if (q.dtype == DFSNUFFT_F64) fill_stage_twiddles<double2, double>((double2 *)h, logn, DFS_FFT_E);
+        else fill_stage_twiddles<float2, float>((float2 *)h, logn, DFS_FFT_E);
+        cudaError_t e = cudaMemcpy(dst[k], h, cs * sz, cudaMemcpyHostToDevice);
+        free(h);
+        if (e) return fail_cuda(p, "upload stage twiddles", e);
+    }
+    return DFSNUFFT_OK;
 }
 
 static int upload_tables(dfsnufft_plan p) {
@@ -315,7 +368,6 @@ extern "C" int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype,
     p->nbx = prm.n1 / prm.tile_x + 1;
     p->nby = prm.n2 / prm.tile_y + 1;
     p->nbins = p->nbx * p->nby;
-    p->n_row_blocks = (prm.n2 + DFS_ROW_BLOCK - 1) / DFS_ROW_BLOCK;
 
     size_t cs = dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
     size_t nf = (size_t)n_fields;
@@ -324,13 +376,16 @@ extern "C" int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype,
         {&p->d_inv2, cs / 2 * prm.N2, "deconvolution factors"},
         {&p->d_tw1, cs * prm.n1, "twiddles"},
         {&p->d_tw2, cs * prm.n2, "twiddles"},
+        {&p->d_stw_theta, cs * stage_table_len(prm.n2 / 2), "stage twiddles"},
+        {&p->d_stw_phi, cs * stage_table_len(prm.n1 / 2), "stage twiddles"},
         {&p->d_T, cs * nf * prm.n2 * prm.N1, "theta-pass buffer"},
         {&p->d_G, cs / 2 * nf * prm.n2 * prm.n1, "fine grid (real part)"},
         {(void **)&p->d_bin_count, sizeof(int) * p->nbins, "bin counts"},
         {(void **)&p->d_bin_start, sizeof(int) * (p->nbins + 1), "bin starts"},
         {(void **)&p->d_task_bin, sizeof(int) * p->nbins, "bin list"},
         {(void **)&p->d_n_tasks, sizeof(int), "bin list size"},
-        {(void **)&p->d_rowmask, (size_t)p->n_row_blocks, "row mask"},
+        {(void **)&p->d_status, sizeof(int), "status word"},
+        {(void **)&p->d_rowrange, sizeof(int2), "row range"},
     };
     for (size_t i = 0; i < sizeof(allocs) / sizeof(allocs[0]); ++i) {
         rc = dfs_alloc(p, allocs[i].ptr, allocs[i].bytes, allocs[i].what);
@@ -341,6 +396,14 @@ extern "C" int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype,
         }
     }
     rc = upload_tables(p);
+    if (rc == DFSNUFFT_OK) rc = upload_stage_tables(p);
+    if (rc == DFSNUFFT_OK) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (!e) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (!e) e = cudaMemset(p->d_status, 0, sizeof(int));
+        if (e) rc = fail_cuda(p, "device query", e);
+    }
     if (rc != DFSNUFFT_OK) {
         release(p);
         delete p;
@@ -359,6 +422,19 @@ extern "C" int dfsnufft_destroy(dfsnufft_plan p) {
 }
 
 extern "C" const char *dfsnufft_plan_last_error(dfsnufft_plan p) { return p ? p->msg : ""; }
+
+extern "C" int dfsnufft_plan_check(dfsnufft_plan p) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    DFS_CK(p, cudaStreamSynchronize(p->stream));
+    int st = 0;
+    DFS_CK(p, cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        p->status = DFSNUFFT_ERR_TIMEOUT;
+        snprintf(p->msg, sizeof(p->msg), "a kernel gave up waiting on an asynchronous copy");
+    }
+    return p->status;
+}
 
 extern "C" int dfsnufft_plan_get_params(dfsnufft_plan p, dfsnufft_params *out) {
     if (!p || !out) return DFSNUFFT_ERR_INVALID_ARG;
@@ -482,8 +558,7 @@ extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *
     rc = dfsnufft_execute(p, p->d_coef_stage, p->d_val_stage);
     if (rc) return rc;
     DFS_CK(p, cudaMemcpyAsync(values, p->d_val_stage, vb, cudaMemcpyDeviceToHost, p->stream));
-    DFS_CK(p, cudaStreamSynchronize(p->stream));
-    return DFSNUFFT_OK;
+    return dfsnufft_plan_check(p);
 }
 
 // ------------------------------------------------------------------ measurement aids
@@ -524,16 +599,13 @@ extern "C" int dfsnufft_plan_point_stats(dfsnufft_plan p, int64_t *rows_needed,
     if (p->status) return p->status;
     if (!p->has_points) return DFSNUFFT_ERR_NO_POINTS;
     DFS_CK(p, cudaStreamSynchronize(p->stream));
-    unsigned char *mask = (unsigned char *)malloc(p->n_row_blocks);
-    if (!mask) return DFSNUFFT_ERR_OOM;
+    int2 range = make_int2(0, 0);
     int ntask = 0;
-    cudaError_t e1 = cudaMemcpy(mask, p->d_rowmask, p->n_row_blocks, cudaMemcpyDeviceToHost);
+    cudaError_t e1 = cudaMemcpy(&range, p->d_rowrange, sizeof(int2), cudaMemcpyDeviceToHost);
     cudaError_t e2 = cudaMemcpy(&ntask, p->d_n_tasks, sizeof(int), cudaMemcpyDeviceToHost);
-    int64_t blocks = 0;
-    for (int i = 0; i < p->n_row_blocks; ++i) blocks += mask[i] != 0;
-    free(mask);
-    if (e1) return fail_cuda(p, "read row mask", e1);
+    if (e1) return fail_cuda(p, "read row range", e1);
     if (e2) return fail_cuda(p, "read bin count", e2);
+    const int64_t blocks = range.y / DFS_ROW_BLOCK;
     *rows_needed = blocks * DFS_ROW_BLOCK;
     *nonempty_bins = ntask;
     return DFSNUFFT_OK;

@@ -1,6 +1,6 @@
 // set_points: fold the departure points onto the fine-grid torus, sort them by
-// interpolation bin with a counting sort, and mark the fine rows their stencils
-// touch.
+// interpolation bin with a counting sort, and find the range of fine rows their
+// stencils touch.
 //
 // The doubled torus is 2 pi periodic in both angles (Sec. 4-5), so a coordinate
 // only matters as a fraction of a turn.  That fraction is computed exactly in
@@ -102,13 +102,12 @@ __device__ __forceinline__ int bin_of(const FoldParams &f, int bx, int by) {
 __global__ void __launch_bounds__(256) k_fold_count(int n, const double *__restrict__ lon,
                                                     const double *__restrict__ colat,
                                                     FoldParams f, int *__restrict__ bin_count,
-                                                    int *__restrict__ rank,
-                                                    unsigned char *__restrict__ rowmask) {
+                                                    int *__restrict__ rank) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = p < n;
-    int bin = -1, by = 0;
+    int bin = -1;
     if (live) {
-        int bx;
+        int bx, by;
         long long tx, ty;
         fold_point(f, lon[p], colat[p], bx, by, tx, ty);
         bin = bin_of(f, bx, by);
@@ -123,21 +122,53 @@ __global__ void __launch_bounds__(256) k_fold_count(int n, const double *__restr
     if (lane == leader) base = atomicAdd(&bin_count[bin], __popc(peers));
     base = __shfl_sync(peers, base, leader);
     rank[p] = base + __popc(peers & ((1u << lane) - 1u));
-    // fine rows j0 .. j0 + w - 1 (mod n2) span at most two row blocks (w <= 16)
-    const int j0 = by - f.c0;
-    const int nmask = (1 << f.L2) - 1;
-    rowmask[(j0 & nmask) / DFS_ROW_BLOCK] = 1;
-    rowmask[((j0 + f.w - 1) & nmask) / DFS_ROW_BLOCK] = 1;
 }
 
+// Smallest index i in [from, from + nb) (circular over nb bits) whose bit in
+// `bits` equals `value`; from + nb if there is none.
+__device__ int next_bit(const unsigned *bits, int nb, int from, int value) {
+    int i = from;
+    const int end = from + nb;
+    while (i < end) {
+        const int k = i < nb ? i : i - nb;
+        unsigned w = bits[k >> 5];
+        if (!value) w = ~w;
+        w >>= (k & 31);
+        // bits past nb in the last word do not count
+        const int avail = min(32 - (k & 31), nb - k);
+        if (avail < 32) w &= (1u << avail) - 1u;
+        if (w) {
+            const int hit = i + __ffs(w) - 1;
+            return hit < end ? hit : end;
+        }
+        i += avail;
+    }
+    return end;
+}
+
+struct ScanParams {
+    int nbins, nbx, nbr;      // bins, bins per bin row, bin rows in use (n2 / tile_y)
+    int tile_y, c0, w, n2;
+};
+
 // One CTA: exclusive scan of the bin counts and the list of non-empty bins, in
-// chunks of 4 * blockDim bins (each thread four consecutive bins).
-__global__ void __launch_bounds__(1024) k_scan_bins(int nbins, const int *__restrict__ count,
+// chunks of 4 * blockDim bins (each thread four consecutive bins).  Then the
+// circular range of fine rows the stencils touch: the points of bin row by use
+// rows by*tile_y - c0 .. (by+1)*tile_y - c0 + w - 2, so the range is the
+// complement of the longest circular run of empty bin rows, widened by the
+// stencil and rounded out to whole row blocks.
+__global__ void __launch_bounds__(1024) k_scan_bins(ScanParams sp, const int *__restrict__ count,
                                                     int *__restrict__ start,
                                                     int *__restrict__ task_bin,
-                                                    int *__restrict__ n_tasks) {
+                                                    int *__restrict__ n_tasks,
+                                                    int2 *__restrict__ rowrange) {
     __shared__ int s_sum[32], s_ne[32];
+    __shared__ unsigned char s_row[DFS_MAX_ROW_BLOCKS + 1];
+    __shared__ unsigned s_bits[(DFS_MAX_ROW_BLOCKS + 31) / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int nbins = sp.nbins;
+    for (int i = tid; i <= sp.nbr; i += blockDim.x) s_row[i] = 0;
+    __syncthreads();
     int carry = 0, carry_n = 0;
     for (int base = 0; base < nbins; base += 4 * blockDim.x) {
         const int i0 = base + 4 * tid;
@@ -193,7 +224,10 @@ __global__ void __launch_bounds__(1024) k_scan_bins(int nbins, const int *__rest
         for (int k = 0; k < 4; ++k) {
             if (i0 + k < nbins) {
                 start[i0 + k] = off_s;
-                if (c[k] > 0) task_bin[off_n++] = i0 + k;
+                if (c[k] > 0) {
+                    task_bin[off_n++] = i0 + k;
+                    s_row[(i0 + k) / sp.nbx] = 1;
+                }
             }
             off_s += c[k];
         }
@@ -201,9 +235,44 @@ __global__ void __launch_bounds__(1024) k_scan_bins(int nbins, const int *__rest
         carry_n += s_ne[nw - 1];
         __syncthreads();
     }
+    // bin-row flags -> bits
+    for (int k = wid; k * 32 < sp.nbr; k += nw) {
+        const int i = k * 32 + lane;
+        const unsigned b = __ballot_sync(0xffffffffu, i < sp.nbr && s_row[i]);
+        if (lane == 0) s_bits[k] = b;
+    }
+    __syncthreads();
     if (tid == 0) {
         start[nbins] = carry;
         *n_tasks = carry_n;
+        const int nb = sp.nbr;
+        const int s0 = next_bit(s_bits, nb, 0, 1);
+        int2 range = make_int2(0, 0);
+        if (s0 < nb) {
+            int best = 0, best_at = 0;
+            int pos = s0;
+            while (pos < s0 + nb) {
+                const int z0 = next_bit(s_bits, nb, pos >= nb ? pos - nb : pos, 0) +
+                               (pos >= nb ? nb : 0);
+                if (z0 >= s0 + nb) break;
+                const int z1 = next_bit(s_bits, nb, z0 >= nb ? z0 - nb : z0, 1) +
+                               (z0 >= nb ? nb : 0);
+                const int end = z1 < s0 + nb ? z1 : s0 + nb;
+                if (end - z0 > best) {
+                    best = end - z0;
+                    best_at = z0;
+                }
+                pos = end;
+            }
+            // needed rows: after the gap, through the last non-empty bin row's stencil
+            int first = ((best_at + best) % nb) * sp.tile_y - sp.c0;
+            int cnt = (nb - best) * sp.tile_y + sp.w - 1;
+            first &= sp.n2 - 1;
+            const int fb = first & ~(DFS_ROW_BLOCK - 1);
+            cnt = ((cnt + (first - fb) + DFS_ROW_BLOCK - 1) / DFS_ROW_BLOCK) * DFS_ROW_BLOCK;
+            range = make_int2(fb, cnt < sp.n2 ? cnt : sp.n2);
+        }
+        *rowrange = range;
     }
 }
 
@@ -250,13 +319,19 @@ cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const doub
     const int n = (int)p->n_points;
     cudaError_t e;
     if ((e = cudaMemsetAsync(p->d_bin_count, 0, sizeof(int) * p->nbins, p->stream))) return e;
-    if ((e = cudaMemsetAsync(p->d_rowmask, 0, p->n_row_blocks, p->stream))) return e;
     const int tpb = 256;
     const int blocks = (n + tpb - 1) / tpb;
-    k_fold_count<<<blocks, tpb, 0, p->stream>>>(n, lon, colat, f, p->d_bin_count, p->d_rank,
-                                               p->d_rowmask);
-    k_scan_bins<<<1, 1024, 0, p->stream>>>(p->nbins, p->d_bin_count, p->d_bin_start,
-                                          p->d_task_bin, p->d_n_tasks);
+    k_fold_count<<<blocks, tpb, 0, p->stream>>>(n, lon, colat, f, p->d_bin_count, p->d_rank);
+    ScanParams sp;
+    sp.nbins = p->nbins;
+    sp.nbx = p->nbx;
+    sp.nbr = q.n2 / q.tile_y;
+    sp.tile_y = q.tile_y;
+    sp.c0 = p->c0;
+    sp.w = q.w;
+    sp.n2 = q.n2;
+    k_scan_bins<<<1, 1024, 0, p->stream>>>(sp, p->d_bin_count, p->d_bin_start, p->d_task_bin,
+                                          p->d_n_tasks, p->d_rowrange);
     if (q.dtype == DFSNUFFT_F64)
         k_scatter<double><<<blocks, tpb, 0, p->stream>>>(n, lon, colat, f, p->d_bin_start,
                                                         p->d_rank, p->d_base,

@@ -25,6 +25,7 @@ ERR_NO_POINTS = 3
 ERR_OOM = 4
 ERR_CUDA = 5
 ERR_UNSUPPORTED = 6
+ERR_TIMEOUT = 7
 
 # Every symbol include/dfsnufft.h declares.
 EXPORTS = (
@@ -33,7 +34,7 @@ EXPORTS = (
     "dfsnufft_strerror", "dfsnufft_plan_last_error", "dfsnufft_plan_get_params",
     "dfsnufft_choose_params", "dfsnufft_es_kernel", "dfsnufft_kernel_ft", "dfsnufft_version",
     "dfsnufft_plan_enable_timing", "dfsnufft_plan_read_timing", "dfsnufft_plan_point_stats",
-    "dfsnufft_probe_fma_rate", "dfsnufft_execute_noalloc",
+    "dfsnufft_probe_fma_rate", "dfsnufft_execute_noalloc", "dfsnufft_plan_check",
 )
 N_STAGES = 4
 STAGES = ("set_points", "theta_pass", "phi_pass", "interp")
@@ -86,6 +87,7 @@ def lib():
         L.dfsnufft_plan_last_error.argtypes = [vp]
         L.dfsnufft_plan_last_error.restype = ctypes.c_char_p
         L.dfsnufft_plan_get_params.argtypes = [vp, ctypes.POINTER(Params)]
+        L.dfsnufft_plan_check.argtypes = [vp]
         L.dfsnufft_choose_params.argtypes = [i32, i32, f64, i32, ctypes.POINTER(Params)]
         L.dfsnufft_es_kernel.argtypes = [f64, i32, f64]
         L.dfsnufft_es_kernel.restype = f64
@@ -182,6 +184,11 @@ def dfsnufft_execute_host(h, coeffs_ptr, values_ptr):
 
 def dfsnufft_destroy(h):
     _check(lib().dfsnufft_destroy(h))
+
+
+def dfsnufft_plan_check(h):
+    """Synchronise and raise DfsError if the plan (or a kernel of it) failed."""
+    _check(lib().dfsnufft_plan_check(h), h)
 
 
 def dfsnufft_plan_enable_timing(h, enable=True):
@@ -306,6 +313,10 @@ class Plan:
             out = np.empty((self.n_fields, self.n_points), dtype=rd)
         dfsnufft_execute_host(self._h, c.ctypes.data, out.ctypes.data)
         return out
+
+    def check(self):
+        """Synchronise the plan's stream; raise DfsError on a recorded failure."""
+        dfsnufft_plan_check(self._h)
 
     def destroy(self):
         if getattr(self, "_h", None) is not None and self._h.value:

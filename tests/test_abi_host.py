@@ -44,11 +44,11 @@ def test_version(lib):
 
 def test_strerror_covers_every_code(lib):
     seen = set()
-    for code in range(0, 7):
+    for code in range(0, 8):
         s = lib.dfsnufft_strerror(code).decode()
         assert s and s != "unknown status"
         seen.add(s)
-    assert len(seen) == 7
+    assert len(seen) == 8
     assert lib.dfsnufft_strerror(99).decode() == "unknown status"
 
 
