@@ -152,8 +152,11 @@ def stage_bytes(prm, n_fields, n_points, rows):
 
 
 def interp_flops(prm, n_fields, n_points):
+    """Algorithmic flops of one interpolation launch: per point, the w x w real
+    tap sum and the w-row combination for every field (2 w (w + 1) each) plus
+    the 2 w kernel weights by degree-w Horner polynomials (4 w^2)."""
     w = prm["w"]
-    return n_fields * n_points * 4 * w * (w + 1)
+    return n_fields * n_points * 2 * w * (w + 1) + n_points * 4 * w * w
 
 
 def profile_traffic(kernel, workload):

@@ -199,6 +199,16 @@ double dfsnufft_es_kernel(double z, int w, double beta);
  * by Gauss-Legendre quadrature in FP64.  Deconvolution divides by these. */
 int dfsnufft_kernel_ft(int w, double beta, int n_fine, int n_modes, double *out);
 
+/* Piecewise-polynomial form of the kernel used by the interpolation kernels:
+ * for tap a (0 <= a < w) the weight phi((a - c0) - t) as a polynomial of degree
+ * w in s = t - mid, where t is the point's offset from its base cell
+ * (t in [-1/2, 1/2), mid = 0, for odd w; t in [0, 1), mid = 1/2, for even w)
+ * and c0 = (w - 1)/2 or w/2 - 1.  out[a * (w + 1) + k] is the coefficient of
+ * s^k, from Chebyshev interpolation at w + 1 nodes (FP64).  The fit is
+ * accurate to about e^-beta, the size of the kernel's own jump at the edge of
+ * its support. */
+int dfsnufft_es_horner(int w, double beta, double *out);
+
 /* Library version string. */
 const char *dfsnufft_version(void);
 

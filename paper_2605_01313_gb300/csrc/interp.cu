@@ -5,7 +5,8 @@
 //
 // with phi the exponential-of-semicircle kernel
 // phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)) and z_a = (a - c0) - t the
-// offsets produced by set_points.
+// offsets produced by set_points; the weights come from a per-tap polynomial
+// fit of phi in t (see Horner below).
 //
 // The weights are real, so only the real part of the fine grid is read (the
 // phi pass stores nothing else).  Points arrive sorted by bin (tile_x x tile_y
@@ -23,35 +24,34 @@ struct InterpArgs {
     int c0;
     int F, FG;            // fields, fields staged per pass
     int P;
-    double beta;
 };
 
-// FP32: the hardware exponential (exp2 of x log2 e); for arguments in
-// [-beta, 0] its relative error stays near 1e-7, far below the FP32 form's
-// tolerance.  FP64 keeps the correctly rounded library exp.
-template <typename R> __device__ __forceinline__ R kexp(R x);
-template <> __device__ __forceinline__ float kexp<float>(float x) { return __expf(x); }
-template <> __device__ __forceinline__ double kexp<double>(double x) { return exp(x); }
-template <typename R> __device__ __forceinline__ R ksqrt(R x);
-template <> __device__ __forceinline__ float ksqrt<float>(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double ksqrt<double>(double x) { return sqrt(x); }
-
-// Kernel values at the W taps of one dimension: z_a = (a - c0) - t.
+// Kernel weights by Horner's rule: for tap a the weight phi((a - c0) - t) is a
+// degree-W polynomial in s = t - mid (mid = 0 for odd W, 1/2 for even W),
+// fitted on the host (dfsnufft_es_horner) to about e^-beta, the size of the
+// kernel's own jump at the edge of its support.  The coefficients ride in the
+// kernel's parameter block, so every Horner step is one FMA with a constant
+// operand; a NaN offset gives NaN weights.
 template <typename R, int W>
-__device__ __forceinline__ void es_weights(R t, int c0, R beta, R *wv) {
-    const R two_over_w = (R)2 / (R)W;
+struct Horner {
+    R c[W][W + 1];
+};
+
+template <typename R, int W>
+__device__ __forceinline__ void es_weights(R t, const Horner<R, W> &h, R *wv) {
+    const R s = t - (W % 2 == 0 ? (R)0.5 : (R)0);
 #pragma unroll
     for (int a = 0; a < W; ++a) {
-        const R z = (R)(a - c0) - t;
-        const R u = z * two_over_w;
-        const R s = ((R)1 - u) * ((R)1 + u);
-        // written so that a NaN offset propagates to the value
-        wv[a] = s <= (R)0 ? (R)0 : kexp<R>(beta * (ksqrt<R>(s) - (R)1));
+        R acc = h.c[a][W];
+#pragma unroll
+        for (int k = W - 1; k >= 0; --k) acc = fma(acc, s, h.c[a][k]);
+        wv[a] = acc;
     }
 }
 
 template <typename R, int W>
-__global__ void __launch_bounds__(256) k_interp(InterpArgs a, const R *__restrict__ grid,
+__global__ void __launch_bounds__(256) k_interp(InterpArgs a, const __grid_constant__ Horner<R, W> hw,
+                                                const R *__restrict__ grid,
                                                 const int2 *__restrict__ base,
                                                 const R *__restrict__ frac,
                                                 const int *__restrict__ idx,
@@ -65,7 +65,6 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const R *__restric
     const int TW = a.tile_x + W - 1;
     const int tsz = TH * TW;
     const int ntask = *n_tasks;
-    const R beta = (R)a.beta;
     for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
         const int bin = task_bin[task];
         const int by = bin / a.nbx;
@@ -91,8 +90,8 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const R *__restric
             for (int pi = s + threadIdx.x; pi < e; pi += blockDim.x) {
                 const int2 b = base[pi];
                 R wx[W], wy[W];
-                es_weights<R, W>(frac[2 * pi], a.c0, beta, wx);
-                es_weights<R, W>(frac[2 * pi + 1], a.c0, beta, wy);
+                es_weights<R, W>(frac[2 * pi], hw, wx);
+                es_weights<R, W>(frac[2 * pi + 1], hw, wy);
                 const int ox = b.x - col0;
                 const int oy = b.y - row0;
                 const int dst = idx[pi];
@@ -120,7 +119,9 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const R *__restric
 // The point's parity within its pair shifts its w weights into a zero-padded
 // vector of WP weights.
 template <int W>
-__global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a, const float *__restrict__ grid,
+__global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a,
+                                                    const __grid_constant__ Horner<float, W> hw,
+                                                    const float *__restrict__ grid,
                                                     const int2 *__restrict__ base,
                                                     const float *__restrict__ frac,
                                                     const int *__restrict__ idx,
@@ -136,7 +137,6 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a, const float *_
     const int Q = TW / 2;                     // pairs per tile row
     const int tsz = TH * TW;
     const int ntask = *n_tasks;
-    const float beta = (float)a.beta;
     for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
         const int bin = task_bin[task];
         const int by = bin / a.nbx;
@@ -181,8 +181,8 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a, const float *_
             for (int pi = s + threadIdx.x; pi < e; pi += blockDim.x) {
                 const int2 b = base[pi];
                 float wx[W], wy[W], w8[WP];
-                es_weights<float, W>(frac[2 * pi], a.c0, beta, wx);
-                es_weights<float, W>(frac[2 * pi + 1], a.c0, beta, wy);
+                es_weights<float, W>(frac[2 * pi], hw, wx);
+                es_weights<float, W>(frac[2 * pi + 1], hw, wy);
                 const int ox = b.x - col0;
                 const int odd = ox & 1;
 #pragma unroll
@@ -227,7 +227,13 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
     a.c0 = p->c0;
     a.F = p->n_fields;
     a.P = (int)p->n_points;
-    a.beta = q.beta;
+    Horner<R, W> hw;
+    {
+        double hc[W * (W + 1)];
+        dfsnufft_es_horner(W, q.beta, hc);
+        for (int i = 0; i < W; ++i)
+            for (int k = 0; k <= W; ++k) hw.c[i][k] = (R)hc[i * (W + 1) + k];
+    }
     // FP32: paired loads, tile rows of at most 32 pairs
     const bool pair = sizeof(R) == 4 && W <= 8 && (q.tile_x + ((W + 2) & ~1)) / 2 <= 32;
     const int tw = pair ? q.tile_x + ((W + 2) & ~1) : q.tile_x + W - 1;
@@ -245,8 +251,11 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
                                                  (int)smem);
             if (e) return e;
         }
+        Horner<float, W> hf;
+        for (int i = 0; i < W; ++i)
+            for (int k = 0; k <= W; ++k) hf.c[i][k] = (float)hw.c[i][k];
         k_interp_f32<W><<<blocks, 128, smem, p->stream>>>(
-            a, (const float *)p->d_G, p->d_base, (const float *)p->d_frac, p->d_idx,
+            a, hf, (const float *)p->d_G, p->d_base, (const float *)p->d_frac, p->d_idx,
             p->d_bin_start, p->d_task_bin, p->d_n_tasks, (float *)values);
     } else {
         if (smem > 48 * 1024) {
@@ -257,7 +266,7 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
         }
         const int threads = sizeof(R) == 4 ? 128 : 256;
         k_interp<R, W><<<blocks, threads, smem, p->stream>>>(
-            a, (const R *)p->d_G, p->d_base, (const R *)p->d_frac, p->d_idx, p->d_bin_start,
+            a, hw, (const R *)p->d_G, p->d_base, (const R *)p->d_frac, p->d_idx, p->d_bin_start,
             p->d_task_bin, p->d_n_tasks, (R *)values);
     }
     return cudaGetLastError();

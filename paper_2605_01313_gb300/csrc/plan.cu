@@ -172,6 +172,48 @@ extern "C" int dfsnufft_kernel_ft(int w, double beta, int n_fine, int n_modes, d
     return DFSNUFFT_OK;
 }
 
+extern "C" int dfsnufft_es_horner(int w, double beta, double *out) {
+    if (w < 2 || w > 16 || !(beta > 0) || !out) return DFSNUFFT_ERR_INVALID_ARG;
+    const int D = w;                                   // degree
+    const int c0 = (w % 2 == 0) ? w / 2 - 1 : (w - 1) / 2;
+    const double mid = (w % 2 == 0) ? 0.5 : 0.0;
+    double f[17], cheb[17], mono[17], tk[17], tk1[17], tk2[17];
+    for (int a = 0; a < w; ++a) {
+        // Chebyshev interpolation in x = 2 s on [-1, 1]
+        for (int j = 0; j <= D; ++j) {
+            const double x = cos(kPi * (j + 0.5) / (D + 1));
+            f[j] = dfsnufft_es_kernel((double)(a - c0) - (mid + 0.5 * x), w, beta);
+        }
+        for (int k = 0; k <= D; ++k) {
+            double acc = 0.0;
+            for (int j = 0; j <= D; ++j) acc += f[j] * cos(kPi * k * (j + 0.5) / (D + 1));
+            cheb[k] = acc * 2.0 / (D + 1);
+        }
+        cheb[0] *= 0.5;
+        // monomials in x via T_{k+1} = 2 x T_k - T_{k-1}
+        for (int k = 0; k <= D; ++k) mono[k] = tk[k] = tk1[k] = tk2[k] = 0.0;
+        tk2[0] = 1.0;                                  // T_0
+        tk1[1] = 1.0;                                  // T_1
+        mono[0] += cheb[0];
+        if (D >= 1) mono[1] += cheb[1];
+        for (int k = 2; k <= D; ++k) {
+            for (int i = 0; i <= D; ++i) tk[i] = (i > 0 ? 2.0 * tk1[i - 1] : 0.0) - tk2[i];
+            for (int i = 0; i <= D; ++i) {
+                mono[i] += cheb[k] * tk[i];
+                tk2[i] = tk1[i];
+                tk1[i] = tk[i];
+            }
+        }
+        // x = 2 s: coefficient of s^k is 2^k times that of x^k
+        double sc = 1.0;
+        for (int k = 0; k <= D; ++k) {
+            out[a * (D + 1) + k] = mono[k] * sc;
+            sc *= 2.0;
+        }
+    }
+    return DFSNUFFT_OK;
+}
+
 extern "C" int dfsnufft_choose_params(int n_lon, int n_lat, double tol, int dtype,
                                       dfsnufft_params *out) {
     if (!out) return DFSNUFFT_ERR_INVALID_ARG;

@@ -35,6 +35,7 @@ EXPORTS = (
     "dfsnufft_choose_params", "dfsnufft_es_kernel", "dfsnufft_kernel_ft", "dfsnufft_version",
     "dfsnufft_plan_enable_timing", "dfsnufft_plan_read_timing", "dfsnufft_plan_point_stats",
     "dfsnufft_probe_fma_rate", "dfsnufft_execute_noalloc", "dfsnufft_plan_check",
+    "dfsnufft_es_horner",
 )
 N_STAGES = 4
 STAGES = ("set_points", "theta_pass", "phi_pass", "interp")
@@ -92,6 +93,7 @@ def lib():
         L.dfsnufft_es_kernel.argtypes = [f64, i32, f64]
         L.dfsnufft_es_kernel.restype = f64
         L.dfsnufft_kernel_ft.argtypes = [i32, f64, i32, i32, vp]
+        L.dfsnufft_es_horner.argtypes = [i32, f64, vp]
         L.dfsnufft_version.restype = ctypes.c_char_p
         L.dfsnufft_plan_enable_timing.argtypes = [vp, i32]
         L.dfsnufft_plan_read_timing.argtypes = [vp, vp, vp]
@@ -147,6 +149,13 @@ def dfsnufft_kernel_ft(w, beta, n_fine, n_modes) -> np.ndarray:
     _check(lib().dfsnufft_kernel_ft(int(w), float(beta), int(n_fine), int(n_modes),
                                     out.ctypes.data))
     return out
+
+
+def dfsnufft_es_horner(w, beta) -> np.ndarray:
+    """(w, w + 1) polynomial coefficients of the kernel taps in s = t - mid."""
+    out = np.empty(int(w) * (int(w) + 1), dtype=np.float64)
+    _check(lib().dfsnufft_es_horner(int(w), float(beta), out.ctypes.data))
+    return out.reshape(int(w), int(w) + 1)
 
 
 def dfsnufft_version() -> str:

@@ -119,3 +119,24 @@ def test_kernel_ft_against_adaptive_quadrature(lib, w):
 def test_kernel_ft_bad_args(lib):
     with pytest.raises(nufft.DfsError):
         nufft.dfsnufft_kernel_ft(1, 2.3, 64, 32)
+
+
+@pytest.mark.parametrize("w", [4, 6, 7, 8, 10, 13, 15])
+def test_horner_kernel_fit(lib, w):
+    """The per-tap polynomials the interpolation kernels evaluate match the kernel
+    itself to within a few e^-beta (the kernel's own jump at its support edge)."""
+    beta = 2.30 * w
+    P = nufft.dfsnufft_es_horner(w, beta)
+    assert P.shape == (w, w + 1)
+    odd = w % 2
+    c0 = (w - 1) // 2 if odd else w // 2 - 1
+    mid = 0.0 if odd else 0.5
+    ts = np.linspace(mid - 0.5, mid + 0.5 - 1e-12, 1001)
+    worst = 0.0
+    for a in range(w):
+        acc = np.zeros_like(ts)
+        for k in range(w, -1, -1):
+            acc = acc * (ts - mid) + P[a, k]
+        exact = np.array([nufft.dfsnufft_es_kernel((a - c0) - t, w, beta) for t in ts])
+        worst = max(worst, float(np.max(np.abs(acc - exact))))
+    assert worst < max(8 * math.exp(-beta), 2e-14), worst
