@@ -91,16 +91,65 @@ typedef struct {
 int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype, int n_fields,
                          void *stream, dfsnufft_plan *out);
 
-/* Give the plan its departure points (device pointers, float64 radians,
- * n_points each, 1 <= n_points < 2^31).  Folds them onto the fine-grid torus
- * in FP64, sorts them by interpolation bin (counting sort) and marks the fine
- * rows they touch.  Replaces any previous points. */
+/* Give a one-member plan its departure points (device pointers, float64
+ * radians, n_points each, 1 <= n_points < 2^31).  Folds them onto the
+ * fine-grid torus (exact integer reduction of the angles), sorts them by
+ * interpolation bin (counting sort) and finds the fine rows their stencils
+ * touch.  Replaces any previous points. */
 int dfsnufft_set_points(dfsnufft_plan plan, int64_t n_points, const double *lon,
                         const double *colat);
 
+/* Batched plans: n_members members on the same n_lat x n_lon grid, each with
+ * its own departure points and n_fields fields (an ensemble, or several
+ * requests of one size).  Arguments as dfsnufft_plan_create; 1 <= n_members
+ * <= 4096 and n_members x n_fields <= 65535.  A plan from dfsnufft_plan_create is a batched plan of one member.
+ * Member data are concatenated in member order:
+ *   coeffs : n_members x n_fields x N2 x N1 complex,
+ *   points : all members' longitudes (then colatitudes) back to back,
+ *   values : for member k, n_fields x n_points[k] reals, members back to back. */
+int dfsnufft_plan_create_batch(int n_members, int n_lon, int n_lat, double tol, int dtype,
+                               int n_fields, void *stream, dfsnufft_plan *out);
+
+/* Points of every member of a batched plan: n_points is a host array of
+ * n_members counts (each >= 1, total < 2^31); lon and colat are device arrays
+ * of the total length, member k's points at offset sum_{j<k} n_points[j].
+ * The offsets are uploaded (a small host-to-device copy on the plan's stream)
+ * only when the counts differ from the previous call's. */
+int dfsnufft_set_points_batch(dfsnufft_plan plan, const int64_t *n_points, const double *lon,
+                              const double *colat);
+
+/* Ensembles on uneven grids: n_groups batched plans (group g: n_members[g]
+ * members on an n_lat[g] x n_lon[g] grid, all with n_fields fields, one
+ * tolerance and precision), each on a stream of its own. */
+typedef struct dfsnufft_ensemble_s *dfsnufft_ensemble;
+int dfsnufft_ensemble_create(int n_groups, const int *n_members, const int *n_lon,
+                             const int *n_lat, double tol, int dtype, int n_fields, void *stream,
+                             dfsnufft_ensemble *out);
+
+/* One step for every member of every group: per group g, n_points[g] (host
+ * array of the group's member counts), lon[g], colat[g], coeffs[g], values[g]
+ * (device pointers laid out as for dfsnufft_set_points_batch and
+ * dfsnufft_execute).  The step is recorded as one CUDA graph (a fork over the
+ * group streams and a join back into the ensemble's stream) and replayed with
+ * one graph launch on later calls with the same pointers and counts; a call
+ * with other pointers or counts runs the step once as is and records it anew.
+ * Asynchronous on the ensemble's stream. */
+int dfsnufft_ensemble_run(dfsnufft_ensemble ens, const int64_t *const *n_points,
+                          const double *const *lon, const double *const *colat,
+                          const void *const *coeffs, void *const *values);
+
+/* Synchronise and report the first failure of any group (DFSNUFFT_OK if none). */
+int dfsnufft_ensemble_check(dfsnufft_ensemble ens);
+
+/* The batched plan of group g (owned by the ensemble). */
+int dfsnufft_ensemble_plan(dfsnufft_ensemble ens, int group, dfsnufft_plan *out);
+
+int dfsnufft_ensemble_destroy(dfsnufft_ensemble ens);
+
 /* Evaluate all n_fields series at the plan's points (Eq. 5.3).
- *   coeffs : device pointer, n_fields x N2 x N1 complex (see conventions).
- *   values : device pointer, n_fields x n_points real, written in full. */
+ *   coeffs : device pointer, (n_members x) n_fields x N2 x N1 complex (see conventions).
+ *   values : device pointer, (members back to back) n_fields x n_points real,
+ *            written in full. */
 int dfsnufft_execute(dfsnufft_plan plan, const void *coeffs, void *values);
 
 /* Host-buffer variants: the same operations with host pointers.  The data are

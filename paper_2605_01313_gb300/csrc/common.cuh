@@ -35,9 +35,11 @@ __host__ __device__ __forceinline__ C cmul(C a, C b) {
 
 struct dfsnufft_plan_s {
     dfsnufft_params prm;
-    int n_fields;
+    int n_members;          // members of the same grid, each with its own points
+    int n_fields;           // fields per member (lines of the FFT passes: n_members x n_fields)
     int c0;                 // first tap sits c0 cells left of the point's base cell
     int nbx, nby, nbins;    // interpolation bins
+    int bstride;            // per-member stride of the bin arrays: >= nbins + 1, multiple of 4
     cudaStream_t stream;
 
     // device buffers owned by the plan
@@ -47,18 +49,21 @@ struct dfsnufft_plan_s {
     void *d_tw2;            // n2 twiddles
     void *d_stw_theta;      // stage-ordered twiddles of the length-n2/2 theta transforms
     void *d_stw_phi;        // stage-ordered twiddles of the length-n1/2 phi transforms
-    void *d_T;              // theta-pass output, n_fields x n2 x N1
-    void *d_G;              // fine grids (real part), n_fields x n2 x n1, plan precision
-    int *d_bin_count;       // nbins
-    int *d_bin_start;       // nbins + 1
-    int *d_task_bin;        // nbins: list of non-empty bins
-    int *d_n_tasks;         // 1
-    int2 *d_rowrange;           // circular range of needed fine rows: (first, count)
+    void *d_T;              // theta-pass output, (members x fields) x n2 x N1
+    void *d_G;              // fine grids (real part), (members x fields) x n2 x n1, plan precision
+    int *d_bin_count;       // members x bstride
+    int *d_bin_start;       // members x bstride (nbins + 1 used), member-local positions
+    int *d_task_bin;        // members x bstride: lists of non-empty bins
+    int *d_n_tasks;         // members
+    int2 *d_rowrange;           // per member: circular range of needed fine rows (first, count)
+    int *d_pofs;                // members + 1 point offsets (device)
+    int64_t *h_pofs;            // members + 1 point offsets of the current points (host)
+    int64_t max_member_points;  // largest member's point count
     int *d_status;              // device status word (DFS_STATUS_*), zero when healthy
     int num_sms;                // multiprocessors of the plan's device
 
     // point data (capacity grows with set_points)
-    int64_t n_points, cap_points;
+    int64_t n_points, cap_points;   // all members' points
     int *d_rank;            // rank of each point inside its bin (input order)
     int2 *d_base;           // sorted: first-tap fine index (i0, j0)
     void *d_frac;           // sorted: offsets (tx, ty) in plan precision

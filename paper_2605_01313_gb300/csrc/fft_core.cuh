@@ -6,6 +6,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace dfs_fft {
 
@@ -256,8 +257,7 @@ __host__ __device__ __forceinline__ int ilog2(int n) {
 
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return dfs_allow_smem((const void *)kernel, bytes);
 }
 
 }  // namespace dfs_fft

@@ -19,9 +19,10 @@ namespace {
 struct PhiArgs {
     int N1, n1, logm, n2;     // logm = log2(n1 / 2)
     int CB;                   // rows per CTA (divides DFS_ROW_BLOCK)
+    int F;                    // fields per member (line f belongs to member f / F)
 };
 
-// grid (n2 / CB, n_fields); block CB * M/E threads, thread = (t, c) with t fastest.
+// grid (n2 / CB, lines); block CB * M/E threads, thread = (t, c) with t fastest.
 // LOGM > 0 fixes the transform length at compile time; 0 takes it from a.logm.
 template <typename R, int E, int MAXT, int MINB, int LOGM>
 __global__ void __launch_bounds__(MAXT, MINB)
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
                R *__restrict__ grid) {
     typedef typename CxT<R>::type C;
     const int row0 = blockIdx.x * a.CB;
-    const int2 rr = *rowrange;
+    const int2 rr = rowrange[blockIdx.y / a.F];
     // whole CTA (within one row block): no stencil touches these rows
     if (((row0 - rr.x) & (a.n2 - 1)) >= rr.y) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -98,6 +99,7 @@ cudaError_t launch_phi(dfsnufft_plan p) {
     a.n1 = q.n1;
     a.logm = ilog2(q.n1) - 1;
     a.n2 = q.n2;
+    a.F = p->n_fields;
     const int M = q.n1 / 2;
     const int T = M / E;
     int cb = MAXT / T;
@@ -107,7 +109,7 @@ cudaError_t launch_phi(dfsnufft_plan p) {
     while (cb > 1 && per_row * cb > 160 * 1024) cb >>= 1;
     a.CB = cb;
     const size_t smem = per_row * cb;
-    const dim3 grid(q.n2 / cb, p->n_fields);
+    const dim3 grid(q.n2 / cb, p->n_members * p->n_fields);
     if (!p->d_stw_phi) return run_phi<R, 0>(p, a, smem, grid, cb * T);
     switch (a.logm) {
         case 9: return run_phi<R, 9>(p, a, smem, grid, cb * T);

@@ -23,9 +23,10 @@ namespace {
 struct ThetaArgs {
     int N1, N2, n2, logn2;
     int CB;                   // columns per CTA
+    int F;                    // fields per member (line f belongs to member f / F)
 };
 
-// grid (ceil(N1 / CB), n_fields); block CB * n2/E threads, thread = (t, c) with c fastest.
+// grid (ceil(N1 / CB), lines); block CB * n2/E threads, thread = (t, c) with c fastest.
 template <typename R, int E, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_theta_pass(ThetaArgs a, const typename CxT<R>::type *__restrict__ coef,
@@ -35,11 +36,11 @@ __global__ void __launch_bounds__(MAXT, MINB)
     typedef typename CxT<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *smem = reinterpret_cast<C *>(smem_raw);
-    const int2 rr = *rowrange;
     const int c = threadIdx.x % a.CB;
     const int t = threadIdx.x / a.CB;
     const int q = blockIdx.x * a.CB + c;
     const int f = blockIdx.y;
+    const int2 rr = rowrange[f / a.F];
     const bool col_ok = q < a.N1;
     const C *src = coef + (size_t)f * a.N2 * a.N1 + q;
     C *dst = out + (size_t)f * a.n2 * a.N1 + q;
@@ -65,8 +66,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
 
 struct ThetaTmaArgs {
     int N1, N2, n2, logh;     // logh = log2(n2 / 2)
-    int nbq;                  // column blocks per field, ceil(N1 / CB)
-    int total;                // nbq * n_fields
+    int nbq;                  // column blocks per line, ceil(N1 / CB)
+    int total;                // nbq * lines (members x fields)
+    int F;                    // fields per member (line f belongs to member f / F)
     int nbox, box_rows;       // TMA boxes per block and rows per box
     int in_elems;             // complex elements delivered per block
     int nbuf;                 // input buffers (2: prefetch the next block)
@@ -96,7 +98,6 @@ __global__ void __launch_bounds__(MAXT, 1)
     const int c = threadIdx.x % CB;
     const int t = threadIdx.x / CB;
     const int half = a.N2 / 2;
-    const int2 rr = *rowrange;
     C *sm = ex + (size_t)c * region_len<C>(H);
     for (int i = threadIdx.x; i < a.N2; i += blockDim.x) f2[i] = inv2[i];
     if (threadIdx.x == 0) {
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(MAXT, 1)
             return;
         }
         const int f = blk / a.nbq;
+        const int2 rr = rowrange[f / a.F];
         const int q = (blk - f * a.nbq) * CB + c;
         const bool col_ok = q < a.N1;
         const R sq = col_ok ? inv1[q] : (R)0;
@@ -180,8 +182,7 @@ cudaError_t run_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUtensor
                           size_t smem, int grid, int threads) {
     typedef typename CxT<R>::type C;
     constexpr int E = ThetaCfg<R>::E, CB = ThetaCfg<R>::CB, MAXT = ThetaCfg<R>::MAXT;
-    cudaError_t e = cudaFuncSetAttribute(k_theta_tma<R, E, CB, MAXT, LOGH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(k_theta_tma<R, E, CB, MAXT, LOGH>, smem);
     if (e) return e;
     k_theta_tma<R, E, CB, MAXT, LOGH><<<grid, threads, smem, p->stream>>>(
         a, tmap, (const R *)p->d_inv1, (const R *)p->d_inv2, (const C *)p->d_tw2,
@@ -205,7 +206,9 @@ cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
     a.n2 = q.n2;
     a.logh = ilog2(H);
     a.nbq = (q.N1 + CB - 1) / CB;
-    a.total = a.nbq * p->n_fields;
+    const int lines = p->n_members * p->n_fields;
+    a.total = a.nbq * lines;
+    a.F = p->n_fields;
     // boxes of CB columns x box_rows rows, each a multiple of 128 bytes
     // (CB * sizeof(C) = 32 bytes a row, box_rows a multiple of 4)
     a.box_rows = q.N2 < 256 ? ((q.N2 + 3) & ~3) : 256;
@@ -221,7 +224,7 @@ cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
     if (smem > limit) return cudaErrorNotSupported;
     CUtensorMap tmap;
     cudaError_t e = dfs_encode_tensor_map_2d(&tmap, coeffs, (uint64_t)q.N1 * (sizeof(C) / 8),
-                                             (uint64_t)q.N2 * p->n_fields,
+                                             (uint64_t)q.N2 * lines,
                                              sizeof(C) * (uint64_t)q.N1,
                                              (uint32_t)(CB * (sizeof(C) / 8)),
                                              (uint32_t)a.box_rows);
@@ -253,6 +256,7 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs) {
     a.N2 = q.N2;
     a.n2 = q.n2;
     a.logn2 = ilog2(q.n2);
+    a.F = p->n_fields;
     const int T = q.n2 / E;
     int cb = MAXT / T;
     if (cb < 1) cb = 1;
@@ -265,7 +269,7 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs) {
     const size_t smem = per_col * cb;
     cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB>, smem);
     if (e) return e;
-    dim3 grid((q.N1 + cb - 1) / cb, p->n_fields);
+    dim3 grid((q.N1 + cb - 1) / cb, p->n_members * p->n_fields);
     k_theta_pass<R, E, MAXT, MINB><<<grid, cb * T, smem, p->stream>>>(
         a, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2, (const C *)p->d_tw2,
         p->d_rowrange, (C *)p->d_T);

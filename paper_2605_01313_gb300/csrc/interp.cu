@@ -15,6 +15,7 @@
 // evaluates one point at a time from shared memory, computing its 2w kernel
 // values once for all fields.
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace {
 
@@ -22,8 +23,8 @@ struct InterpArgs {
     int n1, n2;
     int tile_x, tile_y, nbx;
     int c0;
-    int F, FG;            // fields, fields staged per pass
-    int P;
+    int F, FG;            // fields per member, fields staged per pass
+    int bstride;          // per-member stride of the bin arrays
 };
 
 // Kernel weights by Horner's rule: for tap a the weight phi((a - c0) - t) is a
@@ -55,24 +56,32 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const __grid_const
                                                 const int2 *__restrict__ base,
                                                 const R *__restrict__ frac,
                                                 const int *__restrict__ idx,
-                                                const int *__restrict__ bin_start,
-                                                const int *__restrict__ task_bin,
+                                                const int *__restrict__ bin_start_all,
+                                                const int *__restrict__ task_all,
                                                 const int *__restrict__ n_tasks,
-                                                R *__restrict__ out) {
+                                                const int *__restrict__ pofs,
+                                                R *__restrict__ out_all) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *tile = reinterpret_cast<R *>(smem_raw);
     const int TH = a.tile_y + W - 1;
     const int TW = a.tile_x + W - 1;
     const int tsz = TH * TW;
-    const int ntask = *n_tasks;
+    // member k = blockIdx.y: its bins, sorted records [p0, p0 + Pk), F fine grids
+    // and F x Pk outputs
+    const int k = blockIdx.y;
+    const int p0 = pofs[k];
+    const int Pk = pofs[k + 1] - p0;
+    const int ntask = n_tasks[k];
+    const int *task_bin = task_all + (size_t)k * a.bstride;
+    const int *bin_start = bin_start_all + (size_t)k * a.bstride;
     for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
         const int bin = task_bin[task];
         const int by = bin / a.nbx;
         const int bx = bin - by * a.nbx;
         const int col0 = bx * a.tile_x - a.c0;
         const int row0 = by * a.tile_y - a.c0;
-        const int s = bin_start[bin];
-        const int e = bin_start[bin + 1];
+        const int s = p0 + bin_start[bin];
+        const int e = p0 + bin_start[bin + 1];
         for (int f0 = 0; f0 < a.F; f0 += a.FG) {
             const int fg = min(a.FG, a.F - f0);
             __syncthreads();
@@ -81,7 +90,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const __grid_const
                 const int ff = rr / TH;
                 const int r = rr - ff * TH;
                 const int gr = (row0 + r) & (a.n2 - 1);
-                const R *src = grid + ((size_t)(f0 + ff) * a.n2 + gr) * a.n1;
+                const R *src = grid + ((size_t)(k * a.F + f0 + ff) * a.n2 + gr) * a.n1;
                 R *dst = tile + ff * tsz + r * TW;
                 for (int cc = threadIdx.x & 31; cc < TW; cc += 32)
                     dst[cc] = src[(col0 + cc) & (a.n1 - 1)];
@@ -105,7 +114,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const __grid_const
                         for (int aa = 0; aa < W; ++aa) rr += wx[aa] * tp[bb * TW + aa];
                         acc += wy[bb] * rr;
                     }
-                    out[(size_t)(f0 + ff) * a.P + dst] = acc;
+                    out_all[(size_t)a.F * p0 + (size_t)(f0 + ff) * Pk + dst] = acc;
                 }
             }
         }
@@ -125,10 +134,11 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a,
                                                     const int2 *__restrict__ base,
                                                     const float *__restrict__ frac,
                                                     const int *__restrict__ idx,
-                                                    const int *__restrict__ bin_start,
-                                                    const int *__restrict__ task_bin,
+                                                    const int *__restrict__ bin_start_all,
+                                                    const int *__restrict__ task_all,
                                                     const int *__restrict__ n_tasks,
-                                                    float *__restrict__ out) {
+                                                    const int *__restrict__ pofs,
+                                                    float *__restrict__ out_all) {
     constexpr int WP = (W + 2) & ~1;          // taps read per row, even
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *tile = reinterpret_cast<float *>(smem_raw);
@@ -136,15 +146,22 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a,
     const int TW = a.tile_x + WP;             // even: rows stay 8-byte aligned
     const int Q = TW / 2;                     // pairs per tile row
     const int tsz = TH * TW;
-    const int ntask = *n_tasks;
+    // member k = blockIdx.y: its bins, sorted records [p0, p0 + Pk), F fine grids
+    // and F x Pk outputs
+    const int k = blockIdx.y;
+    const int p0 = pofs[k];
+    const int Pk = pofs[k + 1] - p0;
+    const int ntask = n_tasks[k];
+    const int *task_bin = task_all + (size_t)k * a.bstride;
+    const int *bin_start = bin_start_all + (size_t)k * a.bstride;
     for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
         const int bin = task_bin[task];
         const int by = bin / a.nbx;
         const int bx = bin - by * a.nbx;
         const int col0 = (bx * a.tile_x - a.c0) & ~1;
         const int row0 = by * a.tile_y - a.c0;
-        const int s = bin_start[bin];
-        const int e = bin_start[bin + 1];
+        const int s = p0 + bin_start[bin];
+        const int e = p0 + bin_start[bin + 1];
         for (int f0 = 0; f0 < a.F; f0 += a.FG) {
             const int fg = min(a.FG, a.F - f0);
             __syncthreads();
@@ -163,7 +180,7 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a,
                             const int ff = rr / TH;
                             const int gr = (row0 + rr - ff * TH) & (a.n2 - 1);
                             v[u] = *reinterpret_cast<const float2 *>(
-                                grid + ((size_t)(f0 + ff) * a.n2 + gr) * a.n1 + gc);
+                                grid + ((size_t)(k * a.F + f0 + ff) * a.n2 + gr) * a.n1 + gc);
                         }
                     }
 #pragma unroll
@@ -207,7 +224,7 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a,
                         }
                         acc += wy[bb] * rr;
                     }
-                    out[(size_t)(f0 + ff) * a.P + dst] = acc;
+                    out_all[(size_t)a.F * p0 + (size_t)(f0 + ff) * Pk + dst] = acc;
                 }
             }
         }
@@ -226,7 +243,7 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
     a.nbx = p->nbx;
     a.c0 = p->c0;
     a.F = p->n_fields;
-    a.P = (int)p->n_points;
+    a.bstride = p->bstride;
     Horner<R, W> hw;
     {
         double hc[W * (W + 1)];
@@ -243,31 +260,27 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
     if (fg > a.F) fg = a.F;
     a.FG = fg;
     const size_t smem = per_field * fg;
-    int blocks = p->nbins < 152 * 16 ? p->nbins : 152 * 16;
+    // blocks per member: enough to fill the GPU across all members
+    int per = (152 * 16 + p->n_members - 1) / p->n_members;
+    if (per > p->nbins) per = p->nbins;
+    if (per < 1) per = 1;
+    const dim3 blocks(per, p->n_members);
     if (pair) {
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_interp_f32<W>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e) return e;
-        }
+        cudaError_t e = dfs_allow_smem((const void *)k_interp_f32<W>, smem);
+        if (e) return e;
         Horner<float, W> hf;
         for (int i = 0; i < W; ++i)
             for (int k = 0; k <= W; ++k) hf.c[i][k] = (float)hw.c[i][k];
         k_interp_f32<W><<<blocks, 128, smem, p->stream>>>(
             a, hf, (const float *)p->d_G, p->d_base, (const float *)p->d_frac, p->d_idx,
-            p->d_bin_start, p->d_task_bin, p->d_n_tasks, (float *)values);
+            p->d_bin_start, p->d_task_bin, p->d_n_tasks, p->d_pofs, (float *)values);
     } else {
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_interp<R, W>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e) return e;
-        }
+        cudaError_t e = dfs_allow_smem((const void *)k_interp<R, W>, smem);
+        if (e) return e;
         const int threads = sizeof(R) == 4 ? 128 : 256;
         k_interp<R, W><<<blocks, threads, smem, p->stream>>>(
             a, hw, (const R *)p->d_G, p->d_base, (const R *)p->d_frac, p->d_idx, p->d_bin_start,
-            p->d_task_bin, p->d_n_tasks, (R *)values);
+            p->d_task_bin, p->d_n_tasks, p->d_pofs, (R *)values);
     }
     return cudaGetLastError();
 }

@@ -32,6 +32,7 @@ std::mutex g_mutex;                              // set-up and table uploads
 // Host staging for the tables (static: nothing is allocated per call).
 double2 g_tw_stage[2 * kMaxFine];
 double g_ft_stage[kMaxFine];
+int g_pofs_stage[2];
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -128,8 +129,11 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     p.nbx = prm.n1 / prm.tile_x + 1;
     p.nby = prm.n2 / prm.tile_y + 1;
     p.nbins = p.nbx * p.nby;
+    p.bstride = (p.nbins + 4) & ~3;
+    p.n_members = 1;
     p.n_points = n_points;
     p.cap_points = n_points;
+    p.max_member_points = n_points;
     p.has_points = 1;
     const size_t cs = dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
     const size_t rs = cs / 2;                    // factor tables are in plan precision
@@ -137,8 +141,8 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     size_t off[20], total = 0;
     const size_t sizes[] = {rs * prm.N1, rs * prm.N2, cs * prm.n1,
                             cs * prm.n2, cs * nf * prm.n2 * prm.N1, rs * nf * prm.n2 * prm.n1,
-                            sizeof(int) * p.nbins, sizeof(int) * (p.nbins + 1),
-                            sizeof(int) * p.nbins, sizeof(int), (size_t)0 /* unused */,
+                            sizeof(int) * p.bstride, sizeof(int) * p.bstride,
+                            sizeof(int) * p.bstride, sizeof(int), 2 * sizeof(int),
                             sizeof(int) * P, sizeof(int2) * P, 2 * rs * P, sizeof(int) * P,
                             sizeof(int2)};
     const int nbuf = (int)(sizeof(sizes) / sizeof(sizes[0]));
@@ -175,6 +179,7 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     p.d_base = (int2 *)(b + off[12]);
     p.d_frac = b + off[13];
     p.d_idx = (int *)(b + off[14]);
+    p.d_pofs = (int *)(b + off[10]);
     p.d_rowrange = (int2 *)(b + off[15]);
 
     // kernel tables: uploaded only when the configuration differs from the
@@ -206,7 +211,13 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
         ds.dtype = dtype;
         ds.beta = prm.beta;
     }
-    // set_points clears the bin counters and row mask before counting
+    // one member: point offsets {0, P}
+    g_pofs_stage[0] = 0;
+    g_pofs_stage[1] = (int)n_points;
+    if (cudaMemcpyAsync(p.d_pofs, g_pofs_stage, sizeof(g_pofs_stage), cudaMemcpyHostToDevice,
+                        p.stream) != cudaSuccess)
+        return DFSNUFFT_ERR_CUDA;
+    // set_points clears the bin counters before counting
     if (dfs_launch_set_points(&p, lon, colat) != cudaSuccess ||
         dfs_launch_theta_pass(&p, coeffs) != cudaSuccess ||
         dfs_launch_phi_pass(&p) != cudaSuccess || dfs_launch_interp(&p, values) != cudaSuccess)

@@ -269,10 +269,12 @@ static void release(dfsnufft_plan p) {
     void **bufs[] = {&p->d_inv1, &p->d_inv2, &p->d_tw1, &p->d_tw2, &p->d_stw_theta, &p->d_stw_phi,
                      &p->d_T, &p->d_G, (void **)&p->d_bin_count, (void **)&p->d_bin_start,
                      (void **)&p->d_task_bin, (void **)&p->d_n_tasks,
-                     (void **)&p->d_status, (void **)&p->d_rowrange,
+                     (void **)&p->d_status, (void **)&p->d_rowrange, (void **)&p->d_pofs,
                      (void **)&p->d_rank, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
                      (void **)&p->d_pts_stage, &p->d_coef_stage, &p->d_val_stage};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) dfs_free(bufs[i]);
+    free(p->h_pofs);
+    p->h_pofs = nullptr;
     if (p->ev) {
         for (int i = 0; i < 2 * DFS_TIMING_SLOTS * DFSNUFFT_N_STAGES; ++i)
             if (p->ev[i]) cudaEventDestroy(p->ev[i]);
@@ -391,11 +393,13 @@ static int upload_tables(dfsnufft_plan p) {
     return rc;
 }
 
-extern "C" int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype, int n_fields,
-                                    void *stream, dfsnufft_plan *out) {
+static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int dtype,
+                            int n_fields, void *stream, dfsnufft_plan *out) {
     if (!out) return DFSNUFFT_ERR_INVALID_ARG;
     *out = nullptr;
-    if (n_fields < 1 || n_fields > 64) return DFSNUFFT_ERR_INVALID_ARG;
+    if (n_fields < 1 || n_fields > 64 || n_members < 1 || n_members > 4096 ||
+        n_members * n_fields > 65535)
+        return DFSNUFFT_ERR_INVALID_ARG;
     dfsnufft_params prm;
     int rc = dfsnufft_choose_params(n_lon, n_lat, tol, dtype, &prm);
     if (rc != DFSNUFFT_OK) return rc;
@@ -404,15 +408,18 @@ extern "C" int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype,
     if (!p) return DFSNUFFT_ERR_OOM;
     memset(p, 0, sizeof(*p));
     p->prm = prm;
+    p->n_members = n_members;
     p->n_fields = n_fields;
     p->stream = (cudaStream_t)stream;
     p->c0 = (prm.w % 2 == 0) ? prm.w / 2 - 1 : (prm.w - 1) / 2;
     p->nbx = prm.n1 / prm.tile_x + 1;
     p->nby = prm.n2 / prm.tile_y + 1;
     p->nbins = p->nbx * p->nby;
+    p->bstride = (p->nbins + 4) & ~3;     // 16-byte aligned member slices
 
     size_t cs = dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
-    size_t nf = (size_t)n_fields;
+    const size_t nf = (size_t)n_fields * n_members;      // FFT lines
+    const size_t nm = (size_t)n_members;
     struct { void **ptr; size_t bytes; const char *what; } allocs[] = {
         {&p->d_inv1, cs / 2 * prm.N1, "deconvolution factors"},
         {&p->d_inv2, cs / 2 * prm.N2, "deconvolution factors"},
@@ -422,13 +429,19 @@ extern "C" int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype,
         {&p->d_stw_phi, cs * stage_table_len(prm.n1 / 2), "stage twiddles"},
         {&p->d_T, cs * nf * prm.n2 * prm.N1, "theta-pass buffer"},
         {&p->d_G, cs / 2 * nf * prm.n2 * prm.n1, "fine grid (real part)"},
-        {(void **)&p->d_bin_count, sizeof(int) * p->nbins, "bin counts"},
-        {(void **)&p->d_bin_start, sizeof(int) * (p->nbins + 1), "bin starts"},
-        {(void **)&p->d_task_bin, sizeof(int) * p->nbins, "bin list"},
-        {(void **)&p->d_n_tasks, sizeof(int), "bin list size"},
+        {(void **)&p->d_bin_count, sizeof(int) * p->bstride * nm, "bin counts"},
+        {(void **)&p->d_bin_start, sizeof(int) * p->bstride * nm, "bin starts"},
+        {(void **)&p->d_task_bin, sizeof(int) * p->bstride * nm, "bin list"},
+        {(void **)&p->d_n_tasks, sizeof(int) * nm, "bin list size"},
         {(void **)&p->d_status, sizeof(int), "status word"},
-        {(void **)&p->d_rowrange, sizeof(int2), "row range"},
+        {(void **)&p->d_rowrange, sizeof(int2) * nm, "row ranges"},
+        {(void **)&p->d_pofs, sizeof(int) * (nm + 1), "point offsets"},
     };
+    p->h_pofs = (int64_t *)calloc(nm + 1, sizeof(int64_t));
+    if (!p->h_pofs) {
+        delete p;
+        return DFSNUFFT_ERR_OOM;
+    }
     for (size_t i = 0; i < sizeof(allocs) / sizeof(allocs[0]); ++i) {
         rc = dfs_alloc(p, allocs[i].ptr, allocs[i].bytes, allocs[i].what);
         if (rc != DFSNUFFT_OK) {
@@ -453,6 +466,17 @@ extern "C" int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype,
     }
     *out = p;
     return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype, int n_fields,
+                                    void *stream, dfsnufft_plan *out) {
+    return plan_create_impl(1, n_lon, n_lat, tol, dtype, n_fields, stream, out);
+}
+
+extern "C" int dfsnufft_plan_create_batch(int n_members, int n_lon, int n_lat, double tol,
+                                          int dtype, int n_fields, void *stream,
+                                          dfsnufft_plan *out) {
+    return plan_create_impl(n_members, n_lon, n_lat, tol, dtype, n_fields, stream, out);
 }
 
 extern "C" int dfsnufft_destroy(dfsnufft_plan p) {
@@ -506,21 +530,58 @@ static int ensure_point_capacity(dfsnufft_plan p, int64_t n) {
     return DFSNUFFT_OK;
 }
 
-extern "C" int dfsnufft_set_points(dfsnufft_plan p, int64_t n_points, const double *lon,
-                                   const double *colat) {
+// Record the members' point counts; the device offsets are uploaded only when
+// they change (so that repeated calls enqueue no host-to-device copy).
+static int update_counts(dfsnufft_plan p, const int64_t *counts) {
+    const int M = p->n_members;
+    int64_t total = 0, mx = 0;
+    bool same = p->has_points;
+    for (int k = 0; k < M; ++k) {
+        if (counts[k] < 1) return DFSNUFFT_ERR_INVALID_ARG;
+        if (p->h_pofs[k + 1] - p->h_pofs[k] != counts[k]) same = false;
+        total += counts[k];
+        if (counts[k] > mx) mx = counts[k];
+    }
+    if (total > 0x7fffffffLL) return DFSNUFFT_ERR_INVALID_ARG;
+    int rc = ensure_point_capacity(p, total);
+    if (rc) return rc;
+    if (!same) {
+        p->h_pofs[0] = 0;
+        for (int k = 0; k < M; ++k) p->h_pofs[k + 1] = p->h_pofs[k] + counts[k];
+        int *tmp = (int *)malloc(sizeof(int) * (M + 1));
+        if (!tmp) return DFSNUFFT_ERR_OOM;
+        for (int k = 0; k <= M; ++k) tmp[k] = (int)p->h_pofs[k];
+        cudaError_t e = cudaMemcpyAsync(p->d_pofs, tmp, sizeof(int) * (M + 1),
+                                        cudaMemcpyHostToDevice, p->stream);
+        free(tmp);
+        if (e) return fail_cuda(p, "upload point offsets", e);
+    }
+    p->n_points = total;
+    p->max_member_points = mx;
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_set_points_batch(dfsnufft_plan p, const int64_t *n_points,
+                                         const double *lon, const double *colat) {
     if (!p) return DFSNUFFT_ERR_INVALID_ARG;
     if (p->status) return p->status;
-    if (n_points < 1 || n_points > 0x7fffffffLL || !lon || !colat)
-        return DFSNUFFT_ERR_INVALID_ARG;
-    int rc = ensure_point_capacity(p, n_points);
+    if (!n_points || !lon || !colat) return DFSNUFFT_ERR_INVALID_ARG;
+    int rc = update_counts(p, n_points);
     if (rc) return rc;
-    p->n_points = n_points;
     p->has_points = 0;
     DFS_CK(p, timing_begin(p, 0));
     DFS_CK(p, dfs_launch_set_points(p, lon, colat));
     DFS_CK(p, timing_end(p, 0));
     p->has_points = 1;
     return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_set_points(dfsnufft_plan p, int64_t n_points, const double *lon,
+                                   const double *colat) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->n_members != 1) return DFSNUFFT_ERR_INVALID_ARG;
+    if (n_points < 1 || n_points > 0x7fffffffLL) return DFSNUFFT_ERR_INVALID_ARG;
+    return dfsnufft_set_points_batch(p, &n_points, lon, colat);
 }
 
 extern "C" int dfsnufft_execute(dfsnufft_plan p, const void *coeffs, void *values) {
@@ -546,9 +607,9 @@ extern "C" int dfsnufft_set_points_host(dfsnufft_plan p, int64_t n_points, const
                                         const double *colat) {
     if (!p) return DFSNUFFT_ERR_INVALID_ARG;
     if (p->status) return p->status;
-    if (n_points < 1 || n_points > 0x7fffffffLL || !lon || !colat)
+    if (p->n_members != 1 || n_points < 1 || n_points > 0x7fffffffLL || !lon || !colat)
         return DFSNUFFT_ERR_INVALID_ARG;
-    int rc = ensure_point_capacity(p, n_points);
+    int rc = update_counts(p, &n_points);
     if (rc) return rc;
     if (p->pts_stage_cap < p->cap_points) {
         // staging sized to the point capacity
@@ -564,7 +625,6 @@ extern "C" int dfsnufft_set_points_host(dfsnufft_plan p, int64_t n_points, const
     DFS_CK(p, cudaMemcpyAsync(p->d_pts_stage, lon, b, cudaMemcpyHostToDevice, p->stream));
     DFS_CK(p, cudaMemcpyAsync(p->d_pts_stage + p->pts_stage_cap, colat, b,
                               cudaMemcpyHostToDevice, p->stream));
-    p->n_points = n_points;
     p->has_points = 0;
     DFS_CK(p, timing_begin(p, 0));
     DFS_CK(p, dfs_launch_set_points(p, p->d_pts_stage, p->d_pts_stage + p->pts_stage_cap));
@@ -581,7 +641,7 @@ extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *
     const dfsnufft_params &q = p->prm;
     size_t cs = q.dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
     size_t rs = cs / 2;
-    size_t cb = cs * (size_t)p->n_fields * q.N2 * q.N1;
+    size_t cb = cs * (size_t)p->n_members * p->n_fields * q.N2 * q.N1;
     size_t vb = rs * (size_t)p->n_fields * (size_t)p->n_points;
     int rc;
     if (!p->d_coef_stage) {
@@ -641,14 +701,28 @@ extern "C" int dfsnufft_plan_point_stats(dfsnufft_plan p, int64_t *rows_needed,
     if (p->status) return p->status;
     if (!p->has_points) return DFSNUFFT_ERR_NO_POINTS;
     DFS_CK(p, cudaStreamSynchronize(p->stream));
-    int2 range = make_int2(0, 0);
-    int ntask = 0;
-    cudaError_t e1 = cudaMemcpy(&range, p->d_rowrange, sizeof(int2), cudaMemcpyDeviceToHost);
-    cudaError_t e2 = cudaMemcpy(&ntask, p->d_n_tasks, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e1) return fail_cuda(p, "read row range", e1);
-    if (e2) return fail_cuda(p, "read bin count", e2);
-    const int64_t blocks = range.y / DFS_ROW_BLOCK;
+    const int M = p->n_members;
+    int2 *range = (int2 *)malloc(sizeof(int2) * M);
+    int *ntask = (int *)malloc(sizeof(int) * M);
+    if (!range || !ntask) {
+        free(range);
+        free(ntask);
+        return DFSNUFFT_ERR_OOM;
+    }
+    cudaError_t e1 = cudaMemcpy(range, p->d_rowrange, sizeof(int2) * M, cudaMemcpyDeviceToHost);
+    cudaError_t e2 = cudaMemcpy(ntask, p->d_n_tasks, sizeof(int) * M, cudaMemcpyDeviceToHost);
+    int64_t rows = 0, bins = 0;
+    for (int k = 0; k < M; ++k) {
+        rows += range[k].y;
+        bins += ntask[k];
+    }
+    free(range);
+    free(ntask);
+    if (e1) return fail_cuda(p, "read row ranges", e1);
+    if (e2) return fail_cuda(p, "read bin counts", e2);
+    // per field: the members' average
+    const int64_t blocks = (rows / M) / DFS_ROW_BLOCK;
     *rows_needed = blocks * DFS_ROW_BLOCK;
-    *nonempty_bins = ntask;
+    *nonempty_bins = bins;
     return DFSNUFFT_OK;
 }

@@ -99,17 +99,21 @@ __device__ __forceinline__ int bin_of(const FoldParams &f, int bx, int by) {
     return (by / f.tile_y) * f.nbx + bx / f.tile_x;
 }
 
-__global__ void __launch_bounds__(256) k_fold_count(int n, const double *__restrict__ lon,
+// grid (ceil(max member points / 256), members): member k = blockIdx.y.
+__global__ void __launch_bounds__(256) k_fold_count(const double *__restrict__ lon,
                                                     const double *__restrict__ colat,
-                                                    FoldParams f, int *__restrict__ bin_count,
+                                                    FoldParams f, const int *__restrict__ pofs,
+                                                    int bstride, int *__restrict__ bin_count,
                                                     int *__restrict__ rank) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = p < n;
+    const int k = blockIdx.y;
+    const int p0 = pofs[k];
+    const int pl = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = pl < pofs[k + 1] - p0;
     int bin = -1;
     if (live) {
         int bx, by;
         long long tx, ty;
-        fold_point(f, lon[p], colat[p], bx, by, tx, ty);
+        fold_point(f, lon[p0 + pl], colat[p0 + pl], bx, by, tx, ty);
         bin = bin_of(f, bx, by);
     }
     // warp-aggregated increment: lanes sharing a bin take consecutive ranks
@@ -119,9 +123,9 @@ __global__ void __launch_bounds__(256) k_fold_count(int n, const double *__restr
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(peers) - 1;
     int base = 0;
-    if (lane == leader) base = atomicAdd(&bin_count[bin], __popc(peers));
+    if (lane == leader) base = atomicAdd(&bin_count[(size_t)k * bstride + bin], __popc(peers));
     base = __shfl_sync(peers, base, leader);
-    rank[p] = base + __popc(peers & ((1u << lane) - 1u));
+    rank[p0 + pl] = base + __popc(peers & ((1u << lane) - 1u));
 }
 
 // Smallest index i in [from, from + nb) (circular over nb bits) whose bit in
@@ -148,6 +152,7 @@ __device__ int next_bit(const unsigned *bits, int nb, int from, int value) {
 
 struct ScanParams {
     int nbins, nbx, nbr;      // bins, bins per bin row, bin rows in use (n2 / tile_y)
+    int bstride;              // per-member stride of the bin arrays (multiple of 4)
     int tile_y, c0, w, n2;
 };
 
@@ -157,11 +162,17 @@ struct ScanParams {
 // rows by*tile_y - c0 .. (by+1)*tile_y - c0 + w - 2, so the range is the
 // complement of the longest circular run of empty bin rows, widened by the
 // stencil and rounded out to whole row blocks.
-__global__ void __launch_bounds__(1024) k_scan_bins(ScanParams sp, const int *__restrict__ count,
-                                                    int *__restrict__ start,
-                                                    int *__restrict__ task_bin,
+// grid (members): member k = blockIdx.x.
+__global__ void __launch_bounds__(1024) k_scan_bins(ScanParams sp, const int *__restrict__ count_all,
+                                                    int *__restrict__ start_all,
+                                                    int *__restrict__ task_all,
                                                     int *__restrict__ n_tasks,
                                                     int2 *__restrict__ rowrange) {
+    const int member = blockIdx.x;
+    // member slices start on 16-byte boundaries (bstride is a multiple of 4)
+    const int *count = count_all + (size_t)member * sp.bstride;
+    int *start = start_all + (size_t)member * sp.bstride;
+    int *task_bin = task_all + (size_t)member * sp.bstride;
     __shared__ int s_sum[32], s_ne[32];
     __shared__ unsigned char s_row[DFS_MAX_ROW_BLOCKS + 1];
     __shared__ unsigned s_bits[(DFS_MAX_ROW_BLOCKS + 31) / 32];
@@ -244,7 +255,7 @@ __global__ void __launch_bounds__(1024) k_scan_bins(ScanParams sp, const int *__
     __syncthreads();
     if (tid == 0) {
         start[nbins] = carry;
-        *n_tasks = carry_n;
+        n_tasks[member] = carry_n;
         const int nb = sp.nbr;
         const int s0 = next_bit(s_bits, nb, 0, 1);
         int2 range = make_int2(0, 0);
@@ -272,29 +283,35 @@ __global__ void __launch_bounds__(1024) k_scan_bins(ScanParams sp, const int *__
             cnt = ((cnt + (first - fb) + DFS_ROW_BLOCK - 1) / DFS_ROW_BLOCK) * DFS_ROW_BLOCK;
             range = make_int2(fb, cnt < sp.n2 ? cnt : sp.n2);
         }
-        *rowrange = range;
+        rowrange[member] = range;
     }
 }
 
+// grid (ceil(max member points / 256), members): member k = blockIdx.y.  Sorted
+// records go to the member's slice [pofs[k], pofs[k+1]); idx holds member-local
+// point indices.
 template <typename R>
-__global__ void __launch_bounds__(256) k_scatter(int n, const double *__restrict__ lon,
+__global__ void __launch_bounds__(256) k_scatter(const double *__restrict__ lon,
                                                  const double *__restrict__ colat, FoldParams f,
-                                                 const int *__restrict__ start,
+                                                 const int *__restrict__ pofs, int bstride,
+                                                 const int *__restrict__ start_all,
                                                  const int *__restrict__ rank,
                                                  int2 *__restrict__ base, R *__restrict__ frac,
                                                  int *__restrict__ idx) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
+    const int k = blockIdx.y;
+    const int p0 = pofs[k];
+    const int pl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pl >= pofs[k + 1] - p0) return;
     int bx, by;
     long long tx, ty;
-    const bool ok = fold_point(f, lon[p], colat[p], bx, by, tx, ty);
-    const int pos = start[bin_of(f, bx, by)] + rank[p];
+    const bool ok = fold_point(f, lon[p0 + pl], colat[p0 + pl], bx, by, tx, ty);
+    const int pos = p0 + start_all[(size_t)k * bstride + bin_of(f, bx, by)] + rank[p0 + pl];
     base[pos] = make_int2(bx - f.c0, by - f.c0);
     R ox = offset_value<R>(tx, f.odd_w), oy = offset_value<R>(ty, f.odd_w);
     if (!ok) ox = oy = (R)__int_as_float(0x7fc00000);
     frac[2 * pos] = ox;
     frac[2 * pos + 1] = oy;
-    idx[pos] = p;
+    idx[pos] = pl;
 }
 
 int ilog2(int n) {
@@ -316,29 +333,32 @@ cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const doub
     f.tile_x = q.tile_x;
     f.tile_y = q.tile_y;
     f.nbx = p->nbx;
-    const int n = (int)p->n_points;
+    const int M = p->n_members;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(p->d_bin_count, 0, sizeof(int) * p->nbins, p->stream))) return e;
+    if ((e = cudaMemsetAsync(p->d_bin_count, 0, sizeof(int) * (size_t)M * p->bstride, p->stream)))
+        return e;
     const int tpb = 256;
-    const int blocks = (n + tpb - 1) / tpb;
-    k_fold_count<<<blocks, tpb, 0, p->stream>>>(n, lon, colat, f, p->d_bin_count, p->d_rank);
+    const dim3 grid((unsigned)((p->max_member_points + tpb - 1) / tpb), M);
+    k_fold_count<<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->bstride, p->d_bin_count,
+                                              p->d_rank);
     ScanParams sp;
     sp.nbins = p->nbins;
+    sp.bstride = p->bstride;
     sp.nbx = p->nbx;
     sp.nbr = q.n2 / q.tile_y;
     sp.tile_y = q.tile_y;
     sp.c0 = p->c0;
     sp.w = q.w;
     sp.n2 = q.n2;
-    k_scan_bins<<<1, 1024, 0, p->stream>>>(sp, p->d_bin_count, p->d_bin_start, p->d_task_bin,
+    k_scan_bins<<<M, 1024, 0, p->stream>>>(sp, p->d_bin_count, p->d_bin_start, p->d_task_bin,
                                           p->d_n_tasks, p->d_rowrange);
     if (q.dtype == DFSNUFFT_F64)
-        k_scatter<double><<<blocks, tpb, 0, p->stream>>>(n, lon, colat, f, p->d_bin_start,
-                                                        p->d_rank, p->d_base,
-                                                        (double *)p->d_frac, p->d_idx);
+        k_scatter<double><<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->bstride,
+                                                      p->d_bin_start, p->d_rank, p->d_base,
+                                                      (double *)p->d_frac, p->d_idx);
     else
-        k_scatter<float><<<blocks, tpb, 0, p->stream>>>(n, lon, colat, f, p->d_bin_start,
-                                                       p->d_rank, p->d_base, (float *)p->d_frac,
-                                                       p->d_idx);
+        k_scatter<float><<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->bstride,
+                                                     p->d_bin_start, p->d_rank, p->d_base,
+                                                     (float *)p->d_frac, p->d_idx);
     return cudaGetLastError();
 }

@@ -9,7 +9,33 @@
 namespace {
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_once;
+
+struct SmemEntry {
+    const void *kernel;
+    size_t bytes;
+};
+SmemEntry g_smem[256];
+int g_smem_n = 0;
+std::mutex g_smem_mutex;
 }  // namespace
+
+cudaError_t dfs_allow_smem(const void *kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(g_smem_mutex);
+    int i = 0;
+    while (i < g_smem_n && g_smem[i].kernel != kernel) ++i;
+    if (i < g_smem_n && g_smem[i].bytes >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e) return e;
+    if (i == g_smem_n) {
+        if (g_smem_n == 256) return cudaSuccess;   // table full: keep setting each time
+        g_smem[g_smem_n++] = {kernel, bytes};
+    } else {
+        g_smem[i].bytes = bytes;
+    }
+    return cudaSuccess;
+}
 
 cudaError_t dfs_encode_tensor_map_2d(CUtensorMap *map, const void *base, uint64_t width,
                                      uint64_t height, uint64_t pitch_bytes, uint32_t box_w,

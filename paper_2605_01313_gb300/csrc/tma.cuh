@@ -74,6 +74,11 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Host: raise a kernel's dynamic shared-memory limit to at least `bytes`,
+// calling cudaFuncSetAttribute only the first time a larger size is needed (so
+// that launches recorded into a CUDA graph make no attribute calls).
+cudaError_t dfs_allow_smem(const void *kernel, size_t bytes);
+
 // Host: encode a 2-D tensor map of 8-byte elements (rows of `width` elements,
 // `height` rows, row pitch `pitch_bytes`) with box `box_w` x `box_h`.
 // Returns cudaErrorNotSupported when the driver offers no encoder.

@@ -35,7 +35,9 @@ EXPORTS = (
     "dfsnufft_choose_params", "dfsnufft_es_kernel", "dfsnufft_kernel_ft", "dfsnufft_version",
     "dfsnufft_plan_enable_timing", "dfsnufft_plan_read_timing", "dfsnufft_plan_point_stats",
     "dfsnufft_probe_fma_rate", "dfsnufft_execute_noalloc", "dfsnufft_plan_check",
-    "dfsnufft_es_horner",
+    "dfsnufft_es_horner", "dfsnufft_plan_create_batch", "dfsnufft_set_points_batch",
+    "dfsnufft_ensemble_create", "dfsnufft_ensemble_run", "dfsnufft_ensemble_check",
+    "dfsnufft_ensemble_plan", "dfsnufft_ensemble_destroy",
 )
 N_STAGES = 4
 STAGES = ("set_points", "theta_pass", "phi_pass", "interp")
@@ -78,6 +80,15 @@ def lib():
         L = ctypes.CDLL(path)
         vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
         L.dfsnufft_plan_create.argtypes = [i32, i32, f64, i32, i32, vp, ctypes.POINTER(vp)]
+        L.dfsnufft_plan_create_batch.argtypes = [i32, i32, i32, f64, i32, i32, vp,
+                                                 ctypes.POINTER(vp)]
+        L.dfsnufft_set_points_batch.argtypes = [vp, vp, vp, vp]
+        L.dfsnufft_ensemble_create.argtypes = [i32, vp, vp, vp, f64, i32, i32, vp,
+                                               ctypes.POINTER(vp)]
+        L.dfsnufft_ensemble_run.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.dfsnufft_ensemble_check.argtypes = [vp]
+        L.dfsnufft_ensemble_plan.argtypes = [vp, i32, ctypes.POINTER(vp)]
+        L.dfsnufft_ensemble_destroy.argtypes = [vp]
         L.dfsnufft_set_points.argtypes = [vp, i64, vp, vp]
         L.dfsnufft_set_points_host.argtypes = [vp, i64, vp, vp]
         L.dfsnufft_execute.argtypes = [vp, vp, vp]
@@ -172,6 +183,20 @@ def dfsnufft_plan_create(n_lon, n_lat, tol, dtype, n_fields, stream) -> ctypes.c
     return h
 
 
+def dfsnufft_plan_create_batch(n_members, n_lon, n_lat, tol, dtype, n_fields, stream):
+    h = ctypes.c_void_p()
+    _check(lib().dfsnufft_plan_create_batch(int(n_members), int(n_lon), int(n_lat), float(tol),
+                                            _dtype_code(dtype), int(n_fields),
+                                            ctypes.c_void_p(int(stream or 0)), ctypes.byref(h)))
+    return h
+
+
+def dfsnufft_set_points_batch(h, counts, lon_ptr, colat_ptr):
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    _check(lib().dfsnufft_set_points_batch(h, c.ctypes.data, ctypes.c_void_p(lon_ptr),
+                                           ctypes.c_void_p(colat_ptr)), h)
+
+
 def dfsnufft_set_points(h, n_points, lon_ptr, colat_ptr):
     _check(lib().dfsnufft_set_points(h, int(n_points), ctypes.c_void_p(lon_ptr),
                                      ctypes.c_void_p(colat_ptr)), h)
@@ -248,27 +273,39 @@ class Plan:
     ``set_points`` takes CUDA float64 tensors; ``execute`` takes a CUDA complex
     tensor (complex128 for 'f64', complex64 for 'f32') and returns or fills a
     (F, P) real tensor.  Work is enqueued on ``stream`` (default: torch's
-    current stream at creation).
+    current stream at creation).  With ``n_members`` > 1 the plan is batched:
+    coefficients (members, F, 2 n_lat, n_lon), points given per member
+    (``set_points(lon, colat, counts)`` with concatenated arrays), values
+    concatenated per member (each F x P_k).
     """
 
-    def __init__(self, n_lon, n_lat, tol=1e-12, dtype="f64", n_fields=1, stream=None):
+    def __init__(self, n_lon, n_lat, tol=1e-12, dtype="f64", n_fields=1, stream=None,
+                 n_members=1):
         import torch
         self.n_lon, self.n_lat = int(n_lon), int(n_lat)
         self.dtype = "f64" if _dtype_code(dtype) == F64 else "f32"
         self.n_fields = int(n_fields)
+        self.n_members = int(n_members)
         self.tol = float(tol)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-        self._h = dfsnufft_plan_create(n_lon, n_lat, tol, self.dtype, n_fields, handle)
+        if self.n_members == 1:
+            self._h = dfsnufft_plan_create(n_lon, n_lat, tol, self.dtype, n_fields, handle)
+        else:
+            self._h = dfsnufft_plan_create_batch(self.n_members, n_lon, n_lat, tol, self.dtype,
+                                                 n_fields, handle)
         self.params = dfsnufft_plan_get_params(self._h)
         self.n_points = 0
+        self.counts = None
         self._keep = None
 
     @property
     def coeff_shape(self):
-        return (self.n_fields, 2 * self.n_lat, self.n_lon)
+        if self.n_members == 1:
+            return (self.n_fields, 2 * self.n_lat, self.n_lon)
+        return (self.n_members, self.n_fields, 2 * self.n_lat, self.n_lon)
 
     def _real_dtype(self):
         import torch
@@ -278,15 +315,23 @@ class Plan:
         import torch
         return torch.complex128 if self.dtype == "f64" else torch.complex64
 
-    def set_points(self, lon, colat):
+    def set_points(self, lon, colat, counts=None):
         import torch
         for t in (lon, colat):
             if not (t.is_cuda and t.dtype == torch.float64 and t.dim() == 1 and t.is_contiguous()):
                 raise ValueError("points must be contiguous 1-D CUDA float64 tensors")
         if lon.numel() != colat.numel():
             raise ValueError("lon and colat differ in length")
-        dfsnufft_set_points(self._h, lon.numel(), lon.data_ptr(), colat.data_ptr())
+        if counts is None:
+            if self.n_members != 1:
+                raise ValueError("a batched plan needs the per-member point counts")
+            counts = [lon.numel()]
+        counts = [int(c) for c in counts]
+        if len(counts) != self.n_members or sum(counts) != lon.numel():
+            raise ValueError("counts must give every member's points and sum to the total")
+        dfsnufft_set_points_batch(self._h, counts, lon.data_ptr(), colat.data_ptr())
         self.n_points = lon.numel()
+        self.counts = counts
         self._keep = (lon, colat)
 
     def execute(self, coeffs, out=None):
@@ -295,14 +340,24 @@ class Plan:
                 or not coeffs.is_cuda or not coeffs.is_contiguous():
             raise ValueError("coeffs must be a contiguous CUDA %s tensor of shape %s"
                              % (self._cplx_dtype(), self.coeff_shape))
+        shape = (self.n_fields, self.n_points) if self.n_members == 1 else \
+            (self.n_fields * self.n_points,)
         if out is None:
-            out = torch.empty((self.n_fields, self.n_points), dtype=self._real_dtype(),
-                              device=coeffs.device)
-        elif tuple(out.shape) != (self.n_fields, self.n_points) or \
+            out = torch.empty(shape, dtype=self._real_dtype(), device=coeffs.device)
+        elif out.numel() != self.n_fields * self.n_points or \
                 out.dtype != self._real_dtype() or not out.is_contiguous():
-            raise ValueError("out must be a contiguous (F, P) %s tensor" % self._real_dtype())
+            raise ValueError("out must be a contiguous %s tensor of %d values"
+                             % (self._real_dtype(), self.n_fields * self.n_points))
         dfsnufft_execute(self._h, coeffs.data_ptr(), out.data_ptr())
         return out
+
+    def split_values(self, out):
+        """Per-member (F, P_k) views of a batched plan's output."""
+        views, o = [], 0
+        for c in self.counts:
+            views.append(out[o:o + self.n_fields * c].view(self.n_fields, c))
+            o += self.n_fields * c
+        return views
 
     def set_points_host(self, lon, colat):
         lon = np.ascontiguousarray(lon, dtype=np.float64)
@@ -343,3 +398,61 @@ class Plan:
 
     def __exit__(self, *exc):
         self.destroy()
+
+
+class Ensemble:
+    """Members on uneven grids: ``groups`` is a list of (n_members, n_lon, n_lat).
+    ``run(points, coeffs, out)`` takes, per group, (lon, colat, counts) CUDA
+    float64 tensors/list, a (members, F, 2 n_lat, n_lon) complex tensor and an
+    output tensor of F x sum(counts) reals; the whole step is one CUDA graph."""
+
+    def __init__(self, groups, tol=1e-6, dtype="f32", n_fields=3, stream=None):
+        import torch
+        self.groups = [tuple(int(x) for x in g) for g in groups]
+        self.dtype = "f64" if _dtype_code(dtype) == F64 else "f32"
+        self.n_fields = int(n_fields)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        G = len(self.groups)
+        ai = lambda xs: (ctypes.c_int * G)(*xs)
+        h = ctypes.c_void_p()
+        _check(lib().dfsnufft_ensemble_create(
+            G, ai([g[0] for g in self.groups]), ai([g[1] for g in self.groups]),
+            ai([g[2] for g in self.groups]), float(tol), _dtype_code(dtype), self.n_fields,
+            ctypes.c_void_p(int(handle)), ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+
+    def plan_handle(self, g):
+        h = ctypes.c_void_p()
+        _check(lib().dfsnufft_ensemble_plan(self._h, int(g), ctypes.byref(h)))
+        return h
+
+    def run(self, points, coeffs, outs):
+        G = len(self.groups)
+        counts = [np.ascontiguousarray(p[2], dtype=np.int64) for p in points]
+        cptr = (ctypes.c_void_p * G)(*[c.ctypes.data for c in counts])
+        vp = lambda xs: (ctypes.c_void_p * G)(*[x.data_ptr() for x in xs])
+        rc = lib().dfsnufft_ensemble_run(self._h, cptr, vp([p[0] for p in points]),
+                                         vp([p[1] for p in points]), vp(coeffs), vp(outs))
+        self._keep = (counts, points, coeffs, outs)
+        if rc != OK:
+            raise DfsError(rc)
+
+    def check(self):
+        rc = lib().dfsnufft_ensemble_check(self._h)
+        if rc != OK:
+            raise DfsError(rc)
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().dfsnufft_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

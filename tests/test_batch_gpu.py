@@ -1,0 +1,114 @@
+"""Batched plans (members of one grid, each with its own points) and ensembles on
+uneven grids (one CUDA graph per step) against single-member plans and the
+oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_01313_gb300 import build, nufft, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for the -m gpu tests")
+    build.build()
+    return torch
+
+
+def _single(torch, wl):
+    from paper_2605_01313_gb300 import Plan
+    cd = torch.complex128 if wl.dtype == "f64" else torch.complex64
+    with Plan(wl.n_lon, wl.n_lat, wl.tol, wl.dtype, wl.n_fields) as plan:
+        plan.set_points(torch.from_numpy(wl.lon).cuda(), torch.from_numpy(wl.colat).cuda())
+        out = plan.execute(torch.from_numpy(wl.coeffs).to(cd).cuda())
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+def _members(n, n_lon, n_lat, dtype, seed0, ragged=True):
+    wls = []
+    rng = np.random.default_rng(seed0)
+    for k in range(n):
+        wl = synth.workload_member(seed0 + k, n_lon, n_lat, dtype, n_sample=64)
+        if ragged and k % 2:
+            keep = np.sort(rng.choice(wl.n_points, wl.n_points - 37 * k, replace=False))
+            wl = synth.Workload(wl.name, n_lon, n_lat, wl.coeffs, wl.lon[keep], wl.colat[keep],
+                                wl.tol, dtype, sample=np.arange(0, keep.size, 7))
+        wls.append(wl)
+    return wls
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batched_plan_equals_single_plans(torch_cuda, dtype):
+    from paper_2605_01313_gb300 import Plan
+    torch = torch_cuda
+    wls = _members(5, 128, 64, dtype, 500)
+    cd = torch.complex128 if dtype == "f64" else torch.complex64
+    coeffs = torch.from_numpy(np.stack([w.coeffs for w in wls])).to(cd).cuda()
+    lon = torch.from_numpy(np.concatenate([w.lon for w in wls])).cuda()
+    colat = torch.from_numpy(np.concatenate([w.colat for w in wls])).cuda()
+    counts = [w.n_points for w in wls]
+    with Plan(128, 64, wls[0].tol, dtype, 3, n_members=len(wls)) as plan:
+        plan.set_points(lon, colat, counts)
+        out = plan.execute(coeffs)
+        torch.cuda.synchronize()
+        views = [v.cpu().numpy() for v in plan.split_values(out)]
+    bound = 1e-11 if dtype == "f64" else 2e-5
+    for wl, got in zip(wls, views):
+        assert np.array_equal(got, _single(torch, wl))
+        ref = oracle.evaluate(wl.coeffs, wl.lon[wl.sample], wl.colat[wl.sample])
+        for f in range(3):
+            assert oracle.rel_linf(got[f][wl.sample], ref[f].real) <= bound
+
+
+def test_ensemble_graph_uneven_grids(torch_cuda):
+    """Groups of 128x64, 256x128 and 512x256 members in one graph; replays give
+    the same values, and new points re-record the graph."""
+    torch = torch_cuda
+    groups = [(3, 128, 64), (2, 256, 128), (2, 512, 256)]
+    ens = nufft.Ensemble(groups, tol=1e-6, dtype="f32", n_fields=3)
+    all_wls, pts, cfs, outs = [], [], [], []
+    for gi, (m, n_lon, n_lat) in enumerate(groups):
+        wls = _members(m, n_lon, n_lat, "f32", 700 + 10 * gi)
+        all_wls.append(wls)
+        pts.append((torch.from_numpy(np.concatenate([w.lon for w in wls])).cuda(),
+                    torch.from_numpy(np.concatenate([w.colat for w in wls])).cuda(),
+                    [w.n_points for w in wls]))
+        cfs.append(torch.from_numpy(np.stack([w.coeffs for w in wls])).to(torch.complex64).cuda())
+        outs.append(torch.zeros(3 * sum(w.n_points for w in wls), dtype=torch.float32,
+                                device="cuda"))
+    ens.run(pts, cfs, outs)          # runs, then records
+    ens.check()
+    first = [o.cpu().numpy().copy() for o in outs]
+    for o in outs:
+        o.zero_()
+    ens.run(pts, cfs, outs)          # graph replay
+    ens.check()
+    for a, o in zip(first, outs):
+        assert np.array_equal(a, o.cpu().numpy())
+    for wls, vals in zip(all_wls, first):
+        off = 0
+        for wl in wls:
+            got = vals[off:off + 3 * wl.n_points].reshape(3, wl.n_points)
+            off += 3 * wl.n_points
+            assert np.array_equal(got, _single(torch, wl))
+    # other points for the first group: the graph is recorded again
+    wl2 = _members(3, 128, 64, "f32", 900, ragged=False)
+    pts[0] = (torch.from_numpy(np.concatenate([w.lon for w in wl2])).cuda(),
+              torch.from_numpy(np.concatenate([w.colat for w in wl2])).cuda(),
+              [w.n_points for w in wl2])
+    cfs[0] = torch.from_numpy(np.stack([w.coeffs for w in wl2])).to(torch.complex64).cuda()
+    outs[0] = torch.zeros(3 * sum(w.n_points for w in wl2), dtype=torch.float32, device="cuda")
+    ens.run(pts, cfs, outs)
+    ens.check()
+    vals = outs[0].cpu().numpy()
+    off = 0
+    for wl in wl2:
+        got = vals[off:off + 3 * wl.n_points].reshape(3, wl.n_points)
+        off += 3 * wl.n_points
+        assert np.array_equal(got, _single(torch, wl))
+    ens.destroy()
