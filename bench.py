@@ -38,6 +38,7 @@ L2_FLUSH_BYTES = 512 << 20          # written between timed steps (L2 is 126 MB)
 
 WORKLOADS = {
     "c3_2048x1024_f32": ("f32", "c3"),
+    "c4_ensemble_f32": ("f32", "c4"),
     "c3_2048x1024_f64": ("f64", "c3"),
     "c2_512x256_f64": ("f64", "c2"),
     "c2_512x256_f32": ("f32", "c2"),
@@ -49,6 +50,8 @@ DEFAULT_WORKLOAD = "c3_2048x1024_f32"
 def make_workload(name):
     from paper_2605_01313_gb300 import synth
     dtype, kind = WORKLOADS[name]
+    if kind == "c4":
+        return synth.workload_c4()
     if kind == "c3":
         return synth.workload_c3(dtype)
     if kind == "c2":
@@ -339,6 +342,8 @@ def run_ours(args):
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], line["error"] = cpu_baseline(wl, out.cpu().numpy(), args.cpu_seconds)
     plan.destroy()
+    if ws == 1 and args.serve_seconds > 0:
+        line["serving"] = serving_sweep(dev, [100, 500, 1000, 2000, 5000], args.serve_seconds)
     print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -373,6 +378,179 @@ def cpu_baseline(wl, gpu_vals, seconds):
                   "points_checked": int(n)}
 
 
+# ------------------------------------------------------------------ ensemble and serving
+
+def run_ensemble(args):
+    """64 members on four grids, three FP32 fields each: one CUDA graph per step."""
+    import torch
+    from paper_2605_01313_gb300 import nufft
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    members = make_workload(args.workload)
+    groups, pts, cfs, outs, host_in, host_out = [], [], [], [], [], []
+    by_size = {}
+    for wl in members:
+        by_size.setdefault((wl.n_lon, wl.n_lat), []).append(wl)
+    total_pf = 0
+    for (n_lon, n_lat), wls in sorted(by_size.items()):
+        groups.append((len(wls), n_lon, n_lat))
+        lon = np.concatenate([w.lon for w in wls])
+        colat = np.concatenate([w.colat for w in wls])
+        coef = np.stack([w.coeffs for w in wls]).astype(np.complex64)
+        pts.append((torch.from_numpy(lon).to(dev), torch.from_numpy(colat).to(dev),
+                    [w.n_points for w in wls]))
+        cfs.append(torch.from_numpy(coef).to(dev))
+        outs.append(torch.empty(3 * lon.size, dtype=torch.float32, device=dev))
+        host_in.append(tuple(torch.from_numpy(a).pin_memory() for a in (lon, colat, coef)))
+        host_out.append(torch.empty(3 * lon.size, dtype=torch.float32).pin_memory())
+        total_pf += 3 * lon.size
+    stream = torch.cuda.current_stream(dev)
+    ens = nufft.Ensemble(groups, tol=1e-6, dtype="f32", n_fields=3, stream=stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        ens.run(pts, cfs, outs)
+    ens.check()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    sampler = ClockSampler(("GPU-" + str(uuid)) if uuid else None)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    for i in range(args.steps):
+        flush.fill_(i & 255)
+        ev[i][0].record(stream)
+        ens.run(pts, cfs, outs)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ens.check()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * total_pf * args.steps / (total_ms * 1e-3)
+    # end to end: pinned host inputs in, values out, inside the timed region
+    e2e_ms = []
+    for i in range(max(3, min(args.steps, 8))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for g in range(len(groups)):
+            pts[g][0].copy_(host_in[g][0], non_blocking=True)
+            pts[g][1].copy_(host_in[g][1], non_blocking=True)
+            cfs[g].copy_(host_in[g][2], non_blocking=True)
+        ens.run(pts, cfs, outs)
+        for g in range(len(groups)):
+            host_out[g].copy_(outs[g], non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = sum(sum(t.numel() * t.element_size() for t in hi) for hi in host_in)
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+    # algorithmic bytes of every stage of every group, one step
+    step_bytes = 0
+    for gi, (m, n_lon, n_lat) in enumerate(groups):
+        prm = nufft.dfsnufft_plan_get_params(ens.plan_handle(gi))
+        st = nufft.dfsnufft_plan_point_stats(ens.plan_handle(gi))
+        step_bytes += sum(stage_bytes(prm, 3 * m, sum(pts[gi][2]), st["rows_needed"]).values())
+    pk, pk_kind = peaks()
+    achieved = step_bytes / (total_ms / args.steps * 1e-3) / 1e9
+    if rank != 0:
+        ens.destroy()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload,
+                   "groups": ["%dx(%dx%d)" % g for g in groups], "fields": 3,
+                   "members": sum(g[0] for g in groups), "point_fields": total_pf, "tol": 1e-6,
+                   "graph": "one CUDA graph launch per step (fork/join over group streams)",
+                   "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": {"kernel": "whole step (all stages, all groups)", "bound": "hbm",
+                     "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "peak_source": "%s hbm_gbs" % pk_kind,
+                     "traffic": None},
+        "gpu_launches": 6 * len(groups) * args.steps,
+        "e2e": {"value": total_pf / (np.mean(e2e_ms) * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": float(np.mean(e2e_ms))},
+        "clocks": clocks,
+    }
+    ens.destroy()
+    print(json.dumps(line), flush=True)
+
+
+def serving_sweep(dev, rates, seconds, budget_gb=120):
+    """Poisson request streams (grid uniform over five sizes, three FP32 fields,
+    inputs resident on the device) through the continuous-batching server, and
+    the same requests per call through FP64 plans."""
+    import torch
+    from paper_2605_01313_gb300 import Plan, synth
+    from paper_2605_01313_gb300.serve import Server, poisson_run
+    reqs, reqs64 = [], []
+    for gi, (n_lon, n_lat) in enumerate(synth.SERVE_GRIDS):
+        for j in range(2):
+            wl = synth.workload_member(5 + 10 * gi + j, n_lon, n_lat, "f32", n_sample=8)
+            base = {"n_lon": n_lon, "n_lat": n_lat, "pf": 3 * wl.n_points,
+                    "lon": torch.from_numpy(wl.lon).to(dev),
+                    "colat": torch.from_numpy(wl.colat).to(dev)}
+            r = dict(base, coeffs=torch.from_numpy(wl.coeffs).to(torch.complex64).to(dev),
+                     values=torch.empty((3, wl.n_points), dtype=torch.float32, device=dev))
+            reqs.append(r)
+            reqs64.append(dict(base, coeffs=torch.from_numpy(wl.coeffs).to(dev),
+                               values=torch.empty((3, wl.n_points), dtype=torch.float64,
+                                                  device=dev)))
+    order = np.random.default_rng(55).permutation(len(reqs))
+    reqs = [reqs[i] for i in order]
+    reqs64 = [reqs64[i] for i in order]
+    srv = Server(tol=1e-6, dtype="f32", n_fields=3, hbm_budget=int(budget_gb) << 30, max_batch=8)
+    poisson_run(srv, reqs, 200, 0.5, seed=1)        # warm: slots created, plans resident
+    out = []
+    for k, rate in enumerate(rates):
+        lat, pf, wall, n = poisson_run(srv, reqs, rate, seconds, seed=10 + k)
+        out.append({"rate": rate, "requests": n, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                    "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                    "value": pf / wall})
+    stats = srv.stats()
+    srv.close()
+    # FP64, one request at a time (plans cached per grid)
+    plans = {}
+    stream = torch.cuda.current_stream(dev)
+    for r in reqs64:
+        key = (r["n_lon"], r["n_lat"])
+        if key not in plans:
+            plans[key] = Plan(r["n_lon"], r["n_lat"], 1e-12, "f64", 3, stream=stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    pf64, n64 = 0, 0
+    while time.perf_counter() - t0 < seconds:
+        r = reqs64[n64 % len(reqs64)]
+        p = plans[(r["n_lon"], r["n_lat"])]
+        p.set_points(r["lon"], r["colat"])
+        p.execute(r["coeffs"], r["values"])
+        torch.cuda.synchronize(dev)
+        pf64 += r["pf"]
+        n64 += 1
+    fp64 = {"value": pf64 / (time.perf_counter() - t0), "requests": n64, "tol": 1e-12}
+    for p in plans.values():
+        p.destroy()
+    return {"unit": UNIT, "dtype": "f32", "tol": 1e-6, "budget_gb": budget_gb, "max_batch": 8,
+            "grids": ["%dx%d" % g for g in synth.SERVE_GRIDS], "sweep": out,
+            "batches": stats["batches"], "requests_batched": stats["members"],
+            "slots": stats["slots"], "fp64_per_call": fp64}
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args):
@@ -380,27 +558,41 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    wl = make_workload(args.workload)
+    wls = make_workload(args.workload)
+    if not isinstance(wls, list):
+        wls = [wls]
+    wl = wls[-1]
     per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
-    n = _oracle_sample_size(wl, per_step)
+    # points per step, spread over the members (largest grid sets the cost)
+    n = max(len(wls), _oracle_sample_size(wl, per_step))
     times = []
+    pf = 0
     for i in range(args.warmup + args.steps):
-        s = wl.sample[(i * n) % wl.sample.size:][:n]
-        if s.size < n:
-            s = wl.sample[:n]
-        t0 = time.perf_counter()
-        oracle.evaluate(wl.coeffs, wl.lon[s], wl.colat[s])
+        t_step = 0.0
+        pf_step = 0
+        for j, w in enumerate(wls):
+            k = n // len(wls) + (1 if j < n % len(wls) else 0)
+            if k == 0:
+                continue
+            s = w.sample[(i * k) % w.sample.size:][:k]
+            if s.size < k:
+                s = w.sample[:k]
+            t0 = time.perf_counter()
+            oracle.evaluate(w.coeffs, w.lon[s], w.colat[s])
+            t_step += time.perf_counter() - t0
+            pf_step += s.size * w.n_fields
         if i >= args.warmup:
-            times.append(time.perf_counter() - t0)
+            times.append(t_step)
+            pf += pf_step
     total = sum(times)
-    value = args.steps * n * wl.n_fields / total
+    value = pf / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": "%dx%d" % (wl.n_lon, wl.n_lat),
-                   "fields": wl.n_fields, "points": wl.n_points},
+                   "members": len(wls), "fields": wl.n_fields, "points": wl.n_points},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
                          "kind": "oracle",
                          "sample": "%d points x %d fields per step, FP64 direct sum"
@@ -419,6 +611,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="seconds per rate of the serving sweep in the default run (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -433,7 +627,10 @@ def main():
     else:
         from paper_2605_01313_gb300 import build
         build.build()
-        run_ours(args)
+        if WORKLOADS[args.workload][1] == "c4":
+            run_ensemble(args)
+        else:
+            run_ours(args)
 
 
 if __name__ == "__main__":

@@ -146,6 +146,56 @@ int dfsnufft_ensemble_plan(dfsnufft_ensemble ens, int group, dfsnufft_plan *out)
 
 int dfsnufft_ensemble_destroy(dfsnufft_ensemble ens);
 
+/* ---- serving: continuous batching under an HBM budget ------------------- */
+
+/* One member's interpolation step: its grid, n_points departure points and
+ * n_fields coefficient arrays (device pointers, layouts as for a one-member
+ * plan), and a device buffer of n_fields x n_points values to fill.  The
+ * buffers must stay valid until the request completes. */
+typedef struct {
+    int n_lon, n_lat;
+    int64_t n_points;
+    const double *lon;
+    const double *colat;
+    const void *coeffs;
+    void *values;
+} dfsnufft_request;
+
+typedef struct {
+    int64_t submitted, completed;   /* requests                                   */
+    int64_t batches, members;       /* batched launches and requests they carried */
+    int slots;                      /* live slots (stream + batched plan + staging) */
+    int64_t reserved_bytes;         /* device bytes the slots hold                */
+    int64_t budget_bytes;           /* the HBM budget                             */
+} dfsnufft_server_stats;
+
+typedef struct dfsnufft_server_s *dfsnufft_server;
+
+/* A server for requests of any grid at tolerance tol, precision dtype, with
+ * n_fields fields each.  A dispatcher thread groups queued requests by grid and
+ * launches up to max_batch of one grid as one batched plan execution on a free
+ * slot; slots are created while the device memory they need fits hbm_budget
+ * (bytes) and are kept for reuse.  Requests arriving while others run are
+ * admitted as soon as a slot frees up, so their work overlaps on the device.
+ * Uses the device current at creation. */
+int dfsnufft_server_create(double tol, int dtype, int n_fields, int64_t hbm_budget,
+                           int max_batch, dfsnufft_server *out);
+
+/* Queue a request (thread-safe; returns at once with a ticket). */
+int dfsnufft_server_submit(dfsnufft_server srv, const dfsnufft_request *req, int64_t *ticket);
+
+/* Wait up to timeout_s seconds for a ticket: *status is the request's outcome
+ * (DFSNUFFT_OK, or DFSNUFFT_ERR_OOM when no slot for its grid can ever fit the
+ * budget, or a CUDA error), *latency_s the time from submit to completion.
+ * Returns DFSNUFFT_ERR_TIMEOUT if the request is still running. */
+int dfsnufft_server_wait(dfsnufft_server srv, int64_t ticket, double timeout_s, int *status,
+                         double *latency_s);
+
+int dfsnufft_server_stats_get(dfsnufft_server srv, dfsnufft_server_stats *out);
+
+/* Finish queued and running requests, then release every slot. */
+int dfsnufft_server_destroy(dfsnufft_server srv);
+
 /* Evaluate all n_fields series at the plan's points (Eq. 5.3).
  *   coeffs : device pointer, (n_members x) n_fields x N2 x N1 complex (see conventions).
  *   values : device pointer, (members back to back) n_fields x n_points real,

@@ -38,6 +38,8 @@ EXPORTS = (
     "dfsnufft_es_horner", "dfsnufft_plan_create_batch", "dfsnufft_set_points_batch",
     "dfsnufft_ensemble_create", "dfsnufft_ensemble_run", "dfsnufft_ensemble_check",
     "dfsnufft_ensemble_plan", "dfsnufft_ensemble_destroy",
+    "dfsnufft_server_create", "dfsnufft_server_submit", "dfsnufft_server_wait",
+    "dfsnufft_server_stats_get", "dfsnufft_server_destroy",
 )
 N_STAGES = 4
 STAGES = ("set_points", "theta_pass", "phi_pass", "interp")
@@ -48,6 +50,21 @@ class Params(ctypes.Structure):
                 ("N2", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int),
                 ("w", ctypes.c_int), ("beta", ctypes.c_double), ("tol", ctypes.c_double),
                 ("dtype", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n_lon", ctypes.c_int), ("n_lat", ctypes.c_int), ("n_points", ctypes.c_int64),
+                ("lon", ctypes.c_void_p), ("colat", ctypes.c_void_p), ("coeffs", ctypes.c_void_p),
+                ("values", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("members", ctypes.c_int64), ("slots", ctypes.c_int),
+                ("reserved_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +106,11 @@ def lib():
         L.dfsnufft_ensemble_check.argtypes = [vp]
         L.dfsnufft_ensemble_plan.argtypes = [vp, i32, ctypes.POINTER(vp)]
         L.dfsnufft_ensemble_destroy.argtypes = [vp]
+        L.dfsnufft_server_create.argtypes = [f64, i32, i32, i64, i32, ctypes.POINTER(vp)]
+        L.dfsnufft_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(i64)]
+        L.dfsnufft_server_wait.argtypes = [vp, i64, f64, ctypes.POINTER(i32), ctypes.POINTER(f64)]
+        L.dfsnufft_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.dfsnufft_server_destroy.argtypes = [vp]
         L.dfsnufft_set_points.argtypes = [vp, i64, vp, vp]
         L.dfsnufft_set_points_host.argtypes = [vp, i64, vp, vp]
         L.dfsnufft_execute.argtypes = [vp, vp, vp]
