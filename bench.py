@@ -191,6 +191,24 @@ def profile_traffic(kernel, workload):
     return None
 
 
+def max_over_ranks(x, ws, device="cpu"):
+    """Largest value of x over the ranks of the default process group (x itself
+    for one rank).  NCCL needs a CUDA device; gloo runs on the CPU."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(ws, units_per_rank_step, steps, max_total_ms):
+    """Whole-job throughput: every rank processes its own replica of the
+    workload; the job's time is the slowest rank's."""
+    return ws * units_per_rank_step * steps / (max_total_ms * 1e-3)
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args):
@@ -253,12 +271,8 @@ def run_ours(args):
     total_ms = sum(step_ms)
     stage = nufft.dfsnufft_plan_read_timing(plan._h)
     nufft.dfsnufft_plan_enable_timing(plan._h, False)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * F * P * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(total_ms, ws, dev)
+    value = weak_scaling_value(ws, F * P, args.steps, total_ms)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -277,13 +291,8 @@ def run_ours(args):
         plan.set_points_host(h_lon, h_colat)
         plan.execute_host(h_coef, h_out)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = sum(e2e_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = ws * F * P * e2e_steps / (e2e_total * 1e-3)
+    e2e_total = max_over_ranks(sum(e2e_ms), ws, dev)
+    e2e_value = weak_scaling_value(ws, F * P, e2e_steps, e2e_total)
     h2d = 2 * 8 * P + h_coef.nbytes
     d2h = h_out.nbytes
     assert np.array_equal(h_out, out.cpu().numpy()), "host and device paths disagree"
@@ -431,13 +440,8 @@ def run_ensemble(args):
     clocks = sampler.stop()
     ens.check()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * total_pf * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
+    value = weak_scaling_value(ws, total_pf, args.steps, total_ms)
     # end to end: pinned host inputs in, values out, inside the timed region
     e2e_ms = []
     for i in range(max(3, min(args.steps, 8))):
