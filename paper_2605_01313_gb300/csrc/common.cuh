@@ -1,6 +1,7 @@
 // Internal definitions shared by the dfsnufft translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -61,6 +62,9 @@ struct dfsnufft_plan_s {
     int64_t max_member_points;  // largest member's point count
     int *d_status;              // device status word (DFS_STATUS_*), zero when healthy
     int num_sms;                // multiprocessors of the plan's device
+    CUtensorMap tmap_G;         // 2-D map of d_G (8-byte elements), box set by the interpolation
+    int tmap_G_ok;              // tmap_G is valid (FP32 plans that own their buffers)
+    int interp_ctas_per_sm;     // resident CTAs of the TMA interpolation (0: not yet known)
 
     // point data (capacity grows with set_points)
     int64_t n_points, cap_points;   // all members' points

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(MAXT, 1)
                 const typename CxT<R>::type *__restrict__ stw, const int2 *__restrict__ rowrange,
                 typename CxT<R>::type *__restrict__ out, int *__restrict__ status) {
     typedef typename CxT<R>::type C;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     // TMA destinations start on 128-byte boundaries (base rounded up here;
     // buffer and box sizes are multiples of 128 bytes by construction)
     unsigned char *base = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
@@ -93,7 +93,6 @@ __global__ void __launch_bounds__(MAXT, 1)
     C *inb = reinterpret_cast<C *>(base + 128);
     C *ex = inb + (size_t)a.nbuf * a.in_elems;
     const int H = LOGH ? (1 << LOGH) : (a.n2 >> 1);
-    const int T = H / E;
     R *f2 = reinterpret_cast<R *>(ex + (size_t)CB * region_len<C>(H));   // 1 / phihat2, N2 rows
     const int c = threadIdx.x % CB;
     const int t = threadIdx.x / CB;

@@ -10,10 +10,16 @@
 //
 // The weights are real, so only the real part of the fine grid is read (the
 // phi pass stores nothing else).  Points arrive sorted by bin (tile_x x tile_y
-// fine cells); one CTA takes a bin, stages the bin's tile plus its halo of
-// every field into shared memory with coalesced loads, and each thread then
-// evaluates one point at a time from shared memory, computing its 2w kernel
-// values once for all fields.
+// fine cells); a CTA takes a bin, has the bin's tile plus its halo of every
+// field in shared memory, and each thread then evaluates one point at a time
+// from shared memory, computing its 2w kernel values once for all fields.
+//
+// FP32 plans run k_interp_tma: persistent CTAs walk their bins with the next
+// bin's tiles arriving by TMA (one 2-D box per field) while the current bin is
+// evaluated; the few bins whose tile wraps around the torus seam are staged
+// with plain loads instead.  k_interp_f32 (plain loads, the same arithmetic)
+// serves plans without a tensor map, and k_interp the FP64 form and wide
+// kernels.
 #include "common.cuh"
 #include "tma.cuh"
 
@@ -24,6 +30,8 @@ struct InterpArgs {
     int tile_x, tile_y, nbx;
     int c0;
     int F, FG;            // fields per member, fields staged per pass
+    int NG;               // field groups per bin, ceil(F / FG)
+    int BW, box_f;        // TMA box width (cells, multiple of 4), floats per staged box
     int bstride;          // per-member stride of the bin arrays
 };
 
@@ -121,6 +129,24 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const __grid_const
     }
 }
 
+// Weights of one FP32 point for the paired reads: wy[W] and the x weights
+// shifted by the parity of the first tap into a zero-padded vector w8[WP].
+template <int W>
+__device__ __forceinline__ void paired_weights(float tx, float ty, int odd,
+                                               const Horner<float, W> &hw, float *w8,
+                                               float *wy) {
+    constexpr int WP = (W + 2) & ~1;
+    float wx[W];
+    es_weights<float, W>(tx, hw, wx);
+    es_weights<float, W>(ty, hw, wy);
+#pragma unroll
+    for (int k = 0; k < WP; ++k) {
+        const float lo = k < W ? wx[k] : 0.f;
+        const float hi = (k >= 1 && k - 1 < W) ? wx[k - 1] : 0.f;
+        w8[k] = odd ? hi : lo;
+    }
+}
+
 // FP32 form: the tile starts at an even column and each stencil row is read as
 // WP/2 aligned pairs of cells (8-byte shared loads).  Neighbouring points of
 // the departure grid sit about two cells apart, so a warp's loads fall on
@@ -197,17 +223,10 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a,
             __syncthreads();
             for (int pi = s + threadIdx.x; pi < e; pi += blockDim.x) {
                 const int2 b = base[pi];
-                float wx[W], wy[W], w8[WP];
-                es_weights<float, W>(frac[2 * pi], hw, wx);
-                es_weights<float, W>(frac[2 * pi + 1], hw, wy);
                 const int ox = b.x - col0;
                 const int odd = ox & 1;
-#pragma unroll
-                for (int k = 0; k < WP; ++k) {
-                    const float lo = k < W ? wx[k] : 0.f;
-                    const float hi = (k >= 1 && k - 1 < W) ? wx[k - 1] : 0.f;
-                    w8[k] = odd ? hi : lo;
-                }
+                float wy[W], w8[WP];
+                paired_weights<W>(frac[2 * pi], frac[2 * pi + 1], odd, hw, w8, wy);
                 const int oy = b.y - row0;
                 const int dst = idx[pi];
                 for (int ff = 0; ff < fg; ++ff) {
@@ -231,9 +250,168 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a,
     }
 }
 
+// FP32 with TMA staging.  grid (CTAs per member, members); CTA i of member k
+// takes sub-tasks i, i + gridDim.x, ... of the member, a sub-task being one
+// non-empty bin and one group of FG fields.  Two stages: while sub-task j is
+// evaluated from stage j & 1, the boxes of sub-task j + gridDim.x land in the
+// other stage (issued by thread 0 after the barrier that ends sub-task j - 1's
+// reads of it).  A box starts at the bin's first stencil column rounded down
+// to 4 cells (16 bytes, the TMA alignment rule), so a point's first tap sits
+// at column ox in [0, tile_x + 2] of the box and its paired reads end below
+// tile_x + 2 + WP <= BW.  A box that would leave [0, n1) x [0, n2) (a bin at
+// the torus seam) is not copied by TMA: its barrier phase completes on the
+// issuing thread's arrival alone, and the CTA stages the tile with wrapped
+// plain loads.  A wait that runs out (about a second) sets the status word to
+// DFS_STATUS_TIMEOUT and ends the CTA after its copies land.
+template <int W>
+__global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
+                                                    const __grid_constant__ Horner<float, W> hw,
+                                                    const __grid_constant__ CUtensorMap gmap,
+                                                    const float *__restrict__ grid,
+                                                    const int2 *__restrict__ base,
+                                                    const float *__restrict__ frac,
+                                                    const int *__restrict__ idx,
+                                                    const int *__restrict__ bin_start_all,
+                                                    const int *__restrict__ task_all,
+                                                    const int *__restrict__ n_tasks,
+                                                    const int *__restrict__ pofs,
+                                                    float *__restrict__ out_all,
+                                                    int *__restrict__ status) {
+    constexpr int WP = (W + 2) & ~1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *sb = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sb);
+    float *stage = reinterpret_cast<float *>(sb + 128);
+    const int TH = a.tile_y + W - 1;
+    const int Q = a.BW / 2;                   // pairs per box row
+    const int k = blockIdx.y;
+    const int p0 = pofs[k];
+    const int Pk = pofs[k + 1] - p0;
+    const int total = n_tasks[k] * a.NG;
+    const int *task_bin = task_all + (size_t)k * a.bstride;
+    const int *bin_start = bin_start_all + (size_t)k * a.bstride;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const unsigned box_bytes = (unsigned)(a.BW * TH * 4);
+    auto wraps = [&](int col0, int row0) {
+        return col0 < 0 || col0 + a.BW > a.n1 || row0 < 0 || row0 + TH > a.n2;
+    };
+    auto issue = [&](int sub, int b) {
+        const int task = sub / a.NG;
+        const int f0 = (sub - task * a.NG) * a.FG;
+        const int fg = min(a.FG, a.F - f0);
+        const int bin = task_bin[task];
+        const int by = bin / a.nbx;
+        const int bx = bin - by * a.nbx;
+        const int col0 = (bx * a.tile_x - a.c0) & ~3;
+        const int row0 = by * a.tile_y - a.c0;
+        if (wraps(col0, row0)) {
+            mbar_arrive_expect_tx(&bar[b], 0);
+            return;
+        }
+        float *dst = stage + (size_t)b * a.FG * a.box_f;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar[b], box_bytes * fg);
+        for (int ff = 0; ff < fg; ++ff)
+            tma_load_2d(dst + (size_t)ff * a.box_f, &gmap, col0 >> 1,   // 8-byte units
+                        (k * a.F + f0 + ff) * a.n2 + row0, &bar[b]);
+    };
+    uint32_t ph0 = 0, ph1 = 0;
+    int it = 0;
+    if (threadIdx.x == 0 && (int)blockIdx.x < total) issue(blockIdx.x, 0);
+    for (int sub = blockIdx.x; sub < total; sub += gridDim.x, ++it) {
+        const int cur = it & 1;
+        const int nxt = sub + gridDim.x;
+        if (threadIdx.x == 0 && nxt < total) issue(nxt, cur ^ 1);
+        // geometry and the first point's record, fetched while the boxes land
+        const int task = sub / a.NG;
+        const int f0 = (sub - task * a.NG) * a.FG;
+        const int fg = min(a.FG, a.F - f0);
+        const int bin = task_bin[task];
+        const int by = bin / a.nbx;
+        const int bx = bin - by * a.nbx;
+        const int col0 = (bx * a.tile_x - a.c0) & ~3;
+        const int row0 = by * a.tile_y - a.c0;
+        const int s = p0 + bin_start[bin];
+        const int e = p0 + bin_start[bin + 1];
+        int pi = s + threadIdx.x;
+        int2 b = make_int2(0, 0);
+        float2 t = make_float2(0.f, 0.f);
+        int dst = 0;
+        if (pi < e) {
+            b = base[pi];
+            t = reinterpret_cast<const float2 *>(frac)[pi];
+            dst = idx[pi];
+        }
+        const bool ok = mbar_wait_bounded(&bar[cur], cur ? ph1 : ph0);
+        if (cur) ph1 ^= 1;
+        else ph0 ^= 1;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(status, DFS_STATUS_TIMEOUT);
+                mbar_wait_bounded(&bar[cur], cur ? ph1 ^ 1 : ph0 ^ 1);
+                if (nxt < total) mbar_wait_bounded(&bar[cur ^ 1], cur ? ph0 : ph1);
+            }
+            __syncthreads();
+            return;
+        }
+        float *tile = stage + (size_t)cur * a.FG * a.box_f;
+        if (wraps(col0, row0)) {
+            // seam bin: the same box, gathered with indices taken mod n
+            const int nq = fg * TH * Q;
+            for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+                const int rr = i / Q;
+                const int qq = i - rr * Q;
+                const int ff = rr / TH;
+                const int r = rr - ff * TH;
+                const int gr = (row0 + r) & (a.n2 - 1);
+                const int gc = (col0 + 2 * qq) & (a.n1 - 1);
+                *reinterpret_cast<float2 *>(tile + (size_t)ff * a.box_f + r * a.BW + 2 * qq) =
+                    *reinterpret_cast<const float2 *>(
+                        grid + ((size_t)(k * a.F + f0 + ff) * a.n2 + gr) * a.n1 + gc);
+            }
+            __syncthreads();
+        }
+        while (pi < e) {
+            const int ox = b.x - col0;
+            const int odd = ox & 1;
+            float w8[WP], wy[W];
+            paired_weights<W>(t.x, t.y, odd, hw, w8, wy);
+            const int oy = b.y - row0;
+            const int d = dst;
+            pi += blockDim.x;
+            if (pi < e) {                      // next record in flight during the sums
+                b = base[pi];
+                t = reinterpret_cast<const float2 *>(frac)[pi];
+                dst = idx[pi];
+            }
+            for (int ff = 0; ff < fg; ++ff) {
+                const float2 *tp = reinterpret_cast<const float2 *>(
+                    tile + (size_t)ff * a.box_f + oy * a.BW + (ox - odd));
+                float acc = 0.f;
+#pragma unroll
+                for (int bb = 0; bb < W; ++bb) {
+                    float rr = 0.f;
+#pragma unroll
+                    for (int kk = 0; kk < WP / 2; ++kk) {
+                        const float2 g = tp[bb * Q + kk];
+                        rr += w8[2 * kk] * g.x + w8[2 * kk + 1] * g.y;
+                    }
+                    acc += wy[bb] * rr;
+                }
+                out_all[(size_t)a.F * p0 + (size_t)(f0 + ff) * Pk + d] = acc;
+            }
+        }
+        __syncthreads();                       // stage cur is free for sub-task + 2 gridDim.x
+    }
+}
+
 template <typename R, int W>
 cudaError_t launch_w(dfsnufft_plan p, void *values) {
-    typedef typename CxT<R>::type C;
     const dfsnufft_params &q = p->prm;
     InterpArgs a;
     a.n1 = q.n1;
@@ -244,6 +422,9 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
     a.c0 = p->c0;
     a.F = p->n_fields;
     a.bstride = p->bstride;
+    a.NG = 1;
+    a.BW = 0;
+    a.box_f = 0;
     Horner<R, W> hw;
     {
         double hc[W * (W + 1)];
@@ -251,9 +432,76 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
         for (int i = 0; i < W; ++i)
             for (int k = 0; k <= W; ++k) hw.c[i][k] = (R)hc[i * (W + 1) + k];
     }
-    // FP32: paired loads, tile rows of at most 32 pairs
-    const bool pair = sizeof(R) == 4 && W <= 8 && (q.tile_x + ((W + 2) & ~1)) / 2 <= 32;
-    const int tw = pair ? q.tile_x + ((W + 2) & ~1) : q.tile_x + W - 1;
+    const int M = p->n_members;
+    constexpr int WP = (W + 2) & ~1;
+    if constexpr (sizeof(R) == 4 && W <= 8) {
+        Horner<float, W> hf;
+        for (int i = 0; i < W; ++i)
+            for (int k = 0; k <= W; ++k) hf.c[i][k] = (float)hw.c[i][k];
+        // TMA form: plans that own their buffers (status word, fixed d_G)
+        const int TH = q.tile_y + W - 1;
+        const int BW = (q.tile_x + WP + 2 + 3) & ~3;
+        if (p->d_status && BW / 2 <= 256 && TH <= 256) {
+            if (!p->tmap_G_ok) {
+                if (dfs_encode_tensor_map_2d(&p->tmap_G, p->d_G, (uint64_t)(q.n1 / 2),
+                                             (uint64_t)M * a.F * q.n2,
+                                             (uint64_t)q.n1 * sizeof(float), (uint32_t)(BW / 2),
+                                             (uint32_t)TH) == cudaSuccess)
+                    p->tmap_G_ok = 1;
+            }
+            if (p->tmap_G_ok) {
+                a.BW = BW;
+                a.box_f = (BW * TH + 31) & ~31;           // 128-byte aligned boxes
+                // fields per stage: two stages within about 26 KB
+                int fg = (13 * 1024) / (a.box_f * 4);
+                if (fg < 1) fg = 1;
+                if (fg > a.F) fg = a.F;
+                a.FG = fg;
+                a.NG = (a.F + fg - 1) / fg;
+                const size_t smem = 128 + 128 + 2 * (size_t)fg * a.box_f * sizeof(float);
+                cudaError_t e = dfs_allow_smem((const void *)k_interp_tma<W>, smem);
+                if (e) return e;
+                if (p->interp_ctas_per_sm <= 0) {
+                    int occ = 0;
+                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_interp_tma<W>, 128,
+                                                                      smem) != cudaSuccess ||
+                        occ < 1)
+                        occ = 1;
+                    p->interp_ctas_per_sm = occ;
+                }
+                int64_t want = ((int64_t)p->num_sms * p->interp_ctas_per_sm + M - 1) / M;
+                const int64_t cap = (int64_t)p->nbins * a.NG;
+                if (want > cap) want = cap;
+                if (want < 1) want = 1;
+                k_interp_tma<W><<<dim3((unsigned)want, M), 128, smem, p->stream>>>(
+                    a, hf, p->tmap_G, (const float *)p->d_G, p->d_base,
+                    (const float *)p->d_frac, p->d_idx,
+                    p->d_bin_start, p->d_task_bin, p->d_n_tasks, p->d_pofs, (float *)values,
+                    p->d_status);
+                return cudaGetLastError();
+            }
+        }
+        // plain loads: tile rows of at most 32 pairs
+        if ((q.tile_x + WP) / 2 <= 32) {
+            const int tw = q.tile_x + WP;
+            const size_t per_field = sizeof(float) * (size_t)TH * tw;
+            int fg = (int)((96 * 1024) / per_field);
+            if (fg < 1) fg = 1;
+            if (fg > a.F) fg = a.F;
+            a.FG = fg;
+            const size_t smem = per_field * fg;
+            int per = (152 * 16 + M - 1) / M;
+            if (per > p->nbins) per = p->nbins;
+            if (per < 1) per = 1;
+            cudaError_t e = dfs_allow_smem((const void *)k_interp_f32<W>, smem);
+            if (e) return e;
+            k_interp_f32<W><<<dim3(per, M), 128, smem, p->stream>>>(
+                a, hf, (const float *)p->d_G, p->d_base, (const float *)p->d_frac, p->d_idx,
+                p->d_bin_start, p->d_task_bin, p->d_n_tasks, p->d_pofs, (float *)values);
+            return cudaGetLastError();
+        }
+    }
+    const int tw = q.tile_x + W - 1;
     const size_t per_field = sizeof(R) * (size_t)(q.tile_y + W - 1) * tw;
     int fg = (int)((96 * 1024) / per_field);
     if (fg < 1) fg = 1;
@@ -261,27 +509,15 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
     a.FG = fg;
     const size_t smem = per_field * fg;
     // blocks per member: enough to fill the GPU across all members
-    int per = (152 * 16 + p->n_members - 1) / p->n_members;
+    int per = (152 * 16 + M - 1) / M;
     if (per > p->nbins) per = p->nbins;
     if (per < 1) per = 1;
-    const dim3 blocks(per, p->n_members);
-    if (pair) {
-        cudaError_t e = dfs_allow_smem((const void *)k_interp_f32<W>, smem);
-        if (e) return e;
-        Horner<float, W> hf;
-        for (int i = 0; i < W; ++i)
-            for (int k = 0; k <= W; ++k) hf.c[i][k] = (float)hw.c[i][k];
-        k_interp_f32<W><<<blocks, 128, smem, p->stream>>>(
-            a, hf, (const float *)p->d_G, p->d_base, (const float *)p->d_frac, p->d_idx,
-            p->d_bin_start, p->d_task_bin, p->d_n_tasks, p->d_pofs, (float *)values);
-    } else {
-        cudaError_t e = dfs_allow_smem((const void *)k_interp<R, W>, smem);
-        if (e) return e;
-        const int threads = sizeof(R) == 4 ? 128 : 256;
-        k_interp<R, W><<<blocks, threads, smem, p->stream>>>(
-            a, hw, (const R *)p->d_G, p->d_base, (const R *)p->d_frac, p->d_idx, p->d_bin_start,
-            p->d_task_bin, p->d_n_tasks, p->d_pofs, (R *)values);
-    }
+    cudaError_t e = dfs_allow_smem((const void *)k_interp<R, W>, smem);
+    if (e) return e;
+    const int threads = sizeof(R) == 4 ? 128 : 256;
+    k_interp<R, W><<<dim3(per, M), threads, smem, p->stream>>>(
+        a, hw, (const R *)p->d_G, p->d_base, (const R *)p->d_frac, p->d_idx, p->d_bin_start,
+        p->d_task_bin, p->d_n_tasks, p->d_pofs, (R *)values);
     return cudaGetLastError();
 }
 

@@ -126,8 +126,8 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     p.n_fields = n_fields;
     p.stream = (cudaStream_t)stream;
     p.c0 = (prm.w % 2 == 0) ? prm.w / 2 - 1 : (prm.w - 1) / 2;
-    p.nbx = prm.n1 / prm.tile_x + 1;
-    p.nby = prm.n2 / prm.tile_y + 1;
+    p.nbx = prm.n1 / prm.tile_x;    // base cells lie in [0, n): no wrap bin
+    p.nby = prm.n2 / prm.tile_y;
     p.nbins = p.nbx * p.nby;
     p.bstride = (p.nbins + 4) & ~3;
     p.n_members = 1;
@@ -189,19 +189,15 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
                       ds.dtype == dtype && ds.beta == prm.beta;
     if (!same) {
         ds.have_tables = 0;
-        cudaError_t e;
-        if ((e = upload_factors(prm, dtype, prm.n1, prm.N1, p.d_inv1, p.stream)) ||
-            (e = upload_factors(prm, dtype, prm.n2, prm.N2, p.d_inv2, p.stream)))
-            return DFSNUFFT_ERR_CUDA;
-        if (dtype == DFSNUFFT_F64) {
-            if ((e = upload_twiddles<double2, double>(prm.n1, p.d_tw1, p.stream)) ||
-                (e = upload_twiddles<double2, double>(prm.n2, p.d_tw2, p.stream)))
-                return DFSNUFFT_ERR_CUDA;
-        } else {
-            if ((e = upload_twiddles<float2, float>(prm.n1, p.d_tw1, p.stream)) ||
-                (e = upload_twiddles<float2, float>(prm.n2, p.d_tw2, p.stream)))
-                return DFSNUFFT_ERR_CUDA;
-        }
+        const bool ok =
+            !upload_factors(prm, dtype, prm.n1, prm.N1, p.d_inv1, p.stream) &&
+            !upload_factors(prm, dtype, prm.n2, prm.N2, p.d_inv2, p.stream) &&
+            (dtype == DFSNUFFT_F64
+                 ? !upload_twiddles<double2, double>(prm.n1, p.d_tw1, p.stream) &&
+                       !upload_twiddles<double2, double>(prm.n2, p.d_tw2, p.stream)
+                 : !upload_twiddles<float2, float>(prm.n1, p.d_tw1, p.stream) &&
+                       !upload_twiddles<float2, float>(prm.n2, p.d_tw2, p.stream));
+        if (!ok) return DFSNUFFT_ERR_CUDA;
         ds.have_tables = 1;
         ds.n1 = prm.n1;
         ds.n2 = prm.n2;

@@ -412,8 +412,8 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
     p->n_fields = n_fields;
     p->stream = (cudaStream_t)stream;
     p->c0 = (prm.w % 2 == 0) ? prm.w / 2 - 1 : (prm.w - 1) / 2;
-    p->nbx = prm.n1 / prm.tile_x + 1;
-    p->nby = prm.n2 / prm.tile_y + 1;
+    p->nbx = prm.n1 / prm.tile_x;    // base cells lie in [0, n): no wrap bin
+    p->nby = prm.n2 / prm.tile_y;
     p->nbins = p->nbx * p->nby;
     p->bstride = (p->nbins + 4) & ~3;     // 16-byte aligned member slices
 

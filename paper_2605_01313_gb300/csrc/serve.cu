@@ -89,7 +89,7 @@ size_t slot_bytes(const dfsnufft_params &q, int F, int cap, int64_t pts_cap) {
     b += lines * q.N2 * q.N1 * cs;             // staged coefficients
     b += (size_t)pts_cap * (16 + 4 + 8 + 2 * rs + 4);   // points, ranks, sorted records
     b += (size_t)F * pts_cap * rs;             // staged values
-    b += (size_t)cap * 3 * 4 * (q.n1 / q.tile_x + 1) * (q.n2 / q.tile_y + 1);   // bins
+    b += (size_t)cap * 3 * 4 * (q.n1 / q.tile_x) * (q.n2 / q.tile_y);   // bins
     return b + (4u << 20);                      // tables and slack
 }
 

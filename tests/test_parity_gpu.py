@@ -102,6 +102,24 @@ def test_small_grids_every_point(torch_cuda, n_lon, n_lat, dtype):
         check_against_oracle(vals, wl, accept(dtype, wl.tol))
 
 
+def test_f32_many_fields_whole_torus(torch_cuda):
+    """Seven FP32 fields (more than one field group per bin) at points spread
+    over the whole doubled torus, colatitude in [-pi, pi), so that bins on
+    both seams (their tiles wrap around) are exercised with the rest."""
+    rng = np.random.default_rng(41)
+    base = synth.small_workload(41, 512, 256, n_fields=7, dtype="f32", decay=3.0)
+    P = 40000
+    lon = rng.uniform(0, 2 * math.pi, P)
+    colat = rng.uniform(-math.pi, math.pi, P)
+    # points piled up against the seams of both angles
+    lon[:2000] = rng.uniform(-1e-3, 1e-3, 2000)
+    colat[2000:4000] = rng.uniform(-1e-3, 1e-3, 2000)
+    colat[4000:5000] = math.pi + rng.uniform(-1e-3, 1e-3, 1000)
+    vals = run_gpu(torch_cuda, base, lon=lon, colat=colat)
+    sample = np.concatenate([np.arange(0, 5000, 5), rng.choice(P, 1000, replace=False)])
+    check_against_oracle(vals, base, TOL_F32, sample=sample, lon=lon, colat=colat)
+
+
 def test_tolerance_sweep_monotone(torch_cuda):
     wl = synth.small_workload(7, 64, 32, n_fields=1, dtype="f64", points="uniform")
     ref = oracle.evaluate(wl.coeffs, wl.lon, wl.colat)[0].real
