@@ -77,7 +77,45 @@ typedef struct {
     double tol;            /* requested tolerance                                  */
     int dtype;             /* DFSNUFFT_F64 or DFSNUFFT_F32                          */
     int tile_x, tile_y;    /* interpolation bin size in fine cells                 */
+    int sigma;             /* oversampling factor (2 or 4)                          */
+    unsigned flags;        /* DFSNUFFT_REAL_FIELDS or 0                             */
 } dfsnufft_params;
+
+/* ---- plan options -------------------------------------------------------- */
+
+/* The fields are real on the sphere (the SWE fields h, u, v of the paper are),
+ * so their coefficients are Hermitian: c_{-n,-m} = conj(c_{n,m}) for every
+ * pair of entries that both lie in the array.  The plan then reads only the
+ * columns m >= 0, the Nyquist column m = -N1/2 and the Nyquist row
+ * n = -N2/2, transforms half of the columns and keeps half of the theta-pass
+ * buffer.  The values are Re v for the coefficients whose columns
+ * -N1/2 < m < 0 are, off the Nyquist row, the conjugate mirrors of columns -m;
+ * every entry of the Nyquist row and column is evaluated literally, as in a
+ * general plan.  For Hermitian input this is Re v exactly. */
+#define DFSNUFFT_REAL_FIELDS 1u
+
+/* Options of dfsnufft_plan_create_opts.  A zero-filled struct gives the
+ * defaults of dfsnufft_plan_create.
+ *   flags  : DFSNUFFT_REAL_FIELDS or 0.
+ *   sigma  : oversampling factor, 0 (= 2), 2 or 4.  With 4 the fine grid has
+ *            4x the cells of sigma 2 and the kernel may be narrower (the width
+ *            rule keeps the kernel's modelled interpolation error at or below
+ *            that of sigma 2 at the same tol); beta = 0.97 pi (1 - 1/(2 sigma)) w.
+ *   w      : kernel width 2..16, 0 = from tol and sigma.  A width below the
+ *            rule's lowers the accuracy (the autotuner checks it).
+ *   tile_x, tile_y : interpolation bin in fine cells, powers of two from 8 to
+ *            128 (0 = the default: 32 x 16 for F32, 32 x 32 for F64); tile_y is
+ *            raised to n2/512 when smaller. */
+typedef struct {
+    unsigned flags;
+    int sigma;
+    int w;
+    int tile_x, tile_y;
+} dfsnufft_options;
+
+/* Parameters with options (opts may be NULL for the defaults). */
+int dfsnufft_choose_params_opts(int n_lon, int n_lat, double tol, int dtype,
+                                const dfsnufft_options *opts, dfsnufft_params *out);
 
 /* Create a plan for an n_lat x n_lon grid.
  *   n_lon : even, >= 4; N1 = n_lon phi-modes.  n_lat >= 2; N2 = 2 n_lat.
@@ -90,6 +128,12 @@ typedef struct {
  * Fine grids up to 8192 x 8192 are supported (ERR_UNSUPPORTED above). */
 int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype, int n_fields,
                          void *stream, dfsnufft_plan *out);
+
+/* A batched plan (n_members >= 1, see dfsnufft_plan_create_batch) with
+ * options (opts may be NULL: the defaults). */
+int dfsnufft_plan_create_opts(int n_members, int n_lon, int n_lat, double tol, int dtype,
+                              int n_fields, const dfsnufft_options *opts, void *stream,
+                              dfsnufft_plan *out);
 
 /* Give a one-member plan its departure points (device pointers, float64
  * radians, n_points each, 1 <= n_points < 2^31).  Folds them onto the
@@ -125,6 +169,13 @@ typedef struct dfsnufft_ensemble_s *dfsnufft_ensemble;
 int dfsnufft_ensemble_create(int n_groups, const int *n_members, const int *n_lon,
                              const int *n_lat, double tol, int dtype, int n_fields, void *stream,
                              dfsnufft_ensemble *out);
+
+/* The same with per-group plan options: opts is NULL (defaults) or an array of
+ * n_groups options (for instance the autotuner's choice per grid size). */
+int dfsnufft_ensemble_create_opts(int n_groups, const int *n_members, const int *n_lon,
+                                  const int *n_lat, double tol, int dtype, int n_fields,
+                                  const dfsnufft_options *opts, void *stream,
+                                  dfsnufft_ensemble *out);
 
 /* One step for every member of every group: per group g, n_points[g] (host
  * array of the group's member counts), lon[g], colat[g], coeffs[g], values[g]

@@ -5,11 +5,11 @@ The compute path is the CUDA library built from ``csrc/`` (C ABI in
 ``include/dfsnufft.h``); :mod:`.nufft` is its Python binding and :mod:`.synth`
 draws seeded synthetic inputs.
 """
-__all__ = ["Plan", "nufft", "synth"]
+__all__ = ["Plan", "Options", "Ensemble", "nufft", "synth"]
 
 
 def __getattr__(name):
-    if name == "Plan":
-        from .nufft import Plan
-        return Plan
+    if name in ("Plan", "Options", "Ensemble"):
+        from . import nufft
+        return getattr(nufft, name)
     raise AttributeError(name)

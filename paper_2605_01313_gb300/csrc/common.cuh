@@ -39,6 +39,7 @@ struct dfsnufft_plan_s {
     int n_members;          // members of the same grid, each with its own points
     int n_fields;           // fields per member (lines of the FFT passes: n_members x n_fields)
     int c0;                 // first tap sits c0 cells left of the point's base cell
+    int herm;               // DFSNUFFT_REAL_FIELDS: theta pass on columns m >= 0 only
     int nbx, nby, nbins;    // interpolation bins
     int bstride;            // per-member stride of the bin arrays: >= nbins + 1, multiple of 4
     cudaStream_t stream;
@@ -50,7 +51,7 @@ struct dfsnufft_plan_s {
     void *d_tw2;            // n2 twiddles
     void *d_stw_theta;      // stage-ordered twiddles of the length-n2/2 theta transforms
     void *d_stw_phi;        // stage-ordered twiddles of the length-n1/2 phi transforms
-    void *d_T;              // theta-pass output, (members x fields) x n2 x N1
+    void *d_T;              // theta-pass output, (members x fields) x n2 x dfs_tpitch columns
     void *d_G;              // fine grids (real part), (members x fields) x n2 x n1, plan precision
     int *d_bin_count;       // members x bstride
     int *d_bin_start;       // members x bstride (nbins + 1 used), member-local positions
@@ -89,6 +90,14 @@ struct dfsnufft_plan_s {
     int status;             // sticky CUDA status
     char msg[512];
 };
+
+// Columns of the theta-pass output: all N1 phi-modes, or for real fields the
+// N1/2 + 1 modes m = 0..N1/2 (the rest follow by conjugate symmetry), stored
+// with a row pitch rounded up to 4 elements.
+__host__ __device__ __forceinline__ int dfs_tcols(int herm, int N1) { return herm ? N1 / 2 + 1 : N1; }
+__host__ __device__ __forceinline__ int dfs_tpitch(int herm, int N1) {
+    return herm ? ((N1 / 2 + 1 + 3) & ~3) : N1;
+}
 
 // ---------------------------------------------------------------- launches
 // points.cu

@@ -71,6 +71,15 @@ void release(dfsnufft_ensemble e) {
 extern "C" int dfsnufft_ensemble_create(int n_groups, const int *n_members, const int *n_lon,
                                         const int *n_lat, double tol, int dtype, int n_fields,
                                         void *stream, dfsnufft_ensemble *out) {
+    return dfsnufft_ensemble_create_opts(n_groups, n_members, n_lon, n_lat, tol, dtype, n_fields,
+                                         nullptr, stream, out);
+}
+
+extern "C" int dfsnufft_ensemble_create_opts(int n_groups, const int *n_members,
+                                             const int *n_lon, const int *n_lat, double tol,
+                                             int dtype, int n_fields,
+                                             const dfsnufft_options *opts, void *stream,
+                                             dfsnufft_ensemble *out) {
     if (!out || n_groups < 1 || n_groups > 64 || !n_members || !n_lon || !n_lat)
         return DFSNUFFT_ERR_INVALID_ARG;
     *out = nullptr;
@@ -96,8 +105,8 @@ extern "C" int dfsnufft_ensemble_create(int n_groups, const int *n_members, cons
             rc = DFSNUFFT_ERR_CUDA;
             break;
         }
-        rc = dfsnufft_plan_create_batch(n_members[g], n_lon[g], n_lat[g], tol, dtype, n_fields,
-                                        e->streams[g], &e->plans[g]);
+        rc = dfsnufft_plan_create_opts(n_members[g], n_lon[g], n_lat[g], tol, dtype, n_fields,
+                                       opts ? &opts[g] : nullptr, e->streams[g], &e->plans[g]);
     }
     if (rc) {
         release(e);

@@ -7,8 +7,10 @@
 // Hermitian.  With M = n1 / 2 and Z_k = (H_k + H_{k+M}) + i e^{2 pi i k / n1}
 // (H_k - H_{k+M}), the length-M inverse FFT z of Z gives
 // Re g(2j) = Re z_j and Re g(2j+1) = Im z_j.  T_k is the theta-pass value at
-// phi-mode k mod n1 (zero outside the N1 modes).  Each CTA handles CB rows
-// inside the plan's needed row range; the row's N1 values are staged in
+// phi-mode k mod n1 (zero outside the N1 modes).  A real-field plan's theta
+// pass already transformed the Hermitian part of the coefficients, so its row
+// holds H_k itself for k = 0..N1/2, and H_{-k} = conj H_k.  Each CTA handles CB
+// rows inside the plan's needed row range; the row's values are staged in
 // shared memory first, since every one of them enters two Z_k.
 #include "fft_core.cuh"
 
@@ -20,11 +22,12 @@ struct PhiArgs {
     int N1, n1, logm, n2;     // logm = log2(n1 / 2)
     int CB;                   // rows per CTA (divides DFS_ROW_BLOCK)
     int F;                    // fields per member (line f belongs to member f / F)
+    int tcols, tpitch;        // theta-pass columns per row and row pitch
 };
 
 // grid (n2 / CB, lines); block CB * M/E threads, thread = (t, c) with t fastest.
 // LOGM > 0 fixes the transform length at compile time; 0 takes it from a.logm.
-template <typename R, int E, int MAXT, int MINB, int LOGM>
+template <typename R, int E, int MAXT, int MINB, int LOGM, bool HERM>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_phi_pass(PhiArgs a, const typename CxT<R>::type *__restrict__ in,
                const typename CxT<R>::type *__restrict__ tw,
@@ -43,14 +46,23 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int c = threadIdx.x / T;
     const int row = row0 + c;
     const int f = blockIdx.y;
-    const C *src = in + ((size_t)f * a.n2 + row) * a.N1;
+    const C *src = in + ((size_t)f * a.n2 + row) * a.tpitch;
     R *dst = grid + ((size_t)f * a.n2 + row) * a.n1;
     const int half = a.N1 / 2;
     const int nmask = a.n1 - 1;
     C *sm = smem + (size_t)c * region_len<C>(M);
-    C *srow = smem + (size_t)a.CB * region_len<C>(M) + (size_t)c * a.N1;
-    for (int i = t; i < a.N1; i += T) srow[i] = src[i];
+    C *srow = smem + (size_t)a.CB * region_len<C>(M) + (size_t)c * a.tcols;
+    for (int i = t; i < a.tcols; i += T) srow[i] = src[i];
     __syncthreads();
+    auto hval = [&](int k) -> C {              // real-field rows: H_k, k taken mod n1
+        k &= nmask;
+        if (k <= half) return srow[k];
+        if (k >= a.n1 - half) {
+            const C v = srow[a.n1 - k];
+            return cmake(v.x, -v.y);
+        }
+        return cmake((R)0, (R)0);
+    };
     auto tval = [&](int k) -> C {              // T_k, k taken mod n1
         k &= nmask;
         int m;
@@ -60,6 +72,11 @@ __global__ void __launch_bounds__(MAXT, MINB)
         return srow[m + half];
     };
     auto ld = [&](int k) -> C {
+        if constexpr (HERM) {
+            const C h0 = hval(k), h1 = hval(k + M);
+            const C d = cmul(cmake(h0.x - h1.x, h0.y - h1.y), __ldg(&tw[k]));
+            return cmake(h0.x + h1.x - d.y, h0.y + h1.y + d.x);
+        }
         const C t0 = tval(k), t1 = tval(-k), t2 = tval(k + M), t3 = tval(M - k);
         // 2 H_k = T_k + conj T_{-k},  2 H_{k+M} = T_{k+M} + conj T_{M-k}
         const C h0 = cmake(t0.x + t1.x, t0.y - t1.y);
@@ -77,16 +94,27 @@ template <typename R> struct PhiCfg;
 template <> struct PhiCfg<float> { static const int E = DFS_FFT_E, MAXT = 256, MINB = 3; };
 template <> struct PhiCfg<double> { static const int E = DFS_FFT_E, MAXT = 512, MINB = 1; };
 
-template <typename R, int LOGM>
+template <typename R, int LOGM, bool HERM>
 cudaError_t run_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
     typedef typename CxT<R>::type C;
     constexpr int E = PhiCfg<R>::E, MAXT = PhiCfg<R>::MAXT, MINB = PhiCfg<R>::MINB;
-    cudaError_t e = allow_smem(k_phi_pass<R, E, MAXT, MINB, LOGM>, smem);
+    cudaError_t e = allow_smem(k_phi_pass<R, E, MAXT, MINB, LOGM, HERM>, smem);
     if (e) return e;
-    k_phi_pass<R, E, MAXT, MINB, LOGM><<<grid, threads, smem, p->stream>>>(
+    k_phi_pass<R, E, MAXT, MINB, LOGM, HERM><<<grid, threads, smem, p->stream>>>(
         a, (const C *)p->d_T, (const C *)p->d_tw1, (const C *)p->d_stw_phi, p->d_rowrange,
         (R *)p->d_G);
     return cudaGetLastError();
+}
+
+template <typename R, bool HERM>
+cudaError_t dispatch_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
+    if (!p->d_stw_phi) return run_phi<R, 0, HERM>(p, a, smem, grid, threads);
+    switch (a.logm) {
+        case 9: return run_phi<R, 9, HERM>(p, a, smem, grid, threads);
+        case 10: return run_phi<R, 10, HERM>(p, a, smem, grid, threads);
+        case 11: return run_phi<R, 11, HERM>(p, a, smem, grid, threads);
+        default: return run_phi<R, 0, HERM>(p, a, smem, grid, threads);
+    }
 }
 
 template <typename R>
@@ -100,23 +128,20 @@ cudaError_t launch_phi(dfsnufft_plan p) {
     a.logm = ilog2(q.n1) - 1;
     a.n2 = q.n2;
     a.F = p->n_fields;
+    a.tcols = dfs_tcols(p->herm, q.N1);
+    a.tpitch = dfs_tpitch(p->herm, q.N1);
     const int M = q.n1 / 2;
     const int T = M / E;
     int cb = MAXT / T;
     if (cb < 1) cb = 1;
     if (cb > DFS_ROW_BLOCK) cb = DFS_ROW_BLOCK;
-    const size_t per_row = sizeof(C) * (size_t)(region_len<C>(M) + q.N1);
+    const size_t per_row = sizeof(C) * (size_t)(region_len<C>(M) + a.tcols);
     while (cb > 1 && per_row * cb > 160 * 1024) cb >>= 1;
     a.CB = cb;
     const size_t smem = per_row * cb;
     const dim3 grid(q.n2 / cb, p->n_members * p->n_fields);
-    if (!p->d_stw_phi) return run_phi<R, 0>(p, a, smem, grid, cb * T);
-    switch (a.logm) {
-        case 9: return run_phi<R, 9>(p, a, smem, grid, cb * T);
-        case 10: return run_phi<R, 10>(p, a, smem, grid, cb * T);
-        case 11: return run_phi<R, 11>(p, a, smem, grid, cb * T);
-        default: return run_phi<R, 0>(p, a, smem, grid, cb * T);
-    }
+    if (p->herm) return dispatch_phi<R, true>(p, a, smem, grid, cb * T);
+    return dispatch_phi<R, false>(p, a, smem, grid, cb * T);
 }
 
 }  // namespace

@@ -1,18 +1,32 @@
 // theta pass: deconvolve-and-pad fused with the column FFTs of the oversampled
 // 2-D inverse FFT (sign +1, unnormalised), a middle stage of the type-2 NUFFT
-// evaluating Eq. 5.3 (Sec. 5).  For each phi-mode column q (m = q - N1/2), the
-// N2 theta modes, each divided by phihat2(n) phihat1(m), are placed at fine
+// evaluating Eq. 5.3 (Sec. 5).  For each phi-mode column (m), the theta modes
+// of that column, each divided by phihat2(n) phihat1(m), are placed at fine
 // index n mod n2 (zeros elsewhere) and transformed along the column; only the
-// fine rows inside the plan's needed row range are stored: T[f][row][q].
+// fine rows inside the plan's needed row range are stored: T[f][row][column].
+//
+// General plans transform every column m = -N1/2 .. N1/2-1 (column q of the
+// array, m = q - N1/2).  Plans for real fields (DFSNUFFT_REAL_FIELDS) transform
+// only m = 0 .. N1/2 (column k of T is m = k): the values are Re v, which only
+// depend on the Hermitian part h_{n,m} = (c_{n,m} + conj c_{-n,-m}) / 2 of the
+// coefficients, and the phi pass rebuilds the columns m < 0 from
+// H_{-m} = conj H_m.  For a real field h = c at every pair of entries that are
+// both in the array; the entries whose mirror lies outside it (the Nyquist
+// row n = -N2/2 and column m = -N1/2) are split exactly into their two halves
+// c/2 at (n, m) and conj(c)/2 at (-n, -m), so they are evaluated literally as in
+// a general plan.  Column m = 0 takes its Hermitian part in full (its mirror is
+// the same column).  This halves the column transforms and the T buffer.
 //
 // Main kernel (k_theta_tma): persistent CTAs take blocks of CB columns (32-byte
 // row segments).  The block's N2 coefficient rows arrive in shared memory by
 // 2-D TMA boxes, double-buffered so that the next block streams in while this
 // one is transformed.  Each column's length-n2 transform is done as two
 // length-n2/2 transforms: output row 2q + s = sum_n c_n e^{2 pi i n s / n2}
-// e^{2 pi i n q / (n2/2)}, s = 0, 1 (the N2 modes fit in n2/2 without aliasing).
-// k_theta_pass is the plain-load version for shapes the TMA kernel does not
-// take (unaligned coefficient pointer, CTA or shared-memory limits).
+// e^{2 pi i n q / (n2/2)}, s = 0, 1 (the modes fit in n2/2; when n2 = 2 N2 the
+// two Nyquist modes n = -N2/2 and n = +N2/2 of a real-field plan share index
+// N2/2 and are added there).  k_theta_pass is the plain-load version for shapes
+// the TMA kernel does not take (unaligned coefficient pointer, CTA or
+// shared-memory limits).
 #include "fft_core.cuh"
 #include "tma.cuh"
 
@@ -20,14 +34,40 @@ using namespace dfs_fft;
 
 namespace {
 
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake(a.x, -a.y); }
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) {
+    return cmake(a.x * s, a.y * s);
+}
+
+// h_{n,k} of a real-field plan (see above) for -half <= n <= half and
+// 0 <= k <= N1/2, from a reader cf(row, col) of the coefficient array that
+// returns zero outside it.  half = N2/2.
+template <typename C, class Rd>
+__device__ __forceinline__ C herm_coef(int n, int k, int half, int N1, Rd &cf) {
+    typedef decltype(C().x) R;
+    const int N1h = N1 / 2;
+    const int qa = N1h + k;                        // array column of m = k (N1 if k = N1/2)
+    if (k == N1h)                                  // mirror of the Nyquist column
+        return n == -half ? cmake((R)0, (R)0) : cscale(cconj(cf(half - n, 0)), (R)0.5);
+    if (n == half) return cscale(cconj(cf(0, N1 - qa)), (R)0.5);   // mirror of the Nyquist row
+    const C c = cf(n + half, qa);
+    if (n == -half) return cscale(c, (R)0.5);
+    if (k == 0) {
+        const C mirror = cf(half - n, qa);
+        return cscale(cmake(c.x + mirror.x, c.y - mirror.y), (R)0.5);
+    }
+    return c;
+}
+
 struct ThetaArgs {
     int N1, N2, n2, logn2;
     int CB;                   // columns per CTA
     int F;                    // fields per member (line f belongs to member f / F)
+    int tcols, tpitch;        // transformed columns, row pitch of T
 };
 
-// grid (ceil(N1 / CB), lines); block CB * n2/E threads, thread = (t, c) with c fastest.
-template <typename R, int E, int MAXT, int MINB>
+// grid (ceil(tcols / CB), lines); block CB * n2/E threads, thread = (t, c) with c fastest.
+template <typename R, int E, int MAXT, int MINB, bool HERM>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_theta_pass(ThetaArgs a, const typename CxT<R>::type *__restrict__ coef,
                  const R *__restrict__ inv1, const R *__restrict__ inv2,
@@ -38,48 +78,56 @@ __global__ void __launch_bounds__(MAXT, MINB)
     C *smem = reinterpret_cast<C *>(smem_raw);
     const int c = threadIdx.x % a.CB;
     const int t = threadIdx.x / a.CB;
-    const int q = blockIdx.x * a.CB + c;
+    const int q = blockIdx.x * a.CB + c;           // column of T
     const int f = blockIdx.y;
     const int2 rr = rowrange[f / a.F];
-    const bool col_ok = q < a.N1;
-    const C *src = coef + (size_t)f * a.N2 * a.N1 + q;
-    C *dst = out + (size_t)f * a.n2 * a.N1 + q;
+    const bool col_ok = q < a.tcols;
+    const C *cf0 = coef + (size_t)f * a.N2 * a.N1;
+    C *dst = out + (size_t)f * a.n2 * a.tpitch + q;
     const int half = a.N2 / 2;
-    const R sq = col_ok ? inv1[q] : (R)0;
+    const int qa = HERM ? a.N1 / 2 + q : q;        // array column
+    const R sq = col_ok ? inv1[qa < a.N1 ? qa : 0] : (R)0;
     C *sm = smem + (size_t)c * region_len<C>(a.n2);
+    auto cf = [&](int r, int col) -> C {
+        return (r < a.N2 && col < a.N1) ? cf0[(size_t)r * a.N1 + col] : cmake((R)0, (R)0);
+    };
     auto ld = [&](int i) -> C {
+        if (!col_ok) return cmake((R)0, (R)0);
         int n;
         if (i < half) n = i;
         else if (i >= a.n2 - half) n = i - a.n2;
+        else if (HERM && i == half) n = half;
         else return cmake((R)0, (R)0);
-        if (!col_ok) return cmake((R)0, (R)0);
         const int r = n + half;
-        const C v = src[(size_t)r * a.N1];
-        const R s = sq * inv2[r];
-        return cmake(v.x * s, v.y * s);
+        const R s = sq * inv2[r < a.N2 ? r : 0];
+        if constexpr (HERM) return cscale(herm_coef<C>(n, q, half, a.N1, cf), s);
+        else return cscale(cf(r, qa), s);
     };
     auto st = [&](int i, C v) {
-        if (col_ok && ((i - rr.x) & (a.n2 - 1)) < rr.y) dst[(size_t)i * a.N1] = v;
+        if (col_ok && ((i - rr.x) & (a.n2 - 1)) < rr.y) dst[(size_t)i * a.tpitch] = v;
     };
     line_fft<E>(a.logn2, tw, 0, sm, t, ld, st);
 }
 
 struct ThetaTmaArgs {
     int N1, N2, n2, logh;     // logh = log2(n2 / 2)
-    int nbq;                  // column blocks per line, ceil(N1 / CB)
+    int nbq;                  // column blocks per line, ceil(tcols / CB)
     int total;                // nbq * lines (members x fields)
     int F;                    // fields per member (line f belongs to member f / F)
     int nbox, box_rows;       // TMA boxes per block and rows per box
     int in_elems;             // complex elements delivered per block
     int nbuf;                 // input buffers (2: prefetch the next block)
     unsigned tx_bytes;        // bytes delivered per block
+    int tcols, tpitch;        // transformed columns, row pitch of T
+    int col_base;             // array column of transformed column 0
 };
 
 // LOGH > 0: half length 2^LOGH fixed at compile time (unrolled transform);
 // LOGH == 0: taken from the arguments.
-template <typename R, int E, int CB, int MAXT, int LOGH>
+template <typename R, int E, int CB, int MAXT, int LOGH, bool HERM>
 __global__ void __launch_bounds__(MAXT, 1)
     k_theta_tma(ThetaTmaArgs a, const __grid_constant__ CUtensorMap tmap,
+                const typename CxT<R>::type *__restrict__ coef,
                 const R *__restrict__ inv1, const R *__restrict__ inv2,
                 const typename CxT<R>::type *__restrict__ tw,
                 const typename CxT<R>::type *__restrict__ stw, const int2 *__restrict__ rowrange,
@@ -111,7 +159,7 @@ __global__ void __launch_bounds__(MAXT, 1)
         C *dst = inb + (size_t)b * a.in_elems;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bar[b], a.tx_bytes);
-        const int x = qb * CB * (int)(sizeof(C) / 8);
+        const int x = (a.col_base + qb * CB) * (int)(sizeof(C) / 8);
         for (int i = 0; i < a.nbox; ++i)
             tma_load_2d(dst + (size_t)i * a.box_rows * CB, &tmap, x, f * a.N2 + i * a.box_rows,
                         &bar[b]);
@@ -139,28 +187,40 @@ __global__ void __launch_bounds__(MAXT, 1)
         }
         const int f = blk / a.nbq;
         const int2 rr = rowrange[f / a.F];
-        const int q = (blk - f * a.nbq) * CB + c;
-        const bool col_ok = q < a.N1;
-        const R sq = col_ok ? inv1[q] : (R)0;
+        const int q = (blk - f * a.nbq) * CB + c;      // column of T
+        const int qa = a.col_base + q;                 // array column
+        const bool col_ok = q < a.tcols;
+        const R sq = col_ok ? inv1[qa < a.N1 ? qa : 0] : (R)0;
         const C *in = inb + (size_t)cur * a.in_elems;
-        C *dst = out + (size_t)f * a.n2 * a.N1 + q;
+        const C *cf0 = coef + (size_t)f * a.N2 * a.N1;
+        C *dst = out + (size_t)f * a.n2 * a.tpitch + q;
+        // coefficient (row, col): this thread's column from the staged block,
+        // any other (Nyquist mirrors) from global memory
+        auto cf = [&](int r, int col) -> C {
+            if (r >= a.N2 || col >= a.N1) return cmake((R)0, (R)0);
+            if (col == qa) return in[r * CB + c];
+            return cf0[(size_t)r * a.N1 + col];
+        };
 #pragma unroll 1
         for (int s = 0; s < 2; ++s) {
-            auto ld = [&](int i) -> C {
-                int n;
-                if (i < half) n = i;
-                else if (i >= H - half) n = i - H;
-                else return cmake((R)0, (R)0);
+            auto term = [&](int n) -> C {
                 const int r = n + half;
-                const C v = in[r * CB + c];
-                const R sc = sq * f2[r];
-                C y = cmake(v.x * sc, v.y * sc);
+                C y = cscale(HERM ? herm_coef<C>(n, q, half, a.N1, cf) : in[r * CB + c],
+                             sq * f2[r < a.N2 ? r : 0]);
                 if (s) y = cmul(y, __ldg(&tw[n & (a.n2 - 1)]));
+                return y;
+            };
+            auto ld = [&](int i) -> C {
+                C y = cmake((R)0, (R)0);
+                if (!col_ok) return y;
+                if (i < half) y = term(i);
+                else if (i >= H - half) y = term(i - H);
+                if (HERM && i == half) y = y + term(half);
                 return y;
             };
             auto st = [&](int qq, C v) {
                 const int row = 2 * qq + s;
-                if (col_ok && ((row - rr.x) & (a.n2 - 1)) < rr.y) dst[(size_t)row * a.N1] = v;
+                if (col_ok && ((row - rr.x) & (a.n2 - 1)) < rr.y) dst[(size_t)row * a.tpitch] = v;
             };
             if constexpr (LOGH > 0) line_fft_ct<LOGH, E>(stw, sm, t, ld, st);
             else line_fft<E>(a.logh, tw, 1, sm, t, ld, st);
@@ -176,17 +236,29 @@ template <typename R> struct ThetaCfg;
 template <> struct ThetaCfg<float> { static const int E = DFS_FFT_E, MAXT = 1024, MINB = 1, CB = 4; };
 template <> struct ThetaCfg<double> { static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, CB = 2; };
 
-template <typename R, int LOGH>
+template <typename R, int LOGH, bool HERM>
 cudaError_t run_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUtensorMap &tmap,
-                          size_t smem, int grid, int threads) {
+                          const void *coeffs, size_t smem, int grid, int threads) {
     typedef typename CxT<R>::type C;
     constexpr int E = ThetaCfg<R>::E, CB = ThetaCfg<R>::CB, MAXT = ThetaCfg<R>::MAXT;
-    cudaError_t e = allow_smem(k_theta_tma<R, E, CB, MAXT, LOGH>, smem);
+    cudaError_t e = allow_smem(k_theta_tma<R, E, CB, MAXT, LOGH, HERM>, smem);
     if (e) return e;
-    k_theta_tma<R, E, CB, MAXT, LOGH><<<grid, threads, smem, p->stream>>>(
-        a, tmap, (const R *)p->d_inv1, (const R *)p->d_inv2, (const C *)p->d_tw2,
-        (const C *)p->d_stw_theta, p->d_rowrange, (C *)p->d_T, p->d_status);
+    k_theta_tma<R, E, CB, MAXT, LOGH, HERM><<<grid, threads, smem, p->stream>>>(
+        a, tmap, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2,
+        (const C *)p->d_tw2, (const C *)p->d_stw_theta, p->d_rowrange, (C *)p->d_T, p->d_status);
     return cudaGetLastError();
+}
+
+template <typename R, bool HERM>
+cudaError_t dispatch_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUtensorMap &tmap,
+                               const void *coeffs, size_t smem, int grid, int threads) {
+    if (!p->d_stw_theta) return run_theta_tma<R, 0, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+    switch (a.logh) {
+        case 9: return run_theta_tma<R, 9, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+        case 10: return run_theta_tma<R, 10, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+        case 11: return run_theta_tma<R, 11, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+        default: return run_theta_tma<R, 0, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+    }
 }
 
 // Launch the TMA theta pass; returns cudaErrorNotSupported (without launching)
@@ -204,7 +276,12 @@ cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
     a.N2 = q.N2;
     a.n2 = q.n2;
     a.logh = ilog2(H);
-    a.nbq = (q.N1 + CB - 1) / CB;
+    a.tcols = dfs_tcols(p->herm, q.N1);
+    a.tpitch = dfs_tpitch(p->herm, q.N1);
+    a.col_base = p->herm ? q.N1 / 2 : 0;
+    // the box's first column must sit on a 16-byte boundary
+    if ((a.col_base * sizeof(C)) % 16 != 0) return cudaErrorNotSupported;
+    a.nbq = (a.tcols + CB - 1) / CB;
     const int lines = p->n_members * p->n_fields;
     a.total = a.nbq * lines;
     a.F = p->n_fields;
@@ -231,13 +308,21 @@ cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
     int grid = p->num_sms > 0 ? p->num_sms : 1;
     if (grid > a.total) grid = a.total;
     const int threads = CB * (H / E);
-    if (!p->d_stw_theta) return run_theta_tma<R, 0>(p, a, tmap, smem, grid, threads);
-    switch (a.logh) {
-        case 9: return run_theta_tma<R, 9>(p, a, tmap, smem, grid, threads);
-        case 10: return run_theta_tma<R, 10>(p, a, tmap, smem, grid, threads);
-        case 11: return run_theta_tma<R, 11>(p, a, tmap, smem, grid, threads);
-        default: return run_theta_tma<R, 0>(p, a, tmap, smem, grid, threads);
-    }
+    if (p->herm) return dispatch_theta_tma<R, true>(p, a, tmap, coeffs, smem, grid, threads);
+    return dispatch_theta_tma<R, false>(p, a, tmap, coeffs, smem, grid, threads);
+}
+
+template <typename R, bool HERM>
+cudaError_t run_theta_plain(dfsnufft_plan p, const ThetaArgs &a, const void *coeffs, size_t smem,
+                            dim3 grid, int threads) {
+    typedef typename CxT<R>::type C;
+    constexpr int E = ThetaCfg<R>::E, MAXT = ThetaCfg<R>::MAXT, MINB = ThetaCfg<R>::MINB;
+    cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM>, smem);
+    if (e) return e;
+    k_theta_pass<R, E, MAXT, MINB, HERM><<<grid, threads, smem, p->stream>>>(
+        a, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2, (const C *)p->d_tw2,
+        p->d_rowrange, (C *)p->d_T);
+    return cudaGetLastError();
 }
 
 template <typename R>
@@ -248,7 +333,7 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs) {
         if (e != cudaErrorNotSupported) return e;
         cudaGetLastError();
     }
-    constexpr int E = ThetaCfg<R>::E, MAXT = ThetaCfg<R>::MAXT, MINB = ThetaCfg<R>::MINB;
+    constexpr int E = ThetaCfg<R>::E, MAXT = ThetaCfg<R>::MAXT;
     const dfsnufft_params &q = p->prm;
     ThetaArgs a;
     a.N1 = q.N1;
@@ -256,23 +341,21 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs) {
     a.n2 = q.n2;
     a.logn2 = ilog2(q.n2);
     a.F = p->n_fields;
+    a.tcols = dfs_tcols(p->herm, q.N1);
+    a.tpitch = dfs_tpitch(p->herm, q.N1);
     const int T = q.n2 / E;
     int cb = MAXT / T;
     if (cb < 1) cb = 1;
-    int n1p = 1;
-    while (n1p < q.N1) n1p <<= 1;
-    if (cb > n1p) cb = n1p;
+    int ncp = 1;
+    while (ncp < a.tcols) ncp <<= 1;
+    if (cb > ncp) cb = ncp;
     const size_t per_col = sizeof(C) * (size_t)region_len<C>(q.n2);
     while (cb > 1 && per_col * cb > 160 * 1024) cb >>= 1;
     a.CB = cb;
     const size_t smem = per_col * cb;
-    cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB>, smem);
-    if (e) return e;
-    dim3 grid((q.N1 + cb - 1) / cb, p->n_members * p->n_fields);
-    k_theta_pass<R, E, MAXT, MINB><<<grid, cb * T, smem, p->stream>>>(
-        a, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2, (const C *)p->d_tw2,
-        p->d_rowrange, (C *)p->d_T);
-    return cudaGetLastError();
+    const dim3 grid((a.tcols + cb - 1) / cb, p->n_members * p->n_fields);
+    if (p->herm) return run_theta_plain<R, true>(p, a, coeffs, smem, grid, cb * T);
+    return run_theta_plain<R, false>(p, a, coeffs, smem, grid, cb * T);
 }
 
 }  // namespace

@@ -214,37 +214,83 @@ extern "C" int dfsnufft_es_horner(int w, double beta, double *out) {
     return DFSNUFFT_OK;
 }
 
-extern "C" int dfsnufft_choose_params(int n_lon, int n_lat, double tol, int dtype,
-                                      dfsnufft_params *out) {
+// Kernel width rule for sigma = 4.  Modelled worst error of the 1-D kernel
+// interpolation of e^{i omega x} over |omega| <= pi / sigma (the band the
+// deconvolution inverts), with beta as the plan uses it, for w = 0..16:
+// entry w of kErr2 (sigma 2, beta = 2.30 w) and of kErr4 (sigma 4,
+// beta = 0.97 pi (1 - 1/8) w).  A sigma-4 plan takes the narrowest w whose
+// modelled error is at most that of the sigma-2 width for the same tol.  The
+// values come from direct evaluation of the model (kernel samples against
+// phihat by adaptive quadrature) on 801 offsets at 4 frequencies.
+static const double kErr2[17] = {1, 1, 1.55e-01, 2.66e-02, 3.73e-03, 3.76e-04, 3.11e-05,
+                                 2.49e-06, 3.89e-07, 4.51e-08, 7.29e-09, 8.40e-10, 7.82e-11,
+                                 6.94e-12, 5.87e-13, 1.05e-13, 2.97e-14};
+static const double kErr4[17] = {1, 1, 7.69e-02, 6.65e-03, 4.51e-04, 1.98e-05, 1.29e-06,
+                                 1.36e-07, 1.33e-08, 7.95e-10, 3.32e-11, 3.55e-12, 2.97e-13,
+                                 2.56e-14, 4.56e-15, 4.79e-15, 4.71e-15};
+
+static bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+extern "C" int dfsnufft_choose_params_opts(int n_lon, int n_lat, double tol, int dtype,
+                                           const dfsnufft_options *opts, dfsnufft_params *out) {
     if (!out) return DFSNUFFT_ERR_INVALID_ARG;
     memset(out, 0, sizeof(*out));
+    dfsnufft_options o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
     if (n_lon < 4 || (n_lon & 1) || n_lat < 2) return DFSNUFFT_ERR_INVALID_ARG;
     if (dtype != DFSNUFFT_F64 && dtype != DFSNUFFT_F32) return DFSNUFFT_ERR_INVALID_ARG;
     if (!(tol > 0.0) || !(tol < 1.0)) return DFSNUFFT_ERR_INVALID_ARG;
+    if ((o.flags & ~DFSNUFFT_REAL_FIELDS) != 0) return DFSNUFFT_ERR_INVALID_ARG;
+    const int sigma = o.sigma == 0 ? 2 : o.sigma;
+    if (sigma != 2 && sigma != 4) return DFSNUFFT_ERR_INVALID_ARG;
+    if (o.w != 0 && (o.w < 2 || o.w > 16)) return DFSNUFFT_ERR_INVALID_ARG;
+    if ((o.tile_x != 0 && !pow2_in(o.tile_x, 8, 128)) ||
+        (o.tile_y != 0 && !pow2_in(o.tile_y, 8, 128)))
+        return DFSNUFFT_ERR_INVALID_ARG;
     if (dtype == DFSNUFFT_F64 && tol < 1e-15) return DFSNUFFT_ERR_TOL_UNATTAINABLE;
     if (dtype == DFSNUFFT_F32 && tol < 1e-7) return DFSNUFFT_ERR_TOL_UNATTAINABLE;
+    // sigma 2: w = ceil(log10(1/tol)) + 1, beta = 2.30 w
     int w = (int)ceil(-log10(tol) - 1e-9) + 1;
     if (w < 2) w = 2;
     if (w > 16) w = 16;
+    double beta = 2.30 * w;
+    if (sigma == 4) {
+        int w4 = 2;
+        while (w4 < 16 && kErr4[w4] > kErr2[w]) ++w4;
+        w = w4;
+    }
+    if (o.w != 0) w = o.w;
+    if (sigma == 4) beta = 0.97 * 3.14159265358979323846 * (1.0 - 1.0 / (2.0 * sigma)) * w;
+    else beta = 2.30 * w;
     out->n_lon = n_lon;
     out->n_lat = n_lat;
     out->N1 = n_lon;
     out->N2 = 2 * n_lat;
-    int a1 = 2 * out->N1 > 2 * w ? 2 * out->N1 : 2 * w;
-    int a2 = 2 * out->N2 > 2 * w ? 2 * out->N2 : 2 * w;
+    const int a1 = sigma * out->N1 > 2 * w ? sigma * out->N1 : 2 * w;
+    const int a2 = sigma * out->N2 > 2 * w ? sigma * out->N2 : 2 * w;
     out->n1 = next_pow2(a1 > 16 ? a1 : 16);
     out->n2 = next_pow2(a2 > 16 ? a2 : 16);
     if (out->n1 > (1 << DFS_FFT_MAX_LOG) || out->n2 > (1 << DFS_FFT_MAX_LOG))
         return DFSNUFFT_ERR_UNSUPPORTED;
     out->w = w;
-    out->beta = 2.30 * w;
+    out->beta = beta;
     out->tol = tol;
     out->dtype = dtype;
-    out->tile_x = 32;
-    out->tile_y = dtype == DFSNUFFT_F32 ? 16 : 32;
+    out->sigma = sigma;
+    out->flags = o.flags;
+    out->tile_x = o.tile_x ? o.tile_x : 32;
+    out->tile_y = o.tile_y ? o.tile_y : (dtype == DFSNUFFT_F32 ? 16 : 32);
     if (out->tile_x > out->n1) out->tile_x = out->n1;
     if (out->tile_y > out->n2) out->tile_y = out->n2;
+    // at most DFS_MAX_ROW_BLOCKS bin rows
+    while (out->n2 / out->tile_y > DFS_MAX_ROW_BLOCKS) out->tile_y *= 2;
     return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_choose_params(int n_lon, int n_lat, double tol, int dtype,
+                                      dfsnufft_params *out) {
+    return dfsnufft_choose_params_opts(n_lon, n_lat, tol, dtype, nullptr, out);
 }
 
 extern "C" const char *dfsnufft_strerror(int status) {
@@ -394,14 +440,15 @@ static int upload_tables(dfsnufft_plan p) {
 }
 
 static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int dtype,
-                            int n_fields, void *stream, dfsnufft_plan *out) {
+                            int n_fields, const dfsnufft_options *opts, void *stream,
+                            dfsnufft_plan *out) {
     if (!out) return DFSNUFFT_ERR_INVALID_ARG;
     *out = nullptr;
     if (n_fields < 1 || n_fields > 64 || n_members < 1 || n_members > 4096 ||
         n_members * n_fields > 65535)
         return DFSNUFFT_ERR_INVALID_ARG;
     dfsnufft_params prm;
-    int rc = dfsnufft_choose_params(n_lon, n_lat, tol, dtype, &prm);
+    int rc = dfsnufft_choose_params_opts(n_lon, n_lat, tol, dtype, opts, &prm);
     if (rc != DFSNUFFT_OK) return rc;
 
     dfsnufft_plan p = new (std::nothrow) dfsnufft_plan_s;
@@ -411,6 +458,7 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
     p->n_members = n_members;
     p->n_fields = n_fields;
     p->stream = (cudaStream_t)stream;
+    p->herm = (prm.flags & DFSNUFFT_REAL_FIELDS) ? 1 : 0;
     p->c0 = (prm.w % 2 == 0) ? prm.w / 2 - 1 : (prm.w - 1) / 2;
     p->nbx = prm.n1 / prm.tile_x;    // base cells lie in [0, n): no wrap bin
     p->nby = prm.n2 / prm.tile_y;
@@ -427,7 +475,7 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
         {&p->d_tw2, cs * prm.n2, "twiddles"},
         {&p->d_stw_theta, cs * stage_table_len(prm.n2 / 2), "stage twiddles"},
         {&p->d_stw_phi, cs * stage_table_len(prm.n1 / 2), "stage twiddles"},
-        {&p->d_T, cs * nf * prm.n2 * prm.N1, "theta-pass buffer"},
+        {&p->d_T, cs * nf * prm.n2 * dfs_tpitch(p->herm, prm.N1), "theta-pass buffer"},
         {&p->d_G, cs / 2 * nf * prm.n2 * prm.n1, "fine grid (real part)"},
         {(void **)&p->d_bin_count, sizeof(int) * p->bstride * nm, "bin counts"},
         {(void **)&p->d_bin_start, sizeof(int) * p->bstride * nm, "bin starts"},
@@ -470,13 +518,19 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
 
 extern "C" int dfsnufft_plan_create(int n_lon, int n_lat, double tol, int dtype, int n_fields,
                                     void *stream, dfsnufft_plan *out) {
-    return plan_create_impl(1, n_lon, n_lat, tol, dtype, n_fields, stream, out);
+    return plan_create_impl(1, n_lon, n_lat, tol, dtype, n_fields, nullptr, stream, out);
 }
 
 extern "C" int dfsnufft_plan_create_batch(int n_members, int n_lon, int n_lat, double tol,
                                           int dtype, int n_fields, void *stream,
                                           dfsnufft_plan *out) {
-    return plan_create_impl(n_members, n_lon, n_lat, tol, dtype, n_fields, stream, out);
+    return plan_create_impl(n_members, n_lon, n_lat, tol, dtype, n_fields, nullptr, stream, out);
+}
+
+extern "C" int dfsnufft_plan_create_opts(int n_members, int n_lon, int n_lat, double tol,
+                                         int dtype, int n_fields, const dfsnufft_options *opts,
+                                         void *stream, dfsnufft_plan *out) {
+    return plan_create_impl(n_members, n_lon, n_lat, tol, dtype, n_fields, opts, stream, out);
 }
 
 extern "C" int dfsnufft_destroy(dfsnufft_plan p) {

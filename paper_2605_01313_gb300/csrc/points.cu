@@ -28,7 +28,7 @@ struct FoldParams {
     int L1, L2;         // log2 of the fine sizes
     int odd_w;
     int c0, w;
-    int tile_x, tile_y, nbx;
+    int ltx, lty, nbx;  // log2 of the bin size (powers of two), bins per bin row
 };
 
 // Fraction of a turn of v in Q0.64.  False for inf/nan and for |v| >= 2^53,
@@ -96,7 +96,7 @@ __device__ __forceinline__ bool fold_point(const FoldParams &f, double lon, doub
 }
 
 __device__ __forceinline__ int bin_of(const FoldParams &f, int bx, int by) {
-    return (by / f.tile_y) * f.nbx + bx / f.tile_x;
+    return (by >> f.lty) * f.nbx + (bx >> f.ltx);
 }
 
 // grid (ceil(max member points / 256), members): member k = blockIdx.y.
@@ -116,16 +116,22 @@ __global__ void __launch_bounds__(256) k_fold_count(const double *__restrict__ l
         fold_point(f, lon[p0 + pl], colat[p0 + pl], bx, by, tx, ty);
         bin = bin_of(f, bx, by);
     }
-    // warp-aggregated increment: lanes sharing a bin take consecutive ranks
-    const unsigned live_mask = __ballot_sync(0xffffffffu, live);
-    if (!live) return;
-    const unsigned peers = __match_any_sync(live_mask, bin);
+    // warp aggregation over runs of equal bins (points arrive nearly sorted):
+    // the first lane of each run takes the run's ranks with one atomicAdd
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
+    const int prev = __shfl_up_sync(0xffffffffu, bin, 1);
+    const bool head = live && (lane == 0 || prev != bin);
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const unsigned live_mask = __ballot_sync(0xffffffffu, live);
+    // this lane's run: from its head to the lane before the next head (or the
+    // last live lane)
+    const int my_head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const unsigned later = heads & ~(0xffffffffu >> (31 - lane));   // heads after this lane
+    const int run_end = later ? __ffs(later) - 1 : 32 - __clz(live_mask);
     int base = 0;
-    if (lane == leader) base = atomicAdd(&bin_count[(size_t)k * bstride + bin], __popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    rank[p0 + pl] = base + __popc(peers & ((1u << lane) - 1u));
+    if (head) base = atomicAdd(&bin_count[(size_t)k * bstride + bin], run_end - lane);
+    base = __shfl_sync(0xffffffffu, base, my_head);
+    if (live) rank[p0 + pl] = base + lane - my_head;
 }
 
 // Smallest index i in [from, from + nb) (circular over nb bits) whose bit in
@@ -157,7 +163,7 @@ struct ScanParams {
 };
 
 // One CTA: exclusive scan of the bin counts and the list of non-empty bins, in
-// chunks of 4 * blockDim bins (each thread four consecutive bins).  Then the
+// chunks of 16 * blockDim bins (each thread sixteen consecutive bins).  Then the
 // circular range of fine rows the stencils touch: the points of bin row by use
 // rows by*tile_y - c0 .. (by+1)*tile_y - c0 + w - 2, so the range is the
 // complement of the longest circular run of empty bin rows, widened by the
@@ -181,21 +187,32 @@ __global__ void __launch_bounds__(1024) k_scan_bins(ScanParams sp, const int *__
     for (int i = tid; i <= sp.nbr; i += blockDim.x) s_row[i] = 0;
     __syncthreads();
     int carry = 0, carry_n = 0;
-    for (int base = 0; base < nbins; base += 4 * blockDim.x) {
-        const int i0 = base + 4 * tid;
-        int c[4];
-        if (i0 + 3 < nbins) {
-            const int4 v = *reinterpret_cast<const int4 *>(count + i0);
-            c[0] = v.x;
-            c[1] = v.y;
-            c[2] = v.z;
-            c[3] = v.w;
-        } else {
+    // each thread SCAN_V consecutive groups of four bins per pass, all loads
+    // issued before any is used
+    constexpr int SCAN_V = 4;
+    for (int base = 0; base < nbins; base += 4 * SCAN_V * blockDim.x) {
+        const int i0 = base + 4 * SCAN_V * tid;
+        int c[4 * SCAN_V];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) c[k] = i0 + k < nbins ? count[i0 + k] : 0;
+        for (int u = 0; u < SCAN_V; ++u) {
+            const int i = i0 + 4 * u;
+            if (i + 3 < nbins) {
+                const int4 v = *reinterpret_cast<const int4 *>(count + i);
+                c[4 * u] = v.x;
+                c[4 * u + 1] = v.y;
+                c[4 * u + 2] = v.z;
+                c[4 * u + 3] = v.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) c[4 * u + q] = i + q < nbins ? count[i + q] : 0;
+            }
         }
-        const int sum = c[0] + c[1] + c[2] + c[3];
-        const int ne = (c[0] > 0) + (c[1] > 0) + (c[2] > 0) + (c[3] > 0);
+        int sum = 0, ne = 0;
+#pragma unroll
+        for (int q = 0; q < 4 * SCAN_V; ++q) {
+            sum += c[q];
+            ne += c[q] > 0;
+        }
         int xs = sum, xn = ne;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -232,15 +249,25 @@ __global__ void __launch_bounds__(1024) k_scan_bins(ScanParams sp, const int *__
         int off_s = carry + xs - sum + (wid > 0 ? s_sum[wid - 1] : 0);
         int off_n = carry_n + xn - ne + (wid > 0 ? s_ne[wid - 1] : 0);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (i0 + k < nbins) {
-                start[i0 + k] = off_s;
-                if (c[k] > 0) {
-                    task_bin[off_n++] = i0 + k;
-                    s_row[(i0 + k) / sp.nbx] = 1;
+        for (int u = 0; u < SCAN_V; ++u) {
+            const int i = i0 + 4 * u;
+            int st[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                st[q] = off_s;
+                off_s += c[4 * u + q];
+                if (c[4 * u + q] > 0 && i + q < nbins) {
+                    task_bin[off_n++] = i + q;
+                    s_row[(i + q) / sp.nbx] = 1;
                 }
             }
-            off_s += c[k];
+            if (i + 3 < nbins) {
+                *reinterpret_cast<int4 *>(start + i) = make_int4(st[0], st[1], st[2], st[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (i + q < nbins) start[i + q] = st[q];
+            }
         }
         carry += s_sum[nw - 1];
         carry_n += s_ne[nw - 1];
@@ -330,8 +357,8 @@ cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const doub
     f.odd_w = q.w & 1;
     f.c0 = p->c0;
     f.w = q.w;
-    f.tile_x = q.tile_x;
-    f.tile_y = q.tile_y;
+    f.ltx = ilog2(q.tile_x);
+    f.lty = ilog2(q.tile_y);
     f.nbx = p->nbx;
     const int M = p->n_members;
     cudaError_t e;

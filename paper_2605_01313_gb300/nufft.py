@@ -40,7 +40,9 @@ EXPORTS = (
     "dfsnufft_ensemble_plan", "dfsnufft_ensemble_destroy",
     "dfsnufft_server_create", "dfsnufft_server_submit", "dfsnufft_server_wait",
     "dfsnufft_server_stats_get", "dfsnufft_server_destroy",
+    "dfsnufft_choose_params_opts", "dfsnufft_plan_create_opts", "dfsnufft_ensemble_create_opts",
 )
+REAL_FIELDS = 1
 N_STAGES = 4
 STAGES = ("set_points", "theta_pass", "phi_pass", "interp")
 
@@ -49,7 +51,27 @@ class Params(ctypes.Structure):
     _fields_ = [("n_lon", ctypes.c_int), ("n_lat", ctypes.c_int), ("N1", ctypes.c_int),
                 ("N2", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int),
                 ("w", ctypes.c_int), ("beta", ctypes.c_double), ("tol", ctypes.c_double),
-                ("dtype", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int)]
+                ("dtype", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("sigma", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Options(ctypes.Structure):
+    """dfsnufft_options: zero fields take the defaults."""
+    _fields_ = [("flags", ctypes.c_uint), ("sigma", ctypes.c_int), ("w", ctypes.c_int),
+                ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int)]
+
+    @classmethod
+    def make(cls, real_fields=False, sigma=0, w=0, tile=None):
+        o = cls()
+        o.flags = REAL_FIELDS if real_fields else 0
+        o.sigma = int(sigma or 0)
+        o.w = int(w or 0)
+        if tile:
+            o.tile_x, o.tile_y = int(tile[0]), int(tile[1])
+        return o
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +121,13 @@ def lib():
         L.dfsnufft_plan_create.argtypes = [i32, i32, f64, i32, i32, vp, ctypes.POINTER(vp)]
         L.dfsnufft_plan_create_batch.argtypes = [i32, i32, i32, f64, i32, i32, vp,
                                                  ctypes.POINTER(vp)]
+        L.dfsnufft_plan_create_opts.argtypes = [i32, i32, i32, f64, i32, i32,
+                                                ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
+        L.dfsnufft_choose_params_opts.argtypes = [i32, i32, f64, i32, ctypes.POINTER(Options),
+                                                  ctypes.POINTER(Params)]
+        L.dfsnufft_ensemble_create_opts.argtypes = [i32, vp, vp, vp, f64, i32, i32,
+                                                    ctypes.POINTER(Options), vp,
+                                                    ctypes.POINTER(vp)]
         L.dfsnufft_set_points_batch.argtypes = [vp, vp, vp, vp]
         L.dfsnufft_ensemble_create.argtypes = [i32, vp, vp, vp, f64, i32, i32, vp,
                                                ctypes.POINTER(vp)]
@@ -166,10 +195,15 @@ def _dtype_code(dtype) -> int:
 
 # ------------------------------------------------------------ host-only helpers
 
-def dfsnufft_choose_params(n_lon, n_lat, tol, dtype="f64") -> dict:
+def dfsnufft_choose_params(n_lon, n_lat, tol, dtype="f64", options=None) -> dict:
     p = Params()
-    _check(lib().dfsnufft_choose_params(int(n_lon), int(n_lat), float(tol), _dtype_code(dtype),
-                                        ctypes.byref(p)))
+    if options is None:
+        _check(lib().dfsnufft_choose_params(int(n_lon), int(n_lat), float(tol),
+                                            _dtype_code(dtype), ctypes.byref(p)))
+    else:
+        _check(lib().dfsnufft_choose_params_opts(int(n_lon), int(n_lat), float(tol),
+                                                 _dtype_code(dtype), ctypes.byref(options),
+                                                 ctypes.byref(p)))
     return p.as_dict()
 
 
@@ -210,6 +244,15 @@ def dfsnufft_plan_create_batch(n_members, n_lon, n_lat, tol, dtype, n_fields, st
     _check(lib().dfsnufft_plan_create_batch(int(n_members), int(n_lon), int(n_lat), float(tol),
                                             _dtype_code(dtype), int(n_fields),
                                             ctypes.c_void_p(int(stream or 0)), ctypes.byref(h)))
+    return h
+
+
+def dfsnufft_plan_create_opts(n_members, n_lon, n_lat, tol, dtype, n_fields, options, stream):
+    h = ctypes.c_void_p()
+    _check(lib().dfsnufft_plan_create_opts(int(n_members), int(n_lon), int(n_lat), float(tol),
+                                           _dtype_code(dtype), int(n_fields),
+                                           ctypes.byref(options) if options is not None else None,
+                                           ctypes.c_void_p(int(stream or 0)), ctypes.byref(h)))
     return h
 
 
@@ -298,11 +341,12 @@ class Plan:
     current stream at creation).  With ``n_members`` > 1 the plan is batched:
     coefficients (members, F, 2 n_lat, n_lon), points given per member
     (``set_points(lon, colat, counts)`` with concatenated arrays), values
-    concatenated per member (each F x P_k).
+    concatenated per member (each F x P_k).  ``options`` (an :class:`Options`)
+    sets the real-field mode, oversampling, kernel width and bin size.
     """
 
     def __init__(self, n_lon, n_lat, tol=1e-12, dtype="f64", n_fields=1, stream=None,
-                 n_members=1):
+                 n_members=1, options=None):
         import torch
         self.n_lon, self.n_lat = int(n_lon), int(n_lat)
         self.dtype = "f64" if _dtype_code(dtype) == F64 else "f32"
@@ -313,7 +357,10 @@ class Plan:
             stream = torch.cuda.current_stream()
         self.stream = stream
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-        if self.n_members == 1:
+        if options is not None:
+            self._h = dfsnufft_plan_create_opts(self.n_members, n_lon, n_lat, tol, self.dtype,
+                                                n_fields, options, handle)
+        elif self.n_members == 1:
             self._h = dfsnufft_plan_create(n_lon, n_lat, tol, self.dtype, n_fields, handle)
         else:
             self._h = dfsnufft_plan_create_batch(self.n_members, n_lon, n_lat, tol, self.dtype,
@@ -428,7 +475,7 @@ class Ensemble:
     float64 tensors/list, a (members, F, 2 n_lat, n_lon) complex tensor and an
     output tensor of F x sum(counts) reals; the whole step is one CUDA graph."""
 
-    def __init__(self, groups, tol=1e-6, dtype="f32", n_fields=3, stream=None):
+    def __init__(self, groups, tol=1e-6, dtype="f32", n_fields=3, stream=None, options=None):
         import torch
         self.groups = [tuple(int(x) for x in g) for g in groups]
         self.dtype = "f64" if _dtype_code(dtype) == F64 else "f32"
@@ -440,10 +487,15 @@ class Ensemble:
         G = len(self.groups)
         ai = lambda xs: (ctypes.c_int * G)(*xs)
         h = ctypes.c_void_p()
-        _check(lib().dfsnufft_ensemble_create(
+        opts = None
+        if options is not None:       # one Options per group
+            if len(options) != G:
+                raise ValueError("options must give one entry per group")
+            opts = (Options * G)(*options)
+        _check(lib().dfsnufft_ensemble_create_opts(
             G, ai([g[0] for g in self.groups]), ai([g[1] for g in self.groups]),
             ai([g[2] for g in self.groups]), float(tol), _dtype_code(dtype), self.n_fields,
-            ctypes.c_void_p(int(handle)), ctypes.byref(h)))
+            opts, ctypes.c_void_p(int(handle)), ctypes.byref(h)))
         self._h = h
         self._keep = None
 

@@ -85,6 +85,48 @@ def test_parameter_errors(lib):
         assert ei.value.status == code, args
 
 
+def test_options_defaults_equal_plain_choice(lib):
+    for args in ((64, 32, 1e-12, "f64"), (2048, 1024, 1e-6, "f32"), (8, 4, 1e-3, "f32")):
+        a = nufft.dfsnufft_choose_params(*args)
+        b = nufft.dfsnufft_choose_params(*args, options=nufft.Options())
+        assert a == b
+        assert a["sigma"] == 2 and a["flags"] == 0
+
+
+@pytest.mark.parametrize("tol,w2,w4", [(1e-12, 13, 11), (1e-9, 10, 9), (1e-6, 7, 6),
+                                       (1e-3, 4, 4), (1e-14, 15, 13)])
+def test_sigma4_width_rule(lib, tol, w2, w4):
+    """Oversampling 4: the narrowest width whose modelled error is at most
+    that of the sigma-2 width; beta = 0.97 pi (1 - 1/8) w; fine grid 4 N."""
+    p = nufft.dfsnufft_choose_params(256, 128, tol, "f64", options=nufft.Options.make(sigma=4))
+    assert nufft.dfsnufft_choose_params(256, 128, tol, "f64")["w"] == w2
+    assert p["w"] == w4 and p["sigma"] == 4
+    assert p["beta"] == pytest.approx(0.97 * math.pi * 0.875 * w4)
+    assert p["n1"] == 1024 and p["n2"] == 1024
+
+
+def test_options_explicit_fields(lib):
+    o = nufft.Options.make(real_fields=True, w=9, tile=(64, 8))
+    p = nufft.dfsnufft_choose_params(512, 256, 1e-6, "f32", options=o)
+    assert (p["w"], p["tile_x"], p["tile_y"], p["flags"]) == (9, 64, 8, 1)
+    assert p["beta"] == pytest.approx(2.30 * 9)
+    # at most 512 bin rows: tile_y is raised on a fine grid of 8192 rows
+    p = nufft.dfsnufft_choose_params(2048, 2048, 1e-6, "f32",
+                                     options=nufft.Options.make(tile=(32, 8)))
+    assert p["n2"] == 8192 and p["tile_y"] == 16
+
+
+@pytest.mark.parametrize("field,value", [("sigma", 3), ("sigma", 1), ("w", 1), ("w", 17),
+                                         ("tile_x", 48), ("tile_x", 4), ("tile_y", 256),
+                                         ("flags", 2)])
+def test_options_errors(lib, field, value):
+    o = nufft.Options()
+    setattr(o, field, value)
+    with pytest.raises(nufft.DfsError) as ei:
+        nufft.dfsnufft_choose_params(64, 32, 1e-6, "f64", options=o)
+    assert ei.value.status == nufft.ERR_INVALID_ARG
+
+
 def test_es_kernel_shape(lib):
     w, beta = 7, 2.30 * 7
     assert nufft.dfsnufft_es_kernel(0.0, w, beta) == 1.0
