@@ -140,18 +140,35 @@ class ClockSampler:
 
 
 def stage_bytes(prm, n_fields, n_points, rows):
-    """Algorithmic HBM bytes per launch of each stage (one execute of all fields)."""
+    """Algorithmic HBM bytes per launch of each stage (one execute of all fields):
+    what each stage must read and write once.  A real-field plan reads the
+    coefficient columns m >= 0 (plus the Nyquist column) and keeps N1/2 + 1
+    theta-pass columns; the fine grid holds the real part only."""
     cs = 16 if prm["dtype"] == 0 else 8
     rs = cs // 2
     N1, N2, n1 = prm["N1"], prm["N2"], prm["n1"]
     F, P = n_fields, n_points
+    herm = prm.get("flags", 0) & 1
+    cin = N1 // 2 + 2 if herm else N1            # coefficient columns read
+    tc = N1 // 2 + 1 if herm else N1             # theta-pass columns
     rec = 8 + 2 * rs + 4                       # sorted record: base int2, offsets, index
     return {
         "set_points": P * (16 + 4) + P * (16 + 4) + P * rec,
-        "theta_pass": F * (N2 * N1 * cs + rows * N1 * cs) + 8 * (N1 + N2),
-        "phi_pass": F * (rows * N1 * cs + rows * n1 * rs),     # writes the real part only
+        "theta_pass": F * (N2 * cin * cs + rows * tc * cs) + 8 * (N1 + N2),
+        "phi_pass": F * (rows * tc * cs + rows * n1 * rs),     # writes the real part only
         "interp": F * (rows * n1 * rs + P * rs) + P * rec,
     }
+
+
+def model_bytes(prm, n_fields, n_points):
+    """Bytes of the reference traffic model of one step: a complex oversampled
+    grid, two-pass pruned FFT and one interpolation pass, per field
+    N1 N2 c (1 + 2 sigma + 2 sigma^2) + 16 P / F + s_out P (13 N1 N2 c at sigma 2)."""
+    cs = 16 if prm["dtype"] == 0 else 8
+    rs = cs // 2
+    sg = prm.get("sigma", 2) or 2
+    per_field = prm["N1"] * prm["N2"] * cs * (1 + 2 * sg + 2 * sg * sg) + rs * n_points
+    return n_fields * per_field + 16 * n_points
 
 
 def interp_flops(prm, n_fields, n_points):
@@ -233,7 +250,8 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    plan = Plan(wl.n_lon, wl.n_lat, wl.tol, wl.dtype, F, stream=stream)
+    opts = nufft.Options.make(real_fields=not args.general)
+    plan = Plan(wl.n_lon, wl.n_lat, wl.tol, wl.dtype, F, stream=stream, options=opts)
     prm = plan.params
 
     def step():
@@ -329,6 +347,17 @@ def run_ours(args):
         ms = per_stage_ms[k]
         stages_out[k] = {"ms": ms, "bytes": sbytes[k],
                          "gbs": (sbytes[k] / (ms * 1e-3) / 1e9) if ms else None}
+    # whole step against HBM: this path's own algorithmic bytes, and the
+    # reference traffic model's (effective bandwidth)
+    step_s = total_ms / args.steps * 1e-3
+    own = sum(sbytes.values())
+    mod = model_bytes(prm, F, P)
+    roof_step = {"bound": "hbm", "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "own_bytes": own, "own_achieved": own / step_s / 1e9,
+                 "own_frac": own / step_s / 1e9 / pk["hbm_gbs"],
+                 "model_bytes": mod, "model_achieved": mod / step_s / 1e9,
+                 "model_frac": mod / step_s / 1e9 / pk["hbm_gbs"],
+                 "model": "13 N1 N2 c + 16 P / F + s_out P per field (complex grid, sigma 2)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -340,8 +369,11 @@ def run_ours(args):
                    "modes": "%dx%d" % (2 * wl.n_lat, wl.n_lon), "fields": F, "points": P,
                    "tol": wl.tol, "w": prm["w"], "fine": "%dx%d" % (prm["n2"], prm["n1"]),
                    "rows_needed": stats["rows_needed"], "l2": "flushed between steps (512 MiB write)",
+                   "real_fields": bool(prm["flags"] & 1), "tile": [prm["tile_x"], prm["tile_y"]],
+                   "sigma": prm["sigma"],
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
+        "roofline_step": roof_step,
         "stages": stages_out,
         "gpu_launches": 6 * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -419,7 +451,9 @@ def run_ensemble(args):
         host_out.append(torch.empty(3 * lon.size, dtype=torch.float32).pin_memory())
         total_pf += 3 * lon.size
     stream = torch.cuda.current_stream(dev)
-    ens = nufft.Ensemble(groups, tol=1e-6, dtype="f32", n_fields=3, stream=stream)
+    ens = nufft.Ensemble(groups, tol=1e-6, dtype="f32", n_fields=3, stream=stream,
+                         options=[nufft.Options.make(real_fields=not args.general)
+                                  for _ in groups])
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         flush.fill_(1)
@@ -518,7 +552,9 @@ def serving_sweep(dev, rates, seconds, budget_gb=120):
     order = np.random.default_rng(55).permutation(len(reqs))
     reqs = [reqs[i] for i in order]
     reqs64 = [reqs64[i] for i in order]
-    srv = Server(tol=1e-6, dtype="f32", n_fields=3, hbm_budget=int(budget_gb) << 30, max_batch=8)
+    from paper_2605_01313_gb300.nufft import Options
+    srv = Server(tol=1e-6, dtype="f32", n_fields=3, hbm_budget=int(budget_gb) << 30, max_batch=8,
+                 options=Options.make(real_fields=True))
     poisson_run(srv, reqs, 200, 0.5, seed=1)        # warm: slots created, plans resident
     out = []
     for k, rate in enumerate(rates):
@@ -615,6 +651,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--general", action="store_true",
+                    help="general plans (no real-field symmetry) instead of real-field plans")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds per rate of the serving sweep in the default run (0: skip)")
     args = ap.parse_args()

@@ -232,6 +232,12 @@ typedef struct dfsnufft_server_s *dfsnufft_server;
 int dfsnufft_server_create(double tol, int dtype, int n_fields, int64_t hbm_budget,
                            int max_batch, dfsnufft_server *out);
 
+/* The same with plan options for every slot (opts may be NULL; tile sizes
+ * that do not fit a grid are clamped as for a plan). */
+int dfsnufft_server_create_opts(double tol, int dtype, int n_fields, int64_t hbm_budget,
+                                int max_batch, const dfsnufft_options *opts,
+                                dfsnufft_server *out);
+
 /* Queue a request (thread-safe; returns at once with a ticket). */
 int dfsnufft_server_submit(dfsnufft_server srv, const dfsnufft_request *req, int64_t *ticket);
 

@@ -17,8 +17,8 @@
 // a general plan.  Column m = 0 takes its Hermitian part in full (its mirror is
 // the same column).  This halves the column transforms and the T buffer.
 //
-// Main kernel (k_theta_tma): persistent CTAs take blocks of CB columns (32-byte
-// row segments).  The block's N2 coefficient rows arrive in shared memory by
+// Main kernel (k_theta_tma): persistent CTAs take blocks of CB columns (16- or
+// 32-byte row segments).  The block's N2 coefficient rows arrive in shared memory by
 // 2-D TMA boxes, double-buffered so that the next block streams in while this
 // one is transformed.  Each column's length-n2 transform is done as two
 // length-n2/2 transforms: output row 2q + s = sum_n c_n e^{2 pi i n s / n2}
@@ -124,8 +124,8 @@ struct ThetaTmaArgs {
 
 // LOGH > 0: half length 2^LOGH fixed at compile time (unrolled transform);
 // LOGH == 0: taken from the arguments.
-template <typename R, int E, int CB, int MAXT, int LOGH, bool HERM>
-__global__ void __launch_bounds__(MAXT, 1)
+template <typename R, int E, int CB, int MAXT, int MINB, int LOGH, bool HERM>
+__global__ void __launch_bounds__(MAXT, MINB)
     k_theta_tma(ThetaTmaArgs a, const __grid_constant__ CUtensorMap tmap,
                 const typename CxT<R>::type *__restrict__ coef,
                 const R *__restrict__ inv1, const R *__restrict__ inv2,
@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(MAXT, 1)
     C *ex = inb + (size_t)a.nbuf * a.in_elems;
     const int H = LOGH ? (1 << LOGH) : (a.n2 >> 1);
     R *f2 = reinterpret_cast<R *>(ex + (size_t)CB * region_len<C>(H));   // 1 / phihat2, N2 rows
+    C *nyq = reinterpret_cast<C *>(f2 + ((a.N2 + 3) & ~3));   // real-field plans: CB values
     const int c = threadIdx.x % CB;
     const int t = threadIdx.x / CB;
     const int half = a.N2 / 2;
@@ -172,6 +173,16 @@ __global__ void __launch_bounds__(MAXT, 1)
         const int nxt = blk + gridDim.x;
         const bool pre = a.nbuf == 2 && nxt < a.total;
         if (pre && threadIdx.x == 0) issue(nxt, cur ^ 1);
+        if (HERM && threadIdx.x < CB) {
+            // conj c_{-N2/2,-m} of each column (the mirror of the Nyquist row),
+            // fetched while the block's boxes land
+            const int f = blk / a.nbq;
+            const int q = (blk - f * a.nbq) * CB + threadIdx.x;
+            const int qa = a.col_base + q;
+            C v = cmake((R)0, (R)0);
+            if (q < a.tcols) v = coef[(size_t)f * a.N2 * a.N1 + (a.N1 - qa)];
+            nyq[threadIdx.x] = cconj(v);
+        }
         const bool ok = mbar_wait_bounded(&bar[cur], cur ? phase1 : phase0);
         if (cur) phase1 ^= 1;
         else phase0 ^= 1;
@@ -194,19 +205,34 @@ __global__ void __launch_bounds__(MAXT, 1)
         const C *in = inb + (size_t)cur * a.in_elems;
         const C *cf0 = coef + (size_t)f * a.N2 * a.N1;
         C *dst = out + (size_t)f * a.n2 * a.tpitch + q;
-        // coefficient (row, col): this thread's column from the staged block,
-        // any other (Nyquist mirrors) from global memory
-        auto cf = [&](int r, int col) -> C {
-            if (r >= a.N2 || col >= a.N1) return cmake((R)0, (R)0);
-            if (col == qa) return in[r * CB + c];
-            return cf0[(size_t)r * a.N1 + col];
-        };
+        const bool k_zero = HERM && q == 0;            // m = 0: its own mirror
+        const bool k_nyq = HERM && qa == a.N1;         // m = N1/2: mirror of the Nyquist column
+        const C nyq_row = HERM ? nyq[c] : cmake((R)0, (R)0);
 #pragma unroll 1
         for (int s = 0; s < 2; ++s) {
+            // h_{n,m} (real-field plans, see herm_coef) or c_{n,m}, deconvolved
             auto term = [&](int n) -> C {
                 const int r = n + half;
-                C y = cscale(HERM ? herm_coef<C>(n, q, half, a.N1, cf) : in[r * CB + c],
-                             sq * f2[r < a.N2 ? r : 0]);
+                C v;
+                if constexpr (HERM) {
+                    if (k_nyq) {                       // one column per line: global loads
+                        v = n == -half ? cmake((R)0, (R)0)
+                                       : cscale(cconj(cf0[(size_t)(half - n) * a.N1]), (R)0.5);
+                    } else if (n == half) {
+                        v = cscale(nyq_row, (R)0.5);
+                    } else {
+                        v = in[r * CB + c];
+                        if (n == -half) {
+                            v = cscale(v, (R)0.5);
+                        } else if (k_zero) {
+                            const C mirror = in[(a.N2 - r) * CB + c];
+                            v = cscale(cmake(v.x + mirror.x, v.y - mirror.y), (R)0.5);
+                        }
+                    }
+                } else {
+                    v = in[r * CB + c];
+                }
+                C y = cscale(v, sq * f2[r < a.N2 ? r : 0]);
                 if (s) y = cmul(y, __ldg(&tw[n & (a.n2 - 1)]));
                 return y;
             };
@@ -231,19 +257,27 @@ __global__ void __launch_bounds__(MAXT, 1)
 }
 
 // Per precision: elements per thread E, threads per CTA at most MAXT, resident
-// CTAs MINB the register budget is set for (plain kernel); columns per block CB.
+// CTAs MINB the register budget is set for (plain kernel); for the TMA kernel
+// columns per block CB, threads at most TMAXT and TMINB resident CTAs per SM
+// (two CTAs of two columns each keep an SM busy while either waits at a
+// barrier of its transform).
 template <typename R> struct ThetaCfg;
-template <> struct ThetaCfg<float> { static const int E = DFS_FFT_E, MAXT = 1024, MINB = 1, CB = 4; };
-template <> struct ThetaCfg<double> { static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, CB = 2; };
+template <> struct ThetaCfg<float> {
+    static const int E = DFS_FFT_E, MAXT = 1024, MINB = 1, CB = 2, TMAXT = 512, TMINB = 2;
+};
+template <> struct ThetaCfg<double> {
+    static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, CB = 2, TMAXT = 512, TMINB = 1;
+};
 
 template <typename R, int LOGH, bool HERM>
 cudaError_t run_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUtensorMap &tmap,
                           const void *coeffs, size_t smem, int grid, int threads) {
     typedef typename CxT<R>::type C;
-    constexpr int E = ThetaCfg<R>::E, CB = ThetaCfg<R>::CB, MAXT = ThetaCfg<R>::MAXT;
-    cudaError_t e = allow_smem(k_theta_tma<R, E, CB, MAXT, LOGH, HERM>, smem);
+    constexpr int E = ThetaCfg<R>::E, CB = ThetaCfg<R>::CB, MAXT = ThetaCfg<R>::TMAXT,
+                  MINB = ThetaCfg<R>::TMINB;
+    cudaError_t e = allow_smem(k_theta_tma<R, E, CB, MAXT, MINB, LOGH, HERM>, smem);
     if (e) return e;
-    k_theta_tma<R, E, CB, MAXT, LOGH, HERM><<<grid, threads, smem, p->stream>>>(
+    k_theta_tma<R, E, CB, MAXT, MINB, LOGH, HERM><<<grid, threads, smem, p->stream>>>(
         a, tmap, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2,
         (const C *)p->d_tw2, (const C *)p->d_stw_theta, p->d_rowrange, (C *)p->d_T, p->d_status);
     return cudaGetLastError();
@@ -266,7 +300,8 @@ cudaError_t dispatch_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUt
 template <typename R>
 cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
     typedef typename CxT<R>::type C;
-    constexpr int E = ThetaCfg<R>::E, CB = ThetaCfg<R>::CB, MAXT = ThetaCfg<R>::MAXT;
+    constexpr int E = ThetaCfg<R>::E, CB = ThetaCfg<R>::CB, MAXT = ThetaCfg<R>::TMAXT,
+                  MINB = ThetaCfg<R>::TMINB;
     const dfsnufft_params &q = p->prm;
     if (((uintptr_t)coeffs & 15) != 0 || !p->d_status) return cudaErrorNotSupported;
     const int H = q.n2 / 2;
@@ -285,15 +320,16 @@ cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
     const int lines = p->n_members * p->n_fields;
     a.total = a.nbq * lines;
     a.F = p->n_fields;
-    // boxes of CB columns x box_rows rows, each a multiple of 128 bytes
-    // (CB * sizeof(C) = 32 bytes a row, box_rows a multiple of 4)
-    a.box_rows = q.N2 < 256 ? ((q.N2 + 3) & ~3) : 256;
+    // boxes of CB columns x box_rows rows, each a multiple of 128 bytes (box
+    // destinations stay 128-byte aligned): box_rows a multiple of ra rows
+    constexpr int ra = 128 / (CB * (int)sizeof(C));
+    a.box_rows = q.N2 < 256 ? ((q.N2 + ra - 1) / ra * ra) : 256;
     a.nbox = (q.N2 + a.box_rows - 1) / a.box_rows;
     a.in_elems = a.nbox * a.box_rows * CB;
     a.tx_bytes = (unsigned)(sizeof(C) * a.in_elems);
     const size_t ex_bytes = sizeof(C) * (size_t)CB * region_len<C>(H);
-    const size_t f2_bytes = sizeof(R) * (size_t)q.N2;
-    const size_t limit = 220 * 1024;
+    const size_t f2_bytes = sizeof(R) * (size_t)((q.N2 + 3) & ~3) + sizeof(C) * CB;
+    const size_t limit = (MINB > 1 ? 226 / MINB : 220) * 1024;
     const size_t in_bytes = sizeof(C) * (size_t)a.in_elems;
     a.nbuf = 256 + 2 * in_bytes + ex_bytes + f2_bytes <= limit ? 2 : 1;
     const size_t smem = 256 + a.nbuf * in_bytes + ex_bytes + f2_bytes;
@@ -305,7 +341,7 @@ cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
                                              (uint32_t)(CB * (sizeof(C) / 8)),
                                              (uint32_t)a.box_rows);
     if (e) return e;
-    int grid = p->num_sms > 0 ? p->num_sms : 1;
+    int grid = (p->num_sms > 0 ? p->num_sms : 1) * MINB;
     if (grid > a.total) grid = a.total;
     const int threads = CB * (H / E);
     if (p->herm) return dispatch_theta_tma<R, true>(p, a, tmap, coeffs, smem, grid, threads);

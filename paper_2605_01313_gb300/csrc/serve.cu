@@ -62,6 +62,7 @@ struct Slot {
 struct dfsnufft_server_s {
     double tol;
     int dtype, n_fields, max_batch;
+    dfsnufft_options opts;      // plan options of every slot
     size_t budget, reserved;
     int device;
     std::mutex mu;
@@ -84,7 +85,8 @@ size_t slot_bytes(const dfsnufft_params &q, int F, int cap, int64_t pts_cap) {
     const size_t rs = real_size(q.dtype), cs = 2 * rs;
     const size_t lines = (size_t)F * cap;
     size_t b = 0;
-    b += lines * q.n2 * q.N1 * cs;             // theta-pass output
+    const int herm = (q.flags & DFSNUFFT_REAL_FIELDS) ? 1 : 0;
+    b += lines * q.n2 * dfs_tpitch(herm, q.N1) * cs;   // theta-pass output
     b += lines * q.n2 * q.n1 * rs;             // fine grids
     b += lines * q.N2 * q.N1 * cs;             // staged coefficients
     b += (size_t)pts_cap * (16 + 4 + 8 + 2 * rs + 4);   // points, ranks, sorted records
@@ -106,7 +108,8 @@ void free_slot(Slot *s) {
 // A slot for this grid, or nullptr if the budget cannot hold one.
 Slot *make_slot(dfsnufft_server sv, int n_lon, int n_lat, int64_t pts_cap) {
     dfsnufft_params q;
-    if (dfsnufft_choose_params(n_lon, n_lat, sv->tol, sv->dtype, &q)) return nullptr;
+    if (dfsnufft_choose_params_opts(n_lon, n_lat, sv->tol, sv->dtype, &sv->opts, &q))
+        return nullptr;
     const int cap = sv->max_batch;
     const size_t need = slot_bytes(q, sv->n_fields, cap, pts_cap);
     if (sv->reserved + need > sv->budget) return nullptr;
@@ -120,8 +123,8 @@ Slot *make_slot(dfsnufft_server sv, int n_lon, int n_lat, int64_t pts_cap) {
     const size_t rs = real_size(sv->dtype), cs = 2 * rs;
     bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&s->event, cudaEventDisableTiming) == cudaSuccess &&
-              dfsnufft_plan_create_batch(cap, n_lon, n_lat, sv->tol, sv->dtype, sv->n_fields,
-                                         s->stream, &s->plan) == DFSNUFFT_OK &&
+              dfsnufft_plan_create_opts(cap, n_lon, n_lat, sv->tol, sv->dtype, sv->n_fields,
+                                        &sv->opts, s->stream, &s->plan) == DFSNUFFT_OK &&
               cudaMalloc(&s->coeffs, cs * (size_t)cap * sv->n_fields * q.N2 * q.N1) ==
                   cudaSuccess &&
               cudaMalloc((void **)&s->pts, 2 * sizeof(double) * (size_t)pts_cap) == cudaSuccess &&
@@ -302,14 +305,22 @@ void worker_loop(dfsnufft_server sv) {
 
 extern "C" int dfsnufft_server_create(double tol, int dtype, int n_fields, int64_t hbm_budget,
                                       int max_batch, dfsnufft_server *out) {
+    return dfsnufft_server_create_opts(tol, dtype, n_fields, hbm_budget, max_batch, nullptr, out);
+}
+
+extern "C" int dfsnufft_server_create_opts(double tol, int dtype, int n_fields,
+                                           int64_t hbm_budget, int max_batch,
+                                           const dfsnufft_options *opts, dfsnufft_server *out) {
     if (!out || n_fields < 1 || n_fields > 64 || hbm_budget <= 0 || max_batch < 1 ||
         max_batch > 256)
         return DFSNUFFT_ERR_INVALID_ARG;
     dfsnufft_params q;
-    int rc = dfsnufft_choose_params(64, 32, tol, dtype, &q);
+    int rc = dfsnufft_choose_params_opts(64, 32, tol, dtype, opts, &q);
     if (rc) return rc;
     dfsnufft_server sv = new (std::nothrow) dfsnufft_server_s();
     if (!sv) return DFSNUFFT_ERR_OOM;
+    memset(&sv->opts, 0, sizeof(sv->opts));
+    if (opts) sv->opts = *opts;
     sv->tol = tol;
     sv->dtype = dtype;
     sv->n_fields = n_fields;
@@ -334,7 +345,7 @@ extern "C" int dfsnufft_server_submit(dfsnufft_server sv, const dfsnufft_request
         !req->lon || !req->colat || !req->coeffs || !req->values)
         return DFSNUFFT_ERR_INVALID_ARG;
     dfsnufft_params q;
-    int rc = dfsnufft_choose_params(req->n_lon, req->n_lat, sv->tol, sv->dtype, &q);
+    int rc = dfsnufft_choose_params_opts(req->n_lon, req->n_lat, sv->tol, sv->dtype, &sv->opts, &q);
     if (rc) return rc;
     Request r;
     r.r = *req;

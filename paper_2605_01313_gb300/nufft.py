@@ -41,6 +41,7 @@ EXPORTS = (
     "dfsnufft_server_create", "dfsnufft_server_submit", "dfsnufft_server_wait",
     "dfsnufft_server_stats_get", "dfsnufft_server_destroy",
     "dfsnufft_choose_params_opts", "dfsnufft_plan_create_opts", "dfsnufft_ensemble_create_opts",
+    "dfsnufft_server_create_opts",
 )
 REAL_FIELDS = 1
 N_STAGES = 4
@@ -136,6 +137,8 @@ def lib():
         L.dfsnufft_ensemble_plan.argtypes = [vp, i32, ctypes.POINTER(vp)]
         L.dfsnufft_ensemble_destroy.argtypes = [vp]
         L.dfsnufft_server_create.argtypes = [f64, i32, i32, i64, i32, ctypes.POINTER(vp)]
+        L.dfsnufft_server_create_opts.argtypes = [f64, i32, i32, i64, i32,
+                                                  ctypes.POINTER(Options), ctypes.POINTER(vp)]
         L.dfsnufft_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(i64)]
         L.dfsnufft_server_wait.argtypes = [vp, i64, f64, ctypes.POINTER(i32), ctypes.POINTER(f64)]
         L.dfsnufft_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]

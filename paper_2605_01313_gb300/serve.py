@@ -16,13 +16,14 @@ class Server:
     tensors: lon, colat (float64, P), coeffs (F, 2 n_lat, n_lon complex), values
     (F, P real); the tensors are kept alive until the request completes."""
 
-    def __init__(self, tol=1e-6, dtype="f32", n_fields=3, hbm_budget=120 << 30, max_batch=8):
+    def __init__(self, tol=1e-6, dtype="f32", n_fields=3, hbm_budget=120 << 30, max_batch=8,
+                 options=None):
         self.dtype = dtype
         self.n_fields = int(n_fields)
         h = ctypes.c_void_p()
-        nufft._check(nufft.lib().dfsnufft_server_create(
+        nufft._check(nufft.lib().dfsnufft_server_create_opts(
             float(tol), nufft._dtype_code(dtype), self.n_fields, int(hbm_budget), int(max_batch),
-            ctypes.byref(h)))
+            ctypes.byref(options) if options is not None else None, ctypes.byref(h)))
         self._h = h
         self._live = {}
         self._lock = threading.Lock()
