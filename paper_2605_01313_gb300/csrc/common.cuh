@@ -29,6 +29,10 @@ __host__ __device__ __forceinline__ C cmul(C a, C b) {
 // Row-block granularity of the "fine rows needed" mask (rows per flag).
 #define DFS_ROW_BLOCK 16
 #define DFS_MAX_ROW_BLOCKS (8192 / DFS_ROW_BLOCK)
+// Bin scan: chunks of DFS_SCAN_CHUNK bins (one CTA each), at most
+// DFS_SCAN_MAXCH chunks (bins <= (8192/8) x DFS_MAX_ROW_BLOCKS).
+#define DFS_SCAN_CHUNK 4096
+#define DFS_SCAN_MAXCH 128
 #define DFS_FFT_MIN_LOG 4
 #define DFS_FFT_MAX_LOG 13
 // Event pairs kept per stage before read_timing must drain them.
@@ -42,6 +46,8 @@ struct dfsnufft_plan_s {
     int herm;               // DFSNUFFT_REAL_FIELDS: theta pass on columns m >= 0 only
     int nbx, nby, nbins;    // interpolation bins
     int bstride;            // per-member stride of the bin arrays: >= nbins + 1, multiple of 4
+    int cstride;            // per-member stride of d_bin_count: bstride + the scan workspace
+    int nch;                // bin-scan chunks, ceil(nbins / DFS_SCAN_CHUNK)
     cudaStream_t stream;
 
     // device buffers owned by the plan
@@ -53,7 +59,7 @@ struct dfsnufft_plan_s {
     void *d_stw_phi;        // stage-ordered twiddles of the length-n1/2 phi transforms
     void *d_T;              // theta-pass output, (members x fields) x n2 x dfs_tpitch columns
     void *d_G;              // fine grids (real part), (members x fields) x n2 x n1, plan precision
-    int *d_bin_count;       // members x bstride
+    int *d_bin_count;       // members x cstride: counts, then the scan workspace
     int *d_bin_start;       // members x bstride (nbins + 1 used), member-local positions
     int *d_task_bin;        // members x bstride: lists of non-empty bins
     int *d_n_tasks;         // members
@@ -97,6 +103,12 @@ struct dfsnufft_plan_s {
 __host__ __device__ __forceinline__ int dfs_tcols(int herm, int N1) { return herm ? N1 / 2 + 1 : N1; }
 __host__ __device__ __forceinline__ int dfs_tpitch(int herm, int N1) {
     return herm ? ((N1 / 2 + 1 + 3) & ~3) : N1;
+}
+
+// Ints per member of the count array: counts (bstride), completion counter (4),
+// bin-row flags (DFS_MAX_ROW_BLOCKS bytes), chunk sums and non-empty counts.
+__host__ __device__ __forceinline__ int dfs_cstride(int bstride) {
+    return bstride + 4 + DFS_MAX_ROW_BLOCKS / 4 + 2 * DFS_SCAN_MAXCH;
 }
 
 // ---------------------------------------------------------------- launches

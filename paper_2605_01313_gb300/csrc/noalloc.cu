@@ -130,6 +130,8 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     p.nby = prm.n2 / prm.tile_y;
     p.nbins = p.nbx * p.nby;
     p.bstride = (p.nbins + 4) & ~3;
+    p.cstride = dfs_cstride(p.bstride);
+    p.nch = (p.nbins + DFS_SCAN_CHUNK - 1) / DFS_SCAN_CHUNK;
     p.n_members = 1;
     p.n_points = n_points;
     p.cap_points = n_points;
@@ -141,7 +143,7 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     size_t off[20], total = 0;
     const size_t sizes[] = {rs * prm.N1, rs * prm.N2, cs * prm.n1,
                             cs * prm.n2, cs * nf * prm.n2 * prm.N1, rs * nf * prm.n2 * prm.n1,
-                            sizeof(int) * p.bstride, sizeof(int) * p.bstride,
+                            sizeof(int) * p.cstride, sizeof(int) * p.bstride,
                             sizeof(int) * p.bstride, sizeof(int), 2 * sizeof(int),
                             sizeof(int) * P, sizeof(int2) * P, 2 * rs * P, sizeof(int) * P,
                             sizeof(int2)};

@@ -464,6 +464,8 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
     p->nby = prm.n2 / prm.tile_y;
     p->nbins = p->nbx * p->nby;
     p->bstride = (p->nbins + 4) & ~3;     // 16-byte aligned member slices
+    p->cstride = dfs_cstride(p->bstride);
+    p->nch = (p->nbins + DFS_SCAN_CHUNK - 1) / DFS_SCAN_CHUNK;
 
     size_t cs = dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
     const size_t nf = (size_t)n_fields * n_members;      // FFT lines
@@ -477,7 +479,7 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
         {&p->d_stw_phi, cs * stage_table_len(prm.n1 / 2), "stage twiddles"},
         {&p->d_T, cs * nf * prm.n2 * dfs_tpitch(p->herm, prm.N1), "theta-pass buffer"},
         {&p->d_G, cs / 2 * nf * prm.n2 * prm.n1, "fine grid (real part)"},
-        {(void **)&p->d_bin_count, sizeof(int) * p->bstride * nm, "bin counts"},
+        {(void **)&p->d_bin_count, sizeof(int) * p->cstride * nm, "bin counts and scan workspace"},
         {(void **)&p->d_bin_start, sizeof(int) * p->bstride * nm, "bin starts"},
         {(void **)&p->d_task_bin, sizeof(int) * p->bstride * nm, "bin list"},
         {(void **)&p->d_n_tasks, sizeof(int) * nm, "bin list size"},

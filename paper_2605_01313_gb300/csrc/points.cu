@@ -103,7 +103,7 @@ __device__ __forceinline__ int bin_of(const FoldParams &f, int bx, int by) {
 __global__ void __launch_bounds__(256) k_fold_count(const double *__restrict__ lon,
                                                     const double *__restrict__ colat,
                                                     FoldParams f, const int *__restrict__ pofs,
-                                                    int bstride, int *__restrict__ bin_count,
+                                                    int cstride, int *__restrict__ bin_count,
                                                     int *__restrict__ rank) {
     const int k = blockIdx.y;
     const int p0 = pofs[k];
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) k_fold_count(const double *__restrict__ l
     const unsigned later = heads & ~(0xffffffffu >> (31 - lane));   // heads after this lane
     const int run_end = later ? __ffs(later) - 1 : 32 - __clz(live_mask);
     int base = 0;
-    if (head) base = atomicAdd(&bin_count[(size_t)k * bstride + bin], run_end - lane);
+    if (head) base = atomicAdd(&bin_count[(size_t)k * cstride + bin], run_end - lane);
     base = __shfl_sync(0xffffffffu, base, my_head);
     if (live) rank[p0 + pl] = base + lane - my_head;
 }
@@ -158,131 +158,202 @@ __device__ int next_bit(const unsigned *bits, int nb, int from, int value) {
 
 struct ScanParams {
     int nbins, nbx, nbr;      // bins, bins per bin row, bin rows in use (n2 / tile_y)
-    int bstride;              // per-member stride of the bin arrays (multiple of 4)
+    int bstride;              // per-member stride of the start and task arrays (multiple of 4)
+    int cstride;              // per-member stride of the count slice (counts + scan workspace)
+    int nch;                  // chunks of DFS_SCAN_CHUNK bins
     int tile_y, c0, w, n2;
 };
 
-// One CTA: exclusive scan of the bin counts and the list of non-empty bins, in
-// chunks of 16 * blockDim bins (each thread sixteen consecutive bins).  Then the
-// circular range of fine rows the stencils touch: the points of bin row by use
-// rows by*tile_y - c0 .. (by+1)*tile_y - c0 + w - 2, so the range is the
-// complement of the longest circular run of empty bin rows, widened by the
-// stencil and rounded out to whole row blocks.
-// grid (members): member k = blockIdx.x.
-__global__ void __launch_bounds__(1024) k_scan_bins(ScanParams sp, const int *__restrict__ count_all,
-                                                    int *__restrict__ start_all,
-                                                    int *__restrict__ task_all,
-                                                    int *__restrict__ n_tasks,
-                                                    int2 *__restrict__ rowrange) {
-    const int member = blockIdx.x;
-    // member slices start on 16-byte boundaries (bstride is a multiple of 4)
-    const int *count = count_all + (size_t)member * sp.bstride;
-    int *start = start_all + (size_t)member * sp.bstride;
-    int *task_bin = task_all + (size_t)member * sp.bstride;
-    __shared__ int s_sum[32], s_ne[32];
-    __shared__ unsigned char s_row[DFS_MAX_ROW_BLOCKS + 1];
-    __shared__ unsigned s_bits[(DFS_MAX_ROW_BLOCKS + 31) / 32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    const int nbins = sp.nbins;
-    for (int i = tid; i <= sp.nbr; i += blockDim.x) s_row[i] = 0;
+// Layout of a member's count slice (cstride ints, zeroed before each
+// set_points): counts [0, bstride), then the scan workspace: a completion
+// counter, the bin-row flags (bytes) and the chunk sums and non-empty counts.
+__device__ __forceinline__ int *ws_done(int *slice, const ScanParams &sp) { return slice + sp.bstride; }
+__device__ __forceinline__ unsigned char *ws_rows(int *slice, const ScanParams &sp) {
+    return reinterpret_cast<unsigned char *>(slice + sp.bstride + 4);
+}
+__device__ __forceinline__ int *ws_sum(int *slice, const ScanParams &sp) {
+    return slice + sp.bstride + 4 + DFS_MAX_ROW_BLOCKS / 4;
+}
+__device__ __forceinline__ int *ws_ne(int *slice, const ScanParams &sp) {
+    return ws_sum(slice, sp) + DFS_SCAN_MAXCH;
+}
+
+// Counts of bins [i0, i0 + 16) (zero past nbins); all loads issued first.
+__device__ __forceinline__ void load16(const int *count, int i0, int nbins, int *c) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + 4 * u;
+        if (i + 3 < nbins) {
+            const int4 v = *reinterpret_cast<const int4 *>(count + i);
+            c[4 * u] = v.x;
+            c[4 * u + 1] = v.y;
+            c[4 * u + 2] = v.z;
+            c[4 * u + 3] = v.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c[4 * u + q] = i + q < nbins ? count[i + q] : 0;
+        }
+    }
+}
+
+// Exclusive block-wide scan of (a, b) over the CTA's threads; returns the
+// thread's prefixes and the totals.  blockDim.x <= 1024.
+__device__ __forceinline__ void block_scan2(int a, int b, int &pa, int &pb, int &ta, int &tb) {
+    __shared__ int s_a[32], s_b[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int xa = a, xb = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ya = __shfl_up_sync(0xffffffffu, xa, o);
+        const int yb = __shfl_up_sync(0xffffffffu, xb, o);
+        if (lane >= o) {
+            xa += ya;
+            xb += yb;
+        }
+    }
+    if (lane == 31) {
+        s_a[wid] = xa;
+        s_b[wid] = xb;
+    }
     __syncthreads();
-    int carry = 0, carry_n = 0;
-    // each thread SCAN_V consecutive groups of four bins per pass, all loads
-    // issued before any is used
-    constexpr int SCAN_V = 4;
-    for (int base = 0; base < nbins; base += 4 * SCAN_V * blockDim.x) {
-        const int i0 = base + 4 * SCAN_V * tid;
-        int c[4 * SCAN_V];
-#pragma unroll
-        for (int u = 0; u < SCAN_V; ++u) {
-            const int i = i0 + 4 * u;
-            if (i + 3 < nbins) {
-                const int4 v = *reinterpret_cast<const int4 *>(count + i);
-                c[4 * u] = v.x;
-                c[4 * u + 1] = v.y;
-                c[4 * u + 2] = v.z;
-                c[4 * u + 3] = v.w;
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) c[4 * u + q] = i + q < nbins ? count[i + q] : 0;
-            }
-        }
-        int sum = 0, ne = 0;
-#pragma unroll
-        for (int q = 0; q < 4 * SCAN_V; ++q) {
-            sum += c[q];
-            ne += c[q] > 0;
-        }
-        int xs = sum, xn = ne;
+    if (wid == 0) {
+        int va = lane < nw ? s_a[lane] : 0;
+        int vb = lane < nw ? s_b[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int ys = __shfl_up_sync(0xffffffffu, xs, o);
-            const int yn = __shfl_up_sync(0xffffffffu, xn, o);
+            const int ya = __shfl_up_sync(0xffffffffu, va, o);
+            const int yb = __shfl_up_sync(0xffffffffu, vb, o);
             if (lane >= o) {
-                xs += ys;
-                xn += yn;
+                va += ya;
+                vb += yb;
             }
         }
-        if (lane == 31) {
-            s_sum[wid] = xs;
-            s_ne[wid] = xn;
+        if (lane < nw) {
+            s_a[lane] = va;
+            s_b[lane] = vb;
         }
-        __syncthreads();
-        if (wid == 0) {
-            int vs = lane < nw ? s_sum[lane] : 0;
-            int vn = lane < nw ? s_ne[lane] : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int ys = __shfl_up_sync(0xffffffffu, vs, o);
-                const int yn = __shfl_up_sync(0xffffffffu, vn, o);
-                if (lane >= o) {
-                    vs += ys;
-                    vn += yn;
-                }
-            }
-            if (lane < nw) {
-                s_sum[lane] = vs;
-                s_ne[lane] = vn;
-            }
-        }
-        __syncthreads();
-        int off_s = carry + xs - sum + (wid > 0 ? s_sum[wid - 1] : 0);
-        int off_n = carry_n + xn - ne + (wid > 0 ? s_ne[wid - 1] : 0);
-#pragma unroll
-        for (int u = 0; u < SCAN_V; ++u) {
-            const int i = i0 + 4 * u;
-            int st[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                st[q] = off_s;
-                off_s += c[4 * u + q];
-                if (c[4 * u + q] > 0 && i + q < nbins) {
-                    task_bin[off_n++] = i + q;
-                    s_row[(i + q) / sp.nbx] = 1;
-                }
-            }
-            if (i + 3 < nbins) {
-                *reinterpret_cast<int4 *>(start + i) = make_int4(st[0], st[1], st[2], st[3]);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (i + q < nbins) start[i + q] = st[q];
-            }
-        }
-        carry += s_sum[nw - 1];
-        carry_n += s_ne[nw - 1];
-        __syncthreads();
     }
-    // bin-row flags -> bits
+    __syncthreads();
+    pa = xa - a + (wid > 0 ? s_a[wid - 1] : 0);
+    pb = xb - b + (wid > 0 ? s_b[wid - 1] : 0);
+    ta = s_a[nw - 1];
+    tb = s_b[nw - 1];
+    __syncthreads();
+}
+
+// Pass 1 of the bin scan.  grid (nch, members), DFS_SCAN_CHUNK / 16 threads:
+// sum and number of non-empty bins of each chunk of DFS_SCAN_CHUNK bins.
+__global__ void __launch_bounds__(DFS_SCAN_CHUNK / 16) k_scan_sums(ScanParams sp,
+                                                                   int *__restrict__ count_all) {
+    int *slice = count_all + (size_t)blockIdx.y * sp.cstride;
+    int c[16];
+    load16(slice, blockIdx.x * DFS_SCAN_CHUNK + 16 * threadIdx.x, sp.nbins, c);
+    int sum = 0, ne = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        sum += c[q];
+        ne += c[q] > 0;
+    }
+    int pa, pb, ta, tb;
+    block_scan2(sum, ne, pa, pb, ta, tb);
+    if (threadIdx.x == 0) {
+        ws_sum(slice, sp)[blockIdx.x] = ta;
+        ws_ne(slice, sp)[blockIdx.x] = tb;
+    }
+}
+
+// Pass 2.  grid (nch, members): the chunk's offset from the sums of the chunks
+// before it, then each thread's sixteen bins: exclusive start offsets, the
+// list of non-empty bins (in bin order) and the bin-row flags.  The last CTA
+// of a member to finish (completion counter; the CTAs publish their flags with
+// a fence before counting) finds the circular range of fine rows the stencils
+// touch: the points of bin row by use rows by*tile_y - c0 .. (by+1)*tile_y -
+// c0 + w - 2, so the range is the complement of the longest circular run of
+// empty bin rows, widened by the stencil and rounded out to whole row blocks.
+__global__ void __launch_bounds__(DFS_SCAN_CHUNK / 16) k_scan_write(ScanParams sp,
+                                                                    int *__restrict__ count_all,
+                                                                    int *__restrict__ start_all,
+                                                                    int *__restrict__ task_all,
+                                                                    int *__restrict__ n_tasks,
+                                                                    int2 *__restrict__ rowrange) {
+    const int member = blockIdx.y, chunk = blockIdx.x;
+    int *slice = count_all + (size_t)member * sp.cstride;
+    int *start = start_all + (size_t)member * sp.bstride;
+    int *task_bin = task_all + (size_t)member * sp.bstride;
+    unsigned char *rows = ws_rows(slice, sp);
+    __shared__ unsigned char s_row[DFS_SCAN_CHUNK];
+    __shared__ unsigned s_bits[(DFS_MAX_ROW_BLOCKS + 31) / 32];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int nbins = sp.nbins;
+    const int first_bin = chunk * DFS_SCAN_CHUNK;
+    const int row_lo = first_bin / sp.nbx;                 // bin rows this chunk can touch
+    const int nrow = min(DFS_SCAN_CHUNK, (min(first_bin + DFS_SCAN_CHUNK, nbins) - 1) / sp.nbx -
+                                             row_lo + 1);
+    for (int i = tid; i < nrow; i += blockDim.x) s_row[i] = 0;
+    int c[16];
+    const int i0 = first_bin + 16 * tid;
+    load16(slice, i0, nbins, c);
+    // offsets of this chunk: the sums of the chunks before it
+    int cs = 0, cn = 0;
+    if (tid < chunk) {
+        cs = ws_sum(slice, sp)[tid];
+        cn = ws_ne(slice, sp)[tid];
+    }
+    int sum = 0, ne = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        sum += c[q];
+        ne += c[q] > 0;
+    }
+    int pa, pb, base_s, base_n;
+    block_scan2(cs, cn, pa, pb, base_s, base_n);
+    int ps, pn, ts, tn;
+    block_scan2(sum, ne, ps, pn, ts, tn);
+    int off_s = base_s + ps, off_n = base_n + pn;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + 4 * u;
+        int st[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            st[q] = off_s;
+            off_s += c[4 * u + q];
+            if (c[4 * u + q] > 0 && i + q < nbins) {
+                task_bin[off_n++] = i + q;
+                s_row[(i + q) / sp.nbx - row_lo] = 1;
+            }
+        }
+        if (i + 3 < nbins) {
+            *reinterpret_cast<int4 *>(start + i) = make_int4(st[0], st[1], st[2], st[3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (i + q < nbins) start[i + q] = st[q];
+        }
+    }
+    if (chunk == sp.nch - 1 && tid == 0) {
+        start[nbins] = base_s + ts;
+        n_tasks[member] = base_n + tn;
+    }
+    __syncthreads();
+    for (int i = tid; i < nrow; i += blockDim.x)
+        if (s_row[i]) rows[row_lo + i] = 1;
+    // publish the flags, then count this CTA done
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(ws_done(slice, sp), 1) == sp.nch - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // last CTA of the member: bin-row flags -> bits -> needed row range
     for (int k = wid; k * 32 < sp.nbr; k += nw) {
         const int i = k * 32 + lane;
-        const unsigned b = __ballot_sync(0xffffffffu, i < sp.nbr && s_row[i]);
+        const unsigned b = __ballot_sync(0xffffffffu, i < sp.nbr && __ldcg(rows + i) != 0);
         if (lane == 0) s_bits[k] = b;
     }
     __syncthreads();
     if (tid == 0) {
-        start[nbins] = carry;
-        n_tasks[member] = carry_n;
         const int nb = sp.nbr;
         const int s0 = next_bit(s_bits, nb, 0, 1);
         int2 range = make_int2(0, 0);
@@ -362,23 +433,28 @@ cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const doub
     f.nbx = p->nbx;
     const int M = p->n_members;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(p->d_bin_count, 0, sizeof(int) * (size_t)M * p->bstride, p->stream)))
+    if ((e = cudaMemsetAsync(p->d_bin_count, 0, sizeof(int) * (size_t)M * p->cstride, p->stream)))
         return e;
     const int tpb = 256;
     const dim3 grid((unsigned)((p->max_member_points + tpb - 1) / tpb), M);
-    k_fold_count<<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->bstride, p->d_bin_count,
+    k_fold_count<<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->cstride, p->d_bin_count,
                                               p->d_rank);
     ScanParams sp;
     sp.nbins = p->nbins;
     sp.bstride = p->bstride;
+    sp.cstride = p->cstride;
+    sp.nch = p->nch;
     sp.nbx = p->nbx;
     sp.nbr = q.n2 / q.tile_y;
     sp.tile_y = q.tile_y;
     sp.c0 = p->c0;
     sp.w = q.w;
     sp.n2 = q.n2;
-    k_scan_bins<<<M, 1024, 0, p->stream>>>(sp, p->d_bin_count, p->d_bin_start, p->d_task_bin,
-                                          p->d_n_tasks, p->d_rowrange);
+    const dim3 sgrid(p->nch, M);
+    k_scan_sums<<<sgrid, DFS_SCAN_CHUNK / 16, 0, p->stream>>>(sp, p->d_bin_count);
+    k_scan_write<<<sgrid, DFS_SCAN_CHUNK / 16, 0, p->stream>>>(sp, p->d_bin_count, p->d_bin_start,
+                                                             p->d_task_bin, p->d_n_tasks,
+                                                             p->d_rowrange);
     if (q.dtype == DFSNUFFT_F64)
         k_scatter<double><<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->bstride,
                                                       p->d_bin_start, p->d_rank, p->d_base,
