@@ -451,9 +451,22 @@ def run_ensemble(args):
         host_out.append(torch.empty(3 * lon.size, dtype=torch.float32).pin_memory())
         total_pf += 3 * lon.size
     stream = torch.cuda.current_stream(dev)
-    ens = nufft.Ensemble(groups, tol=1e-6, dtype="f32", n_fields=3, stream=stream,
-                         options=[nufft.Options.make(real_fields=not args.general)
-                                  for _ in groups])
+    # bin size, oversampling and kernel width per grid size from the autotuner
+    from paper_2605_01313_gb300 import autotune
+    t_tune = time.perf_counter()
+    opts, tuned = [], []
+    for gi, (m, n_lon, n_lat) in enumerate(groups):
+        best, cands = autotune.tune(n_lon, n_lat, pts[gi][0], pts[gi][1], pts[gi][2], cfs[gi],
+                                    tol=1e-6, dtype="f32", n_fields=3,
+                                    real_fields=not args.general, path=None)
+        opts.append(best)
+        ch = [c for c in cands if c["opts"] == best.as_dict()][0]
+        tuned.append({"grid": "%dx%d" % (n_lon, n_lat), "tile": [ch["params"]["tile_x"],
+                      ch["params"]["tile_y"]], "sigma": ch["params"]["sigma"],
+                      "w": ch["params"]["w"], "tuner_ms": ch["ms"], "tuner_err": ch["err"],
+                      "candidates": len(cands)})
+    t_tune = time.perf_counter() - t_tune
+    ens = nufft.Ensemble(groups, tol=1e-6, dtype="f32", n_fields=3, stream=stream, options=opts)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         flush.fill_(1)
@@ -503,6 +516,21 @@ def run_ensemble(args):
     if rank != 0:
         ens.destroy()
         return
+    # accuracy: the first member of every group against the oracle on its
+    # seeded check points (and the oracle's own rate on them)
+    import oracle
+    errs, o_pf, o_s = {}, 0, 0.0
+    for gi, (m, n_lon, n_lat) in enumerate(groups):
+        wl = by_size[(n_lon, n_lat)][0]
+        vals = outs[gi][:3 * wl.n_points].view(3, wl.n_points).cpu().numpy()
+        n = min(wl.sample.size, _oracle_sample_size(wl, args.cpu_seconds / len(groups)))
+        s_ = wl.sample[:n]
+        t0 = time.perf_counter()
+        ref = oracle.evaluate(wl.coeffs, wl.lon[s_], wl.colat[s_])
+        o_s += time.perf_counter() - t0
+        o_pf += 3 * n
+        errs["%dx%d" % (n_lon, n_lat)] = max(oracle.rel_linf(vals[f][s_], ref[f].real)
+                                             for f in range(3))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -513,6 +541,8 @@ def run_ensemble(args):
                    "groups": ["%dx(%dx%d)" % g for g in groups], "fields": 3,
                    "members": sum(g[0] for g in groups), "point_fields": total_pf, "tol": 1e-6,
                    "graph": "one CUDA graph launch per step (fork/join over group streams)",
+                   "real_fields": not args.general, "autotuned": tuned,
+                   "tune_seconds": t_tune,
                    "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": {"kernel": "whole step (all stages, all groups)", "bound": "hbm",
@@ -524,6 +554,12 @@ def run_ensemble(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": float(np.mean(e2e_ms))},
         "clocks": clocks,
+        "error": {"rel_linf_first_member": errs, "bound": 2e-5,
+                  "ok": max(errs.values()) <= 2e-5},
+        "cpu_baseline": {"value": o_pf / o_s, "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle",
+                         "sample": "seeded check points of the first member of each grid, "
+                                   "3 fields, FP64 direct sum (%d point-fields)" % o_pf},
     }
     ens.destroy()
     print(json.dumps(line), flush=True)

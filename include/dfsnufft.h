@@ -104,7 +104,7 @@ typedef struct {
  *   w      : kernel width 2..16, 0 = from tol and sigma.  A width below the
  *            rule's lowers the accuracy (the autotuner checks it).
  *   tile_x, tile_y : interpolation bin in fine cells, powers of two from 8 to
- *            128 (0 = the default: 32 x 16 for F32, 32 x 32 for F64); tile_y is
+ *            128 (0 = the default: 32 x 16 for F32, 128 x 16 for F64); tile_y is
  *            raised to n2/512 when smaller. */
 typedef struct {
     unsigned flags;
@@ -303,6 +303,47 @@ int dfsnufft_plan_read_timing(dfsnufft_plan plan, double *ms_total, int64_t *cal
  * rows, covering every row the points' stencils touch) and the number of
  * non-empty interpolation bins.  Measurement aid; no paper counterpart. */
 int dfsnufft_plan_point_stats(dfsnufft_plan plan, int64_t *rows_needed, int64_t *nonempty_bins);
+
+/* ---- autotuner -------------------------------------------------------------- */
+
+/* One workload to tune for (device pointers laid out as for a batched plan's
+ * set_points_batch and execute; the buffers are only read). */
+typedef struct {
+    int n_members, n_lon, n_lat;
+    double tol;
+    int dtype, n_fields;
+    unsigned flags;              /* DFSNUFFT_REAL_FIELDS or 0: kept by every candidate */
+    const int64_t *n_points;     /* host: n_members point counts                      */
+    const double *lon, *colat;   /* device: all members' points                        */
+    const void *coeffs;          /* device: n_members x n_fields x N2 x N1, plan type   */
+    int steps;                   /* timed steps per candidate (0: 5)                   */
+    void *stream;                /* cudaStream_t                                       */
+} dfsnufft_tune_args;
+
+typedef struct {
+    dfsnufft_options opts;       /* the candidate                                      */
+    dfsnufft_params prm;         /* the parameters its plan chose                      */
+    double ms;                   /* median time of set_points + execute (ms)           */
+    double err;                  /* largest relative l-inf error over the fields at a
+                                    sample of member 0's points (up to 4096), against an
+                                    FP64 plan at tol 1e-14                             */
+    int status;                  /* DFSNUFFT_OK, or why the candidate did not run      */
+} dfsnufft_tune_result;
+
+/* Choose the interpolation bin size, the oversampling factor and the kernel
+ * width for this workload by timing real plans on it (CUDA events on the given
+ * stream; synchronises it).  Stage 1 times every bin size of the candidate set
+ * (tile_x in 16..128, tile_y in 8..64, 128 to 4096 cells) at the width rule's
+ * kernel and oversampling 2; stage 2 tries, at the fastest bin, one kernel
+ * narrower than the rule and oversampling 4 (its own rule and one narrower).
+ * A candidate is accepted when its error is at most 10 tol (F64) or 20 tol
+ * (F32); *best receives the fastest accepted one (the default configuration is
+ * always a candidate).  Up to max_results candidates are copied to results
+ * (may be NULL) and their number to *n_results.  Allocates device memory for
+ * the reference and one candidate plan at a time.  No paper counterpart: the
+ * paper fixes its parameters by hand. */
+int dfsnufft_autotune(const dfsnufft_tune_args *args, dfsnufft_tune_result *results,
+                      int max_results, int *n_results, dfsnufft_options *best);
 
 /* ---- allocation-free one-shot call -------------------------------------- */
 

@@ -90,14 +90,21 @@ __global__ void __launch_bounds__(MAXT, MINB)
     else line_fft<E>(a.logm, tw, 1, sm, t, ld, st);
 }
 
+// Per precision: elements per thread E, threads per CTA at most MAXT with MINB
+// resident CTAs; rows longer than E x MAXT complex values (FP32 fine grids of
+// 8192 columns) use the wide form of MAXTW threads.
 template <typename R> struct PhiCfg;
-template <> struct PhiCfg<float> { static const int E = DFS_FFT_E, MAXT = 256, MINB = 3; };
-template <> struct PhiCfg<double> { static const int E = DFS_FFT_E, MAXT = 512, MINB = 1; };
+template <> struct PhiCfg<float> {
+    static const int E = DFS_FFT_E, MAXT = 256, MINB = 3, MAXTW = 512;
+};
+template <> struct PhiCfg<double> {
+    static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, MAXTW = 512;
+};
 
-template <typename R, int LOGM, bool HERM>
+template <typename R, int MAXT, int MINB, int LOGM, bool HERM>
 cudaError_t run_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
     typedef typename CxT<R>::type C;
-    constexpr int E = PhiCfg<R>::E, MAXT = PhiCfg<R>::MAXT, MINB = PhiCfg<R>::MINB;
+    constexpr int E = PhiCfg<R>::E;
     cudaError_t e = allow_smem(k_phi_pass<R, E, MAXT, MINB, LOGM, HERM>, smem);
     if (e) return e;
     k_phi_pass<R, E, MAXT, MINB, LOGM, HERM><<<grid, threads, smem, p->stream>>>(
@@ -108,12 +115,14 @@ cudaError_t run_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, i
 
 template <typename R, bool HERM>
 cudaError_t dispatch_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
-    if (!p->d_stw_phi) return run_phi<R, 0, HERM>(p, a, smem, grid, threads);
+    constexpr int MAXT = PhiCfg<R>::MAXT, MINB = PhiCfg<R>::MINB, MAXTW = PhiCfg<R>::MAXTW;
+    if (threads > MAXT) return run_phi<R, MAXTW, 1, 0, HERM>(p, a, smem, grid, threads);
+    if (!p->d_stw_phi) return run_phi<R, MAXT, MINB, 0, HERM>(p, a, smem, grid, threads);
     switch (a.logm) {
-        case 9: return run_phi<R, 9, HERM>(p, a, smem, grid, threads);
-        case 10: return run_phi<R, 10, HERM>(p, a, smem, grid, threads);
-        case 11: return run_phi<R, 11, HERM>(p, a, smem, grid, threads);
-        default: return run_phi<R, 0, HERM>(p, a, smem, grid, threads);
+        case 9: return run_phi<R, MAXT, MINB, 9, HERM>(p, a, smem, grid, threads);
+        case 10: return run_phi<R, MAXT, MINB, 10, HERM>(p, a, smem, grid, threads);
+        case 11: return run_phi<R, MAXT, MINB, 11, HERM>(p, a, smem, grid, threads);
+        default: return run_phi<R, MAXT, MINB, 0, HERM>(p, a, smem, grid, threads);
     }
 }
 

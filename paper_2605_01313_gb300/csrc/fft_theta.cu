@@ -269,12 +269,11 @@ template <> struct ThetaCfg<double> {
     static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, CB = 2, TMAXT = 512, TMINB = 1;
 };
 
-template <typename R, int LOGH, bool HERM>
+template <typename R, int CB, int LOGH, bool HERM>
 cudaError_t run_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUtensorMap &tmap,
                           const void *coeffs, size_t smem, int grid, int threads) {
     typedef typename CxT<R>::type C;
-    constexpr int E = ThetaCfg<R>::E, CB = ThetaCfg<R>::CB, MAXT = ThetaCfg<R>::TMAXT,
-                  MINB = ThetaCfg<R>::TMINB;
+    constexpr int E = ThetaCfg<R>::E, MAXT = ThetaCfg<R>::TMAXT, MINB = ThetaCfg<R>::TMINB;
     cudaError_t e = allow_smem(k_theta_tma<R, E, CB, MAXT, MINB, LOGH, HERM>, smem);
     if (e) return e;
     k_theta_tma<R, E, CB, MAXT, MINB, LOGH, HERM><<<grid, threads, smem, p->stream>>>(
@@ -283,25 +282,27 @@ cudaError_t run_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUtensor
     return cudaGetLastError();
 }
 
-template <typename R, bool HERM>
+template <typename R, int CB, bool HERM>
 cudaError_t dispatch_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUtensorMap &tmap,
                                const void *coeffs, size_t smem, int grid, int threads) {
-    if (!p->d_stw_theta) return run_theta_tma<R, 0, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+    if (!p->d_stw_theta)
+        return run_theta_tma<R, CB, 0, HERM>(p, a, tmap, coeffs, smem, grid, threads);
     switch (a.logh) {
-        case 9: return run_theta_tma<R, 9, HERM>(p, a, tmap, coeffs, smem, grid, threads);
-        case 10: return run_theta_tma<R, 10, HERM>(p, a, tmap, coeffs, smem, grid, threads);
-        case 11: return run_theta_tma<R, 11, HERM>(p, a, tmap, coeffs, smem, grid, threads);
-        default: return run_theta_tma<R, 0, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+        case 9: return run_theta_tma<R, CB, 9, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+        case 10: return run_theta_tma<R, CB, 10, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+        case 11: return run_theta_tma<R, CB, 11, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+        default: return run_theta_tma<R, CB, 0, HERM>(p, a, tmap, coeffs, smem, grid, threads);
     }
 }
 
-// Launch the TMA theta pass; returns cudaErrorNotSupported (without launching)
-// when the shape or the coefficient pointer does not suit it.
-template <typename R>
-cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
+// Launch the TMA theta pass with CB columns per block; returns
+// cudaErrorNotSupported (without launching) when the shape or the coefficient
+// pointer does not suit it.
+template <typename R, int CB>
+cudaError_t launch_theta_tma_cb(dfsnufft_plan p, const void *coeffs) {
     typedef typename CxT<R>::type C;
-    constexpr int E = ThetaCfg<R>::E, CB = ThetaCfg<R>::CB, MAXT = ThetaCfg<R>::TMAXT,
-                  MINB = ThetaCfg<R>::TMINB;
+    constexpr int E = ThetaCfg<R>::E, MAXT = ThetaCfg<R>::TMAXT, MINB = ThetaCfg<R>::TMINB;
+    static_assert(CB * sizeof(C) >= 16, "a TMA box row spans at least 16 bytes");
     const dfsnufft_params &q = p->prm;
     if (((uintptr_t)coeffs & 15) != 0 || !p->d_status) return cudaErrorNotSupported;
     const int H = q.n2 / 2;
@@ -344,15 +345,25 @@ cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
     int grid = (p->num_sms > 0 ? p->num_sms : 1) * MINB;
     if (grid > a.total) grid = a.total;
     const int threads = CB * (H / E);
-    if (p->herm) return dispatch_theta_tma<R, true>(p, a, tmap, coeffs, smem, grid, threads);
-    return dispatch_theta_tma<R, false>(p, a, tmap, coeffs, smem, grid, threads);
+    if (p->herm) return dispatch_theta_tma<R, CB, true>(p, a, tmap, coeffs, smem, grid, threads);
+    return dispatch_theta_tma<R, CB, false>(p, a, tmap, coeffs, smem, grid, threads);
 }
 
-template <typename R, bool HERM>
+// The configured block width, else (FP64 columns of 8192 fine rows) one column.
+template <typename R>
+cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
+    cudaError_t e = launch_theta_tma_cb<R, ThetaCfg<R>::CB>(p, coeffs);
+    if constexpr (sizeof(R) == 8) {
+        if (e == cudaErrorNotSupported) e = launch_theta_tma_cb<R, 1>(p, coeffs);
+    }
+    return e;
+}
+
+template <typename R, int E, bool HERM>
 cudaError_t run_theta_plain(dfsnufft_plan p, const ThetaArgs &a, const void *coeffs, size_t smem,
                             dim3 grid, int threads) {
     typedef typename CxT<R>::type C;
-    constexpr int E = ThetaCfg<R>::E, MAXT = ThetaCfg<R>::MAXT, MINB = ThetaCfg<R>::MINB;
+    constexpr int MAXT = ThetaCfg<R>::MAXT, MINB = ThetaCfg<R>::MINB;
     cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM>, smem);
     if (e) return e;
     k_theta_pass<R, E, MAXT, MINB, HERM><<<grid, threads, smem, p->stream>>>(
@@ -369,8 +380,11 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs) {
         if (e != cudaErrorNotSupported) return e;
         cudaGetLastError();
     }
-    constexpr int E = ThetaCfg<R>::E, MAXT = ThetaCfg<R>::MAXT;
+    constexpr int MAXT = ThetaCfg<R>::MAXT;
     const dfsnufft_params &q = p->prm;
+    // columns longer than E x MAXT values (FP64, 8192 fine rows): 16 a thread
+    const bool wide = q.n2 / ThetaCfg<R>::E > MAXT;
+    const int E = wide ? 16 : ThetaCfg<R>::E;
     ThetaArgs a;
     a.N1 = q.N1;
     a.N2 = q.N2;
@@ -390,8 +404,12 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs) {
     a.CB = cb;
     const size_t smem = per_col * cb;
     const dim3 grid((a.tcols + cb - 1) / cb, p->n_members * p->n_fields);
-    if (p->herm) return run_theta_plain<R, true>(p, a, coeffs, smem, grid, cb * T);
-    return run_theta_plain<R, false>(p, a, coeffs, smem, grid, cb * T);
+    if (wide) {
+        if (p->herm) return run_theta_plain<R, 16, true>(p, a, coeffs, smem, grid, cb * T);
+        return run_theta_plain<R, 16, false>(p, a, coeffs, smem, grid, cb * T);
+    }
+    if (p->herm) return run_theta_plain<R, ThetaCfg<R>::E, true>(p, a, coeffs, smem, grid, cb * T);
+    return run_theta_plain<R, ThetaCfg<R>::E, false>(p, a, coeffs, smem, grid, cb * T);
 }
 
 }  // namespace

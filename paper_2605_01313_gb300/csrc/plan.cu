@@ -279,8 +279,10 @@ extern "C" int dfsnufft_choose_params_opts(int n_lon, int n_lat, double tol, int
     out->dtype = dtype;
     out->sigma = sigma;
     out->flags = o.flags;
-    out->tile_x = o.tile_x ? o.tile_x : 32;
-    out->tile_y = o.tile_y ? o.tile_y : (dtype == DFSNUFFT_F32 ? 16 : 32);
+    // default bins: the autotuner's choice on the 2048 x 1024 workload in
+    // each precision (FP64: wide bins amortise the larger halo of w = 13)
+    out->tile_x = o.tile_x ? o.tile_x : (dtype == DFSNUFFT_F32 ? 32 : 128);
+    out->tile_y = o.tile_y ? o.tile_y : 16;
     if (out->tile_x > out->n1) out->tile_x = out->n1;
     if (out->tile_y > out->n2) out->tile_y = out->n2;
     // at most DFS_MAX_ROW_BLOCKS bin rows

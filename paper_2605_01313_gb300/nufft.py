@@ -41,7 +41,7 @@ EXPORTS = (
     "dfsnufft_server_create", "dfsnufft_server_submit", "dfsnufft_server_wait",
     "dfsnufft_server_stats_get", "dfsnufft_server_destroy",
     "dfsnufft_choose_params_opts", "dfsnufft_plan_create_opts", "dfsnufft_ensemble_create_opts",
-    "dfsnufft_server_create_opts",
+    "dfsnufft_server_create_opts", "dfsnufft_autotune",
 )
 REAL_FIELDS = 1
 N_STAGES = 4
@@ -76,6 +76,24 @@ class Options(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TuneArgs(ctypes.Structure):
+    _fields_ = [("n_members", ctypes.c_int), ("n_lon", ctypes.c_int), ("n_lat", ctypes.c_int),
+                ("tol", ctypes.c_double), ("dtype", ctypes.c_int), ("n_fields", ctypes.c_int),
+                ("flags", ctypes.c_uint), ("n_points", ctypes.c_void_p),
+                ("lon", ctypes.c_void_p), ("colat", ctypes.c_void_p),
+                ("coeffs", ctypes.c_void_p), ("steps", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("opts", Options), ("prm", Params), ("ms", ctypes.c_double),
+                ("err", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"opts": self.opts.as_dict(), "params": self.prm.as_dict(), "ms": self.ms,
+                "err": self.err, "status": self.status}
 
 
 class Request(ctypes.Structure):
@@ -137,6 +155,8 @@ def lib():
         L.dfsnufft_ensemble_plan.argtypes = [vp, i32, ctypes.POINTER(vp)]
         L.dfsnufft_ensemble_destroy.argtypes = [vp]
         L.dfsnufft_server_create.argtypes = [f64, i32, i32, i64, i32, ctypes.POINTER(vp)]
+        L.dfsnufft_autotune.argtypes = [ctypes.POINTER(TuneArgs), ctypes.POINTER(TuneResult), i32,
+                                        ctypes.POINTER(i32), ctypes.POINTER(Options)]
         L.dfsnufft_server_create_opts.argtypes = [f64, i32, i32, i64, i32,
                                                   ctypes.POINTER(Options), ctypes.POINTER(vp)]
         L.dfsnufft_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(i64)]

@@ -120,6 +120,32 @@ def test_f32_many_fields_whole_torus(torch_cuda):
     check_against_oracle(vals, base, TOL_F32, sample=sample, lon=lon, colat=colat)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("real", [False, True])
+def test_largest_fine_grid(torch_cuda, dtype, real):
+    """The largest grid a plan takes: 4096 x 4096 modes, fine grid 8192 x 8192
+    (the wide forms of both FFT passes), one field, points everywhere."""
+    from paper_2605_01313_gb300.nufft import Options
+    rng = np.random.default_rng(71)
+    n_lon, n_lat = 4096, 2048
+    c = synth.random_spectrum(rng, n_lon, n_lat, 3.0, synth.SCALAR)[None]
+    P = 20000
+    lon = rng.uniform(0, 2 * math.pi, P)
+    colat = rng.uniform(-math.pi, math.pi, P)
+    tol = 1e-12 if dtype == "f64" else 1e-6
+    from paper_2605_01313_gb300 import Plan
+    import torch
+    cd = torch.complex128 if dtype == "f64" else torch.complex64
+    with Plan(n_lon, n_lat, tol, dtype, 1, options=Options.make(real_fields=real)) as plan:
+        assert plan.params["n1"] == 8192 and plan.params["n2"] == 8192
+        plan.set_points(torch.from_numpy(lon).cuda(), torch.from_numpy(colat).cuda())
+        vals = plan.execute(torch.from_numpy(c).to(cd).cuda()).cpu().numpy()
+    s = np.arange(0, P, 200)
+    ref = oracle.evaluate(c, lon[s], colat[s])
+    err = oracle.rel_linf(vals[0][s], ref[0].real)
+    assert err <= (TOL_F64 if dtype == "f64" else TOL_F32), err
+
+
 def test_tolerance_sweep_monotone(torch_cuda):
     wl = synth.small_workload(7, 64, 32, n_fields=1, dtype="f64", points="uniform")
     ref = oracle.evaluate(wl.coeffs, wl.lon, wl.colat)[0].real
