@@ -249,6 +249,82 @@ __device__ __forceinline__ void line_fft_ct(const C *__restrict__ stw, C *sm, in
     ct_stages<LOGN, E, 0>(v, t, stw, sm, st);
 }
 
+// ---- two lines at once (compile-time length)
+//
+// The same transform applied to two register sets v0 and v1 (for instance the
+// two half-length transforms of one column): twiddle loads, index arithmetic
+// and barriers are shared, and each set exchanges through its own region.
+// after_first_barrier() runs on every thread right after the first barrier,
+// when no thread reads the inputs any more (the caller may refill them).
+
+template <int R, int E, int K, int NS, int OFF, int T, bool LAST, typename C, class St>
+__device__ __forceinline__ void ct_butterfly2(C *v0, C *v1, int t, const C *__restrict__ stw,
+                                              C *sm0, C *sm1, St &st) {
+    constexpr int G = E / R;
+    if constexpr (K < G) {
+        const int j = t + K * T;
+        const int jm = j & (NS - 1);
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const C w = __ldg(&stw[OFF + (r - 1) * NS + jm]);
+                v0[K + r * G] = cmul(v0[K + r * G], w);
+                v1[K + r * G] = cmul(v1[K + r * G], w);
+            }
+        }
+        dif_levels<R, K, G, R / 2>(v0);
+        dif_levels<R, K, G, R / 2>(v1);
+        const int base = (j - jm) * R + jm;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int o = base + bitrev(r, R) * NS;
+            if constexpr (LAST) {
+                st(o, v0[K + r * G], v1[K + r * G]);
+            } else {
+                sm0[spad<C>(o)] = v0[K + r * G];
+                sm1[spad<C>(o)] = v1[K + r * G];
+            }
+        }
+        ct_butterfly2<R, E, K + 1, NS, OFF, T, LAST>(v0, v1, t, stw, sm0, sm1, st);
+    }
+}
+
+template <int LOGN, int E, int LNS, typename C, class St, class Hook>
+__device__ __forceinline__ void ct_stages2(C *v0, C *v1, int t, const C *__restrict__ stw,
+                                           C *sm0, C *sm1, St &st, Hook &after_first_barrier) {
+    constexpr int LE = E == 16 ? 4 : E == 8 ? 3 : 2;
+    constexpr int REM = LOGN - LNS;
+    if constexpr (REM > 0) {
+        constexpr int LR = REM >= LE ? LE : REM;
+        constexpr int T = (1 << LOGN) / E;
+        if constexpr (LNS > 0) {
+            __syncthreads();
+            if constexpr (LNS == LE) after_first_barrier();
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                v0[e] = sm0[spad<C>(t + e * T)];
+                v1[e] = sm1[spad<C>(t + e * T)];
+            }
+            __syncthreads();
+        }
+        ct_butterfly2<(1 << LR), E, 0, (1 << LNS), stage_table_offset(LOGN, E, LNS), T,
+                      REM == LR>(v0, v1, t, stw, sm0, sm1, st);
+        ct_stages2<LOGN, E, LNS + LR>(v0, v1, t, stw, sm0, sm1, st, after_first_barrier);
+    }
+}
+
+// Two length-2^LOGN inverse FFTs (LOGN > LE: at least two stages) held by the
+// same threads: ld(i, a, b) gives input i of both, st(i, a, b) takes output i.
+template <int LOGN, int E, typename C, class Ld, class St, class Hook>
+__device__ __forceinline__ void line_fft_ct2(const C *__restrict__ stw, C *sm0, C *sm1, int t,
+                                             Ld &ld, St &st, Hook &after_first_barrier) {
+    constexpr int T = (1 << LOGN) / E;
+    C v0[E], v1[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) ld(t + e * T, v0[e], v1[e]);
+    ct_stages2<LOGN, E, 0>(v0, v1, t, stw, sm0, sm1, st, after_first_barrier);
+}
+
 __host__ __device__ __forceinline__ int ilog2(int n) {
     int l = 0;
     while ((1 << l) < n) ++l;

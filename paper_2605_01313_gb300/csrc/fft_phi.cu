@@ -90,6 +90,78 @@ __global__ void __launch_bounds__(MAXT, MINB)
     else line_fft<E>(a.logm, tw, 1, sm, t, ld, st);
 }
 
+// FP32 rows at compile-time lengths: each thread group transforms two rows
+// at once (line_fft_ct2: the twiddles, the index arithmetic and the barriers
+// serve both).  grid (n2 / CB, lines), CB = 2 x threads / (M/E) rows a CTA.
+template <int E, int MAXT, int MINB, int LOGM, bool HERM>
+__global__ void __launch_bounds__(MAXT, MINB)
+    k_phi_pass2(PhiArgs a, const float2 *__restrict__ in, const float2 *__restrict__ tw,
+                const float2 *__restrict__ stw, const int2 *__restrict__ rowrange,
+                float *__restrict__ grid) {
+    typedef float2 C;
+    const int row0 = blockIdx.x * a.CB;
+    const int2 rr = rowrange[blockIdx.y / a.F];
+    if (((row0 - rr.x) & (a.n2 - 1)) >= rr.y) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *smem = reinterpret_cast<C *>(smem_raw);
+    constexpr int M = 1 << LOGM;
+    constexpr int T = M / E;
+    const int t = threadIdx.x % T;
+    const int c = threadIdx.x / T;                 // row pair
+    const int row = row0 + 2 * c;
+    const int f = blockIdx.y;
+    const int half = a.N1 / 2;
+    const int nmask = a.n1 - 1;
+    const C *src = in + ((size_t)f * a.n2 + row) * a.tpitch;
+    float *dst = grid + ((size_t)f * a.n2 + row) * a.n1;
+    C *sm0 = smem + (size_t)(2 * c) * region_len<C>(M);
+    C *sm1 = sm0 + region_len<C>(M);
+    C *srow0 = smem + (size_t)a.CB * region_len<C>(M) + (size_t)(2 * c) * a.tcols;
+    C *srow1 = srow0 + a.tcols;
+    for (int i = t; i < a.tcols; i += T) {
+        srow0[i] = src[i];
+        srow1[i] = src[a.tpitch + i];
+    }
+    __syncthreads();
+    // H_k of a row (k mod n1): real-field rows hold H_k, k = 0..N1/2; general
+    // rows hold T_k and H_k = (T_k + conj T_{-k}) / 2
+    auto hval = [&](const C *sr, int k) -> C {
+        k &= nmask;
+        if constexpr (HERM) {
+            if (k <= half) return sr[k];
+            if (k >= a.n1 - half) {
+                const C v = sr[a.n1 - k];
+                return cmake(v.x, -v.y);
+            }
+            return cmake(0.f, 0.f);
+        } else {
+            auto tv = [&](int kk) -> C {
+                kk &= nmask;
+                if (kk < half) return sr[kk + half];
+                if (kk >= a.n1 - half) return sr[kk - a.n1 + half];
+                return cmake(0.f, 0.f);
+            };
+            const C p = tv(k), m = tv(-k);
+            return cmake(0.5f * (p.x + m.x), 0.5f * (p.y - m.y));
+        }
+    };
+    auto ld2 = [&](int k, C &z0, C &z1) {
+        const C w = __ldg(&tw[k]);
+        const C a0 = hval(srow0, k), b0 = hval(srow0, k + M);
+        const C a1 = hval(srow1, k), b1 = hval(srow1, k + M);
+        const C d0 = cmul(cmake(a0.x - b0.x, a0.y - b0.y), w);
+        const C d1 = cmul(cmake(a1.x - b1.x, a1.y - b1.y), w);
+        z0 = cmake(a0.x + b0.x - d0.y, a0.y + b0.y + d0.x);
+        z1 = cmake(a1.x + b1.x - d1.y, a1.y + b1.y + d1.x);
+    };
+    auto st2 = [&](int j, C z0, C z1) {
+        reinterpret_cast<C *>(dst)[j] = z0;
+        reinterpret_cast<C *>(dst + a.n1)[j] = z1;
+    };
+    auto none = [] {};
+    line_fft_ct2<LOGM, E>(stw, sm0, sm1, t, ld2, st2, none);
+}
+
 // Per precision: elements per thread E, threads per CTA at most MAXT with MINB
 // resident CTAs; rows longer than E x MAXT complex values (FP32 fine grids of
 // 8192 columns) use the wide form of MAXTW threads.
@@ -126,6 +198,17 @@ cudaError_t dispatch_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 gr
     }
 }
 
+template <int LOGM, bool HERM>
+cudaError_t run_phi2(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
+    constexpr int E = PhiCfg<float>::E;
+    cudaError_t e = allow_smem(k_phi_pass2<E, 256, 3, LOGM, HERM>, smem);
+    if (e) return e;
+    k_phi_pass2<E, 256, 3, LOGM, HERM><<<grid, threads, smem, p->stream>>>(
+        a, (const float2 *)p->d_T, (const float2 *)p->d_tw1, (const float2 *)p->d_stw_phi,
+        p->d_rowrange, (float *)p->d_G);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_phi(dfsnufft_plan p) {
     typedef typename CxT<R>::type C;
@@ -141,6 +224,21 @@ cudaError_t launch_phi(dfsnufft_plan p) {
     a.tpitch = dfs_tpitch(p->herm, q.N1);
     const int M = q.n1 / 2;
     const int T = M / E;
+    if (sizeof(R) == 4 && p->d_stw_phi && a.logm >= 9 && a.logm <= 11) {
+        // two rows a thread group, 256 threads a CTA
+        a.CB = 2 * (256 / T);
+        const size_t smem = sizeof(C) * (size_t)a.CB * (region_len<C>(M) + a.tcols);
+        const dim3 grid(q.n2 / a.CB, p->n_members * p->n_fields);
+        const int threads = (a.CB / 2) * T;
+        switch (a.logm) {
+            case 9: return p->herm ? run_phi2<9, true>(p, a, smem, grid, threads)
+                                   : run_phi2<9, false>(p, a, smem, grid, threads);
+            case 10: return p->herm ? run_phi2<10, true>(p, a, smem, grid, threads)
+                                    : run_phi2<10, false>(p, a, smem, grid, threads);
+            default: return p->herm ? run_phi2<11, true>(p, a, smem, grid, threads)
+                                    : run_phi2<11, false>(p, a, smem, grid, threads);
+        }
+    }
     int cb = MAXT / T;
     if (cb < 1) cb = 1;
     if (cb > DFS_ROW_BLOCK) cb = DFS_ROW_BLOCK;

@@ -123,7 +123,13 @@ struct ThetaTmaArgs {
 };
 
 // LOGH > 0: half length 2^LOGH fixed at compile time (unrolled transform);
-// LOGH == 0: taken from the arguments.
+// LOGH == 0: taken from the arguments.  DUAL (FP32 at compile-time lengths):
+// the two half-length transforms of a column run together in the same threads
+// (line_fft_ct2: twiddles, index arithmetic and barriers shared), which needs
+// one input buffer only: the next block's boxes are issued as soon as every
+// thread has read its inputs (after the transforms' first barrier), so they
+// land while this block is transformed.  Otherwise the halves run one after
+// the other and the next block streams into a second buffer when one fits.
 template <typename R, int E, int CB, int MAXT, int MINB, int LOGH, bool HERM>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_theta_tma(ThetaTmaArgs a, const __grid_constant__ CUtensorMap tmap,
@@ -133,6 +139,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
                 const typename CxT<R>::type *__restrict__ stw, const int2 *__restrict__ rowrange,
                 typename CxT<R>::type *__restrict__ out, int *__restrict__ status) {
     typedef typename CxT<R>::type C;
+    constexpr bool DUAL = LOGH > 0 && sizeof(R) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // TMA destinations start on 128-byte boundaries (base rounded up here;
     // buffer and box sizes are multiples of 128 bytes by construction)
@@ -141,12 +148,14 @@ __global__ void __launch_bounds__(MAXT, MINB)
     C *inb = reinterpret_cast<C *>(base + 128);
     C *ex = inb + (size_t)a.nbuf * a.in_elems;
     const int H = LOGH ? (1 << LOGH) : (a.n2 >> 1);
-    R *f2 = reinterpret_cast<R *>(ex + (size_t)CB * region_len<C>(H));   // 1 / phihat2, N2 rows
+    constexpr int NREG = DUAL ? 2 : 1;             // exchange regions per column
+    R *f2 = reinterpret_cast<R *>(ex + (size_t)NREG * CB * region_len<C>(H));   // 1 / phihat2
     C *nyq = reinterpret_cast<C *>(f2 + ((a.N2 + 3) & ~3));   // real-field plans: CB values
     const int c = threadIdx.x % CB;
     const int t = threadIdx.x / CB;
     const int half = a.N2 / 2;
     C *sm = ex + (size_t)c * region_len<C>(H);
+    C *sm1 = ex + (size_t)(CB + c) * region_len<C>(H);      // DUAL: the odd-row transform
     for (int i = threadIdx.x; i < a.N2; i += blockDim.x) f2[i] = inv2[i];
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -208,51 +217,94 @@ __global__ void __launch_bounds__(MAXT, MINB)
         const bool k_zero = HERM && q == 0;            // m = 0: its own mirror
         const bool k_nyq = HERM && qa == a.N1;         // m = N1/2: mirror of the Nyquist column
         const C nyq_row = HERM ? nyq[c] : cmake((R)0, (R)0);
-#pragma unroll 1
-        for (int s = 0; s < 2; ++s) {
-            // h_{n,m} (real-field plans, see herm_coef) or c_{n,m}, deconvolved
-            auto term = [&](int n) -> C {
-                const int r = n + half;
-                C v;
-                if constexpr (HERM) {
-                    if (k_nyq) {                       // one column per line: global loads
-                        v = n == -half ? cmake((R)0, (R)0)
-                                       : cscale(cconj(cf0[(size_t)(half - n) * a.N1]), (R)0.5);
-                    } else if (n == half) {
-                        v = cscale(nyq_row, (R)0.5);
-                    } else {
-                        v = in[r * CB + c];
-                        if (n == -half) {
-                            v = cscale(v, (R)0.5);
-                        } else if (k_zero) {
-                            const C mirror = in[(a.N2 - r) * CB + c];
-                            v = cscale(cmake(v.x + mirror.x, v.y - mirror.y), (R)0.5);
-                        }
-                    }
+        // h_{n,m} (real-field plans, see herm_coef) or c_{n,m}, deconvolved
+        auto coef_nm = [&](int n) -> C {
+            const int r = n + half;
+            C v;
+            if constexpr (HERM) {
+                if (k_nyq) {                           // one column per line: global loads
+                    v = n == -half ? cmake((R)0, (R)0)
+                                   : cscale(cconj(cf0[(size_t)(half - n) * a.N1]), (R)0.5);
+                } else if (n == half) {
+                    v = cscale(nyq_row, (R)0.5);
                 } else {
                     v = in[r * CB + c];
+                    if (n == -half) {
+                        v = cscale(v, (R)0.5);
+                    } else if (k_zero) {
+                        const C mirror = in[(a.N2 - r) * CB + c];
+                        v = cscale(cmake(v.x + mirror.x, v.y - mirror.y), (R)0.5);
+                    }
                 }
-                C y = cscale(v, sq * f2[r < a.N2 ? r : 0]);
-                if (s) y = cmul(y, __ldg(&tw[n & (a.n2 - 1)]));
-                return y;
+            } else {
+                v = in[r * CB + c];
+            }
+            return cscale(v, sq * f2[r < a.N2 ? r : 0]);
+        };
+        auto row_needed = [&](int row) { return ((row - rr.x) & (a.n2 - 1)) < rr.y; };
+        if constexpr (DUAL) {
+            // input i = t + e H/E of both halves: y_n and y_n e^{2 pi i n / n2}.
+            // With n2 = 2H the twiddle is e^{2 pi i t / n2} e^{i pi e / E}, negated
+            // for n = i - H: one table read a thread, the rest rotations by
+            // multiples of pi/8 that are constants once the loop over e unrolls.
+            constexpr int TT = (1 << LOGH) / E;
+            const C wt = __ldg(&tw[t]);
+            auto ld2 = [&](int i, C &y0, C &y1) {
+                y0 = y1 = cmake((R)0, (R)0);
+                if (!col_ok) return;
+                const int e = (i - t) / TT;
+                const C wi = cmul(wt, cmake((R)c16(e * (8 / E)), (R)s16(e * (8 / E))));
+                if (i < half) {
+                    const C y = coef_nm(i);
+                    y0 = y0 + y;
+                    y1 = y1 + cmul(y, wi);
+                } else if (i >= H - half) {
+                    const C y = coef_nm(i - H);
+                    y0 = y0 + y;
+                    y1 = y1 - cmul(y, wi);
+                }
+                if (HERM && i == half) {
+                    const C y = coef_nm(half);
+                    y0 = y0 + y;
+                    y1 = y1 + cmul(y, __ldg(&tw[half]));
+                }
             };
-            auto ld = [&](int i) -> C {
-                C y = cmake((R)0, (R)0);
-                if (!col_ok) return y;
-                if (i < half) y = term(i);
-                else if (i >= H - half) y = term(i - H);
-                if (HERM && i == half) y = y + term(half);
-                return y;
+            auto st2 = [&](int qq, C z0, C z1) {
+                if (!col_ok) return;
+                if (row_needed(2 * qq)) dst[(size_t)(2 * qq) * a.tpitch] = z0;
+                if (row_needed(2 * qq + 1)) dst[(size_t)(2 * qq + 1) * a.tpitch] = z1;
             };
-            auto st = [&](int qq, C v) {
-                const int row = 2 * qq + s;
-                if (col_ok && ((row - rr.x) & (a.n2 - 1)) < rr.y) dst[(size_t)row * a.tpitch] = v;
+            auto refill = [&]() {
+                if (threadIdx.x == 0 && a.nbuf == 1 && nxt < a.total) issue(nxt, 0);
             };
-            if constexpr (LOGH > 0) line_fft_ct<LOGH, E>(stw, sm, t, ld, st);
-            else line_fft<E>(a.logh, tw, 1, sm, t, ld, st);
+            line_fft_ct2<LOGH, E>(stw, sm, sm1, t, ld2, st2, refill);
             __syncthreads();
+        } else {
+#pragma unroll 1
+            for (int s = 0; s < 2; ++s) {
+                auto term = [&](int n) -> C {
+                    C y = coef_nm(n);
+                    if (s) y = cmul(y, __ldg(&tw[n & (a.n2 - 1)]));
+                    return y;
+                };
+                auto ld = [&](int i) -> C {
+                    C y = cmake((R)0, (R)0);
+                    if (!col_ok) return y;
+                    if (i < half) y = term(i);
+                    else if (i >= H - half) y = term(i - H);
+                    if (HERM && i == half) y = y + term(half);
+                    return y;
+                };
+                auto st = [&](int qq, C v) {
+                    const int row = 2 * qq + s;
+                    if (col_ok && row_needed(row)) dst[(size_t)row * a.tpitch] = v;
+                };
+                if constexpr (LOGH > 0) line_fft_ct<LOGH, E>(stw, sm, t, ld, st);
+                else line_fft<E>(a.logh, tw, 1, sm, t, ld, st);
+                __syncthreads();
+            }
+            if (a.nbuf == 1 && threadIdx.x == 0 && nxt < a.total) issue(nxt, 0);
         }
-        if (a.nbuf == 1 && threadIdx.x == 0 && nxt < a.total) issue(nxt, 0);
     }
 }
 
@@ -328,11 +380,13 @@ cudaError_t launch_theta_tma_cb(dfsnufft_plan p, const void *coeffs) {
     a.nbox = (q.N2 + a.box_rows - 1) / a.box_rows;
     a.in_elems = a.nbox * a.box_rows * CB;
     a.tx_bytes = (unsigned)(sizeof(C) * a.in_elems);
-    const size_t ex_bytes = sizeof(C) * (size_t)CB * region_len<C>(H);
+    // compile-time lengths in FP32 run both halves at once (see k_theta_tma)
+    const bool dual = sizeof(R) == 4 && p->d_stw_theta && a.logh >= 9 && a.logh <= 11;
+    const size_t ex_bytes = sizeof(C) * (size_t)(dual ? 2 : 1) * CB * region_len<C>(H);
     const size_t f2_bytes = sizeof(R) * (size_t)((q.N2 + 3) & ~3) + sizeof(C) * CB;
     const size_t limit = (MINB > 1 ? 226 / MINB : 220) * 1024;
     const size_t in_bytes = sizeof(C) * (size_t)a.in_elems;
-    a.nbuf = 256 + 2 * in_bytes + ex_bytes + f2_bytes <= limit ? 2 : 1;
+    a.nbuf = !dual && 256 + 2 * in_bytes + ex_bytes + f2_bytes <= limit ? 2 : 1;
     const size_t smem = 256 + a.nbuf * in_bytes + ex_bytes + f2_bytes;
     if (smem > limit) return cudaErrorNotSupported;
     CUtensorMap tmap;
