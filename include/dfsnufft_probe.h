@@ -1,7 +1,8 @@
 /*
  * dfsnufft_probe -- arithmetic-rate probe used to state the ALU roofline of
- * the FP64 form (the paper has no counterpart: it is a measurement aid of
- * this library, exported by the same shared object as dfsnufft.h).
+ * the FP64 form, and a self-test of the bounded waits (the paper has no
+ * counterpart: measurement and test aids of this library, exported by the
+ * same shared object as dfsnufft.h).
  */
 #ifndef DFSNUFFT_PROBE_H
 #define DFSNUFFT_PROBE_H
@@ -16,6 +17,16 @@ extern "C" {
  * stream for about target_ms milliseconds after a warm-up.  Synchronous.
  * Returns 0 and writes *flops_per_s, or a dfsnufft status code. */
 int dfsnufft_probe_fma_rate(int dtype, double target_ms, double *flops_per_s);
+
+/* Self-test of the bounded waits: one CTA initialises an mbarrier that
+ * nothing ever arrives on and waits on it with the same bounded wait the TMA
+ * kernels use, giving up after `cycles` SM clock cycles (1 <= cycles <= 4e9,
+ * about 2 s at 2 GHz).  The kernel then writes the timeout code to a device
+ * status word and returns, as the TMA kernels do, so the context stays usable.
+ * Synchronous.  *device_status receives the word (1 = timed out, the expected
+ * outcome), *elapsed_ms the kernel's duration.  No paper counterpart: a check
+ * of this library's failure detection that needs no GPU fault. */
+int dfsnufft_selftest_wait_timeout(long long cycles, int *device_status, double *elapsed_ms);
 
 #ifdef __cplusplus
 }

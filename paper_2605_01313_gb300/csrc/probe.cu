@@ -2,6 +2,7 @@
 // enough CTAs to fill every SM, timed with CUDA events.
 #include "common.cuh"
 #include "dfsnufft_probe.h"
+#include "tma.cuh"
 
 namespace {
 
@@ -75,4 +76,42 @@ extern "C" int dfsnufft_probe_fma_rate(int dtype, double target_ms, double *flop
     if (dtype == DFSNUFFT_F64) return probe<double>(target_ms, flops_per_s);
     if (dtype == DFSNUFFT_F32) return probe<float>(target_ms, flops_per_s);
     return DFSNUFFT_ERR_INVALID_ARG;
+}
+
+namespace {
+
+// One thread waits, bounded, on a barrier no one arrives on.
+__global__ void k_wait_nobody(long long cycles, int *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait_bounded(&bar, 0, cycles)) atomicExch(status, DFS_STATUS_TIMEOUT);
+}
+
+}  // namespace
+
+extern "C" int dfsnufft_selftest_wait_timeout(long long cycles, int *device_status,
+                                              double *elapsed_ms) {
+    if (!device_status || cycles < 1 || cycles > 4000000000LL) return DFSNUFFT_ERR_INVALID_ARG;
+    int *d = nullptr;
+    if (cudaMalloc(&d, sizeof(int))) return DFSNUFFT_ERR_OOM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = DFSNUFFT_OK;
+    float ms = 0;
+    if (cudaMemset(d, 0, sizeof(int)) || cudaEventCreate(&e0) || cudaEventCreate(&e1) ||
+        cudaEventRecord(e0, 0)) {
+        rc = DFSNUFFT_ERR_CUDA;
+    } else {
+        k_wait_nobody<<<1, 32>>>(cycles, d);
+        if (cudaGetLastError() || cudaEventRecord(e1, 0) || cudaEventSynchronize(e1) ||
+            cudaEventElapsedTime(&ms, e0, e1) ||
+            cudaMemcpy(device_status, d, sizeof(int), cudaMemcpyDeviceToHost))
+            rc = DFSNUFFT_ERR_CUDA;
+    }
+    if (elapsed_ms) *elapsed_ms = ms;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d);
+    return rc;
 }

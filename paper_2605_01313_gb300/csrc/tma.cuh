@@ -51,13 +51,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for phase `parity` of the barrier, for at most DFS_WAIT_CYCLES.
-// Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// Wait for phase `parity` of the barrier, for at most `budget` SM cycles
+// (DFS_WAIT_CYCLES by default).  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long budget = DFS_WAIT_CYCLES) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > DFS_WAIT_CYCLES) return false;
+        if (clock64() - t0 > budget) return false;
     }
     return true;
 }

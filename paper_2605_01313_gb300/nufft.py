@@ -41,7 +41,7 @@ EXPORTS = (
     "dfsnufft_server_create", "dfsnufft_server_submit", "dfsnufft_server_wait",
     "dfsnufft_server_stats_get", "dfsnufft_server_destroy",
     "dfsnufft_choose_params_opts", "dfsnufft_plan_create_opts", "dfsnufft_ensemble_create_opts",
-    "dfsnufft_server_create_opts", "dfsnufft_autotune",
+    "dfsnufft_server_create_opts", "dfsnufft_autotune", "dfsnufft_selftest_wait_timeout",
 )
 REAL_FIELDS = 1
 N_STAGES = 4
@@ -184,6 +184,8 @@ def lib():
         L.dfsnufft_plan_read_timing.argtypes = [vp, vp, vp]
         L.dfsnufft_plan_point_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.dfsnufft_probe_fma_rate.argtypes = [i32, f64, ctypes.POINTER(f64)]
+        L.dfsnufft_selftest_wait_timeout.argtypes = [ctypes.c_longlong, ctypes.POINTER(i32),
+                                                     ctypes.POINTER(f64)]
         L.dfsnufft_execute_noalloc.argtypes = [i32, i32, f64, i32, i32, i64, vp, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("dfsnufft_strerror", "dfsnufft_plan_last_error", "dfsnufft_es_kernel",
@@ -336,6 +338,15 @@ def dfsnufft_probe_fma_rate(dtype, target_ms=20.0) -> float:
     out = ctypes.c_double()
     _check(lib().dfsnufft_probe_fma_rate(_dtype_code(dtype), float(target_ms), ctypes.byref(out)))
     return out.value
+
+
+def dfsnufft_selftest_wait_timeout(cycles):
+    """(device status word, kernel ms) of a bounded wait on a barrier nothing
+    completes; status 1 means the wait gave up as designed."""
+    st = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(lib().dfsnufft_selftest_wait_timeout(int(cycles), ctypes.byref(st), ctypes.byref(ms)))
+    return st.value, ms.value
 
 
 def dfsnufft_execute_noalloc(n_lon, n_lat, tol, dtype, n_fields, n_points, lon_ptr, colat_ptr,
