@@ -17,6 +17,13 @@ Contents, each following the passage it cites:
   part, m = 0 with n >= 1).
 * :func:`eval_cossin` -- direct evaluation of the standard DFS real form
   (Eq. 4.6-4.7), an independent route to the same field values.
+* :func:`pr_to_std` -- the map from the partial-regularity DFS coefficients
+  (Sec. 4, the expansion with sin(theta) and sin^2(theta) factors) to the
+  standard DFS coefficients, in the paper's four cases (m = 0, m = 1, even
+  m >= 2, odd m >= 3), with the one entry the product-to-sum identities fix
+  differently from the printed list (f~_{0,m} = f_{1,m}/2 for even m >= 2).
+* :func:`eval_pr` -- direct evaluation of the partial-regularity expansion
+  (Sec. 4) from its own basis functions, the route that pins :func:`pr_to_std`.
 
 Every function here is pinned by the ``-m "not gpu"`` tests against closed
 forms, invariants and library special cases (see tests/test_oracle_pins.py).
@@ -160,6 +167,87 @@ def eval_cossin(fc: np.ndarray, fs: np.ndarray, lon: np.ndarray, colat: np.ndarr
         if m > 0:
             fsm = sum(fs[n, m] * basis[n] for n in range(n_lo, N + 1))
             out += fsm * np.sin(m * lon)
+    return out
+
+
+def pr_to_std(pc: np.ndarray, ps: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Sec. 4: partial-regularity DFS coefficients f_{n,m} (index [n, m], n = 0..N,
+    m = 0..M; cosine-in-phi part pc, sine part ps) to the standard DFS
+    coefficients f~_{n,m} of Eq. 4.6-4.7 (same index range).
+
+    Entries outside each case's range are ignored: m = 0 uses n = 0..N (cosine
+    part only); m = 1 uses n = 0..N-1; even m >= 2 uses n = 1..N-1; odd m >= 3
+    uses n = 1..N-2.  The four cases follow the paper; for even m >= 2 the
+    printed f~_{0,m} = 0 is replaced by f_{1,m}/2, which the identity
+    sin(t) sin(n t) = (cos((n-1)t) - cos((n+1)t))/2 gives at n = 1 (with 0 the
+    expansion would not vanish at the poles, as its sin(theta) factor requires).
+    """
+    N, M = pc.shape[0] - 1, pc.shape[1] - 1
+    if N < 6:
+        raise ValueError("the case formulas of the paper need N >= 6")
+    out = []
+    for f in (pc, ps):
+        g = np.zeros((N + 1, M + 1), dtype=np.float64)
+        for m in range(M + 1):
+            a = np.zeros(N + 3)                  # f_{n,m} on the case's range, zero elsewhere
+            if m == 0:
+                if f is ps:
+                    continue
+                g[:, 0] = f[:, 0]
+                continue
+            if m == 1:
+                a[0:N] = f[0:N, 1]
+                # sin t cos n t = (sin (n+1) t - sin (n-1) t) / 2
+                g[1, 1] = 0.5 * (2.0 * a[0] - a[2])
+                for n in range(2, N - 1):
+                    g[n, 1] = 0.5 * (a[n - 1] - a[n + 1])
+                for n in (N - 1, N):
+                    g[n, 1] = 0.5 * a[n - 1]
+            elif m % 2 == 0:
+                a[1:N] = f[1:N, m]
+                g[0, m] = 0.5 * a[1]
+                g[1, m] = 0.5 * a[2]
+                for n in range(2, N - 1):
+                    g[n, m] = 0.5 * (-a[n - 1] + a[n + 1])
+                for n in (N - 1, N):
+                    g[n, m] = -0.5 * a[n - 1]
+            else:
+                a[1:N - 1] = f[1:N - 1, m]
+                # sin^2 t sin n t = (2 sin n t - sin (n-2) t - sin (n+2) t) / 4
+                g[1, m] = 0.25 * (3.0 * a[1] - a[3])
+                g[2, m] = 0.25 * (2.0 * a[2] - a[4])
+                for n in range(3, N - 2):
+                    g[n, m] = 0.25 * (-a[n - 2] + 2.0 * a[n] - a[n + 2])
+                for n in (N - 2, N - 1):
+                    g[n, m] = 0.25 * (-a[n - 2] + 2.0 * a[n])
+                g[N, m] = -0.25 * a[N - 2]
+        out.append(g)
+    return out[0], out[1]
+
+
+def eval_pr(pc: np.ndarray, ps: np.ndarray, lon: np.ndarray, colat: np.ndarray) -> np.ndarray:
+    """Sec. 4: f = sum_m F^c_m(theta) cos m phi + F^s_m(theta) sin m phi with
+    F_0 = sum_{n=0}^N f_{n,0} cos n theta, F_1 = sum_{n=0}^{N-1} f_{n,1} sin theta cos n theta,
+    F_m = sum_{n=1}^{N-1} f_{n,m} sin theta sin n theta (even m >= 2) and
+    F_m = sum_{n=1}^{N-2} f_{n,m} sin^2 theta sin n theta (odd m >= 3)."""
+    lon = np.asarray(lon, dtype=np.float64)
+    colat = np.asarray(colat, dtype=np.float64)
+    N, M = pc.shape[0] - 1, pc.shape[1] - 1
+    st = np.sin(colat)
+    out = np.zeros(lon.shape, dtype=np.float64)
+    for m in range(M + 1):
+        if m == 0:
+            ns, basis = range(0, N + 1), lambda n: np.cos(n * colat)
+        elif m == 1:
+            ns, basis = range(0, N), lambda n: st * np.cos(n * colat)
+        elif m % 2 == 0:
+            ns, basis = range(1, N), lambda n: st * np.sin(n * colat)
+        else:
+            ns, basis = range(1, N - 1), lambda n: st * st * np.sin(n * colat)
+        fcm = sum(pc[n, m] * basis(n) for n in ns)
+        out += fcm * np.cos(m * lon)
+        if m > 0:
+            out += sum(ps[n, m] * basis(n) for n in ns) * np.sin(m * lon)
     return out
 
 

@@ -309,3 +309,69 @@ def test_pins_catch_planted_mistakes(oracle_mod, mistake):
         raise AssertionError(mistake)
 
     assert not (_single_mode_ok(bad) and _brute_ok(bad))
+
+
+# ------------------------------------------- partial-regularity DFS coefficients (Sec. 4)
+
+def _pr_coeffs(rng, N, M):
+    pc = rng.standard_normal((N + 1, M + 1))
+    ps = rng.standard_normal((N + 1, M + 1))
+    ps[:, 0] = 0.0
+    return pc, ps
+
+
+@pytest.mark.parametrize("N,M", [(12, 9), (8, 5), (31, 20)])
+def test_pr_map_matches_direct_pr_evaluation(oracle_mod, N, M):
+    """The standard coefficients from pr_to_std evaluate (Eq. 4.6-4.7) to the same
+    field as the partial-regularity basis functions of Sec. 4 evaluated
+    directly (trigonometric products, no product-to-sum step)."""
+    rng = np.random.default_rng(500 + N)
+    pc, ps = _pr_coeffs(rng, N, M)
+    lon, colat = _rand_points(rng, 400, full_torus=True)
+    fc, fs = oracle_mod.pr_to_std(pc, ps)
+    direct = oracle_mod.eval_pr(pc, ps, lon, colat)
+    assert np.max(np.abs(oracle_mod.eval_cossin(fc, fs, lon, colat) - direct)) < 1e-12
+
+
+def test_pr_expansion_is_pole_regular(oracle_mod):
+    """Every m >= 1 term carries a sin(theta) factor, so a field without m = 0
+    vanishes at both poles, whichever longitude (Sec. 4, property 3)."""
+    rng = np.random.default_rng(503)
+    pc, ps = _pr_coeffs(rng, 14, 10)
+    pc[:, 0] = 0.0
+    fc, fs = oracle_mod.pr_to_std(pc, ps)
+    lon = rng.uniform(0, 2 * math.pi, 50)
+    for pole in (0.0, math.pi):
+        th = np.full(50, pole)
+        assert np.max(np.abs(oracle_mod.eval_pr(pc, ps, lon, th))) < 1e-12
+        assert np.max(np.abs(oracle_mod.eval_cossin(fc, fs, lon, th))) < 1e-12
+
+
+def test_pr_printed_f0_for_even_m_would_fail(oracle_mod):
+    """The list in Sec. 4 prints f~_{0,m} = 0 for even m >= 2; the pin above
+    rejects that value (the sin(theta) sin(theta) term has a constant part)."""
+    rng = np.random.default_rng(504)
+    pc, ps = _pr_coeffs(rng, 12, 6)
+    fc, fs = oracle_mod.pr_to_std(pc, ps)
+    fc_printed, fs_printed = fc.copy(), fs.copy()
+    for m in range(2, 7, 2):
+        fc_printed[0, m] = fs_printed[0, m] = 0.0
+    lon, colat = _rand_points(rng, 200)
+    direct = oracle_mod.eval_pr(pc, ps, lon, colat)
+    assert np.max(np.abs(oracle_mod.eval_cossin(fc_printed, fs_printed, lon, colat)
+                         - direct)) > 1e-3
+
+
+def test_pr_through_complex_map_and_direct_sum(oracle_mod):
+    """The whole chain the GPU takes: partial-regularity -> standard (Sec. 4) ->
+    complex (Eq. 5.4) -> direct sum (Eq. 5.3) equals the direct PR evaluation."""
+    rng = np.random.default_rng(505)
+    n_lon, n_lat = 32, 16
+    N, M = 14, 15
+    pc, ps = _pr_coeffs(rng, N, M)
+    fc, fs = oracle_mod.pr_to_std(pc, ps)
+    c = oracle_mod.complex_from_cossin(fc, fs, n_lon, n_lat)
+    lon, colat = _rand_points(rng, 300, full_torus=True)
+    v = oracle_mod.evaluate(c[None], lon, colat)[0]
+    assert np.max(np.abs(v.imag)) < 1e-12
+    assert np.max(np.abs(v.real - oracle_mod.eval_pr(pc, ps, lon, colat))) < 1e-12
