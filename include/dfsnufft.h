@@ -259,6 +259,24 @@ int dfsnufft_server_destroy(dfsnufft_server srv);
  *            written in full. */
 int dfsnufft_execute(dfsnufft_plan plan, const void *coeffs, void *values);
 
+/* Evaluate fields given by the coefficients of the paper's partial-regularity
+ * DFS expansion (Sec. 4):
+ *   f = sum_m F^c_m(theta) cos m phi + F^s_m(theta) sin m phi,
+ *   F_0 = sum_{n=0}^{N} f_{n,0} cos n theta,
+ *   F_1 = sum_{n=0}^{N-1} f_{n,1} sin theta cos n theta,
+ *   F_m = sum_{n=1}^{N-1} f_{n,m} sin theta sin n theta      (even m >= 2),
+ *   F_m = sum_{n=1}^{N-2} f_{n,m} sin^2 theta sin n theta    (odd m >= 3),
+ * at the plan's points.  The coefficients are converted to the complex ones of
+ * Eq. 5.4 inside the theta pass (through the standard DFS coefficients, Sec. 4),
+ * with no extra pass over memory.
+ *   pr : device pointer, (n_members x) n_fields x (M + 1) x (N + 1) complex in
+ *        plan precision, element [m][n] = f^c_{n,m} + i f^s_{n,m} (n fastest);
+ *        entries outside each m's index range above, and the sine part of
+ *        m = 0, are ignored.
+ *   0 <= M <= n_lon/2 - 1, 1 <= N <= n_lat - 1.  The plan must be a real-field
+ *   plan (DFSNUFFT_REAL_FIELDS); values as for dfsnufft_execute. */
+int dfsnufft_execute_pr(dfsnufft_plan plan, int M, int N, const void *pr, void *values);
+
 /* Host-buffer variants: the same operations with host pointers.  The data are
  * copied to plan-owned device buffers on the plan's stream (pinned host memory
  * makes the copies asynchronous); dfsnufft_execute_host waits for the stream

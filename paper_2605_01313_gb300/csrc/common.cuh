@@ -115,7 +115,9 @@ __host__ __device__ __forceinline__ int dfs_cstride(int bstride) {
 // points.cu
 cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const double *colat);
 // fft.cu
-cudaError_t dfs_launch_theta_pass(dfsnufft_plan p, const void *coeffs);
+// prM >= 0: coeffs holds partial-regularity coefficients truncated at (prM, prN)
+cudaError_t dfs_launch_theta_pass(dfsnufft_plan p, const void *coeffs, int prM = -1,
+                                  int prN = -1);
 cudaError_t dfs_launch_phi_pass(dfsnufft_plan p);
 // interp.cu
 cudaError_t dfs_launch_interp(dfsnufft_plan p, void *values);

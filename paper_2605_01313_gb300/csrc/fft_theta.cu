@@ -59,15 +59,62 @@ __device__ __forceinline__ C herm_coef(int n, int k, int half, int N1, Rd &cf) {
     return c;
 }
 
+// Complex coefficient c_{n,m} (m >= 0, |n| <= N) of a field given by its
+// partial-regularity DFS coefficients (Sec. 4): col[k] = f^c_{k,m} + i f^s_{k,m},
+// k = 0..N, for this m.  First the standard coefficient S = f~^c + i f~^s at |n|
+// (the product-to-sum stencil of Sec. 4 for the case of m; f~_{0,m} = f_{1,m}/2
+// for even m >= 2, which the identity gives in place of the printed 0), then
+// Eq. 5.4: c = S/2 (m = 0, n != 0; S for n = 0), conj(S)/2 or /4 (even m), and
+// -sign(n) i conj(S)/4 (odd m).  The stencils are linear with real weights, so
+// they act on the cosine and sine parts at once.
+template <typename C>
+__device__ __forceinline__ C pr_coef(int n, int m, int N, const C *__restrict__ col) {
+    typedef decltype(C().x) R;
+    const int na = n < 0 ? -n : n;
+    // f_{k,m} on the case's index range, zero elsewhere
+    auto f = [&](int k, int lo, int hi) -> C {
+        return (k >= lo && k <= hi) ? col[k] : cmake((R)0, (R)0);
+    };
+    C S;
+    if (m == 0) {
+        if (na > N) return cmake((R)0, (R)0);
+        const R v = col[na].x;                             // no sine part at m = 0
+        return cmake(na == 0 ? v : (R)0.5 * v, (R)0);
+    } else if (m == 1) {
+        if (na == 0) return cmake((R)0, (R)0);
+        // sin t cos k t = (sin (k+1) t - sin (k-1) t) / 2, k = 0..N-1
+        S = cscale(f(na - 1, 0, N - 1) - f(na + 1, 0, N - 1), (R)0.5);
+        if (na == 1) S = S + cscale(f(0, 0, N - 1), (R)0.5);
+    } else if ((m & 1) == 0) {
+        // sin t sin k t = (cos (k-1) t - cos (k+1) t) / 2, k = 1..N-1
+        S = na == 0 ? cscale(f(1, 1, N - 1), (R)0.5)
+                    : cscale(f(na + 1, 1, N - 1) - f(na - 1, 1, N - 1), (R)0.5);
+    } else {
+        if (na == 0) return cmake((R)0, (R)0);
+        // sin^2 t sin k t = (2 sin k t - sin (k-2) t - sin (k+2) t) / 4, k = 1..N-2
+        S = cscale(cscale(f(na, 1, N - 2), (R)2) - f(na - 2, 1, N - 2) - f(na + 2, 1, N - 2),
+                   (R)0.25);
+        if (na == 1) S = S + cscale(f(1, 1, N - 2), (R)0.25);
+    }
+    const C cs = cmake(S.x, -S.y);                         // conj(S) = f~^c - i f~^s
+    if ((m & 1) == 0) return cscale(cs, na == 0 ? (R)0.5 : (R)0.25);
+    // -sign(n) i conj(S) / 4
+    const R g = n > 0 ? (R)-0.25 : (R)0.25;
+    return cmake(-g * cs.y, g * cs.x);
+}
+
 struct ThetaArgs {
     int N1, N2, n2, logn2;
     int CB;                   // columns per CTA
     int F;                    // fields per member (line f belongs to member f / F)
     int tcols, tpitch;        // transformed columns, row pitch of T
+    int prM, prN;             // partial-regularity input: truncation (prM < 0: complex input)
 };
 
 // grid (ceil(tcols / CB), lines); block CB * n2/E threads, thread = (t, c) with c fastest.
-template <typename R, int E, int MAXT, int MINB, bool HERM>
+// PRIN (real-field plans): the input is partial-regularity DFS coefficients,
+// lines x (prM + 1) x (prN + 1) complex, converted on the fly by pr_coef.
+template <typename R, int E, int MAXT, int MINB, bool HERM, bool PRIN = false>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_theta_pass(ThetaArgs a, const typename CxT<R>::type *__restrict__ coef,
                  const R *__restrict__ inv1, const R *__restrict__ inv2,
@@ -100,8 +147,15 @@ __global__ void __launch_bounds__(MAXT, MINB)
         else return cmake((R)0, (R)0);
         const int r = n + half;
         const R s = sq * inv2[r < a.N2 ? r : 0];
-        if constexpr (HERM) return cscale(herm_coef<C>(n, q, half, a.N1, cf), s);
-        else return cscale(cf(r, qa), s);
+        if constexpr (PRIN) {
+            if (q > a.prM || n > a.prN || n < -a.prN) return cmake((R)0, (R)0);
+            const C *col = coef + ((size_t)f * (a.prM + 1) + q) * (a.prN + 1);
+            return cscale(pr_coef<C>(n, q, a.prN, col), s);
+        } else if constexpr (HERM) {
+            return cscale(herm_coef<C>(n, q, half, a.N1, cf), s);
+        } else {
+            return cscale(cf(r, qa), s);
+        }
     };
     auto st = [&](int i, C v) {
         if (col_ok && ((i - rr.x) & (a.n2 - 1)) < rr.y) dst[(size_t)i * a.tpitch] = v;
@@ -413,23 +467,23 @@ cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
     return e;
 }
 
-template <typename R, int E, bool HERM>
+template <typename R, int E, bool HERM, bool PRIN = false>
 cudaError_t run_theta_plain(dfsnufft_plan p, const ThetaArgs &a, const void *coeffs, size_t smem,
                             dim3 grid, int threads) {
     typedef typename CxT<R>::type C;
     constexpr int MAXT = ThetaCfg<R>::MAXT, MINB = ThetaCfg<R>::MINB;
-    cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM>, smem);
+    cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM, PRIN>, smem);
     if (e) return e;
-    k_theta_pass<R, E, MAXT, MINB, HERM><<<grid, threads, smem, p->stream>>>(
+    k_theta_pass<R, E, MAXT, MINB, HERM, PRIN><<<grid, threads, smem, p->stream>>>(
         a, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2, (const C *)p->d_tw2,
         p->d_rowrange, (C *)p->d_T);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs) {
+cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs, int prM, int prN) {
     typedef typename CxT<R>::type C;
-    {
+    if (prM < 0) {
         cudaError_t e = launch_theta_tma<R>(p, coeffs);
         if (e != cudaErrorNotSupported) return e;
         cudaGetLastError();
@@ -447,6 +501,8 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs) {
     a.F = p->n_fields;
     a.tcols = dfs_tcols(p->herm, q.N1);
     a.tpitch = dfs_tpitch(p->herm, q.N1);
+    a.prM = prM;
+    a.prN = prN;
     const int T = q.n2 / E;
     int cb = MAXT / T;
     if (cb < 1) cb = 1;
@@ -458,6 +514,11 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs) {
     a.CB = cb;
     const size_t smem = per_col * cb;
     const dim3 grid((a.tcols + cb - 1) / cb, p->n_members * p->n_fields);
+    if (prM >= 0) {
+        if (!p->herm) return cudaErrorInvalidValue;
+        if (wide) return run_theta_plain<R, 16, true, true>(p, a, coeffs, smem, grid, cb * T);
+        return run_theta_plain<R, ThetaCfg<R>::E, true, true>(p, a, coeffs, smem, grid, cb * T);
+    }
     if (wide) {
         if (p->herm) return run_theta_plain<R, 16, true>(p, a, coeffs, smem, grid, cb * T);
         return run_theta_plain<R, 16, false>(p, a, coeffs, smem, grid, cb * T);
@@ -468,7 +529,7 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs) {
 
 }  // namespace
 
-cudaError_t dfs_launch_theta_pass(dfsnufft_plan p, const void *coeffs) {
-    return p->prm.dtype == DFSNUFFT_F64 ? launch_theta<double>(p, coeffs)
-                                        : launch_theta<float>(p, coeffs);
+cudaError_t dfs_launch_theta_pass(dfsnufft_plan p, const void *coeffs, int prM, int prN) {
+    return p->prm.dtype == DFSNUFFT_F64 ? launch_theta<double>(p, coeffs, prM, prN)
+                                        : launch_theta<float>(p, coeffs, prM, prN);
 }

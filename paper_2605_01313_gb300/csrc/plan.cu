@@ -659,6 +659,25 @@ extern "C" int dfsnufft_execute(dfsnufft_plan p, const void *coeffs, void *value
     return DFSNUFFT_OK;
 }
 
+extern "C" int dfsnufft_execute_pr(dfsnufft_plan p, int M, int N, const void *pr, void *values) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    if (!p->has_points) return DFSNUFFT_ERR_NO_POINTS;
+    if (!pr || !values || !p->herm) return DFSNUFFT_ERR_INVALID_ARG;
+    if (M < 0 || M > p->prm.N1 / 2 - 1 || N < 1 || N > p->prm.N2 / 2 - 1)
+        return DFSNUFFT_ERR_INVALID_ARG;
+    DFS_CK(p, timing_begin(p, 1));
+    DFS_CK(p, dfs_launch_theta_pass(p, pr, M, N));
+    DFS_CK(p, timing_end(p, 1));
+    DFS_CK(p, timing_begin(p, 2));
+    DFS_CK(p, dfs_launch_phi_pass(p));
+    DFS_CK(p, timing_end(p, 2));
+    DFS_CK(p, timing_begin(p, 3));
+    DFS_CK(p, dfs_launch_interp(p, values));
+    DFS_CK(p, timing_end(p, 3));
+    return DFSNUFFT_OK;
+}
+
 // ------------------------------------------------------------------ host-buffer variants
 
 extern "C" int dfsnufft_set_points_host(dfsnufft_plan p, int64_t n_points, const double *lon,

@@ -42,6 +42,7 @@ EXPORTS = (
     "dfsnufft_server_stats_get", "dfsnufft_server_destroy",
     "dfsnufft_choose_params_opts", "dfsnufft_plan_create_opts", "dfsnufft_ensemble_create_opts",
     "dfsnufft_server_create_opts", "dfsnufft_autotune", "dfsnufft_selftest_wait_timeout",
+    "dfsnufft_execute_pr",
 )
 REAL_FIELDS = 1
 N_STAGES = 4
@@ -166,6 +167,7 @@ def lib():
         L.dfsnufft_set_points.argtypes = [vp, i64, vp, vp]
         L.dfsnufft_set_points_host.argtypes = [vp, i64, vp, vp]
         L.dfsnufft_execute.argtypes = [vp, vp, vp]
+        L.dfsnufft_execute_pr.argtypes = [vp, i32, i32, vp, vp]
         L.dfsnufft_execute_host.argtypes = [vp, vp, vp]
         L.dfsnufft_destroy.argtypes = [vp]
         L.dfsnufft_strerror.argtypes = [i32]
@@ -452,6 +454,25 @@ class Plan:
             raise ValueError("out must be a contiguous %s tensor of %d values"
                              % (self._real_dtype(), self.n_fields * self.n_points))
         dfsnufft_execute(self._h, coeffs.data_ptr(), out.data_ptr())
+        return out
+
+    def execute_pr(self, pr, out=None):
+        """Fields given by partial-regularity DFS coefficients (Sec. 4): ``pr`` a
+        contiguous CUDA complex tensor of shape ([members,] F, M + 1, N + 1) with
+        pr[..., m, n] = f^c_{n,m} + i f^s_{n,m}; the plan must be a real-field plan."""
+        import torch
+        lead = (self.n_fields,) if self.n_members == 1 else (self.n_members, self.n_fields)
+        if tuple(pr.shape[:-2]) != lead or pr.dtype != self._cplx_dtype() or not pr.is_cuda \
+                or not pr.is_contiguous() or pr.dim() != len(lead) + 2:
+            raise ValueError("pr must be a contiguous CUDA %s tensor of shape %s + (M+1, N+1)"
+                             % (self._cplx_dtype(), lead))
+        M, N = pr.shape[-2] - 1, pr.shape[-1] - 1
+        shape = (self.n_fields, self.n_points) if self.n_members == 1 else \
+            (self.n_fields * self.n_points,)
+        if out is None:
+            out = torch.empty(shape, dtype=self._real_dtype(), device=pr.device)
+        _check(lib().dfsnufft_execute_pr(self._h, int(M), int(N), ctypes.c_void_p(pr.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr())), self._h)
         return out
 
     def split_values(self, out):

@@ -380,6 +380,22 @@ def workload_c4(n_per_size: int = 16) -> list[Workload]:
     return out
 
 
+def random_pr_spectrum(rng: np.random.Generator, M: int, N: int, decay: float) -> np.ndarray:
+    """Partial-regularity DFS coefficients (index [m, n], n fastest, complex:
+    cosine part + i sine part) with Gaussian entries of amplitude
+    (1 + |k|)^-decay; zero outside each m's index range (n = 0..N for m = 0,
+    0..N-1 for m = 1, 1..N-1 for even m, 1..N-2 for odd m) and no sine part at m = 0."""
+    m = np.arange(M + 1)[:, None]
+    n = np.arange(N + 1)[None, :]
+    amp = (1.0 + np.sqrt(m * m + n * n)) ** (-decay)
+    c = (rng.standard_normal((M + 1, N + 1)) + 1j * rng.standard_normal((M + 1, N + 1))) * amp
+    lo = np.where(m == 0, 0, np.where(m == 1, 0, 1))
+    hi = np.where(m == 0, N, np.where(m == 1, N - 1, np.where(m % 2 == 0, N - 1, N - 2)))
+    c[(n < lo) | (n > hi)] = 0.0
+    c[0, :] = c[0, :].real
+    return c
+
+
 def small_workload(seed: int, n_lon: int, n_lat: int, n_fields: int = 1, decay: float = 2.0,
                    dtype: str = "f64", tol: float | None = None,
                    points: str = "rotation") -> Workload:
