@@ -38,6 +38,7 @@ L2_FLUSH_BYTES = 512 << 20          # written between timed steps (L2 is 126 MB)
 
 WORKLOADS = {
     "c3_2048x1024_f32": ("f32", "c3"),
+    "c3pr_2048x1024_f32": ("f32", "c3pr"),
     "c4_ensemble_f32": ("f32", "c4"),
     "c3_2048x1024_f64": ("f64", "c3"),
     "c2_512x256_f64": ("f64", "c2"),
@@ -54,6 +55,16 @@ def make_workload(name):
         return synth.workload_c4()
     if kind == "c3":
         return synth.workload_c3(dtype)
+    if kind == "c3pr":
+        # the C3 points; fields given as partial-regularity coefficients (Sec. 4),
+        # truncated as in the paper (N = J - 2, M = J - 1)
+        wl = synth.workload_c3(dtype)
+        rng = np.random.default_rng(33)
+        J = wl.n_lat
+        wl.pr = np.stack([synth.random_pr_spectrum(rng, J - 1, J - 2, 3.0) for _ in range(3)])
+        wl.coeffs = None                  # complex form only for the oracle legs
+        wl.name = "c3pr_%dx%d_%s" % (wl.n_lon, wl.n_lat, dtype)
+        return wl
     if kind == "c2":
         return synth.workload_c2(dtype)
     return synth.workload_c1()
@@ -240,12 +251,13 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
 
     wl = make_workload(args.workload)
-    F, P = wl.n_fields, wl.n_points
+    pr_in = getattr(wl, "pr", None) is not None
+    F, P = (wl.pr.shape[0] if pr_in else wl.n_fields), wl.n_points
     cd = torch.complex128 if wl.dtype == "f64" else torch.complex64
     rd = torch.float64 if wl.dtype == "f64" else torch.float32
     lon = torch.from_numpy(wl.lon).to(dev)
     colat = torch.from_numpy(wl.colat).to(dev)
-    coeffs = torch.from_numpy(wl.coeffs).to(cd).to(dev)
+    coeffs = torch.from_numpy(wl.pr if pr_in else wl.coeffs).to(cd).to(dev)
     out = torch.empty((F, P), dtype=rd, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -256,7 +268,10 @@ def run_ours(args):
 
     def step():
         plan.set_points(lon, colat)
-        plan.execute(coeffs, out)
+        if pr_in:
+            plan.execute_pr(coeffs, out)
+        else:
+            plan.execute(coeffs, out)
 
     for _ in range(args.warmup):
         flush.fill_(1)
@@ -295,19 +310,34 @@ def run_ours(args):
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     h_lon, h_colat = pin(wl.lon), pin(wl.colat)
-    h_coef = pin(wl.coeffs.astype(np.complex128 if wl.dtype == "f64" else np.complex64))
+    h_coef = pin((wl.pr if pr_in else wl.coeffs).astype(
+        np.complex128 if wl.dtype == "f64" else np.complex64))
     h_out = torch.empty((F, P), dtype=rd).pin_memory().numpy()
     e2e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        if not pr_in:
+            plan.set_points_host(h_lon, h_colat)
+            plan.execute_host(h_coef, h_out)
+            return
+        # the host-buffer entry points take complex coefficients: partial-
+        # regularity input goes through pinned copies around execute_pr
+        lon.copy_(torch.from_numpy(h_lon), non_blocking=True)
+        colat.copy_(torch.from_numpy(h_colat), non_blocking=True)
+        coeffs.copy_(torch.from_numpy(h_coef), non_blocking=True)
+        plan.set_points(lon, colat)
+        plan.execute_pr(coeffs, out)
+        torch.from_numpy(h_out).copy_(out, non_blocking=True)
+        torch.cuda.synchronize(dev)
+
     for _ in range(2):
-        plan.set_points_host(h_lon, h_colat)
-        plan.execute_host(h_coef, h_out)
+        e2e_step()
     e2e_ms = []
     for _ in range(e2e_steps):
         flush.fill_(3)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        plan.set_points_host(h_lon, h_colat)
-        plan.execute_host(h_coef, h_out)
+        e2e_step()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_total = max_over_ranks(sum(e2e_ms), ws, dev)
     e2e_value = weak_scaling_value(ws, F * P, e2e_steps, e2e_total)
@@ -326,6 +356,10 @@ def run_ours(args):
     pk, pk_kind = peaks()
     per_stage_ms = {k: (v[0] / v[1] if v[1] else None) for k, v in stage.items()}
     sbytes = stage_bytes(prm, F, P, stats["rows_needed"])
+    if pr_in:       # the theta pass reads the partial-regularity arrays instead
+        cs = 16 if prm["dtype"] == 0 else 8
+        N1, N2 = prm["N1"], prm["N2"]
+        sbytes["theta_pass"] += F * (wl.pr.shape[1] * wl.pr.shape[2] - N2 * (N1 // 2 + 2)) * cs
     dom = max(("theta_pass", "phi_pass", "interp", "set_points"),
               key=lambda k: per_stage_ms[k] or 0.0)
     dom_ms = per_stage_ms[dom]
@@ -380,7 +414,19 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / e2e_steps},
         "clocks": clocks,
     }
+    if pr_in:
+        line["config"]["input"] = "partial-regularity DFS coefficients (Sec. 4), M = %d, N = %d" % (
+            wl.pr.shape[1] - 1, wl.pr.shape[2] - 1)
     if ws == 1 and not args.no_cpu_baseline:
+        if pr_in:
+            # the oracle's own route: partial-regularity -> standard -> complex
+            import oracle
+            cs_ = []
+            for f in range(F):
+                fc, fs = oracle.pr_to_std(np.ascontiguousarray(wl.pr[f].real.T),
+                                          np.ascontiguousarray(wl.pr[f].imag.T))
+                cs_.append(oracle.complex_from_cossin(fc, fs, wl.n_lon, wl.n_lat))
+            wl.coeffs = np.stack(cs_)
         line["cpu_baseline"], line["error"] = cpu_baseline(wl, out.cpu().numpy(), args.cpu_seconds)
     plan.destroy()
     if ws == 1 and args.serve_seconds > 0:
@@ -637,6 +683,12 @@ def run_reference(args):
     wls = make_workload(args.workload)
     if not isinstance(wls, list):
         wls = [wls]
+    for w in wls:
+        if getattr(w, "pr", None) is not None and w.coeffs is None:
+            # partial-regularity input: the oracle's map to complex coefficients
+            w.coeffs = np.stack([oracle.complex_from_cossin(
+                *oracle.pr_to_std(np.ascontiguousarray(p_.real.T), np.ascontiguousarray(p_.imag.T)),
+                w.n_lon, w.n_lat) for p_ in w.pr])
     wl = wls[-1]
     per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     # points per step, spread over the members (largest grid sets the cost)
