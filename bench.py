@@ -262,7 +262,7 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    opts = nufft.Options.make(real_fields=not args.general)
+    opts = nufft.Options.make(real_fields=not args.general, keep_order=args.keep_order)
     plan = Plan(wl.n_lon, wl.n_lat, wl.tol, wl.dtype, F, stream=stream, options=opts)
     prm = plan.params
 
@@ -403,7 +403,8 @@ def run_ours(args):
                    "modes": "%dx%d" % (2 * wl.n_lat, wl.n_lon), "fields": F, "points": P,
                    "tol": wl.tol, "w": prm["w"], "fine": "%dx%d" % (prm["n2"], prm["n1"]),
                    "rows_needed": stats["rows_needed"], "l2": "flushed between steps (512 MiB write)",
-                   "real_fields": bool(prm["flags"] & 1), "tile": [prm["tile_x"], prm["tile_y"]],
+                   "real_fields": bool(prm["flags"] & 1), "keep_order": bool(prm["flags"] & 2),
+                   "tile": [prm["tile_x"], prm["tile_y"]],
                    "sigma": prm["sigma"],
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
@@ -509,7 +510,8 @@ def run_ensemble(args):
         ch = [c for c in cands if c["opts"] == best.as_dict()][0]
         tuned.append({"grid": "%dx%d" % (n_lon, n_lat), "tile": [ch["params"]["tile_x"],
                       ch["params"]["tile_y"]], "sigma": ch["params"]["sigma"],
-                      "w": ch["params"]["w"], "tuner_ms": ch["ms"], "tuner_err": ch["err"],
+                      "w": ch["params"]["w"], "keep_order": bool(ch["params"]["flags"] & 2),
+                      "tuner_ms": ch["ms"], "tuner_err": ch["err"],
                       "candidates": len(cands)})
     t_tune = time.perf_counter() - t_tune
     ens = nufft.Ensemble(groups, tol=1e-6, dtype="f32", n_fields=3, stream=stream, options=opts)
@@ -739,6 +741,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--keep-order", action="store_true",
+                    help="evaluate the points unsorted, in their grid order")
     ap.add_argument("--general", action="store_true",
                     help="general plans (no real-field symmetry) instead of real-field plans")
     ap.add_argument("--serve-seconds", type=float, default=2.0,

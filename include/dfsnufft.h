@@ -78,7 +78,7 @@ typedef struct {
     int dtype;             /* DFSNUFFT_F64 or DFSNUFFT_F32                          */
     int tile_x, tile_y;    /* interpolation bin size in fine cells                 */
     int sigma;             /* oversampling factor (2 or 4)                          */
-    unsigned flags;        /* DFSNUFFT_REAL_FIELDS or 0                             */
+    unsigned flags;        /* DFSNUFFT_REAL_FIELDS | DFSNUFFT_KEEP_ORDER, or 0        */
 } dfsnufft_params;
 
 /* ---- plan options -------------------------------------------------------- */
@@ -94,9 +94,17 @@ typedef struct {
  * general plan.  For Hermitian input this is Re v exactly. */
 #define DFSNUFFT_REAL_FIELDS 1u
 
+/* Points are evaluated in the caller's order, without the sort by
+ * interpolation bin: set_points only folds them (one pass), and each point's
+ * stencil is read from the fine grid through the L1 cache.  Meant for point
+ * sets whose consecutive points are close on the sphere, such as the
+ * semi-Lagrangian departure points of a latitude-longitude grid in raster
+ * order; any order gives the same values (only slower). */
+#define DFSNUFFT_KEEP_ORDER 2u
+
 /* Options of dfsnufft_plan_create_opts.  A zero-filled struct gives the
  * defaults of dfsnufft_plan_create.
- *   flags  : DFSNUFFT_REAL_FIELDS or 0.
+ *   flags  : DFSNUFFT_REAL_FIELDS, DFSNUFFT_KEEP_ORDER (either, both or 0).
  *   sigma  : oversampling factor, 0 (= 2), 2 or 4.  With 4 the fine grid has
  *            4x the cells of sigma 2 and the kernel may be narrower (the width
  *            rule keeps the kernel's modelled interpolation error at or below
@@ -330,7 +338,7 @@ typedef struct {
     int n_members, n_lon, n_lat;
     double tol;
     int dtype, n_fields;
-    unsigned flags;              /* DFSNUFFT_REAL_FIELDS or 0: kept by every candidate */
+    unsigned flags;              /* DFSNUFFT_* option flags: kept by every candidate   */
     const int64_t *n_points;     /* host: n_members point counts                      */
     const double *lon, *colat;   /* device: all members' points                        */
     const void *coeffs;          /* device: n_members x n_fields x N2 x N1, plan type   */

@@ -63,9 +63,10 @@ def tune(n_lon, n_lat, lon, colat, counts, coeffs, tol=1e-6, dtype="f32", n_fiel
     key = cache_key(dev, n_lon, n_lat, counts.size, n_fields, counts, dtype, tol, real_fields)
     table = _load(path) if path else {}
     if key in table:
-        o = table[key]["best"]
-        return nufft.Options.make(real_fields=bool(o["flags"] & 1), sigma=o["sigma"], w=o["w"],
-                                  tile=(o["tile_x"], o["tile_y"])), table[key]["candidates"]
+        best = nufft.Options()
+        for name, value in table[key]["best"].items():
+            setattr(best, name, int(value))
+        return best, table[key]["candidates"]
     if stream is None:
         stream = torch.cuda.current_stream(lon.device)
     a = nufft.TuneArgs()

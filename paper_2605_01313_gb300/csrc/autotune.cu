@@ -8,8 +8,9 @@
 //
 // Search, in two stages: (1) every bin size of the candidate set at the
 // width rule's kernel and oversampling 2; (2) with the fastest accepted bin,
-// one kernel narrower than the rule at oversampling 2, and oversampling 4 at
-// its own width rule and one narrower.  The fastest accepted candidate wins;
+// one kernel narrower than the rule at oversampling 2, the unsorted-points
+// form (DFSNUFFT_KEEP_ORDER), and oversampling 4 at its own width rule and one
+// narrower.  The fastest accepted candidate wins;
 // the default configuration is always among the candidates.
 #include <math.h>
 #include <stdlib.h>
@@ -116,7 +117,7 @@ int run_candidate(const dfsnufft_tune_args *a, const dfsnufft_options &o,
 extern "C" int dfsnufft_autotune(const dfsnufft_tune_args *a, dfsnufft_tune_result *results,
                                  int max_results, int *n_results, dfsnufft_options *best) {
     if (!a || !best || !a->n_points || !a->lon || !a->colat || !a->coeffs || a->n_members < 1 ||
-        a->n_fields < 1 || (a->flags & ~DFSNUFFT_REAL_FIELDS))
+        a->n_fields < 1 || (a->flags & ~(DFSNUFFT_REAL_FIELDS | DFSNUFFT_KEEP_ORDER)))
         return DFSNUFFT_ERR_INVALID_ARG;
     if (n_results) *n_results = 0;
     dfsnufft_params dp;
@@ -215,6 +216,9 @@ extern "C" int dfsnufft_autotune(const dfsnufft_tune_args *a, dfsnufft_tune_resu
         dfsnufft_options o = t;
         o.w = dp.w - 1;
         if (o.w >= 2 && (rc = run(o))) return rc;
+        dfsnufft_options ko = t;                    // unsorted points (same values)
+        ko.flags |= DFSNUFFT_KEEP_ORDER;
+        if ((rc = run(ko))) return rc;
         dfsnufft_params p4;
         dfsnufft_options o4 = t;
         o4.sigma = 4;

@@ -20,6 +20,8 @@
 // with plain loads instead.  k_interp_f32 (plain loads, the same arithmetic)
 // serves plans without a tensor map, and k_interp the FP64 form and wide
 // kernels.
+#include <limits.h>
+
 #include "common.cuh"
 #include "tma.cuh"
 
@@ -410,6 +412,182 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
     }
 }
 
+// Points in the caller's order (DFSNUFFT_KEEP_ORDER): one thread per point,
+// member k = blockIdx.y; the stencil rows are read from the fine grid through
+// the L1 cache (neighbouring points of a grid-ordered set share rows), indices
+// taken mod n.  FP32 reads each row as WP/2 aligned pairs (paired_weights).
+template <typename R, int W>
+__global__ void __launch_bounds__(256) k_interp_direct(InterpArgs a,
+                                                       const __grid_constant__ Horner<R, W> hw,
+                                                       const R *__restrict__ grid,
+                                                       const int2 *__restrict__ base,
+                                                       const R *__restrict__ frac,
+                                                       const int *__restrict__ pofs,
+                                                       R *__restrict__ out_all) {
+    constexpr bool PAIR = sizeof(R) == 4 && W <= 8;
+    constexpr int WP = (W + 2) & ~1;
+    const int k = blockIdx.y;
+    const int p0 = pofs[k];
+    const int Pk = pofs[k + 1] - p0;
+    const int m1 = a.n1 - 1, m2 = a.n2 - 1;
+    for (int pl = blockIdx.x * blockDim.x + threadIdx.x; pl < Pk; pl += gridDim.x * blockDim.x) {
+        const int2 b = base[p0 + pl];
+        const R tx = frac[2 * (size_t)(p0 + pl)], ty = frac[2 * (size_t)(p0 + pl) + 1];
+        R *out = out_all + (size_t)a.F * p0 + pl;
+        if constexpr (PAIR) {
+            const int odd = b.x & 1;
+            const int cx = b.x - odd;                  // even: pairs never straddle a row end
+            float w8[WP], wy[W];
+            paired_weights<W>(tx, ty, odd, hw, w8, wy);
+            for (int f = 0; f < a.F; ++f) {
+                const float *g = grid + (size_t)(k * a.F + f) * a.n2 * a.n1;
+                float acc = 0.f;
+#pragma unroll
+                for (int bb = 0; bb < W; ++bb) {
+                    const float *gr = g + (size_t)((b.y + bb) & m2) * a.n1;
+                    float rr = 0.f;
+#pragma unroll
+                    for (int kk = 0; kk < WP / 2; ++kk) {
+                        const float2 v = __ldg(reinterpret_cast<const float2 *>(
+                            gr + ((cx + 2 * kk) & m1)));
+                        rr += w8[2 * kk] * v.x + w8[2 * kk + 1] * v.y;
+                    }
+                    acc += wy[bb] * rr;
+                }
+                out[(size_t)f * Pk] = acc;
+            }
+        } else {
+            R wx[W], wy[W];
+            es_weights<R, W>(tx, hw, wx);
+            es_weights<R, W>(ty, hw, wy);
+            for (int f = 0; f < a.F; ++f) {
+                const R *g = grid + (size_t)(k * a.F + f) * a.n2 * a.n1;
+                R acc = 0;
+#pragma unroll
+                for (int bb = 0; bb < W; ++bb) {
+                    const R *gr = g + (size_t)((b.y + bb) & m2) * a.n1;
+                    R rr = 0;
+#pragma unroll
+                    for (int aa = 0; aa < W; ++aa) rr += wx[aa] * __ldg(gr + ((b.x + aa) & m1));
+                    acc += wy[bb] * rr;
+                }
+                out[(size_t)f * Pk] = acc;
+            }
+        }
+    }
+}
+
+// Points in the caller's order, FP32: each warp takes 32 consecutive points of
+// a member, finds their stencils' bounding box (coordinates unwrapped around
+// lane 0's, so a chunk across the torus seam stays compact) and, when the box
+// fits half of its shared-memory slice of WT_CAP floats, stages the fields'
+// boxes by asynchronous 8-byte copies (cp.async, indices taken mod n), field
+// f + 1 landing in one half while field f is evaluated from the other; a chunk
+// whose box does not fit reads its stencils from the fine grid directly.  Points of one arrival row sit about two cells apart, so
+// the warp's pair reads fall on consecutive words.  grid (CTAs, members).
+#define WT_CAP 1536
+template <int W>
+__global__ void __launch_bounds__(256) k_interp_wtile(InterpArgs a,
+                                                      const __grid_constant__ Horner<float, W> hw,
+                                                      const float *__restrict__ grid,
+                                                      const int2 *__restrict__ base,
+                                                      const float *__restrict__ frac,
+                                                      const int *__restrict__ pofs,
+                                                      float *__restrict__ out_all) {
+    constexpr int WP = (W + 2) & ~1;
+    __shared__ __align__(16) float tiles[8][WT_CAP];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float *tile = tiles[wid];
+    const int k = blockIdx.y;
+    const int p0 = pofs[k];
+    const int Pk = pofs[k + 1] - p0;
+    const int m1 = a.n1 - 1, m2 = a.n2 - 1;
+    const int nchunk = (Pk + 31) >> 5;
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    for (int ch = blockIdx.x * (blockDim.x >> 5) + wid; ch < nchunk; ch += wstride) {
+        const int pl = (ch << 5) + lane;
+        const bool live = pl < Pk;
+        int2 b = make_int2(0, 0);
+        float2 t = make_float2(0.f, 0.f);
+        if (live) {
+            b = base[p0 + pl];
+            t = reinterpret_cast<const float2 *>(frac)[p0 + pl];
+        }
+        // unwrap around lane 0's cell, then the chunk's box
+        const int bx0 = __shfl_sync(0xffffffffu, b.x, 0), by0 = __shfl_sync(0xffffffffu, b.y, 0);
+        const int ux = bx0 + ((((b.x - bx0) + (a.n1 >> 1)) & m1) - (a.n1 >> 1));
+        const int uy = by0 + ((((b.y - by0) + (a.n2 >> 1)) & m2) - (a.n2 >> 1));
+        const int xmin = __reduce_min_sync(0xffffffffu, live ? ux : INT_MAX);
+        const int xmax = __reduce_max_sync(0xffffffffu, live ? ux : INT_MIN);
+        const int ymin = __reduce_min_sync(0xffffffffu, live ? uy : INT_MAX);
+        const int ymax = __reduce_max_sync(0xffffffffu, live ? uy : INT_MIN);
+        const int col0 = xmin & ~1;                        // even: pairs stay aligned
+        const int TW = ((xmax - col0) + WP + 1) & ~1;      // pair reads end below TW
+        const int TH = ymax - ymin + W;
+        const int Q = TW >> 1;
+        const bool fits = 2 * TW * TH <= WT_CAP;
+        // lanes past the member's last point read the box's first cells
+        const int ox = live ? ux - col0 : 0, odd = ox & 1, oy = live ? uy - ymin : 0;
+        float w8[WP], wy[W];
+        paired_weights<W>(t.x, t.y, odd, hw, w8, wy);
+        float *out = out_all + (size_t)a.F * p0 + pl;
+        // asynchronous copies of field f's box into half f & 1 of the slice
+        auto stage = [&](int f) {
+            const float *g = grid + (size_t)(k * a.F + f) * a.n2 * a.n1;
+            float *dst = tile + (f & 1) * (WT_CAP / 2);
+            for (int r = 0; r < TH; ++r) {
+                const float *gr = g + (size_t)((ymin + r) & m2) * a.n1;
+                for (int q = lane; q < Q; q += 32)
+                    cp_async_8(dst + r * TW + 2 * q, gr + ((col0 + 2 * q) & m1));
+            }
+            cp_async_commit();
+        };
+        __syncwarp();                                      // the previous chunk's boxes are consumed
+        if (fits) stage(0);
+        for (int f = 0; f < a.F; ++f) {
+            const float *g = grid + (size_t)(k * a.F + f) * a.n2 * a.n1;
+            float acc = 0.f;
+            if (fits) {
+                if (f + 1 < a.F) {
+                    __syncwarp();                          // half (f + 1) & 1 was read at f - 1
+                    stage(f + 1);
+                    cp_async_wait_group<1>();
+                } else {
+                    cp_async_wait_group<0>();
+                }
+                __syncwarp();
+                const float2 *tp = reinterpret_cast<const float2 *>(
+                    tile + (f & 1) * (WT_CAP / 2) + oy * TW + (ox - odd));
+#pragma unroll
+                for (int bb = 0; bb < W; ++bb) {
+                    float rr = 0.f;
+#pragma unroll
+                    for (int kk = 0; kk < WP / 2; ++kk) {
+                        const float2 v = tp[bb * Q + kk];
+                        rr += w8[2 * kk] * v.x + w8[2 * kk + 1] * v.y;
+                    }
+                    acc += wy[bb] * rr;
+                }
+            } else {
+                const int cx = b.x - odd;
+#pragma unroll
+                for (int bb = 0; bb < W; ++bb) {
+                    const float *gr = g + (size_t)((b.y + bb) & m2) * a.n1;
+                    float rr = 0.f;
+#pragma unroll
+                    for (int kk = 0; kk < WP / 2; ++kk) {
+                        const float2 v = __ldg(reinterpret_cast<const float2 *>(
+                            gr + ((cx + 2 * kk) & m1)));
+                        rr += w8[2 * kk] * v.x + w8[2 * kk + 1] * v.y;
+                    }
+                    acc += wy[bb] * rr;
+                }
+            }
+            if (live) out[(size_t)f * Pk] = acc;
+        }
+    }
+}
+
 template <typename R, int W>
 cudaError_t launch_w(dfsnufft_plan p, void *values) {
     const dfsnufft_params &q = p->prm;
@@ -434,6 +612,22 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
     }
     const int M = p->n_members;
     constexpr int WP = (W + 2) & ~1;
+    if (p->keep_order) {
+        int64_t blocks = (p->max_member_points + 255) / 256;
+        if (blocks < 1) blocks = 1;
+        if constexpr (sizeof(R) == 4 && W <= 8) {
+            Horner<float, W> hf;
+            for (int i = 0; i < W; ++i)
+                for (int kk = 0; kk <= W; ++kk) hf.c[i][kk] = (float)hw.c[i][kk];
+            k_interp_wtile<W><<<dim3((unsigned)blocks, M), 256, 0, p->stream>>>(
+                a, hf, (const float *)p->d_G, p->d_base, (const float *)p->d_frac, p->d_pofs,
+                (float *)values);
+            return cudaGetLastError();
+        }
+        k_interp_direct<R, W><<<dim3((unsigned)blocks, M), 256, 0, p->stream>>>(
+            a, hw, (const R *)p->d_G, p->d_base, (const R *)p->d_frac, p->d_pofs, (R *)values);
+        return cudaGetLastError();
+    }
     if constexpr (sizeof(R) == 4 && W <= 8) {
         Horner<float, W> hf;
         for (int i = 0; i < W; ++i)

@@ -241,7 +241,8 @@ extern "C" int dfsnufft_choose_params_opts(int n_lon, int n_lat, double tol, int
     if (n_lon < 4 || (n_lon & 1) || n_lat < 2) return DFSNUFFT_ERR_INVALID_ARG;
     if (dtype != DFSNUFFT_F64 && dtype != DFSNUFFT_F32) return DFSNUFFT_ERR_INVALID_ARG;
     if (!(tol > 0.0) || !(tol < 1.0)) return DFSNUFFT_ERR_INVALID_ARG;
-    if ((o.flags & ~DFSNUFFT_REAL_FIELDS) != 0) return DFSNUFFT_ERR_INVALID_ARG;
+    if ((o.flags & ~(DFSNUFFT_REAL_FIELDS | DFSNUFFT_KEEP_ORDER)) != 0)
+        return DFSNUFFT_ERR_INVALID_ARG;
     const int sigma = o.sigma == 0 ? 2 : o.sigma;
     if (sigma != 2 && sigma != 4) return DFSNUFFT_ERR_INVALID_ARG;
     if (o.w != 0 && (o.w < 2 || o.w > 16)) return DFSNUFFT_ERR_INVALID_ARG;
@@ -461,6 +462,7 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
     p->n_fields = n_fields;
     p->stream = (cudaStream_t)stream;
     p->herm = (prm.flags & DFSNUFFT_REAL_FIELDS) ? 1 : 0;
+    p->keep_order = (prm.flags & DFSNUFFT_KEEP_ORDER) ? 1 : 0;
     p->c0 = (prm.w % 2 == 0) ? prm.w / 2 - 1 : (prm.w - 1) / 2;
     p->nbx = prm.n1 / prm.tile_x;    // base cells lie in [0, n): no wrap bin
     p->nby = prm.n2 / prm.tile_y;

@@ -241,6 +241,52 @@ __device__ __forceinline__ void block_scan2(int a, int b, int &pa, int &pb, int 
     __syncthreads();
 }
 
+// Run by every thread of the last CTA of a member once all its bin-row flags
+// are published: the circular range of fine rows the stencils touch.  The
+// points of bin row by use rows by*tile_y - c0 .. (by+1)*tile_y - c0 + w - 2,
+// so the range is the complement of the longest circular run of empty bin
+// rows, widened by the stencil and rounded out to whole row blocks.
+__device__ void finish_rowrange(const ScanParams &sp, const unsigned char *rows,
+                                unsigned *s_bits, int2 *range_out) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    for (int k = wid; k * 32 < sp.nbr; k += nw) {
+        const int i = k * 32 + lane;
+        const unsigned b = __ballot_sync(0xffffffffu, i < sp.nbr && __ldcg(rows + i) != 0);
+        if (lane == 0) s_bits[k] = b;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int nb = sp.nbr;
+        const int s0 = next_bit(s_bits, nb, 0, 1);
+        int2 range = make_int2(0, 0);
+        if (s0 < nb) {
+            int best = 0, best_at = 0;
+            int pos = s0;
+            while (pos < s0 + nb) {
+                const int z0 = next_bit(s_bits, nb, pos >= nb ? pos - nb : pos, 0) +
+                               (pos >= nb ? nb : 0);
+                if (z0 >= s0 + nb) break;
+                const int z1 = next_bit(s_bits, nb, z0 >= nb ? z0 - nb : z0, 1) +
+                               (z0 >= nb ? nb : 0);
+                const int end = z1 < s0 + nb ? z1 : s0 + nb;
+                if (end - z0 > best) {
+                    best = end - z0;
+                    best_at = z0;
+                }
+                pos = end;
+            }
+            // needed rows: after the gap, through the last non-empty bin row's stencil
+            int first = ((best_at + best) % nb) * sp.tile_y - sp.c0;
+            int cnt = (nb - best) * sp.tile_y + sp.w - 1;
+            first &= sp.n2 - 1;
+            const int fb = first & ~(DFS_ROW_BLOCK - 1);
+            cnt = ((cnt + (first - fb) + DFS_ROW_BLOCK - 1) / DFS_ROW_BLOCK) * DFS_ROW_BLOCK;
+            range = make_int2(fb, cnt < sp.n2 ? cnt : sp.n2);
+        }
+        *range_out = range;
+    }
+}
+
 // Pass 1 of the bin scan.  grid (nch, members), DFS_SCAN_CHUNK / 16 threads:
 // sum and number of non-empty bins of each chunk of DFS_SCAN_CHUNK bins.
 __global__ void __launch_bounds__(DFS_SCAN_CHUNK / 16) k_scan_sums(ScanParams sp,
@@ -284,7 +330,7 @@ __global__ void __launch_bounds__(DFS_SCAN_CHUNK / 16) k_scan_write(ScanParams s
     __shared__ unsigned char s_row[DFS_SCAN_CHUNK];
     __shared__ unsigned s_bits[(DFS_MAX_ROW_BLOCKS + 31) / 32];
     __shared__ int s_last;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x;
     const int nbins = sp.nbins;
     const int first_bin = chunk * DFS_SCAN_CHUNK;
     const int row_lo = first_bin / sp.nbx;                 // bin rows this chunk can touch
@@ -346,43 +392,54 @@ __global__ void __launch_bounds__(DFS_SCAN_CHUNK / 16) k_scan_write(ScanParams s
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // last CTA of the member: bin-row flags -> bits -> needed row range
-    for (int k = wid; k * 32 < sp.nbr; k += nw) {
-        const int i = k * 32 + lane;
-        const unsigned b = __ballot_sync(0xffffffffu, i < sp.nbr && __ldcg(rows + i) != 0);
-        if (lane == 0) s_bits[k] = b;
+    // last CTA of the member: bin-row flags -> needed row range
+    finish_rowrange(sp, rows, s_bits, rowrange + member);
+}
+
+// Points kept in the caller's order (DFSNUFFT_KEEP_ORDER): fold every point to
+// its record at its own index, flag the bin rows it touches, and let the last
+// CTA of the member find the needed row range.  grid (ceil(max member points /
+// 256), members).
+template <typename R>
+__global__ void __launch_bounds__(256) k_fold_direct(const double *__restrict__ lon,
+                                                     const double *__restrict__ colat,
+                                                     FoldParams f, ScanParams sp,
+                                                     const int *__restrict__ pofs,
+                                                     int *__restrict__ count_all,
+                                                     int2 *__restrict__ base,
+                                                     R *__restrict__ frac,
+                                                     int2 *__restrict__ rowrange) {
+    __shared__ unsigned char s_row[DFS_MAX_ROW_BLOCKS];
+    __shared__ unsigned s_bits[(DFS_MAX_ROW_BLOCKS + 31) / 32];
+    __shared__ int s_last;
+    const int k = blockIdx.y;
+    const int p0 = pofs[k];
+    const int pl = blockIdx.x * blockDim.x + threadIdx.x;
+    int *slice = count_all + (size_t)k * sp.cstride;
+    unsigned char *rows = ws_rows(slice, sp);
+    for (int i = threadIdx.x; i < sp.nbr; i += blockDim.x) s_row[i] = 0;
+    __syncthreads();
+    if (pl < pofs[k + 1] - p0) {
+        int bx, by;
+        long long tx, ty;
+        const bool ok = fold_point(f, lon[p0 + pl], colat[p0 + pl], bx, by, tx, ty);
+        base[p0 + pl] = make_int2(bx - f.c0, by - f.c0);
+        R ox = offset_value<R>(tx, f.odd_w), oy = offset_value<R>(ty, f.odd_w);
+        if (!ok) ox = oy = (R)__int_as_float(0x7fc00000);
+        frac[2 * (size_t)(p0 + pl)] = ox;
+        frac[2 * (size_t)(p0 + pl) + 1] = oy;
+        s_row[by >> f.lty] = 1;
     }
     __syncthreads();
-    if (tid == 0) {
-        const int nb = sp.nbr;
-        const int s0 = next_bit(s_bits, nb, 0, 1);
-        int2 range = make_int2(0, 0);
-        if (s0 < nb) {
-            int best = 0, best_at = 0;
-            int pos = s0;
-            while (pos < s0 + nb) {
-                const int z0 = next_bit(s_bits, nb, pos >= nb ? pos - nb : pos, 0) +
-                               (pos >= nb ? nb : 0);
-                if (z0 >= s0 + nb) break;
-                const int z1 = next_bit(s_bits, nb, z0 >= nb ? z0 - nb : z0, 1) +
-                               (z0 >= nb ? nb : 0);
-                const int end = z1 < s0 + nb ? z1 : s0 + nb;
-                if (end - z0 > best) {
-                    best = end - z0;
-                    best_at = z0;
-                }
-                pos = end;
-            }
-            // needed rows: after the gap, through the last non-empty bin row's stencil
-            int first = ((best_at + best) % nb) * sp.tile_y - sp.c0;
-            int cnt = (nb - best) * sp.tile_y + sp.w - 1;
-            first &= sp.n2 - 1;
-            const int fb = first & ~(DFS_ROW_BLOCK - 1);
-            cnt = ((cnt + (first - fb) + DFS_ROW_BLOCK - 1) / DFS_ROW_BLOCK) * DFS_ROW_BLOCK;
-            range = make_int2(fb, cnt < sp.n2 ? cnt : sp.n2);
-        }
-        rowrange[member] = range;
-    }
+    for (int i = threadIdx.x; i < sp.nbr; i += blockDim.x)
+        if (s_row[i]) rows[i] = 1;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ws_done(slice, sp), 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    finish_rowrange(sp, rows, s_bits, rowrange + k);
 }
 
 // grid (ceil(max member points / 256), members): member k = blockIdx.y.  Sorted
@@ -437,8 +494,6 @@ cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const doub
         return e;
     const int tpb = 256;
     const dim3 grid((unsigned)((p->max_member_points + tpb - 1) / tpb), M);
-    k_fold_count<<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->cstride, p->d_bin_count,
-                                              p->d_rank);
     ScanParams sp;
     sp.nbins = p->nbins;
     sp.bstride = p->bstride;
@@ -450,6 +505,19 @@ cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const doub
     sp.c0 = p->c0;
     sp.w = q.w;
     sp.n2 = q.n2;
+    if (p->keep_order) {
+        if (q.dtype == DFSNUFFT_F64)
+            k_fold_direct<double><<<grid, tpb, 0, p->stream>>>(lon, colat, f, sp, p->d_pofs,
+                                                              p->d_bin_count, p->d_base,
+                                                              (double *)p->d_frac, p->d_rowrange);
+        else
+            k_fold_direct<float><<<grid, tpb, 0, p->stream>>>(lon, colat, f, sp, p->d_pofs,
+                                                             p->d_bin_count, p->d_base,
+                                                             (float *)p->d_frac, p->d_rowrange);
+        return cudaGetLastError();
+    }
+    k_fold_count<<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->cstride, p->d_bin_count,
+                                              p->d_rank);
     const dim3 sgrid(p->nch, M);
     k_scan_sums<<<sgrid, DFS_SCAN_CHUNK / 16, 0, p->stream>>>(sp, p->d_bin_count);
     k_scan_write<<<sgrid, DFS_SCAN_CHUNK / 16, 0, p->stream>>>(sp, p->d_bin_count, p->d_bin_start,

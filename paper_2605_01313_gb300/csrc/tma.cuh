@@ -75,6 +75,22 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Asynchronous 8-byte copy global -> shared (both 8-byte aligned), completed by
+// the commit/wait groups below (this thread's copies only).
+__device__ __forceinline__ void cp_async_8(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// Wait until at most N of this thread's committed groups are still pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Host: raise a kernel's dynamic shared-memory limit to at least `bytes`,
 // calling cudaFuncSetAttribute only the first time a larger size is needed (so
 // that launches recorded into a CUDA graph make no attribute calls).

@@ -45,6 +45,7 @@ EXPORTS = (
     "dfsnufft_execute_pr",
 )
 REAL_FIELDS = 1
+KEEP_ORDER = 2
 N_STAGES = 4
 STAGES = ("set_points", "theta_pass", "phi_pass", "interp")
 
@@ -66,9 +67,9 @@ class Options(ctypes.Structure):
                 ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int)]
 
     @classmethod
-    def make(cls, real_fields=False, sigma=0, w=0, tile=None):
+    def make(cls, real_fields=False, sigma=0, w=0, tile=None, keep_order=False):
         o = cls()
-        o.flags = REAL_FIELDS if real_fields else 0
+        o.flags = (REAL_FIELDS if real_fields else 0) | (KEEP_ORDER if keep_order else 0)
         o.sigma = int(sigma or 0)
         o.w = int(w or 0)
         if tile:

@@ -1,5 +1,6 @@
 """Plan options on the GPU, against the FP64 oracle: real-field plans
-(DFSNUFFT_REAL_FIELDS), oversampling 4, kernel width and bin size.
+(DFSNUFFT_REAL_FIELDS), unsorted points (DFSNUFFT_KEEP_ORDER), oversampling 4,
+kernel width and bin size.
 
 A real-field plan reads the columns m >= 0, the Nyquist column and the
 Nyquist row only; its values are Re v for the coefficients c' whose columns
@@ -161,3 +162,46 @@ def test_wider_kernel_is_at_least_as_accurate(torch_cuda):
         assert prm["w"] == w
         errs.append(max_rel_err(vals, wl.coeffs, wl.lon, wl.colat))
     assert errs[0] > errs[1] > errs[2], errs
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("points", ["divergent", "uniform"])
+@pytest.mark.parametrize("real", [False, True])
+def test_keep_order_points(torch_cuda, dtype, points, real):
+    """Unsorted evaluation in the caller's order gives the oracle's values for
+    grid-ordered departure points and for scattered points alike."""
+    from paper_2605_01313_gb300.nufft import Options
+    wl = synth.small_workload(81, 256, 128, n_fields=3, dtype=dtype, points=points)
+    vals, prm = run(torch_cuda, wl.coeffs, wl.lon, wl.colat, 256, 128, dtype, wl.tol,
+                    Options.make(keep_order=True, real_fields=real))
+    assert prm["flags"] & 2
+    s = np.arange(0, wl.lon.size, 11)
+    err = max_rel_err(vals[:, s], wl.coeffs, wl.lon[s], wl.colat[s])
+    assert err <= (TOL_F64 if dtype == "f64" else TOL_F32), err
+
+
+def test_keep_order_batched_and_seams(torch_cuda):
+    """Batched members with different point counts, points on both seams of the torus."""
+    from paper_2605_01313_gb300 import Plan
+    from paper_2605_01313_gb300.nufft import Options
+    torch = torch_cuda
+    rng = np.random.default_rng(82)
+    wls = [synth.workload_member(950 + k, 128, 64, "f32", n_sample=300) for k in range(3)]
+    pts = [(w.lon.copy(), w.colat.copy()) for w in wls]
+    pts[1][0][:50] = rng.uniform(-1e-4, 1e-4, 50)
+    pts[1][1][:50] = rng.uniform(-1e-4, 1e-4, 50)
+    pts[2][1][:30] = math.pi + rng.uniform(-1e-4, 1e-4, 30)
+    pts[2] = (pts[2][0][:4000], pts[2][1][:4000])          # a shorter member
+    lon = torch.from_numpy(np.concatenate([p[0] for p in pts])).cuda()
+    colat = torch.from_numpy(np.concatenate([p[1] for p in pts])).cuda()
+    coef = torch.from_numpy(np.stack([w.coeffs for w in wls])).to(torch.complex64).cuda()
+    counts = [p[0].size for p in pts]
+    with Plan(128, 64, 1e-6, "f32", 3, n_members=3,
+              options=Options.make(keep_order=True, real_fields=True)) as plan:
+        plan.set_points(lon, colat, counts)
+        outs = [o.cpu().numpy() for o in plan.split_values(plan.execute(coef))]
+    for w, (plon, pcolat), o in zip(wls, pts, outs):
+        s = np.concatenate([np.arange(50), w.sample[w.sample < plon.size]])
+        ref = oracle.evaluate(w.coeffs, plon[s], pcolat[s])
+        err = max(oracle.rel_linf(o[f][s], ref[f].real) for f in range(3))
+        assert err <= TOL_F32, err
