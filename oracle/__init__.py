@@ -24,6 +24,10 @@ Contents, each following the passage it cites:
   differently from the printed list (f~_{0,m} = f_{1,m}/2 for even m >= 2).
 * :func:`eval_pr` -- direct evaluation of the partial-regularity expansion
   (Sec. 4) from its own basis functions, the route that pins :func:`pr_to_std`.
+* :func:`grid_to_coeffs` -- coefficients of Eq. 5.3 from samples on the Grid [0]
+  arrival grid (Sec. 3): the samples extended to the doubled sphere by the
+  field's parity (Sec. 4), then the plain discrete Fourier sums over the doubled
+  torus (Sec. 4, the transforms in phi and theta written out as sums).
 
 Every function here is pinned by the ``-m "not gpu"`` tests against closed
 forms, invariants and library special cases (see tests/test_oracle_pins.py).
@@ -248,6 +252,37 @@ def eval_pr(pc: np.ndarray, ps: np.ndarray, lon: np.ndarray, colat: np.ndarray) 
         out += fcm * np.cos(m * lon)
         if m > 0:
             out += sum(ps[n, m] * basis(n) for n in ns) * np.sin(m * lon)
+    return out
+
+
+def grid_to_coeffs(samples: np.ndarray, parity) -> np.ndarray:
+    """Sec. 3-4: samples f(phi_k, theta_j) of F fields on Grid [0] (shape (F, n_lat,
+    n_lon); theta_j = (j + 1/2) pi / n_lat, phi_k = 2 pi k / n_lon) to the centred
+    complex coefficients (F, 2 n_lat, n_lon) of the trigonometric interpolant on
+    the doubled torus.
+
+    Doubled sphere: rows j >= n_lat sit at theta_j in (pi, 2 pi), where the field
+    is parity * f(phi + pi, 2 pi - theta), i.e. row 2 n_lat - 1 - j shifted by
+    half a turn in longitude; parity is +1 for scalars and -1 for the wind
+    components.  Then c_{n,m} = (1 / (N1 N2)) sum_{j,k} f_ext(phi_k, theta_j)
+    exp(-i (m phi_k + n theta_j)), n = -N2/2..N2/2-1, m = -N1/2..N1/2-1."""
+    samples = np.asarray(samples, dtype=np.float64)
+    F, n_lat, n_lon = samples.shape
+    n2, n1 = 2 * n_lat, n_lon
+    parity = np.broadcast_to(np.asarray(parity, dtype=np.float64), (F,))
+    th = (np.arange(n2) + 0.5) * (np.pi / n_lat)
+    ph = np.arange(n1) * (2.0 * np.pi / n1)
+    n = np.arange(n2) - n2 // 2
+    m = np.arange(n1) - n1 // 2
+    et = np.exp(-1j * np.outer(n, th))            # (modes n, rows j)
+    ep = np.exp(-1j * np.outer(ph, m))            # (columns k, modes m)
+    out = np.empty((F, n2, n1), dtype=np.complex128)
+    for f in range(F):
+        ext = np.empty((n2, n1))
+        ext[:n_lat] = samples[f]
+        for j in range(n_lat, n2):
+            ext[j] = parity[f] * np.roll(samples[f][n2 - 1 - j], -(n1 // 2))
+        out[f] = et @ ext @ ep / (n1 * n2)
     return out
 
 

@@ -375,3 +375,59 @@ def test_pr_through_complex_map_and_direct_sum(oracle_mod):
     v = oracle_mod.evaluate(c[None], lon, colat)[0]
     assert np.max(np.abs(v.imag)) < 1e-12
     assert np.max(np.abs(v.real - oracle_mod.eval_pr(pc, ps, lon, colat))) < 1e-12
+
+
+# ------------------------------------------------ grid values -> coefficients (Sec. 3-4)
+
+@pytest.mark.parametrize("n_lon,n_lat", [(16, 8), (32, 16), (64, 32)])
+def test_grid_to_coeffs_recovers_band_limited_fields(oracle_mod, n_lon, n_lat):
+    """Real DFS-symmetric fields (scalar and vector parity, Nyquist zero) sampled
+    on the arrival grid by the direct sum give back their own coefficients."""
+    rng = np.random.default_rng(600 + n_lon)
+    c = np.stack([synth.random_spectrum(rng, n_lon, n_lat, 1.5, par)
+                  for par in (synth.SCALAR, synth.VECTOR, synth.VECTOR)])
+    lon, colat = synth.grid0_points(n_lon, n_lat)
+    vals = oracle_mod.evaluate(c, lon, colat).real.reshape(3, n_lat, n_lon)
+    got = oracle_mod.grid_to_coeffs(vals, [1, -1, -1])
+    assert np.max(np.abs(got - c)) < 1e-13
+
+
+def test_grid_to_coeffs_reproduces_samples_and_parity(oracle_mod):
+    """Arbitrary samples: the coefficients' series passes through every sample of
+    the arrival grid, and on the other half of the doubled torus equals the
+    parity extension f(phi + pi, -theta) = +-f(phi, theta)."""
+    rng = np.random.default_rng(610)
+    n_lon, n_lat = 24, 12
+    s = rng.standard_normal((2, n_lat, n_lon))
+    c = oracle_mod.grid_to_coeffs(s, [1, -1])
+    lon, colat = synth.grid0_points(n_lon, n_lat)
+    got = oracle_mod.evaluate(c, lon, colat).real.reshape(2, n_lat, n_lon)
+    assert np.max(np.abs(got - s)) < 1e-12
+    lon2 = lon + math.pi
+    back = oracle_mod.evaluate(c, lon2, -colat).real.reshape(2, n_lat, n_lon)
+    assert np.max(np.abs(back[0] - s[0])) < 1e-12
+    assert np.max(np.abs(back[1] + s[1])) < 1e-12
+
+
+@pytest.mark.parametrize("mistake", ["no_half_cell", "wrong_parity", "no_shift"])
+def test_grid_to_coeffs_pins_catch_mistakes(oracle_mod, mistake):
+    """Copies of grid_to_coeffs with one plausible mistake fail the recovery pin."""
+    rng = np.random.default_rng(620)
+    n_lon, n_lat = 16, 8
+    c = np.stack([synth.random_spectrum(rng, n_lon, n_lat, 1.5, synth.VECTOR)])
+    lon, colat = synth.grid0_points(n_lon, n_lat)
+    vals = oracle_mod.evaluate(c, lon, colat).real.reshape(1, n_lat, n_lon)
+    n2, n1 = 2 * n_lat, n_lon
+    th = (np.arange(n2) + (0.0 if mistake == "no_half_cell" else 0.5)) * (math.pi / n_lat)
+    ph = np.arange(n1) * (2 * math.pi / n1)
+    n = np.arange(n2) - n2 // 2
+    m = np.arange(n1) - n1 // 2
+    ext = np.empty((n2, n1))
+    ext[:n_lat] = vals[0]
+    for j in range(n_lat, n2):
+        row = vals[0][n2 - 1 - j]
+        if mistake != "no_shift":
+            row = np.roll(row, -(n1 // 2))
+        ext[j] = (1.0 if mistake == "wrong_parity" else -1.0) * row
+    bad = np.exp(-1j * np.outer(n, th)) @ ext @ np.exp(-1j * np.outer(ph, m)) / (n1 * n2)
+    assert np.max(np.abs(bad - c[0])) > 1e-3
