@@ -285,6 +285,27 @@ int dfsnufft_execute(dfsnufft_plan plan, const void *coeffs, void *values);
  *   plan (DFSNUFFT_REAL_FIELDS); values as for dfsnufft_execute. */
 int dfsnufft_execute_pr(dfsnufft_plan plan, int M, int N, const void *pr, void *values);
 
+/* Coefficients from samples on the arrival grid (Sec. 3-4): samples of every
+ * field on Grid [0], theta_j = (j + 1/2) pi / n_lat, phi_k = 2 pi k / n_lon,
+ * (members x) n_fields x n_lat x n_lon reals in plan precision (device,
+ * phi fastest); parity is a host array of n_fields values, +1 for a scalar
+ * field and -1 for a wind component, by which the samples are extended to the
+ * doubled sphere (f(phi + pi, -theta) = parity f(phi, theta)).  Writes the
+ * centred coefficients of the trigonometric interpolant on the doubled torus,
+ *   c_{n,m} = (1 / (N1 N2)) sum_{j,k} f_ext(phi_k, theta_j) e^{-i (m phi_k + n theta_j)},
+ * in the layout dfsnufft_execute reads.  Needs n_lon and 2 n_lat powers of two
+ * from 16 to 4096 and n_lat even (else DFSNUFFT_ERR_UNSUPPORTED); uses the
+ * plan's theta-pass buffer as scratch (stream-ordered, so it may be followed by
+ * execute).  A changed parity array is uploaded with a synchronising copy. */
+int dfsnufft_grid_to_coeffs(dfsnufft_plan plan, const void *samples, const int *parity,
+                            void *coeffs);
+
+/* One semi-Lagrangian interpolation step: samples on the arrival grid (as for
+ * dfsnufft_grid_to_coeffs) to values at the plan's points (as for
+ * dfsnufft_execute), through a plan-owned coefficient buffer. */
+int dfsnufft_interpolate_grid(dfsnufft_plan plan, const void *samples, const int *parity,
+                              void *values);
+
 /* Host-buffer variants: the same operations with host pointers.  The data are
  * copied to plan-owned device buffers on the plan's stream (pinned host memory
  * makes the copies asynchronous); dfsnufft_execute_host waits for the stream

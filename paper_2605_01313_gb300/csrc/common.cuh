@@ -69,6 +69,9 @@ struct dfsnufft_plan_s {
     int64_t *h_pofs;            // members + 1 point offsets of the current points (host)
     int64_t max_member_points;  // largest member's point count
     int *d_status;              // device status word (DFS_STATUS_*), zero when healthy
+    int *d_parity;              // fields: +1 scalar / -1 wind component (grid input)
+    int h_parity[64];           // the parities last uploaded
+    int parity_set;
     int num_sms;                // multiprocessors of the plan's device
     CUtensorMap tmap_G;         // 2-D map of d_G (8-byte elements), box set by the interpolation
     int tmap_G_ok;              // tmap_G is valid (FP32 plans that own their buffers)
@@ -122,3 +125,7 @@ cudaError_t dfs_launch_theta_pass(dfsnufft_plan p, const void *coeffs, int prM =
 cudaError_t dfs_launch_phi_pass(dfsnufft_plan p);
 // interp.cu
 cudaError_t dfs_launch_interp(dfsnufft_plan p, void *values);
+// forward.cu
+bool dfs_forward_supported(const dfsnufft_params &q);
+cudaError_t dfs_launch_forward(dfsnufft_plan p, const void *samples, const int *d_parity,
+                               void *coeffs);

@@ -1,0 +1,162 @@
+// Coefficients from samples on the arrival grid (Sec. 3-4): the inverse of the
+// evaluation at the grid points, so that values at the arrival grid can be
+// carried to the departure points in one call.  The samples of Grid [0]
+// (theta_j = (j + 1/2) pi / n_lat, phi_k = 2 pi k / n_lon) are extended to the
+// doubled sphere by the field's parity (row 2 n_lat - 1 - j, half a turn in
+// longitude, sign +1 for scalars and -1 for wind components), then
+//   c_{n,m} = (1 / (N1 N2)) sum_{j,k} f_ext(phi_k, theta_j) e^{-i (m phi_k + n theta_j)}.
+//
+// Two passes on the FFT engine of the NUFFT (sign -1 by conjugation):
+//  k_fwd_phi   the rows: two real rows of a field form one complex sequence,
+//              whose transform splits into the two rows' spectra F_m(theta_j);
+//  k_fwd_theta the columns m: the doubled column (F_m(theta_j) for j < n_lat,
+//              parity (-1)^m F_m(theta_{N2-1-j}) above, the half turn being the
+//              factor (-1)^m), its transform, the half-cell phase e^{-i pi n / N2}
+//              and the 1 / (N1 N2) scale, written in the centred layout of
+//              dfsnufft_execute.
+#include "fft_core.cuh"
+
+using namespace dfs_fft;
+
+namespace {
+
+template <typename C> __device__ __forceinline__ C conjc(C a) { return cmake(a.x, -a.y); }
+template <typename C, typename R> __device__ __forceinline__ C cscale2(C a, R s) {
+    return cmake(a.x * s, a.y * s);
+}
+
+struct FwdArgs {
+    int n_lat, N1, N2;
+    int log1, log2;           // log2 N1, log2 N2
+    int tws1, tws2;           // twiddle strides: tw1[k << tws1] = e^{2 pi i k / N1}
+    int F;                    // fields per member
+    int CB;                   // columns per CTA (theta pass)
+};
+
+// grid (n_lat / 2, lines); block N1 / E threads.  Rows 2r and 2r + 1 of line f.
+template <typename R, int E>
+__global__ void __launch_bounds__(512) k_fwd_phi(FwdArgs a, const R *__restrict__ samples,
+                                                 const typename CxT<R>::type *__restrict__ tw1,
+                                                 typename CxT<R>::type *__restrict__ spec) {
+    typedef typename CxT<R>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    C *z = sm + region_len<C>(a.N1);                   // the pair's transform
+    const int f = blockIdx.y;
+    const int j = 2 * blockIdx.x;
+    const int t = threadIdx.x;
+    const R *x = samples + ((size_t)f * a.n_lat + j) * a.N1;
+    const R *y = x + a.N1;
+    // DFT_-(x + i y) = conj(DFT_+(conj(x + i y)))
+    auto ld = [&](int i) -> C { return cmake(x[i], -y[i]); };
+    auto st = [&](int k, C v) { z[k] = conjc(v); };
+    line_fft<E>(a.log1, tw1, a.tws1, sm, t, ld, st);
+    __syncthreads();
+    // X_m = (Z_m + conj Z_{-m}) / 2,  Y_m = (Z_m - conj Z_{-m}) / (2i)
+    C *sx = spec + ((size_t)f * a.n_lat + j) * a.N1;
+    C *sy = sx + a.N1;
+    for (int m = t; m < a.N1; m += blockDim.x) {
+        const C zp = z[m], zm = conjc(z[(a.N1 - m) & (a.N1 - 1)]);
+        sx[m] = cmake((R)0.5 * (zp.x + zm.x), (R)0.5 * (zp.y + zm.y));
+        sy[m] = cmake((R)0.5 * (zp.y - zm.y), (R)-0.5 * (zp.x - zm.x));
+    }
+}
+
+// grid (ceil(N1 / CB), lines); block CB * N2/E threads, thread = (t, c), c fastest.
+template <typename R, int E>
+__global__ void __launch_bounds__(512) k_fwd_theta(FwdArgs a,
+                                                   const typename CxT<R>::type *__restrict__ spec,
+                                                   const int *__restrict__ parity,
+                                                   const typename CxT<R>::type *__restrict__ tw2,
+                                                   typename CxT<R>::type *__restrict__ coef) {
+    typedef typename CxT<R>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *smem = reinterpret_cast<C *>(smem_raw);
+    const int c = threadIdx.x % a.CB;
+    const int t = threadIdx.x / a.CB;
+    const int m = blockIdx.x * a.CB + c;               // DFT index of the phi mode
+    const int f = blockIdx.y;
+    const bool ok = m < a.N1;
+    C *sm = smem + (size_t)c * region_len<C>(a.N2);
+    const C *col = spec + (size_t)f * a.n_lat * a.N1 + (ok ? m : 0);
+    // the upper half of the doubled column: parity (-1)^m times the mirrored row
+    const R sgn = (R)(parity[f % a.F] < 0 ? -1 : 1) * ((m & 1) ? (R)-1 : (R)1);
+    auto ld = [&](int i) -> C {
+        if (!ok) return cmake((R)0, (R)0);
+        const C v = i < a.n_lat ? col[(size_t)i * a.N1]
+                                : cscale2(col[(size_t)(a.N2 - 1 - i) * a.N1], sgn);
+        return conjc(v);
+    };
+    const R scale = (R)1 / ((R)a.N1 * (R)a.N2);
+    const int mc = m < a.N1 / 2 ? m + a.N1 / 2 : m - a.N1 / 2;   // centred column
+    C *out = coef + (size_t)f * a.N2 * a.N1 + mc;
+    auto st = [&](int k, C v) {
+        if (!ok) return;
+        // mode n = k (k < N2/2) or k - N2; half-cell phase e^{-i pi n / N2}:
+        // tw2 holds e^{+2 pi i k / n2} with n2 = N2 << tws2, so the phase is
+        // conj(tw2[n << (tws2 - 1)]) taken mod n2
+        const int n = k < a.N2 / 2 ? k : k - a.N2;
+        const int n2 = a.N2 << a.tws2;
+        const C ph = conjc(tw2[((n * (1 << (a.tws2 - 1))) % n2 + n2) % n2]);
+        const C g = conjc(v);
+        out[(size_t)(n + a.N2 / 2) * a.N1] = cscale2(cmul(g, ph), scale);
+    };
+    line_fft<E>(a.log2, tw2, a.tws2, sm, t, ld, st);
+}
+
+template <typename R>
+cudaError_t launch_forward(dfsnufft_plan p, const void *samples, const int *d_parity,
+                           void *coeffs, void *spec) {
+    typedef typename CxT<R>::type C;
+    constexpr int E = DFS_FFT_E;
+    const dfsnufft_params &q = p->prm;
+    FwdArgs a;
+    a.n_lat = q.n_lat;
+    a.N1 = q.N1;
+    a.N2 = q.N2;
+    a.log1 = ilog2(q.N1);
+    a.log2 = ilog2(q.N2);
+    a.tws1 = ilog2(q.n1) - a.log1;
+    a.tws2 = ilog2(q.n2) - a.log2;
+    a.F = p->n_fields;
+    const int lines = p->n_members * p->n_fields;
+    {
+        const int threads = q.N1 / E;
+        const size_t smem = sizeof(C) * (size_t)(region_len<C>(q.N1) + q.N1);
+        cudaError_t e = allow_smem(k_fwd_phi<R, E>, smem);
+        if (e) return e;
+        k_fwd_phi<R, E><<<dim3(q.n_lat / 2, lines), threads, smem, p->stream>>>(
+            a, (const R *)samples, (const C *)p->d_tw1, (C *)spec);
+    }
+    {
+        const int T = q.N2 / E;
+        int cb = 512 / T;
+        if (cb < 1) cb = 1;
+        if (cb > 8) cb = 8;
+        a.CB = cb;
+        const size_t smem = sizeof(C) * (size_t)cb * region_len<C>(q.N2);
+        cudaError_t e = allow_smem(k_fwd_theta<R, E>, smem);
+        if (e) return e;
+        k_fwd_theta<R, E><<<dim3((q.N1 + cb - 1) / cb, lines), cb * T, smem, p->stream>>>(
+            a, (const C *)spec, d_parity, (const C *)p->d_tw2, (C *)coeffs);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// The sizes the forward transform takes: N1 = n_lon and N2 = 2 n_lat powers of
+// two with 16 <= N <= 4096 (one line of at most 512 threads at E = 8), n_lat even.
+bool dfs_forward_supported(const dfsnufft_params &q) {
+    auto ok = [](int n) { return (n & (n - 1)) == 0 && n >= 16 && n <= 4096; };
+    return ok(q.N1) && ok(q.N2) && (q.n_lat % 2) == 0;
+}
+
+cudaError_t dfs_launch_forward(dfsnufft_plan p, const void *samples, const int *d_parity,
+                               void *coeffs) {
+    // the row spectra (lines x n_lat x N1 complex) fit in the theta-pass buffer,
+    // which the execute that follows overwrites only later in stream order
+    return p->prm.dtype == DFSNUFFT_F64
+               ? launch_forward<double>(p, samples, d_parity, coeffs, p->d_T)
+               : launch_forward<float>(p, samples, d_parity, coeffs, p->d_T);
+}

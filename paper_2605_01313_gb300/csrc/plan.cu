@@ -318,7 +318,8 @@ static void release(dfsnufft_plan p) {
     void **bufs[] = {&p->d_inv1, &p->d_inv2, &p->d_tw1, &p->d_tw2, &p->d_stw_theta, &p->d_stw_phi,
                      &p->d_T, &p->d_G, (void **)&p->d_bin_count, (void **)&p->d_bin_start,
                      (void **)&p->d_task_bin, (void **)&p->d_n_tasks,
-                     (void **)&p->d_status, (void **)&p->d_rowrange, (void **)&p->d_pofs,
+                     (void **)&p->d_status, (void **)&p->d_parity, (void **)&p->d_rowrange,
+                     (void **)&p->d_pofs,
                      (void **)&p->d_rank, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
                      (void **)&p->d_pts_stage, &p->d_coef_stage, &p->d_val_stage};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) dfs_free(bufs[i]);
@@ -488,6 +489,7 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
         {(void **)&p->d_task_bin, sizeof(int) * p->bstride * nm, "bin list"},
         {(void **)&p->d_n_tasks, sizeof(int) * nm, "bin list size"},
         {(void **)&p->d_status, sizeof(int), "status word"},
+        {(void **)&p->d_parity, sizeof(int) * 64, "field parities"},
         {(void **)&p->d_rowrange, sizeof(int2) * nm, "row ranges"},
         {(void **)&p->d_pofs, sizeof(int) * (nm + 1), "point offsets"},
     };
@@ -678,6 +680,57 @@ extern "C" int dfsnufft_execute_pr(dfsnufft_plan p, int M, int N, const void *pr
     DFS_CK(p, dfs_launch_interp(p, values));
     DFS_CK(p, timing_end(p, 3));
     return DFSNUFFT_OK;
+}
+
+// ------------------------------------------------------------------ grid values
+
+// Upload the fields' parities when they differ from the last ones uploaded.
+static int set_parity(dfsnufft_plan p, const int *parity) {
+    const int F = p->n_fields;
+    bool same = p->parity_set != 0;
+    for (int f = 0; f < F; ++f) {
+        if (parity[f] != 1 && parity[f] != -1) return DFSNUFFT_ERR_INVALID_ARG;
+        if (p->h_parity[f] != parity[f]) same = false;
+    }
+    if (same) return DFSNUFFT_OK;
+    for (int f = 0; f < F; ++f) p->h_parity[f] = parity[f];
+    DFS_CK(p, cudaMemcpyAsync(p->d_parity, p->h_parity, sizeof(int) * F,
+                              cudaMemcpyHostToDevice, p->stream));
+    // the copy reads h_parity; finish it before the host may change the array
+    DFS_CK(p, cudaStreamSynchronize(p->stream));
+    p->parity_set = 1;
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_grid_to_coeffs(dfsnufft_plan p, const void *samples, const int *parity,
+                                       void *coeffs) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    if (!samples || !parity || !coeffs) return DFSNUFFT_ERR_INVALID_ARG;
+    if (!dfs_forward_supported(p->prm)) return DFSNUFFT_ERR_UNSUPPORTED;
+    int rc = set_parity(p, parity);
+    if (rc) return rc;
+    DFS_CK(p, dfs_launch_forward(p, samples, p->d_parity, coeffs));
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_interpolate_grid(dfsnufft_plan p, const void *samples, const int *parity,
+                                         void *values) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    if (!p->has_points) return DFSNUFFT_ERR_NO_POINTS;
+    if (!samples || !parity || !values) return DFSNUFFT_ERR_INVALID_ARG;
+    if (!dfs_forward_supported(p->prm)) return DFSNUFFT_ERR_UNSUPPORTED;
+    if (!p->d_coef_stage) {
+        const size_t cs = p->prm.dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
+        int rc = dfs_alloc(p, &p->d_coef_stage,
+                           cs * (size_t)p->n_members * p->n_fields * p->prm.N2 * p->prm.N1,
+                           "coefficient staging");
+        if (rc) return rc;
+    }
+    int rc = dfsnufft_grid_to_coeffs(p, samples, parity, p->d_coef_stage);
+    if (rc) return rc;
+    return dfsnufft_execute(p, p->d_coef_stage, values);
 }
 
 // ------------------------------------------------------------------ host-buffer variants

@@ -42,7 +42,7 @@ EXPORTS = (
     "dfsnufft_server_stats_get", "dfsnufft_server_destroy",
     "dfsnufft_choose_params_opts", "dfsnufft_plan_create_opts", "dfsnufft_ensemble_create_opts",
     "dfsnufft_server_create_opts", "dfsnufft_autotune", "dfsnufft_selftest_wait_timeout",
-    "dfsnufft_execute_pr",
+    "dfsnufft_execute_pr", "dfsnufft_grid_to_coeffs", "dfsnufft_interpolate_grid",
 )
 REAL_FIELDS = 1
 KEEP_ORDER = 2
@@ -169,6 +169,8 @@ def lib():
         L.dfsnufft_set_points_host.argtypes = [vp, i64, vp, vp]
         L.dfsnufft_execute.argtypes = [vp, vp, vp]
         L.dfsnufft_execute_pr.argtypes = [vp, i32, i32, vp, vp]
+        L.dfsnufft_grid_to_coeffs.argtypes = [vp, vp, vp, vp]
+        L.dfsnufft_interpolate_grid.argtypes = [vp, vp, vp, vp]
         L.dfsnufft_execute_host.argtypes = [vp, vp, vp]
         L.dfsnufft_destroy.argtypes = [vp]
         L.dfsnufft_strerror.argtypes = [i32]
@@ -474,6 +476,43 @@ class Plan:
             out = torch.empty(shape, dtype=self._real_dtype(), device=pr.device)
         _check(lib().dfsnufft_execute_pr(self._h, int(M), int(N), ctypes.c_void_p(pr.data_ptr()),
                                          ctypes.c_void_p(out.data_ptr())), self._h)
+        return out
+
+    def _grid_args(self, samples, parity):
+        lead = (self.n_fields,) if self.n_members == 1 else (self.n_members, self.n_fields)
+        if tuple(samples.shape) != lead + (self.n_lat, self.n_lon) or \
+                samples.dtype != self._real_dtype() or not samples.is_cuda or \
+                not samples.is_contiguous():
+            raise ValueError("samples must be a contiguous CUDA %s tensor of shape %s"
+                             % (self._real_dtype(), lead + (self.n_lat, self.n_lon)))
+        par = np.ascontiguousarray(parity, dtype=np.int32)
+        if par.shape != (self.n_fields,):
+            raise ValueError("parity needs one entry (+1 or -1) per field")
+        return par
+
+    def grid_to_coeffs(self, samples, parity, out=None):
+        """Coefficients (the execute layout) of fields sampled on the arrival grid
+        (Grid [0]); parity +1 for scalars, -1 for wind components."""
+        import torch
+        par = self._grid_args(samples, parity)
+        if out is None:
+            out = torch.empty(self.coeff_shape, dtype=self._cplx_dtype(), device=samples.device)
+        _check(lib().dfsnufft_grid_to_coeffs(self._h, ctypes.c_void_p(samples.data_ptr()),
+                                             par.ctypes.data, ctypes.c_void_p(out.data_ptr())),
+               self._h)
+        return out
+
+    def interpolate_grid(self, samples, parity, out=None):
+        """Values at the plan's points of fields sampled on the arrival grid."""
+        import torch
+        par = self._grid_args(samples, parity)
+        shape = (self.n_fields, self.n_points) if self.n_members == 1 else \
+            (self.n_fields * self.n_points,)
+        if out is None:
+            out = torch.empty(shape, dtype=self._real_dtype(), device=samples.device)
+        _check(lib().dfsnufft_interpolate_grid(self._h, ctypes.c_void_p(samples.data_ptr()),
+                                               par.ctypes.data, ctypes.c_void_p(out.data_ptr())),
+               self._h)
         return out
 
     def split_values(self, out):
