@@ -39,6 +39,7 @@ L2_FLUSH_BYTES = 512 << 20          # written between timed steps (L2 is 126 MB)
 WORKLOADS = {
     "c3_2048x1024_f32": ("f32", "c3"),
     "c3pr_2048x1024_f32": ("f32", "c3pr"),
+    "c3grid_2048x1024_f32": ("f32", "c3grid"),
     "c4_ensemble_f32": ("f32", "c4"),
     "c3_2048x1024_f64": ("f64", "c3"),
     "c2_512x256_f64": ("f64", "c2"),
@@ -55,6 +56,18 @@ def make_workload(name):
         return synth.workload_c4()
     if kind == "c3":
         return synth.workload_c3(dtype)
+    if kind == "c3grid":
+        # the C3 departure points; the fields (h, u, v) of the tilted steady zonal
+        # flow given by their samples on the arrival grid (the whole step)
+        wl = synth.workload_c3(dtype)
+        alpha = math.pi / 2 - 0.05
+        lon_a, colat_a = synth.grid0_points(wl.n_lon, wl.n_lat)
+        h, u, v = synth.zonal_flow_values(lon_a, colat_a, alpha)
+        wl.grid = np.stack([h, u, v]).reshape(3, wl.n_lat, wl.n_lon)
+        wl.parity = [1, -1, -1]
+        wl.coeffs = np.stack(synth.zonal_flow_coeffs(wl.n_lon, wl.n_lat, alpha))
+        wl.name = "c3grid_%dx%d_%s" % (wl.n_lon, wl.n_lat, dtype)
+        return wl
     if kind == "c3pr":
         # the C3 points; fields given as partial-regularity coefficients (Sec. 4),
         # truncated as in the paper (N = J - 2, M = J - 1)
@@ -252,12 +265,16 @@ def run_ours(args):
 
     wl = make_workload(args.workload)
     pr_in = getattr(wl, "pr", None) is not None
+    grid_in = getattr(wl, "grid", None) is not None
     F, P = (wl.pr.shape[0] if pr_in else wl.n_fields), wl.n_points
     cd = torch.complex128 if wl.dtype == "f64" else torch.complex64
     rd = torch.float64 if wl.dtype == "f64" else torch.float32
     lon = torch.from_numpy(wl.lon).to(dev)
     colat = torch.from_numpy(wl.colat).to(dev)
-    coeffs = torch.from_numpy(wl.pr if pr_in else wl.coeffs).to(cd).to(dev)
+    if grid_in:
+        coeffs = torch.from_numpy(wl.grid).to(rd).to(dev)
+    else:
+        coeffs = torch.from_numpy(wl.pr if pr_in else wl.coeffs).to(cd).to(dev)
     out = torch.empty((F, P), dtype=rd, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -270,6 +287,8 @@ def run_ours(args):
         plan.set_points(lon, colat)
         if pr_in:
             plan.execute_pr(coeffs, out)
+        elif grid_in:
+            plan.interpolate_grid(coeffs, wl.parity, out)
         else:
             plan.execute(coeffs, out)
 
@@ -310,23 +329,29 @@ def run_ours(args):
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     h_lon, h_colat = pin(wl.lon), pin(wl.colat)
-    h_coef = pin((wl.pr if pr_in else wl.coeffs).astype(
-        np.complex128 if wl.dtype == "f64" else np.complex64))
+    if grid_in:
+        h_coef = pin(wl.grid.astype(np.float64 if wl.dtype == "f64" else np.float32))
+    else:
+        h_coef = pin((wl.pr if pr_in else wl.coeffs).astype(
+            np.complex128 if wl.dtype == "f64" else np.complex64))
     h_out = torch.empty((F, P), dtype=rd).pin_memory().numpy()
     e2e_steps = max(3, min(args.steps, 10))
 
     def e2e_step():
-        if not pr_in:
+        if not (pr_in or grid_in):
             plan.set_points_host(h_lon, h_colat)
             plan.execute_host(h_coef, h_out)
             return
         # the host-buffer entry points take complex coefficients: partial-
-        # regularity input goes through pinned copies around execute_pr
+        # regularity and grid input go through pinned copies around the call
         lon.copy_(torch.from_numpy(h_lon), non_blocking=True)
         colat.copy_(torch.from_numpy(h_colat), non_blocking=True)
         coeffs.copy_(torch.from_numpy(h_coef), non_blocking=True)
         plan.set_points(lon, colat)
-        plan.execute_pr(coeffs, out)
+        if pr_in:
+            plan.execute_pr(coeffs, out)
+        else:
+            plan.interpolate_grid(coeffs, wl.parity, out)
         torch.from_numpy(h_out).copy_(out, non_blocking=True)
         torch.cuda.synchronize(dev)
 
@@ -418,6 +443,13 @@ def run_ours(args):
     if pr_in:
         line["config"]["input"] = "partial-regularity DFS coefficients (Sec. 4), M = %d, N = %d" % (
             wl.pr.shape[1] - 1, wl.pr.shape[2] - 1)
+    if grid_in:
+        line["config"]["input"] = ("samples of the tilted steady zonal flow (h, u, v) on the "
+                                   "arrival grid; coefficients computed on the GPU each step")
+        # the forward transform has no stage timer of its own: the step minus the stages
+        line["stages"]["grid_to_coeffs"] = {
+            "ms": line["ms_per_step"] - sum(v["ms"] for v in stages_out.values()),
+            "note": "step time minus the four timed stages"}
     if ws == 1 and not args.no_cpu_baseline:
         if pr_in:
             # the oracle's own route: partial-regularity -> standard -> complex
