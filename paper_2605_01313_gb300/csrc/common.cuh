@@ -127,5 +127,7 @@ cudaError_t dfs_launch_phi_pass(dfsnufft_plan p);
 cudaError_t dfs_launch_interp(dfsnufft_plan p, void *values);
 // forward.cu
 bool dfs_forward_supported(const dfsnufft_params &q);
+// full = false: of the columns m < 0 only the Nyquist row n = -N2/2 is written
+// (all that a real-field plan's theta pass reads there)
 cudaError_t dfs_launch_forward(dfsnufft_plan p, const void *samples, const int *d_parity,
-                               void *coeffs);
+                               void *coeffs, bool full);

@@ -9,7 +9,8 @@
 // Two passes on the FFT engine of the NUFFT (sign -1 by conjugation):
 //  k_fwd_phi   the rows: two real rows of a field form one complex sequence,
 //              whose transform splits into the two rows' spectra F_m(theta_j);
-//  k_fwd_theta the columns m: the doubled column (F_m(theta_j) for j < n_lat,
+//  k_fwd_theta the columns m >= 0 (the rest by conjugate symmetry, the samples
+//              being real): the doubled column (F_m(theta_j) for j < n_lat,
 //              parity (-1)^m F_m(theta_{N2-1-j}) above, the half turn being the
 //              factor (-1)^m), its transform, the half-cell phase e^{-i pi n / N2}
 //              and the 1 / (N1 N2) scale, written in the centred layout of
@@ -31,12 +32,15 @@ struct FwdArgs {
     int tws1, tws2;           // twiddle strides: tw1[k << tws1] = e^{2 pi i k / N1}
     int F;                    // fields per member
     int CB;                   // columns per CTA (theta pass)
+    int full;                 // 0: of the columns m < 0 only the Nyquist row is written
 };
 
 // grid (n_lat / 2, lines); block N1 / E threads.  Rows 2r and 2r + 1 of line f.
-template <typename R, int E>
+// LOG > 0: length 2^LOG at compile time with the stage-ordered table stw.
+template <typename R, int E, int LOG>
 __global__ void __launch_bounds__(512) k_fwd_phi(FwdArgs a, const R *__restrict__ samples,
                                                  const typename CxT<R>::type *__restrict__ tw1,
+                                                 const typename CxT<R>::type *__restrict__ stw,
                                                  typename CxT<R>::type *__restrict__ spec) {
     typedef typename CxT<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -50,24 +54,29 @@ __global__ void __launch_bounds__(512) k_fwd_phi(FwdArgs a, const R *__restrict_
     // DFT_-(x + i y) = conj(DFT_+(conj(x + i y)))
     auto ld = [&](int i) -> C { return cmake(x[i], -y[i]); };
     auto st = [&](int k, C v) { z[k] = conjc(v); };
-    line_fft<E>(a.log1, tw1, a.tws1, sm, t, ld, st);
+    if constexpr (LOG > 0) line_fft_ct<LOG, E>(stw, sm, t, ld, st);
+    else line_fft<E>(a.log1, tw1, a.tws1, sm, t, ld, st);
     __syncthreads();
     // X_m = (Z_m + conj Z_{-m}) / 2,  Y_m = (Z_m - conj Z_{-m}) / (2i)
     C *sx = spec + ((size_t)f * a.n_lat + j) * a.N1;
     C *sy = sx + a.N1;
-    for (int m = t; m < a.N1; m += blockDim.x) {
+    for (int m = t; m <= a.N1 / 2; m += blockDim.x) {          // the theta pass reads m <= N1/2
         const C zp = z[m], zm = conjc(z[(a.N1 - m) & (a.N1 - 1)]);
         sx[m] = cmake((R)0.5 * (zp.x + zm.x), (R)0.5 * (zp.y + zm.y));
         sy[m] = cmake((R)0.5 * (zp.y - zm.y), (R)-0.5 * (zp.x - zm.x));
     }
 }
 
-// grid (ceil(N1 / CB), lines); block CB * N2/E threads, thread = (t, c), c fastest.
-template <typename R, int E>
+// grid (ceil((N1/2 + 1) / CB), lines); block CB * N2/E threads, thread = (t, c),
+// c fastest.  The samples are real, so c_{-n,-m} = conj c_{n,m}: only the modes
+// m = 0..N1/2 (DFT index) are transformed, and each column 0 < m < N1/2 also
+// writes its mirror column -m.  LOG > 0: length 2^LOG at compile time.
+template <typename R, int E, int LOG>
 __global__ void __launch_bounds__(512) k_fwd_theta(FwdArgs a,
                                                    const typename CxT<R>::type *__restrict__ spec,
                                                    const int *__restrict__ parity,
                                                    const typename CxT<R>::type *__restrict__ tw2,
+                                                   const typename CxT<R>::type *__restrict__ stw,
                                                    typename CxT<R>::type *__restrict__ coef) {
     typedef typename CxT<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -76,7 +85,7 @@ __global__ void __launch_bounds__(512) k_fwd_theta(FwdArgs a,
     const int t = threadIdx.x / a.CB;
     const int m = blockIdx.x * a.CB + c;               // DFT index of the phi mode
     const int f = blockIdx.y;
-    const bool ok = m < a.N1;
+    const bool ok = m <= a.N1 / 2;
     C *sm = smem + (size_t)c * region_len<C>(a.N2);
     const C *col = spec + (size_t)f * a.n_lat * a.N1 + (ok ? m : 0);
     // the upper half of the doubled column: parity (-1)^m times the mirrored row
@@ -90,6 +99,8 @@ __global__ void __launch_bounds__(512) k_fwd_theta(FwdArgs a,
     const R scale = (R)1 / ((R)a.N1 * (R)a.N2);
     const int mc = m < a.N1 / 2 ? m + a.N1 / 2 : m - a.N1 / 2;   // centred column
     C *out = coef + (size_t)f * a.N2 * a.N1 + mc;
+    C *mirror = coef + (size_t)f * a.N2 * a.N1 + (a.N1 - mc);   // column of -m
+    const bool has_mirror = ok && m > 0 && m < a.N1 / 2;
     auto st = [&](int k, C v) {
         if (!ok) return;
         // mode n = k (k < N2/2) or k - N2; half-cell phase e^{-i pi n / N2}:
@@ -98,16 +109,56 @@ __global__ void __launch_bounds__(512) k_fwd_theta(FwdArgs a,
         const int n = k < a.N2 / 2 ? k : k - a.N2;
         const int n2 = a.N2 << a.tws2;
         const C ph = conjc(tw2[((n * (1 << (a.tws2 - 1))) % n2 + n2) % n2]);
-        const C g = conjc(v);
-        out[(size_t)(n + a.N2 / 2) * a.N1] = cscale2(cmul(g, ph), scale);
+        const C cv = cscale2(cmul(conjc(v), ph), scale);
+        out[(size_t)(n + a.N2 / 2) * a.N1] = cv;
+        // c_{-n,-m} = conj c_{n,m}; the half-cell grid makes the sum antiperiodic
+        // in n (c_{n+N2,m} = -c_{n,m}), so the row n = -N2/2 of column -m is
+        // -conj c_{-N2/2,m}
+        if (has_mirror) {
+            if (n > -a.N2 / 2) {
+                if (a.full) mirror[(size_t)(a.N2 / 2 - n) * a.N1] = conjc(cv);
+            } else {
+                mirror[0] = cmake(-cv.x, cv.y);
+            }
+        }
     };
-    line_fft<E>(a.log2, tw2, a.tws2, sm, t, ld, st);
+    if constexpr (LOG > 0) line_fft_ct<LOG, E>(stw, sm, t, ld, st);
+    else line_fft<E>(a.log2, tw2, a.tws2, sm, t, ld, st);
+}
+
+template <typename R, int LOG>
+cudaError_t run_fwd_phi(dfsnufft_plan p, const FwdArgs &a, const void *samples, void *spec,
+                        int lines) {
+    typedef typename CxT<R>::type C;
+    constexpr int E = DFS_FFT_E;
+    const int threads = a.N1 / E;
+    const size_t smem = sizeof(C) * (size_t)(region_len<C>(a.N1) + a.N1);
+    cudaError_t e = allow_smem(k_fwd_phi<R, E, LOG>, smem);
+    if (e) return e;
+    k_fwd_phi<R, E, LOG><<<dim3(a.n_lat / 2, lines), threads, smem, p->stream>>>(
+        a, (const R *)samples, (const C *)p->d_tw1, (const C *)p->d_stw_phi, (C *)spec);
+    return cudaGetLastError();
+}
+
+template <typename R, int LOG>
+cudaError_t run_fwd_theta(dfsnufft_plan p, const FwdArgs &a, const void *spec,
+                          const int *d_parity, void *coeffs, int lines) {
+    typedef typename CxT<R>::type C;
+    constexpr int E = DFS_FFT_E;
+    const int T = a.N2 / E;
+    const size_t smem = sizeof(C) * (size_t)a.CB * region_len<C>(a.N2);
+    cudaError_t e = allow_smem(k_fwd_theta<R, E, LOG>, smem);
+    if (e) return e;
+    const int ncol = a.N1 / 2 + 1;
+    k_fwd_theta<R, E, LOG><<<dim3((ncol + a.CB - 1) / a.CB, lines), a.CB * T, smem, p->stream>>>(
+        a, (const C *)spec, d_parity, (const C *)p->d_tw2, (const C *)p->d_stw_theta,
+        (C *)coeffs);
+    return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_forward(dfsnufft_plan p, const void *samples, const int *d_parity,
-                           void *coeffs, void *spec) {
-    typedef typename CxT<R>::type C;
+                           void *coeffs, void *spec, bool full) {
     constexpr int E = DFS_FFT_E;
     const dfsnufft_params &q = p->prm;
     FwdArgs a;
@@ -119,28 +170,31 @@ cudaError_t launch_forward(dfsnufft_plan p, const void *samples, const int *d_pa
     a.tws1 = ilog2(q.n1) - a.log1;
     a.tws2 = ilog2(q.n2) - a.log2;
     a.F = p->n_fields;
+    a.full = full ? 1 : 0;
+    const int T = q.N2 / E;
+    int cb = 512 / T;
+    if (cb < 1) cb = 1;
+    if (cb > 8) cb = 8;
+    a.CB = cb;
     const int lines = p->n_members * p->n_fields;
-    {
-        const int threads = q.N1 / E;
-        const size_t smem = sizeof(C) * (size_t)(region_len<C>(q.N1) + q.N1);
-        cudaError_t e = allow_smem(k_fwd_phi<R, E>, smem);
-        if (e) return e;
-        k_fwd_phi<R, E><<<dim3(q.n_lat / 2, lines), threads, smem, p->stream>>>(
-            a, (const R *)samples, (const C *)p->d_tw1, (C *)spec);
+    // the plan's stage-ordered tables are for lengths n1/2 and n2/2: they serve
+    // the compile-time drivers when the fine grid is twice the modes
+    const bool ct1 = p->d_stw_phi && q.n1 == 2 * q.N1 && a.log1 >= 9 && a.log1 <= 11;
+    const bool ct2 = p->d_stw_theta && q.n2 == 2 * q.N2 && a.log2 >= 9 && a.log2 <= 11;
+    cudaError_t e;
+    switch (ct1 ? a.log1 : 0) {
+        case 9: e = run_fwd_phi<R, 9>(p, a, samples, spec, lines); break;
+        case 10: e = run_fwd_phi<R, 10>(p, a, samples, spec, lines); break;
+        case 11: e = run_fwd_phi<R, 11>(p, a, samples, spec, lines); break;
+        default: e = run_fwd_phi<R, 0>(p, a, samples, spec, lines); break;
     }
-    {
-        const int T = q.N2 / E;
-        int cb = 512 / T;
-        if (cb < 1) cb = 1;
-        if (cb > 8) cb = 8;
-        a.CB = cb;
-        const size_t smem = sizeof(C) * (size_t)cb * region_len<C>(q.N2);
-        cudaError_t e = allow_smem(k_fwd_theta<R, E>, smem);
-        if (e) return e;
-        k_fwd_theta<R, E><<<dim3((q.N1 + cb - 1) / cb, lines), cb * T, smem, p->stream>>>(
-            a, (const C *)spec, d_parity, (const C *)p->d_tw2, (C *)coeffs);
+    if (e) return e;
+    switch (ct2 ? a.log2 : 0) {
+        case 9: return run_fwd_theta<R, 9>(p, a, spec, d_parity, coeffs, lines);
+        case 10: return run_fwd_theta<R, 10>(p, a, spec, d_parity, coeffs, lines);
+        case 11: return run_fwd_theta<R, 11>(p, a, spec, d_parity, coeffs, lines);
+        default: return run_fwd_theta<R, 0>(p, a, spec, d_parity, coeffs, lines);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace
@@ -153,10 +207,10 @@ bool dfs_forward_supported(const dfsnufft_params &q) {
 }
 
 cudaError_t dfs_launch_forward(dfsnufft_plan p, const void *samples, const int *d_parity,
-                               void *coeffs) {
+                               void *coeffs, bool full) {
     // the row spectra (lines x n_lat x N1 complex) fit in the theta-pass buffer,
     // which the execute that follows overwrites only later in stream order
     return p->prm.dtype == DFSNUFFT_F64
-               ? launch_forward<double>(p, samples, d_parity, coeffs, p->d_T)
-               : launch_forward<float>(p, samples, d_parity, coeffs, p->d_T);
+               ? launch_forward<double>(p, samples, d_parity, coeffs, p->d_T, full)
+               : launch_forward<float>(p, samples, d_parity, coeffs, p->d_T, full);
 }

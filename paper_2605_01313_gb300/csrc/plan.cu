@@ -702,16 +702,21 @@ static int set_parity(dfsnufft_plan p, const int *parity) {
     return DFSNUFFT_OK;
 }
 
-extern "C" int dfsnufft_grid_to_coeffs(dfsnufft_plan p, const void *samples, const int *parity,
-                                       void *coeffs) {
+static int grid_to_coeffs(dfsnufft_plan p, const void *samples, const int *parity,
+                          void *coeffs, bool full) {
     if (!p) return DFSNUFFT_ERR_INVALID_ARG;
     if (p->status) return p->status;
     if (!samples || !parity || !coeffs) return DFSNUFFT_ERR_INVALID_ARG;
     if (!dfs_forward_supported(p->prm)) return DFSNUFFT_ERR_UNSUPPORTED;
     int rc = set_parity(p, parity);
     if (rc) return rc;
-    DFS_CK(p, dfs_launch_forward(p, samples, p->d_parity, coeffs));
+    DFS_CK(p, dfs_launch_forward(p, samples, p->d_parity, coeffs, full));
     return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_grid_to_coeffs(dfsnufft_plan p, const void *samples, const int *parity,
+                                       void *coeffs) {
+    return grid_to_coeffs(p, samples, parity, coeffs, true);
 }
 
 extern "C" int dfsnufft_interpolate_grid(dfsnufft_plan p, const void *samples, const int *parity,
@@ -728,7 +733,8 @@ extern "C" int dfsnufft_interpolate_grid(dfsnufft_plan p, const void *samples, c
                            "coefficient staging");
         if (rc) return rc;
     }
-    int rc = dfsnufft_grid_to_coeffs(p, samples, parity, p->d_coef_stage);
+    // a real-field plan reads the columns m >= 0 and the Nyquist row only
+    int rc = grid_to_coeffs(p, samples, parity, p->d_coef_stage, !p->herm);
     if (rc) return rc;
     return dfsnufft_execute(p, p->d_coef_stage, values);
 }

@@ -63,17 +63,19 @@ def test_interpolate_grid_reproduces_arrival_samples(torch_cuda, dtype):
     assert err <= (1e-11 if dtype == "f64" else 2e-5), err
 
 
+@pytest.mark.parametrize("real", [True, False])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_interpolate_grid_band_limited_fields(torch_cuda, dtype):
+def test_interpolate_grid_band_limited_fields(torch_cuda, dtype, real):
     """Band-limited fields (scalar and wind parity) sampled on the arrival grid are
-    carried to departure points exactly as their series evaluates there."""
+    carried to departure points exactly as their series evaluates there, by a
+    real-field plan (which stages only the columns m >= 0) and a general one."""
     torch = torch_cuda
     wl = synth.workload_member(820, 256, 128, dtype, n_sample=400)
     c = wl.coeffs
     lon_a, colat_a = synth.grid0_points(256, 128)
     s = oracle.evaluate(c, lon_a, colat_a).real.reshape(3, 128, 256)
     rd = torch.float64 if dtype == "f64" else torch.float32
-    with plan_for(256, 128, dtype, 3) as plan:
+    with plan_for(256, 128, dtype, 3, real=real) as plan:
         plan.set_points(torch.from_numpy(wl.lon).cuda(), torch.from_numpy(wl.colat).cuda())
         v = plan.interpolate_grid(torch.from_numpy(s).to(rd).cuda(), [1, -1, -1]).cpu().numpy()
     ref = oracle.evaluate(c, wl.lon[wl.sample], wl.colat[wl.sample])
