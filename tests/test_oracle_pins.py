@@ -431,3 +431,29 @@ def test_grid_to_coeffs_pins_catch_mistakes(oracle_mod, mistake):
         ext[j] = (1.0 if mistake == "wrong_parity" else -1.0) * row
     bad = np.exp(-1j * np.outer(n, th)) @ ext @ np.exp(-1j * np.outer(ph, m)) / (n1 * n2)
     assert np.max(np.abs(bad - c[0])) > 1e-3
+
+
+def test_grid_to_coeffs_conjugate_symmetry_and_antiperiodic_nyquist_row(oracle_mod):
+    """Real samples give c_{-n,-m} = conj c_{n,m}; on the half-cell theta grid the
+    sum is antiperiodic in n (e^{-i N2 theta_j} = -1), so the Nyquist row of the
+    columns -m is minus the conjugate of the row at m (the GPU transform writes
+    the columns m < 0 from these two facts)."""
+    rng = np.random.default_rng(630)
+    n_lon, n_lat = 16, 6
+    s = rng.standard_normal((1, n_lat, n_lon))
+    c = oracle_mod.grid_to_coeffs(s, [-1])[0]
+    N2, N1 = 2 * n_lat, n_lon
+    for m in range(1, N1 // 2):
+        qm, qn = N1 // 2 + m, N1 // 2 - m
+        for n in range(-N2 // 2 + 1, N2 // 2):
+            assert abs(c[N2 // 2 - n, qn] - np.conj(c[N2 // 2 + n, qm])) < 1e-14
+        assert abs(c[0, qn] + np.conj(c[0, qm])) < 1e-14
+    # the row formula at n = +N2/2 (outside the array) is minus the row at -N2/2
+    th = (np.arange(N2) + 0.5) * (math.pi / n_lat)
+    ph = np.arange(N1) * (2 * math.pi / N1)
+    ext = np.empty((N2, N1))
+    ext[:n_lat] = s[0]
+    for j in range(n_lat, N2):
+        ext[j] = -np.roll(s[0][N2 - 1 - j], -(N1 // 2))
+    top = np.exp(-1j * (N2 // 2) * th) @ ext @ np.exp(-1j * np.outer(ph, np.arange(N1) - N1 // 2))
+    assert np.max(np.abs(top / (N1 * N2) + c[0])) < 1e-14
