@@ -40,6 +40,7 @@ WORKLOADS = {
     "c3_2048x1024_f32": ("f32", "c3"),
     "c3pr_2048x1024_f32": ("f32", "c3pr"),
     "c3grid_2048x1024_f32": ("f32", "c3grid"),
+    "c3sl_2048x1024_f32": ("f32", "c3sl"),
     "c4_ensemble_f32": ("f32", "c4"),
     "c3_2048x1024_f64": ("f64", "c3"),
     "c2_512x256_f64": ("f64", "c2"),
@@ -67,6 +68,25 @@ def make_workload(name):
         wl.parity = [1, -1, -1]
         wl.coeffs = np.stack(synth.zonal_flow_coeffs(wl.n_lon, wl.n_lat, alpha))
         wl.name = "c3grid_%dx%d_%s" % (wl.n_lon, wl.n_lat, dtype)
+        return wl
+    if kind == "c3sl":
+        # the whole semi-Lagrangian interpolation step of the tilted steady zonal
+        # flow (TC2 of Sec. 6, 1800 s): departure points from the Eq. 2.4 terms on
+        # the arrival grid, (h, u, v) from their arrival-grid samples carried
+        # there, the wind rotated back to the arrival frame
+        wl = synth.workload_c3(dtype)
+        alpha = math.pi / 2 - 0.05
+        dt = 1800.0
+        lon_a, colat_a = synth.grid0_points(wl.n_lon, wl.n_lat)
+        h, u, v = synth.zonal_flow_values(lon_a, colat_a, alpha)
+        wl.grid = np.stack([h, u, v]).reshape(3, wl.n_lat, wl.n_lon)
+        wl.parity = [1, -1, -1]
+        wl.coeffs = np.stack(synth.zonal_flow_coeffs(wl.n_lon, wl.n_lat, alpha))
+        w, wa = synth.zonal_flow_settls_terms(lon_a, colat_a, alpha, dt)
+        wl.sl = {"w": w.reshape(2, wl.n_lat, wl.n_lon), "wa": wa.reshape(2, wl.n_lat, wl.n_lon),
+                 "dt_over_a": dt / synth.EARTH_RADIUS, "iterations": 3}
+        wl.lon, wl.colat = lon_a, colat_a       # arrival points; departures come from the step
+        wl.name = "c3sl_%dx%d_%s" % (wl.n_lon, wl.n_lat, dtype)
         return wl
     if kind == "c3pr":
         # the C3 points; fields given as partial-regularity coefficients (Sec. 4),
@@ -266,6 +286,7 @@ def run_ours(args):
     wl = make_workload(args.workload)
     pr_in = getattr(wl, "pr", None) is not None
     grid_in = getattr(wl, "grid", None) is not None
+    sl = getattr(wl, "sl", None)
     F, P = (wl.pr.shape[0] if pr_in else wl.n_fields), wl.n_points
     cd = torch.complex128 if wl.dtype == "f64" else torch.complex64
     rd = torch.float64 if wl.dtype == "f64" else torch.float32
@@ -276,6 +297,9 @@ def run_ours(args):
     else:
         coeffs = torch.from_numpy(wl.pr if pr_in else wl.coeffs).to(cd).to(dev)
     out = torch.empty((F, P), dtype=rd, device=dev)
+    if sl is not None:
+        w_t = torch.from_numpy(sl["w"]).to(rd).to(dev).contiguous()
+        wa_t = torch.from_numpy(sl["wa"]).to(rd).to(dev).contiguous()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -283,7 +307,14 @@ def run_ours(args):
     plan = Plan(wl.n_lon, wl.n_lat, wl.tol, wl.dtype, F, stream=stream, options=opts)
     prm = plan.params
 
-    def step():
+    def step(evs=None):
+        if sl is not None:        # departure points of Eq. 2.4 into the point buffers
+            if evs:
+                evs[0].record(stream)
+            nufft.departure_points(w_t, sl["dt_over_a"], sl["iterations"], wa_t, stream,
+                                   lon_out=lon, colat_out=colat)
+            if evs:
+                evs[1].record(stream)
         plan.set_points(lon, colat)
         if pr_in:
             plan.execute_pr(coeffs, out)
@@ -291,6 +322,13 @@ def run_ours(args):
             plan.interpolate_grid(coeffs, wl.parity, out)
         else:
             plan.execute(coeffs, out)
+        if sl is not None:        # the wind to the arrival frame, in place
+            if evs:
+                evs[2].record(stream)
+            nufft.rotate_to_arrival(wl.n_lon, wl.n_lat, lon, colat, out[1], out[2],
+                                    u_a=out[1], v_a=out[2], stream=stream)
+            if evs:
+                evs[3].record(stream)
 
     for _ in range(args.warmup):
         flush.fill_(1)
@@ -308,13 +346,15 @@ def run_ours(args):
     nufft.dfsnufft_plan_enable_timing(plan._h, True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    sl_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)]
+             for _ in range(args.steps)] if sl is not None else None
     barrier()
     torch.cuda.synchronize(dev)
     sampler.start()
     for i in range(args.steps):
         flush.fill_(i & 255)                  # untimed: evicts L2 between timed steps
         ev[i][0].record(stream)
-        step()
+        step(sl_ev[i] if sl_ev else None)
         ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
     barrier()
@@ -329,6 +369,9 @@ def run_ours(args):
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     h_lon, h_colat = pin(wl.lon), pin(wl.colat)
+    if sl is not None:
+        h_w = pin(sl["w"].astype(np.float64 if wl.dtype == "f64" else np.float32))
+        h_wa = pin(sl["wa"].astype(np.float64 if wl.dtype == "f64" else np.float32))
     if grid_in:
         h_coef = pin(wl.grid.astype(np.float64 if wl.dtype == "f64" else np.float32))
     else:
@@ -344,14 +387,14 @@ def run_ours(args):
             return
         # the host-buffer entry points take complex coefficients: partial-
         # regularity and grid input go through pinned copies around the call
-        lon.copy_(torch.from_numpy(h_lon), non_blocking=True)
-        colat.copy_(torch.from_numpy(h_colat), non_blocking=True)
+        if sl is None:
+            lon.copy_(torch.from_numpy(h_lon), non_blocking=True)
+            colat.copy_(torch.from_numpy(h_colat), non_blocking=True)
+        else:                 # the points come from the step itself
+            w_t.copy_(torch.from_numpy(h_w), non_blocking=True)
+            wa_t.copy_(torch.from_numpy(h_wa), non_blocking=True)
         coeffs.copy_(torch.from_numpy(h_coef), non_blocking=True)
-        plan.set_points(lon, colat)
-        if pr_in:
-            plan.execute_pr(coeffs, out)
-        else:
-            plan.interpolate_grid(coeffs, wl.parity, out)
+        step()
         torch.from_numpy(h_out).copy_(out, non_blocking=True)
         torch.cuda.synchronize(dev)
 
@@ -366,7 +409,7 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_total = max_over_ranks(sum(e2e_ms), ws, dev)
     e2e_value = weak_scaling_value(ws, F * P, e2e_steps, e2e_total)
-    h2d = 2 * 8 * P + h_coef.nbytes
+    h2d = (2 * 8 * P if sl is None else h_w.nbytes + h_wa.nbytes) + h_coef.nbytes
     d2h = h_out.nbytes
     assert np.array_equal(h_out, out.cpu().numpy()), "host and device paths disagree"
 
@@ -435,7 +478,8 @@ def run_ours(args):
         "roofline": roof,
         "roofline_step": roof_step,
         "stages": stages_out,
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": ((4 if prm["flags"] & 2 else 7) + (2 if grid_in else 0)
+                         + (2 if sl is not None else 0)) * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / e2e_steps},
         "clocks": clocks,
@@ -443,13 +487,27 @@ def run_ours(args):
     if pr_in:
         line["config"]["input"] = "partial-regularity DFS coefficients (Sec. 4), M = %d, N = %d" % (
             wl.pr.shape[1] - 1, wl.pr.shape[2] - 1)
+    if sl is not None:
+        rs = 4 if wl.dtype == "f32" else 8
+        dep_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in sl_ev]))
+        rot_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in sl_ev]))
+        dep_b, rot_b = (4 * rs + 16) * P, (16 + 4 * rs) * P
+        stages_out["departure_points"] = {"ms": dep_ms, "bytes": dep_b,
+                                          "gbs": dep_b / (dep_ms * 1e-3) / 1e9,
+                                          "iterations": sl["iterations"]}
+        stages_out["rotate_to_arrival"] = {"ms": rot_ms, "bytes": rot_b,
+                                           "gbs": rot_b / (rot_ms * 1e-3) / 1e9}
     if grid_in:
         line["config"]["input"] = ("samples of the tilted steady zonal flow (h, u, v) on the "
                                    "arrival grid; coefficients computed on the GPU each step")
+        if sl is not None:
+            line["config"]["input"] += ("; departure points of Eq. 2.4 (TC2 flow, dt 1800 s, "
+                                        "%d iterations) and the wind rotated to the arrival "
+                                        "frame each step" % sl["iterations"])
         # the forward transform has no stage timer of its own: the step minus the stages
         line["stages"]["grid_to_coeffs"] = {
             "ms": line["ms_per_step"] - sum(v["ms"] for v in stages_out.values()),
-            "note": "step time minus the four timed stages"}
+            "note": "step time minus the timed stages"}
     if ws == 1 and not args.no_cpu_baseline:
         if pr_in:
             # the oracle's own route: partial-regularity -> standard -> complex
@@ -470,11 +528,29 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _oracle_sample_size(wl, seconds):
+def oracle_values(wl, s):
+    """The oracle's values of the workload's fields at its sampled points s.  For
+    the whole semi-Lagrangian step: the oracle's departure points of those
+    arrival points first, the wind rotated to the arrival frame after."""
     import oracle
+    sl = getattr(wl, "sl", None)
+    if sl is None:
+        return oracle.evaluate(wl.coeffs, wl.lon[s], wl.colat[s]).real
+    from oracle import departure as dep
+    rnd = (lambda a: a.astype(np.float32).astype(np.float64)) if wl.dtype == "f32" else \
+        (lambda a: a)
+    lon_d, colat_d = dep.departure_points(rnd(sl["w"]), rnd(sl["wa"]), sl["dt_over_a"],
+                                          sl["iterations"], index=s)
+    vals = oracle.evaluate(wl.coeffs, lon_d, colat_d).real
+    la, ca = dep.arrival_points(wl.n_lon, wl.n_lat)
+    u, v = dep.rotate_to_arrival(vals[1], vals[2], la[s], ca[s], lon_d, colat_d)
+    return np.stack([vals[0], u, v])
+
+
+def _oracle_sample_size(wl, seconds):
     probe = wl.sample[:4]
     t0 = time.perf_counter()
-    oracle.evaluate(wl.coeffs, wl.lon[probe], wl.colat[probe])
+    oracle_values(wl, probe)
     per_point = (time.perf_counter() - t0) / probe.size
     return int(max(8, min(wl.sample.size, seconds / max(per_point, 1e-9))))
 
@@ -486,13 +562,15 @@ def cpu_baseline(wl, gpu_vals, seconds):
     n = _oracle_sample_size(wl, seconds)
     s = wl.sample[:n]
     t0 = time.perf_counter()
-    ref = oracle.evaluate(wl.coeffs, wl.lon[s], wl.colat[s])
+    ref = oracle_values(wl, s)
     dt = time.perf_counter() - t0
-    err = [oracle.rel_linf(gpu_vals[f][s], ref[f].real) for f in range(wl.n_fields)]
+    err = [oracle.rel_linf(gpu_vals[f][s], ref[f]) for f in range(wl.n_fields)]
+    what = ("departure points (NumPy), FP64 direct sum, rotation"
+            if getattr(wl, "sl", None) is not None else "FP64 direct sum")
     base = {"value": n * wl.n_fields / dt, "unit": UNIT, "cores": oracle.max_threads(),
             "kind": "oracle",
-            "sample": "%d of the workload's seeded check points x %d fields, FP64 direct sum"
-                      % (n, wl.n_fields)}
+            "sample": "%d of the workload's seeded check points x %d fields, %s"
+                      % (n, wl.n_fields, what)}
     bound = 1e-11 if wl.dtype == "f64" else 2e-5
     return base, {"rel_linf_per_field": err, "bound": bound, "ok": max(err) <= bound,
                   "points_checked": int(n)}
@@ -740,7 +818,7 @@ def run_reference(args):
             if s.size < k:
                 s = w.sample[:k]
             t0 = time.perf_counter()
-            oracle.evaluate(w.coeffs, w.lon[s], w.colat[s])
+            oracle_values(w, s)
             t_step += time.perf_counter() - t0
             pf_step += s.size * w.n_fields
         if i >= args.warmup:

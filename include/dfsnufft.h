@@ -306,6 +306,54 @@ int dfsnufft_grid_to_coeffs(dfsnufft_plan plan, const void *samples, const int *
 int dfsnufft_interpolate_grid(dfsnufft_plan plan, const void *samples, const int *parity,
                               void *values);
 
+/* ---- departure points and the vector rotation (Sec. 2) -------------------- */
+
+/* Departure points of the semi-Lagrangian step, Eq. 2.4 of Sec. 2,
+ *   x_D = x - dt [ W(x_D) - W_A(x) ],
+ * solved by fixed-point iteration for every arrival point of Grid [0]
+ * (theta_j = (j + 1/2) pi / n_lat, phi_k = 2 pi k / n_lon), with W(x_D)
+ * carried to the arrival point's frame by the rotation Q of Sec. 2 and the
+ * displacement taken along the great circle through the arrival point:
+ *   D_0 = A;  V_k = Q(A, D_k) W(D_k) - W_A(A);
+ *   D_{k+1} = the point at angle |V_k| dt / a from A in the direction -V_k.
+ * W(D) is tensor-product quintic Lagrange interpolation of the samples of W
+ * (the degree the paper uses for this bracket), stencil rows beyond a pole
+ * taken from the doubled sphere with the wind components' change of sign.
+ *   w         : device, n_members x 2 x n_lat x n_lon (eastward, then
+ *               northward component; phi fastest), dtype reals: the bracket's
+ *               departure term, (v + Omega x r - g dt grad h^(+) / 4) in Eq. 2.4.
+ *   w_arrival : same layout, the arrival term (Omega x r + g dt grad h^0 / 4),
+ *               or NULL for zero.
+ *   dt_over_a : time step divided by the sphere's radius, in the units that
+ *               make |W| dt_over_a an angle in radians.
+ *   iterations: 1..64 evaluations of W (the first one at the grid point).
+ *   lon_d, colat_d: device outputs, n_members x n_lat x n_lon doubles, in grid
+ *               order; longitude in [0, 2 pi), colatitude in [0, pi] up to
+ *               rounding.  FP32 runs the iteration in single precision
+ *               relative to the arrival point (error about 1e-6 of the
+ *               displacement); positions are always written in FP64.
+ * n_lon even >= 6, n_lat >= 3; stream is a cudaStream_t (NULL = legacy
+ * default).  Asynchronous; returns DFSNUFFT_ERR_INVALID_ARG or
+ * DFSNUFFT_ERR_CUDA (launch failure) without touching any plan. */
+int dfsnufft_departure_points(int n_lon, int n_lat, int n_members, int dtype, int iterations,
+                              double dt_over_a, const void *w, const void *w_arrival,
+                              double *lon_d, double *colat_d, void *stream);
+
+/* Vector values at departure points expressed in the arrival points' frame
+ * (Sec. 2): (u_a, v_a) = Q (u_d, v_d), Q = [[p, q], [-q, p]] with
+ *   p = (sin th_A sin th_D + (1 + cos th_A cos th_D) cos(ph_A - ph_D)) / (1 + cos eta),
+ *   q = (cos th_A + cos th_D) sin(ph_A - ph_D) / (1 + cos eta),
+ * for the arrival points of Grid [0] in grid order and the departure points
+ * (lon_d, colat_d) (device doubles, n_members x n_lat x n_lon).  u_d, v_d, u_a,
+ * v_a: device dtype reals, point p of member m at [m * stride + p] (stride >=
+ * n_lat n_lon; with the values of dfsnufft_execute, stride = n_fields times the
+ * points and u_d, v_d the two wind fields).  In place (u_a = u_d, v_a = v_d) is
+ * allowed.  Asynchronous on stream; errors as dfsnufft_departure_points. */
+int dfsnufft_rotate_to_arrival(int n_lon, int n_lat, int n_members, int dtype,
+                               const double *lon_d, const double *colat_d, const void *u_d,
+                               const void *v_d, int64_t stride, void *u_a, void *v_a,
+                               void *stream);
+
 /* Host-buffer variants: the same operations with host pointers.  The data are
  * copied to plan-owned device buffers on the plan's stream (pinned host memory
  * makes the copies asynchronous); dfsnufft_execute_host waits for the stream

@@ -43,6 +43,7 @@ EXPORTS = (
     "dfsnufft_choose_params_opts", "dfsnufft_plan_create_opts", "dfsnufft_ensemble_create_opts",
     "dfsnufft_server_create_opts", "dfsnufft_autotune", "dfsnufft_selftest_wait_timeout",
     "dfsnufft_execute_pr", "dfsnufft_grid_to_coeffs", "dfsnufft_interpolate_grid",
+    "dfsnufft_departure_points", "dfsnufft_rotate_to_arrival",
 )
 REAL_FIELDS = 1
 KEEP_ORDER = 2
@@ -192,6 +193,9 @@ def lib():
         L.dfsnufft_selftest_wait_timeout.argtypes = [ctypes.c_longlong, ctypes.POINTER(i32),
                                                      ctypes.POINTER(f64)]
         L.dfsnufft_execute_noalloc.argtypes = [i32, i32, f64, i32, i32, i64, vp, vp, vp, vp, vp]
+        L.dfsnufft_departure_points.argtypes = [i32, i32, i32, i32, i32, f64, vp, vp, vp, vp, vp]
+        L.dfsnufft_rotate_to_arrival.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, i64, vp, vp,
+                                                 vp]
         for name in EXPORTS:
             if name not in ("dfsnufft_strerror", "dfsnufft_plan_last_error", "dfsnufft_es_kernel",
                             "dfsnufft_version"):
@@ -363,6 +367,77 @@ def dfsnufft_execute_noalloc(n_lon, n_lat, tol, dtype, n_fields, n_points, lon_p
                                           ctypes.c_void_p(colat_ptr), ctypes.c_void_p(coeffs_ptr),
                                           ctypes.c_void_p(values_ptr),
                                           ctypes.c_void_p(int(stream or 0))))
+
+
+def _stream_ptr(tensor, stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(tensor.device)
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _real_code(tensor) -> int:
+    import torch
+    if tensor.dtype == torch.float64:
+        return F64
+    if tensor.dtype == torch.float32:
+        return F32
+    raise TypeError("expected a float32 or float64 tensor, got %s" % tensor.dtype)
+
+
+def departure_points(w, dt_over_a, iterations, w_arrival=None, stream=None, lon_out=None,
+                     colat_out=None):
+    """Departure points (lon, colat) of Eq. 2.4 for every Grid [0] arrival point
+    (dfsnufft_departure_points).  ``w``, ``w_arrival``: CUDA tensors of shape
+    ([members,] 2, n_lat, n_lon), eastward then northward component; returns two
+    float64 tensors of shape ([members,] n_lat * n_lon) (or fills the given ones)."""
+    import torch
+    if not w.is_cuda or not w.is_contiguous() or w.dim() not in (3, 4) or w.shape[-3] != 2:
+        raise ValueError("w must be a contiguous CUDA tensor of shape ([members,] 2, n_lat, n_lon)")
+    if w_arrival is not None and (w_arrival.shape != w.shape or w_arrival.dtype != w.dtype
+                                  or not w_arrival.is_contiguous()):
+        raise ValueError("w_arrival must match w in shape, dtype and layout")
+    members = w.shape[0] if w.dim() == 4 else 1
+    n_lat, n_lon = int(w.shape[-2]), int(w.shape[-1])
+    shape = (members, n_lat * n_lon) if w.dim() == 4 else (n_lat * n_lon,)
+    lon = torch.empty(shape, dtype=torch.float64, device=w.device) if lon_out is None else lon_out
+    colat = (torch.empty(shape, dtype=torch.float64, device=w.device) if colat_out is None
+             else colat_out)
+    for t in (lon, colat):
+        if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != members * n_lat * n_lon:
+            raise ValueError("lon_out / colat_out: contiguous float64, one value per arrival point")
+    _check(lib().dfsnufft_departure_points(
+        n_lon, n_lat, members, _real_code(w), int(iterations), float(dt_over_a),
+        ctypes.c_void_p(w.data_ptr()),
+        ctypes.c_void_p(w_arrival.data_ptr() if w_arrival is not None else 0),
+        ctypes.c_void_p(lon.data_ptr()), ctypes.c_void_p(colat.data_ptr()),
+        _stream_ptr(w, stream)))
+    return lon, colat
+
+
+def rotate_to_arrival(n_lon, n_lat, lon_d, colat_d, u_d, v_d, stride=None, members=1,
+                      u_a=None, v_a=None, stream=None):
+    """(u, v) at the departure points in the arrival points' frame
+    (dfsnufft_rotate_to_arrival); u_d, v_d may be views into one values tensor,
+    member m's point p at element m * stride + p.  Returns (u_a, v_a); pass
+    u_a = u_d, v_a = v_d to rotate in place."""
+    import torch
+    if stride is None:
+        stride = n_lon * n_lat
+    if u_a is None:
+        u_a = torch.empty_like(u_d)
+    if v_a is None:
+        v_a = torch.empty_like(v_d)
+    code = _real_code(u_d)
+    for t in (v_d, u_a, v_a):
+        if t.dtype != u_d.dtype or not t.is_cuda:
+            raise ValueError("u_d, v_d, u_a, v_a must be CUDA tensors of one dtype")
+    _check(lib().dfsnufft_rotate_to_arrival(
+        int(n_lon), int(n_lat), int(members), code, ctypes.c_void_p(lon_d.data_ptr()),
+        ctypes.c_void_p(colat_d.data_ptr()), ctypes.c_void_p(u_d.data_ptr()),
+        ctypes.c_void_p(v_d.data_ptr()), int(stride), ctypes.c_void_p(u_a.data_ptr()),
+        ctypes.c_void_p(v_a.data_ptr()), _stream_ptr(u_d, stream)))
+    return u_a, v_a
 
 
 def dfsnufft_plan_get_params(h) -> dict:

@@ -275,6 +275,30 @@ def zonal_flow_values(lon, colat, alpha: float, u0: float = U0_12DAY,
     return h, u, v
 
 
+def zonal_flow_settls_terms(lon, colat, alpha: float, dt: float, u0: float = U0_12DAY,
+                            radius: float = EARTH_RADIUS, omega: float = EARTH_OMEGA,
+                            gravity: float = GRAVITY):
+    """East/north components of the two terms of the departure-point equation
+    (Sec. 2, Eq. 2.4) for the steady tilted zonal flow (so h^(+) = h^0):
+      departure term  W   = v + Omega x r - g dt grad h / 4,
+      arrival term    W_A = Omega x r + g dt grad h / 4,
+    with Omega x r = Omega a sin(theta) (east) and, for h = h0 - K s^2,
+    grad h = -(2 K s / a) (k . e_east, k . e_north)."""
+    ca, sa = math.cos(alpha), math.sin(alpha)
+    K = zonal_flow_constants(u0, radius, omega, gravity)
+    _, u, v = zonal_flow_values(lon, colat, alpha, u0)
+    s = ca * np.cos(colat) - sa * np.sin(colat) * np.cos(lon)
+    k_east = sa * np.sin(lon)
+    k_north = sa * np.cos(colat) * np.cos(lon) + ca * np.sin(colat)
+    gh_e = -(2.0 * K * s / radius) * k_east
+    gh_n = -(2.0 * K * s / radius) * k_north
+    rot = omega * radius * np.sin(colat)
+    c = gravity * dt / 4.0
+    w = np.stack([u + rot - c * gh_e, v - c * gh_n])
+    wa = np.stack([rot + c * gh_e, c * gh_n])
+    return w, wa
+
+
 # --------------------------------------------------------------------------- workloads
 
 class Workload:

@@ -1,6 +1,7 @@
 """Host-side checks of the C-ABI library (no GPU): it loads, exports every symbol
 the header declares, and its host logic (parameters, kernel, deconvolution
 factors, status strings) is right."""
+import ctypes
 import math
 import os
 import re
@@ -182,3 +183,25 @@ def test_horner_kernel_fit(lib, w):
         exact = np.array([nufft.dfsnufft_es_kernel((a - c0) - t, w, beta) for t in ts])
         worst = max(worst, float(np.max(np.abs(acc - exact))))
     assert worst < max(8 * math.exp(-beta), 2e-14), worst
+
+
+def test_departure_and_rotation_argument_errors(lib):
+    """Invalid sizes, iteration counts, dtypes, strides and null pointers are
+    rejected before anything reaches a GPU (non-null dummies stand for device
+    buffers; no kernel is launched)."""
+    dummy = ctypes.c_void_p(16)
+    bad_dep = [(7, 4, 1, 0, 3, 1e-4), (4, 4, 1, 0, 3, 1e-4), (8, 2, 1, 0, 3, 1e-4),
+               (8, 4, 0, 0, 3, 1e-4), (8, 4, 1, 2, 3, 1e-4), (8, 4, 1, 0, 0, 1e-4),
+               (8, 4, 1, 0, 65, 1e-4), (8, 4, 1, 0, 3, float("nan"))]
+    for n_lon, n_lat, members, dtype, iters, dta in bad_dep:
+        rc = lib.dfsnufft_departure_points(n_lon, n_lat, members, dtype, iters, dta, dummy,
+                                           None, dummy, dummy, None)
+        assert rc == nufft.ERR_INVALID_ARG, (n_lon, n_lat, members, dtype, iters, dta)
+    assert lib.dfsnufft_departure_points(8, 4, 1, 0, 3, 1e-4, None, None, dummy, dummy,
+                                         None) == nufft.ERR_INVALID_ARG
+    assert lib.dfsnufft_rotate_to_arrival(8, 4, 1, 0, dummy, dummy, dummy, dummy, 31, dummy,
+                                          dummy, None) == nufft.ERR_INVALID_ARG
+    assert lib.dfsnufft_rotate_to_arrival(8, 4, 1, 0, dummy, None, dummy, dummy, 32, dummy,
+                                          dummy, None) == nufft.ERR_INVALID_ARG
+    assert lib.dfsnufft_rotate_to_arrival(9, 4, 1, 1, dummy, dummy, dummy, dummy, 36, dummy,
+                                          dummy, None) == nufft.ERR_INVALID_ARG
