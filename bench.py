@@ -300,6 +300,7 @@ def run_ours(args):
     if sl is not None:
         w_t = torch.from_numpy(sl["w"]).to(rd).to(dev).contiguous()
         wa_t = torch.from_numpy(sl["wa"]).to(rd).to(dev).contiguous()
+        pq_t = torch.empty((2, P), dtype=rd, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -312,7 +313,7 @@ def run_ours(args):
             if evs:
                 evs[0].record(stream)
             nufft.departure_points(w_t, sl["dt_over_a"], sl["iterations"], wa_t, stream,
-                                   lon_out=lon, colat_out=colat)
+                                   lon_out=lon, colat_out=colat, pq_out=pq_t)
             if evs:
                 evs[1].record(stream)
         plan.set_points(lon, colat)
@@ -325,8 +326,8 @@ def run_ours(args):
         if sl is not None:        # the wind to the arrival frame, in place
             if evs:
                 evs[2].record(stream)
-            nufft.rotate_to_arrival(wl.n_lon, wl.n_lat, lon, colat, out[1], out[2],
-                                    u_a=out[1], v_a=out[2], stream=stream)
+            nufft.rotate_to_arrival(wl.n_lon, wl.n_lat, None, None, out[1], out[2],
+                                    u_a=out[1], v_a=out[2], stream=stream, pq=pq_t)
             if evs:
                 evs[3].record(stream)
 
@@ -491,7 +492,7 @@ def run_ours(args):
         rs = 4 if wl.dtype == "f32" else 8
         dep_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in sl_ev]))
         rot_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in sl_ev]))
-        dep_b, rot_b = (4 * rs + 16) * P, (16 + 4 * rs) * P
+        dep_b, rot_b = (6 * rs + 16) * P, 6 * rs * P     # + p, q written / read
         stages_out["departure_points"] = {"ms": dep_ms, "bytes": dep_b,
                                           "gbs": dep_b / (dep_ms * 1e-3) / 1e9,
                                           "iterations": sl["iterations"]}

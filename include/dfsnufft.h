@@ -332,27 +332,34 @@ int dfsnufft_interpolate_grid(dfsnufft_plan plan, const void *samples, const int
  *               rounding.  FP32 runs the iteration in single precision
  *               relative to the arrival point (error about 1e-6 of the
  *               displacement); positions are always written in FP64.
+ *   pq        : optional device output (NULL to skip), n_members x 2 x
+ *               n_lat x n_lon dtype reals: p, then q, of the rotation Q from
+ *               each final departure point to its arrival point, for
+ *               dfsnufft_rotate_to_arrival.
  * n_lon even >= 6, n_lat >= 3; stream is a cudaStream_t (NULL = legacy
  * default).  Asynchronous; returns DFSNUFFT_ERR_INVALID_ARG or
  * DFSNUFFT_ERR_CUDA (launch failure) without touching any plan. */
 int dfsnufft_departure_points(int n_lon, int n_lat, int n_members, int dtype, int iterations,
                               double dt_over_a, const void *w, const void *w_arrival,
-                              double *lon_d, double *colat_d, void *stream);
+                              double *lon_d, double *colat_d, void *pq, void *stream);
 
 /* Vector values at departure points expressed in the arrival points' frame
  * (Sec. 2): (u_a, v_a) = Q (u_d, v_d), Q = [[p, q], [-q, p]] with
  *   p = (sin th_A sin th_D + (1 + cos th_A cos th_D) cos(ph_A - ph_D)) / (1 + cos eta),
  *   q = (cos th_A + cos th_D) sin(ph_A - ph_D) / (1 + cos eta),
  * for the arrival points of Grid [0] in grid order and the departure points
- * (lon_d, colat_d) (device doubles, n_members x n_lat x n_lon).  u_d, v_d, u_a,
+ * (lon_d, colat_d) (device doubles, n_members x n_lat x n_lon), or read from pq
+ * as written by dfsnufft_departure_points (then lon_d and colat_d may be NULL;
+ * no trigonometry and no FP64 arithmetic, which on this GPU runs at 1/64 of the
+ * FP32 rate).  u_d, v_d, u_a,
  * v_a: device dtype reals, point p of member m at [m * stride + p] (stride >=
  * n_lat n_lon; with the values of dfsnufft_execute, stride = n_fields times the
  * points and u_d, v_d the two wind fields).  In place (u_a = u_d, v_a = v_d) is
  * allowed.  Asynchronous on stream; errors as dfsnufft_departure_points. */
 int dfsnufft_rotate_to_arrival(int n_lon, int n_lat, int n_members, int dtype,
-                               const double *lon_d, const double *colat_d, const void *u_d,
-                               const void *v_d, int64_t stride, void *u_a, void *v_a,
-                               void *stream);
+                               const double *lon_d, const double *colat_d, const void *pq,
+                               const void *u_d, const void *v_d, int64_t stride, void *u_a,
+                               void *v_a, void *stream);
 
 /* Host-buffer variants: the same operations with host pointers.  The data are
  * copied to plan-owned device buffers on the plan's stream (pinned host memory

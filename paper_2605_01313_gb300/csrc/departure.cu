@@ -27,11 +27,13 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 
-struct DepArgs {
+template <typename R> struct DepArgs {
     int n_lon, n_lat, members, iterations;
     int P;                    // n_lat * n_lon
-    double dt_over_a;
     double h_phi, h_th;       // 2 pi / n_lon, pi / n_lat
+    R dta;                    // dt / a
+    R to_x, to_y;             // n_lon / (2 pi), n_lat / pi: radians to grid cells
+    R h_th_r;                 // pi / n_lat
 };
 
 template <typename R> struct Geo {
@@ -100,13 +102,53 @@ __device__ __forceinline__ void lagrange5(R t, R *L) {
     L[5] = (p012 * a3 * a4) * (R)(1.0 / 120.0);
 }
 
-// grid ceil(members * P / 256); block 256.  w, wa: members x 2 x n_lat x n_lon
-// (east, north); wa may be null.
+// Q = [[p, q], [-q, p]] of A and the departure point g in A's turned frame:
+// cos(phi_D - phi_A) = X / rho, sin(...) = Y / rho, cos th_D = Z, sin th_D = rho.
 template <typename R>
-__global__ void __launch_bounds__(256) k_departure(DepArgs a, const R *__restrict__ w,
+__device__ __forceinline__ void rotation_pq(R sA, R cA, const Geo<R> &g, R *p, R *q) {
+    R cx = 1, sx = 0;
+    if (g.rho > (R)0) {
+        cx = g.X / g.rho;
+        sx = g.Y / g.rho;
+    }
+    const R den = (R)1 + g.cs;                         // 1 + cos eta
+    *p = (sA * g.rho + ((R)1 + cA * g.Z) * cx) / den;
+    *q = -(cA + g.Z) * sx / den;
+}
+
+// One row of the quintic stencil: sum_b L[b] f(row, c0 + b) for both components,
+// columns taken modulo n (c0 in [0, n)); the common case reads six consecutive
+// columns.
+template <typename R>
+__device__ __forceinline__ void stencil_row(const R *__restrict__ ru, const R *__restrict__ rv,
+                                            int c0, int n, const R *L, R &tu, R &tv) {
+    tu = 0;
+    tv = 0;
+    if (c0 <= n - 6) {
+#pragma unroll
+        for (int b = 0; b < 6; ++b) {
+            tu = fma(L[b], __ldg(ru + c0 + b), tu);
+            tv = fma(L[b], __ldg(rv + c0 + b), tv);
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < 6; ++b) {
+            const int c = c0 + b < n ? c0 + b : c0 + b - n;
+            tu = fma(L[b], __ldg(ru + c), tu);
+            tv = fma(L[b], __ldg(rv + c), tv);
+        }
+    }
+}
+
+// grid ceil(members * P / 256); block 256.  w, wa: members x 2 x n_lat x n_lon
+// (east, north); wa may be null; pq (optional): members x 2 x P, p then q of
+// the final departure point.
+template <typename R>
+__global__ void __launch_bounds__(256) k_departure(DepArgs<R> a, const R *__restrict__ w,
                                                    const R *__restrict__ wa,
                                                    double *__restrict__ lon_d,
-                                                   double *__restrict__ colat_d) {
+                                                   double *__restrict__ colat_d,
+                                                   R *__restrict__ pq) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)a.members * a.P) return;
     const int m = (int)(gid / a.P);
@@ -120,13 +162,15 @@ __global__ void __launch_bounds__(256) k_departure(DepArgs a, const R *__restric
         ae = wa[(size_t)m * 2 * a.P + pi];
         an = wa[(size_t)m * 2 * a.P + a.P + pi];
     }
-    const double thA = ((double)j + 0.5) * a.h_th;
+    // sin and cos of theta_A in R, from the row reflected into the northern
+    // half so that the angle carries a relative rounding only
+    const bool south = 2 * j > nl - 1;
     R sA, cA;
-    colat_sc(thA, &sA, &cA);
-    const R dta = (R)a.dt_over_a;
+    sc(((R)(south ? nl - 1 - j : j) + (R)0.5) * a.h_th_r, &sA, &cA);
+    if (south) cA = -cA;
+    const R dta = a.dta, to_x = a.to_x, to_y = a.to_y;
     // D_0 = A: the bracket is the grid value and Q is the identity
     Geo<R> g = move_back(sA, cA, dta * (wu[pi] - ae), dta * (wv[pi] - an));
-    const R to_x = (R)((double)n / (2.0 * kPi)), to_y = (R)((double)nl / kPi);
     for (int it = 1; it < a.iterations; ++it) {
         // position of D in grid-index units relative to A (clamped only to keep
         // the stencil inside the doubled grid; NaN falls to a bound)
@@ -147,40 +191,32 @@ __global__ void __launch_bounds__(256) k_departure(DepArgs a, const R *__restric
             const int r = r0 - 2 + ra;                 // in [-3, nl + 2]
             const bool beyond = r < 0 || r >= nl;
             const int rr = r < 0 ? -1 - r : (r >= nl ? 2 * nl - 1 - r : r);
-            const int shift = beyond ? n / 2 : 0;
-            const R *ru = wu + (size_t)rr * n;
-            const R *rv = wv + (size_t)rr * n;
-            R tu = 0, tv = 0;
-#pragma unroll
-            for (int b = 0; b < 6; ++b) {
-                int c = i0 - 2 + b + shift;            // in [-2, 3n/2 + 3)
-                if (c < 0) c += n;
-                else if (c >= n) c -= n;
-                tu = fma(Lx[b], __ldg(ru + c), tu);
-                tv = fma(Lx[b], __ldg(rv + c), tv);
-            }
+            int c0 = i0 - 2 + (beyond ? n / 2 : 0);    // in [-2, 3n/2 - 2)
+            if (c0 < 0) c0 += n;
+            else if (c0 >= n) c0 -= n;
+            R tu, tv;
+            stencil_row(wu + (size_t)rr * n, wv + (size_t)rr * n, c0, n, Lx, tu, tv);
             const R wy = beyond ? -Ly[ra] : Ly[ra];
             su = fma(wy, tu, su);
             sv = fma(wy, tv, sv);
         }
-        // Q(A, D) from the turned frame
-        R cx = 1, sx = 0;
-        if (g.rho > (R)0) {
-            cx = g.X / g.rho;
-            sx = g.Y / g.rho;
-        }
-        const R den = (R)1 + g.cs;
-        const R p = (sA * g.rho + ((R)1 + cA * g.Z) * cx) / den;
-        const R q = -(cA + g.Z) * sx / den;
+        R p, q;
+        rotation_pq(sA, cA, g, &p, &q);
         const R ve = p * su + q * sv - ae;
         const R vn = -q * su + p * sv - an;
         g = move_back(sA, cA, dta * ve, dta * vn);
+    }
+    if (pq) {
+        R p, q;
+        rotation_pq(sA, cA, g, &p, &q);
+        pq[(size_t)m * 2 * a.P + pi] = p;
+        pq[(size_t)m * 2 * a.P + a.P + pi] = q;
     }
     double lon = (double)k * a.h_phi + (double)g.dphi;
     if (lon < 0.0) lon += 2.0 * kPi;
     else if (lon >= 2.0 * kPi) lon -= 2.0 * kPi;
     lon_d[gid] = lon;
-    colat_d[gid] = thA + (double)g.dth;
+    colat_d[gid] = ((double)j + 0.5) * a.h_th + (double)g.dth;
 }
 
 struct RotArgs {
@@ -189,15 +225,26 @@ struct RotArgs {
     double h_phi, h_th;
 };
 
-// grid ceil(members * P / 256); block 256.  u_d, v_d may alias u_a, v_a.
+// grid ceil(members * P / 256); block 256.  u_d, v_d may alias u_a, v_a.  With
+// pq (members x 2 x P, from k_departure) Q is read; otherwise it is computed
+// from the departure points.
 template <typename R>
 __global__ void __launch_bounds__(256) k_rotate(RotArgs a, const double *__restrict__ lon_d,
                                                 const double *__restrict__ colat_d,
-                                                const R *u_d, const R *v_d, R *u_a, R *v_a) {
+                                                const R *__restrict__ pq, const R *u_d,
+                                                const R *v_d, R *u_a, R *v_a) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)a.members * a.P) return;
     const int m = (int)(gid / a.P);
     const int pi = (int)(gid - (long long)m * a.P);
+    const size_t o = (size_t)m * a.stride + pi;
+    if (pq) {
+        const R p = pq[(size_t)m * 2 * a.P + pi], q = pq[(size_t)m * 2 * a.P + a.P + pi];
+        const R u = u_d[o], v = v_d[o];
+        u_a[o] = p * u + q * v;
+        v_a[o] = -q * u + p * v;
+        return;
+    }
     const int j = pi / a.n_lon, k = pi - j * a.n_lon;
     double dl = (double)k * a.h_phi - lon_d[gid];            // phi_A - phi_D
     dl -= 2.0 * kPi * rint(dl * (0.5 / kPi));
@@ -209,7 +256,6 @@ __global__ void __launch_bounds__(256) k_rotate(RotArgs a, const double *__restr
     const R den = (R)1 + sA * sD * cl + cA * cD;               // 1 + cos eta
     const R p = (sA * sD + ((R)1 + cA * cD) * cl) / den;
     const R q = (cA + cD) * sl / den;
-    const size_t o = (size_t)m * a.stride + pi;
     const R u = u_d[o], v = v_d[o];
     u_a[o] = p * u + q * v;
     v_a[o] = -q * u + p * v;
@@ -220,44 +266,56 @@ bool grid_ok(int n_lon, int n_lat, int members) {
     return (long long)n_lon * n_lat * members <= 0x7fffffffLL;
 }
 
-}  // namespace
 
-extern "C" int dfsnufft_departure_points(int n_lon, int n_lat, int n_members, int dtype,
-                                         int iterations, double dt_over_a, const void *w,
-                                         const void *w_arrival, double *lon_d, double *colat_d,
-                                         void *stream) {
-    if (!grid_ok(n_lon, n_lat, n_members) || iterations < 1 || iterations > 64 || !w ||
-        !lon_d || !colat_d || !(dt_over_a == dt_over_a) || dt_over_a > 1e300 ||
-        dt_over_a < -1e300)
-        return DFSNUFFT_ERR_INVALID_ARG;
-    if (dtype != DFSNUFFT_F64 && dtype != DFSNUFFT_F32) return DFSNUFFT_ERR_INVALID_ARG;
-    DepArgs a;
+template <typename R>
+cudaError_t launch_departure(int n_lon, int n_lat, int n_members, int iterations,
+                             double dt_over_a, const void *w, const void *w_arrival,
+                             double *lon_d, double *colat_d, void *pq, cudaStream_t st) {
+    DepArgs<R> a;
     a.n_lon = n_lon;
     a.n_lat = n_lat;
     a.members = n_members;
     a.iterations = iterations;
     a.P = n_lon * n_lat;
-    a.dt_over_a = dt_over_a;
     a.h_phi = 2.0 * kPi / n_lon;
     a.h_th = kPi / n_lat;
+    a.dta = (R)dt_over_a;
+    a.to_x = (R)(n_lon / (2.0 * kPi));
+    a.to_y = (R)(n_lat / kPi);
+    a.h_th_r = (R)(kPi / n_lat);
     const long long total = (long long)n_members * a.P;
-    const unsigned blocks = (unsigned)((total + 255) / 256);
+    k_departure<R><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+        a, (const R *)w, (const R *)w_arrival, lon_d, colat_d, (R *)pq);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" int dfsnufft_departure_points(int n_lon, int n_lat, int n_members, int dtype,
+                                         int iterations, double dt_over_a, const void *w,
+                                         const void *w_arrival, double *lon_d, double *colat_d,
+                                         void *pq, void *stream) {
+    if (!grid_ok(n_lon, n_lat, n_members) || iterations < 1 || iterations > 64 || !w ||
+        !lon_d || !colat_d || !(dt_over_a == dt_over_a) || dt_over_a > 1e300 ||
+        dt_over_a < -1e300)
+        return DFSNUFFT_ERR_INVALID_ARG;
+    if (dtype != DFSNUFFT_F64 && dtype != DFSNUFFT_F32) return DFSNUFFT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (dtype == DFSNUFFT_F64)
-        k_departure<double><<<blocks, 256, 0, st>>>(a, (const double *)w,
-                                                    (const double *)w_arrival, lon_d, colat_d);
-    else
-        k_departure<float><<<blocks, 256, 0, st>>>(a, (const float *)w, (const float *)w_arrival,
-                                                   lon_d, colat_d);
-    return cudaGetLastError() == cudaSuccess ? DFSNUFFT_OK : DFSNUFFT_ERR_CUDA;
+    const cudaError_t e =
+        dtype == DFSNUFFT_F64
+            ? launch_departure<double>(n_lon, n_lat, n_members, iterations, dt_over_a, w,
+                                       w_arrival, lon_d, colat_d, pq, st)
+            : launch_departure<float>(n_lon, n_lat, n_members, iterations, dt_over_a, w,
+                                      w_arrival, lon_d, colat_d, pq, st);
+    return e == cudaSuccess ? DFSNUFFT_OK : DFSNUFFT_ERR_CUDA;
 }
 
 extern "C" int dfsnufft_rotate_to_arrival(int n_lon, int n_lat, int n_members, int dtype,
                                           const double *lon_d, const double *colat_d,
-                                          const void *u_d, const void *v_d, int64_t stride,
-                                          void *u_a, void *v_a, void *stream) {
-    if (!grid_ok(n_lon, n_lat, n_members) || !lon_d || !colat_d || !u_d || !v_d || !u_a ||
-        !v_a || stride < (int64_t)n_lon * n_lat)
+                                          const void *pq, const void *u_d, const void *v_d,
+                                          int64_t stride, void *u_a, void *v_a, void *stream) {
+    if (!grid_ok(n_lon, n_lat, n_members) || (!pq && (!lon_d || !colat_d)) || !u_d || !v_d ||
+        !u_a || !v_a || stride < (int64_t)n_lon * n_lat)
         return DFSNUFFT_ERR_INVALID_ARG;
     if (dtype != DFSNUFFT_F64 && dtype != DFSNUFFT_F32) return DFSNUFFT_ERR_INVALID_ARG;
     RotArgs a;
@@ -272,11 +330,12 @@ extern "C" int dfsnufft_rotate_to_arrival(int n_lon, int n_lat, int n_members, i
     const unsigned blocks = (unsigned)((total + 255) / 256);
     cudaStream_t st = (cudaStream_t)stream;
     if (dtype == DFSNUFFT_F64)
-        k_rotate<double><<<blocks, 256, 0, st>>>(a, lon_d, colat_d, (const double *)u_d,
-                                                 (const double *)v_d, (double *)u_a,
-                                                 (double *)v_a);
+        k_rotate<double><<<blocks, 256, 0, st>>>(a, lon_d, colat_d, (const double *)pq,
+                                                 (const double *)u_d, (const double *)v_d,
+                                                 (double *)u_a, (double *)v_a);
     else
-        k_rotate<float><<<blocks, 256, 0, st>>>(a, lon_d, colat_d, (const float *)u_d,
-                                                (const float *)v_d, (float *)u_a, (float *)v_a);
+        k_rotate<float><<<blocks, 256, 0, st>>>(a, lon_d, colat_d, (const float *)pq,
+                                                (const float *)u_d, (const float *)v_d,
+                                                (float *)u_a, (float *)v_a);
     return cudaGetLastError() == cudaSuccess ? DFSNUFFT_OK : DFSNUFFT_ERR_CUDA;
 }

@@ -193,9 +193,10 @@ def lib():
         L.dfsnufft_selftest_wait_timeout.argtypes = [ctypes.c_longlong, ctypes.POINTER(i32),
                                                      ctypes.POINTER(f64)]
         L.dfsnufft_execute_noalloc.argtypes = [i32, i32, f64, i32, i32, i64, vp, vp, vp, vp, vp]
-        L.dfsnufft_departure_points.argtypes = [i32, i32, i32, i32, i32, f64, vp, vp, vp, vp, vp]
-        L.dfsnufft_rotate_to_arrival.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, i64, vp, vp,
-                                                 vp]
+        L.dfsnufft_departure_points.argtypes = [i32, i32, i32, i32, i32, f64, vp, vp, vp, vp, vp,
+                                                vp]
+        L.dfsnufft_rotate_to_arrival.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, vp, i64, vp,
+                                                 vp, vp]
         for name in EXPORTS:
             if name not in ("dfsnufft_strerror", "dfsnufft_plan_last_error", "dfsnufft_es_kernel",
                             "dfsnufft_version"):
@@ -386,11 +387,13 @@ def _real_code(tensor) -> int:
 
 
 def departure_points(w, dt_over_a, iterations, w_arrival=None, stream=None, lon_out=None,
-                     colat_out=None):
+                     colat_out=None, pq_out=None):
     """Departure points (lon, colat) of Eq. 2.4 for every Grid [0] arrival point
     (dfsnufft_departure_points).  ``w``, ``w_arrival``: CUDA tensors of shape
     ([members,] 2, n_lat, n_lon), eastward then northward component; returns two
-    float64 tensors of shape ([members,] n_lat * n_lon) (or fills the given ones)."""
+    float64 tensors of shape ([members,] n_lat * n_lon) (or fills the given ones).
+    ``pq_out`` (optional, w's dtype, ([members,] 2, n_lat * n_lon) elements)
+    receives p and q of the rotation to the arrival frame."""
     import torch
     if not w.is_cuda or not w.is_contiguous() or w.dim() not in (3, 4) or w.shape[-3] != 2:
         raise ValueError("w must be a contiguous CUDA tensor of shape ([members,] 2, n_lat, n_lon)")
@@ -406,20 +409,26 @@ def departure_points(w, dt_over_a, iterations, w_arrival=None, stream=None, lon_
     for t in (lon, colat):
         if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != members * n_lat * n_lon:
             raise ValueError("lon_out / colat_out: contiguous float64, one value per arrival point")
+    if pq_out is not None and (pq_out.dtype != w.dtype or not pq_out.is_contiguous()
+                               or pq_out.numel() != 2 * members * n_lat * n_lon):
+        raise ValueError("pq_out: contiguous, w's dtype, two values per arrival point")
     _check(lib().dfsnufft_departure_points(
         n_lon, n_lat, members, _real_code(w), int(iterations), float(dt_over_a),
         ctypes.c_void_p(w.data_ptr()),
         ctypes.c_void_p(w_arrival.data_ptr() if w_arrival is not None else 0),
         ctypes.c_void_p(lon.data_ptr()), ctypes.c_void_p(colat.data_ptr()),
+        ctypes.c_void_p(pq_out.data_ptr() if pq_out is not None else 0),
         _stream_ptr(w, stream)))
     return lon, colat
 
 
 def rotate_to_arrival(n_lon, n_lat, lon_d, colat_d, u_d, v_d, stride=None, members=1,
-                      u_a=None, v_a=None, stream=None):
+                      u_a=None, v_a=None, stream=None, pq=None):
     """(u, v) at the departure points in the arrival points' frame
     (dfsnufft_rotate_to_arrival); u_d, v_d may be views into one values tensor,
-    member m's point p at element m * stride + p.  Returns (u_a, v_a); pass
+    member m's point p at element m * stride + p.  With ``pq`` from
+    :func:`departure_points` the rotation is read instead of computed from
+    (lon_d, colat_d), which may then be None.  Returns (u_a, v_a); pass
     u_a = u_d, v_a = v_d to rotate in place."""
     import torch
     if stride is None:
@@ -433,8 +442,10 @@ def rotate_to_arrival(n_lon, n_lat, lon_d, colat_d, u_d, v_d, stride=None, membe
         if t.dtype != u_d.dtype or not t.is_cuda:
             raise ValueError("u_d, v_d, u_a, v_a must be CUDA tensors of one dtype")
     _check(lib().dfsnufft_rotate_to_arrival(
-        int(n_lon), int(n_lat), int(members), code, ctypes.c_void_p(lon_d.data_ptr()),
-        ctypes.c_void_p(colat_d.data_ptr()), ctypes.c_void_p(u_d.data_ptr()),
+        int(n_lon), int(n_lat), int(members), code,
+        ctypes.c_void_p(lon_d.data_ptr() if lon_d is not None else 0),
+        ctypes.c_void_p(colat_d.data_ptr() if colat_d is not None else 0),
+        ctypes.c_void_p(pq.data_ptr() if pq is not None else 0), ctypes.c_void_p(u_d.data_ptr()),
         ctypes.c_void_p(v_d.data_ptr()), int(stride), ctypes.c_void_p(u_a.data_ptr()),
         ctypes.c_void_p(v_a.data_ptr()), _stream_ptr(u_d, stream)))
     return u_a, v_a

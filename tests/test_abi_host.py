@@ -195,13 +195,16 @@ def test_departure_and_rotation_argument_errors(lib):
                (8, 4, 1, 0, 65, 1e-4), (8, 4, 1, 0, 3, float("nan"))]
     for n_lon, n_lat, members, dtype, iters, dta in bad_dep:
         rc = lib.dfsnufft_departure_points(n_lon, n_lat, members, dtype, iters, dta, dummy,
-                                           None, dummy, dummy, None)
+                                           None, dummy, dummy, None, None)
         assert rc == nufft.ERR_INVALID_ARG, (n_lon, n_lat, members, dtype, iters, dta)
     assert lib.dfsnufft_departure_points(8, 4, 1, 0, 3, 1e-4, None, None, dummy, dummy,
-                                         None) == nufft.ERR_INVALID_ARG
-    assert lib.dfsnufft_rotate_to_arrival(8, 4, 1, 0, dummy, dummy, dummy, dummy, 31, dummy,
-                                          dummy, None) == nufft.ERR_INVALID_ARG
-    assert lib.dfsnufft_rotate_to_arrival(8, 4, 1, 0, dummy, None, dummy, dummy, 32, dummy,
-                                          dummy, None) == nufft.ERR_INVALID_ARG
-    assert lib.dfsnufft_rotate_to_arrival(9, 4, 1, 1, dummy, dummy, dummy, dummy, 36, dummy,
-                                          dummy, None) == nufft.ERR_INVALID_ARG
+                                         None, None) == nufft.ERR_INVALID_ARG
+    rot = lib.dfsnufft_rotate_to_arrival
+    assert rot(8, 4, 1, 0, dummy, dummy, None, dummy, dummy, 31, dummy, dummy,
+               None) == nufft.ERR_INVALID_ARG                       # stride below n_lat n_lon
+    assert rot(8, 4, 1, 0, dummy, None, None, dummy, dummy, 32, dummy, dummy,
+               None) == nufft.ERR_INVALID_ARG                       # no points and no pq
+    assert rot(9, 4, 1, 1, dummy, dummy, None, dummy, dummy, 36, dummy, dummy,
+               None) == nufft.ERR_INVALID_ARG                       # odd n_lon
+    assert rot(8, 4, 1, 1, None, None, dummy, None, dummy, 32, dummy, dummy,
+               None) == nufft.ERR_INVALID_ARG                       # no u

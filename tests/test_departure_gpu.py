@@ -195,14 +195,15 @@ def test_semi_lagrangian_step_chain(torch_cuda, dtype):
     wa = rounded(wa.reshape(2, n_lat, n_lon), dtype)
     dt_over_a = 3600.0 / synth.EARTH_RADIUS
     rd = torch.float64 if dtype == "f64" else torch.float32
+    pq = torch.empty((2, n_lon * n_lat), dtype=rd, device="cuda")
     lon_d, colat_d = nufft.departure_points(torch.from_numpy(w).to(rd).cuda(), dt_over_a, 3,
-                                            torch.from_numpy(wa).to(rd).cuda())
+                                            torch.from_numpy(wa).to(rd).cuda(), pq_out=pq)
     tol = 1e-12 if dtype == "f64" else 1e-6
     with Plan(n_lon, n_lat, tol, dtype, 3, options=Options.make(real_fields=True)) as plan:
         plan.set_points(lon_d, colat_d)
         vals = plan.interpolate_grid(torch.from_numpy(samples).to(rd).cuda(), [1, -1, -1])
-        nufft.rotate_to_arrival(n_lon, n_lat, lon_d, colat_d, vals[1], vals[2],
-                                u_a=vals[1], v_a=vals[2])
+        nufft.rotate_to_arrival(n_lon, n_lat, None, None, vals[1], vals[2],
+                                u_a=vals[1], v_a=vals[2], pq=pq)
         got = vals.cpu().numpy()
     s = np.concatenate([np.arange(0, n_lon * n_lat, 13), np.arange(n_lon)])
     ol, oc = dep.departure_points(w, wa, dt_over_a, 3, index=s)
@@ -213,3 +214,37 @@ def test_semi_lagrangian_step_chain(torch_cuda, dtype):
     for f in range(3):
         err = np.max(np.abs(got[f][s] - ref[f])) / np.max(np.abs(ref[f]))
         assert err <= (1e-11 if dtype == "f64" else 2e-5), (f, err)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_rotation_from_departure_pq(torch_cuda, dtype):
+    """p and q written by the departure kernel for its final points: the
+    rotation read from them equals the oracle's Q at those points, two members."""
+    torch = torch_cuda
+    from paper_2605_01313_gb300 import nufft
+    n_lon, n_lat, members = 96, 48, 2
+    P = n_lon * n_lat
+    w = np.stack([rounded(inputs(n_lon, n_lat, 980 + m)[0], dtype) for m in range(members)])
+    rd = torch.float64 if dtype == "f64" else torch.float32
+    pq = torch.empty((members, 2, P), dtype=rd, device="cuda")
+    lon, colat = nufft.departure_points(torch.from_numpy(w).to(rd).cuda(), 0.15 / 60.0, 3,
+                                        pq_out=pq)
+    rng = np.random.default_rng(981)
+    vals = rounded(rng.standard_normal((members, 2, P)), dtype)
+    vt = torch.from_numpy(vals).to(rd).cuda()
+    flat = vt.view(-1)
+    ua, va = nufft.rotate_to_arrival(n_lon, n_lat, None, None, flat, flat[P:], stride=2 * P,
+                                     members=members, pq=pq)
+    ua = ua.cpu().numpy()
+    va = va.cpu().numpy()
+    lon, colat = lon.cpu().numpy(), colat.cpu().numpy()
+    la, ca = dep.arrival_points(n_lon, n_lat)
+    p_, q_ = pq.cpu().numpy()[:, 0], pq.cpu().numpy()[:, 1]
+    bound = 4e-14 if dtype == "f64" else 1e-5
+    for m in range(members):
+        p_ref, q_ref = dep.rotation_pq(la, ca, lon[m], colat[m])
+        assert np.max(np.abs(p_[m] - p_ref)) <= bound / 4
+        assert np.max(np.abs(q_[m] - q_ref)) <= bound / 4
+        eu, ev = dep.rotate_to_arrival(vals[m, 0], vals[m, 1], la, ca, lon[m], colat[m])
+        assert np.max(np.abs(ua[m * 2 * P:m * 2 * P + P] - eu)) <= bound
+        assert np.max(np.abs(va[m * 2 * P:m * 2 * P + P] - ev)) <= bound
