@@ -37,7 +37,7 @@ template <typename R> struct DepArgs {
 };
 
 template <typename R> struct Geo {
-    R X, Y, Z, rho;           // the departure point in A's turned frame
+    R X, Y, Z, rho, inv_rho;  // the departure point in A's turned frame; rho = |(X, Y)|
     R dphi, dth;              // phi_D - phi_A, theta_D - theta_A
     R cs;                     // cos s = cos eta
 };
@@ -57,35 +57,85 @@ __device__ __forceinline__ void colat_sc(double theta, R *s, R *c) {
     if (south) *c = -*c;
 }
 
+// Elementary functions of the step's geometry.  FP64 takes the library's; FP32,
+// whose angles per time step are small, takes the Taylor series of sin s,
+// cos s - 1 and atan z for |s|, |z| <= 1/16 (the first dropped term is below
+// 1e-10 of the result) and approximate reciprocals, and the library functions
+// beyond.
+__device__ __forceinline__ void sc_step(double s, double *ss, double *c1, double *cs) {
+    sincos(s, ss, cs);
+    *c1 = s < 0.5 ? -*ss * *ss / (1.0 + *cs) : *cs - 1.0;
+}
+__device__ __forceinline__ void sc_step(float s, float *ss, float *c1, float *cs) {
+    if (s <= 0.0625f) {
+        const float s2 = s * s;
+        *ss = s * (1.f - s2 * (1.f / 6.f) * (1.f - s2 * (1.f / 20.f) * (1.f - s2 * (1.f / 42.f))));
+        *c1 = -0.5f * s2 * (1.f - s2 * (1.f / 12.f) * (1.f - s2 * (1.f / 30.f)));
+        *cs = 1.f + *c1;
+    } else {
+        sincosf(s, ss, cs);
+        *c1 = s < 0.5f ? -*ss * *ss / (1.f + *cs) : *cs - 1.f;
+    }
+}
+__device__ __forceinline__ double atan2_step(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float atan2_step(float y, float x) {
+    if (x > 0.f && fabsf(y) <= 0.0625f * x) {
+        const float z = __fdividef(y, x), z2 = z * z;
+        return z * (1.f - z2 * (1.f / 3.f - z2 * (1.f / 5.f - z2 * (1.f / 7.f - z2 * (1.f / 9.f)))));
+    }
+    return atan2f(y, x);
+}
+__device__ __forceinline__ double rsqrt_step(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rsqrt_step(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double div_step(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_step(float a, float b) { return __fdividef(a, b); }
+
 // The point reached from A (sin/cos of its colatitude) by the angle |(se, sn)|
 // along the great circle leaving A in the direction -(se, sn).
 template <typename R>
 __device__ __forceinline__ Geo<R> move_back(R sA, R cA, R se, R sn) {
     Geo<R> g;
-    const R s = sqrt(se * se + sn * sn);
-    if (s == (R)0) {
+    const R s2 = se * se + sn * sn;
+    if (s2 == (R)0) {
         g.X = sA; g.Y = 0; g.Z = cA; g.rho = sA; g.dphi = 0; g.dth = 0; g.cs = 1;
+        g.inv_rho = sA > (R)0 ? (R)1 / sA : (R)0;
         return g;
     }
-    R ss, cs;
-    sc(s, &ss, &cs);
-    const R c1 = s < (R)0.5 ? -ss * ss / ((R)1 + cs) : cs - (R)1;   // cos s - 1
-    const R te = -se / s, tn = -sn / s;
+    const R inv_s = rsqrt_step(s2);
+    R ss, c1, cs;
+    sc_step(s2 * inv_s, &ss, &c1, &cs);
+    const R te = -se * inv_s, tn = -sn * inv_s;
     g.X = sA + (c1 * sA - ss * tn * cA);
     g.Y = ss * te;
     g.Z = cA + (c1 * cA + ss * tn * sA);
-    g.rho = sqrt(g.X * g.X + g.Y * g.Y);
-    g.dphi = atan2(g.Y, g.X);
+    const R rho2 = g.X * g.X + g.Y * g.Y;
+    g.inv_rho = rho2 > (R)0 ? rsqrt_step(rho2) : (R)0;
+    g.rho = rho2 * g.inv_rho;
+    g.dphi = atan2_step(g.Y, g.X);
     if (g.X > (R)0) {
         // rho cos th_A - Z sin th_A = -sin s t_n + (rho - X) cos th_A and
         // rho sin th_A + Z cos th_A = cos s + (rho - X) sin th_A, rho - X small
-        const R drho = g.Y * g.Y / (g.rho + g.X);
-        g.dth = atan2(-ss * tn + drho * cA, cs + drho * sA);
+        const R drho = div_step(g.Y * g.Y, g.rho + g.X);
+        g.dth = atan2_step(-ss * tn + drho * cA, cs + drho * sA);
     } else {                  // across the polar axis: no small difference to keep
-        g.dth = atan2(g.rho * cA - g.Z * sA, g.rho * sA + g.Z * cA);
+        g.dth = atan2_step(g.rho * cA - g.Z * sA, g.rho * sA + g.Z * cA);
     }
     g.cs = cs;
     return g;
+}
+
+// Q = [[p, q], [-q, p]] of A and the departure point g in A's turned frame:
+// cos(phi_D - phi_A) = X / rho, sin(...) = Y / rho, cos th_D = Z, sin th_D = rho.
+template <typename R>
+__device__ __forceinline__ void rotation_pq(R sA, R cA, const Geo<R> &g, R *p, R *q) {
+    R cx = 1, sx = 0;
+    if (g.rho > (R)0) {
+        cx = g.X * g.inv_rho;
+        sx = g.Y * g.inv_rho;
+    }
+    const R inv_den = div_step((R)1, (R)1 + g.cs);      // 1 / (1 + cos eta)
+    *p = (sA * g.rho + ((R)1 + cA * g.Z) * cx) * inv_den;
+    *q = -(cA + g.Z) * sx * inv_den;
 }
 
 // Quintic Lagrange weights on the nodes -2..3 at t in [0, 1).
@@ -100,20 +150,6 @@ __device__ __forceinline__ void lagrange5(R t, R *L) {
     L[3] = (p012 * p45) * (R)(1.0 / 12.0);
     L[4] = -(p012 * a3 * a5) * (R)(1.0 / 24.0);
     L[5] = (p012 * a3 * a4) * (R)(1.0 / 120.0);
-}
-
-// Q = [[p, q], [-q, p]] of A and the departure point g in A's turned frame:
-// cos(phi_D - phi_A) = X / rho, sin(...) = Y / rho, cos th_D = Z, sin th_D = rho.
-template <typename R>
-__device__ __forceinline__ void rotation_pq(R sA, R cA, const Geo<R> &g, R *p, R *q) {
-    R cx = 1, sx = 0;
-    if (g.rho > (R)0) {
-        cx = g.X / g.rho;
-        sx = g.Y / g.rho;
-    }
-    const R den = (R)1 + g.cs;                         // 1 + cos eta
-    *p = (sA * g.rho + ((R)1 + cA * g.Z) * cx) / den;
-    *q = -(cA + g.Z) * sx / den;
 }
 
 // One row of the quintic stencil: sum_b L[b] f(row, c0 + b) for both components,
@@ -186,19 +222,37 @@ __global__ void __launch_bounds__(256) k_departure(DepArgs<R> a, const R *__rest
         int r0 = j + (int)fy;
         r0 = r0 < -1 ? -1 : (r0 > nl - 1 ? nl - 1 : r0);
         R su = 0, sv = 0;
+        const int ci = i0 >= 2 ? i0 - 2 : i0 - 2 + n;     // first stencil column
+        if (r0 >= 2 && r0 + 3 < nl && ci <= n - 6) {
+            // the common case: six rows of six consecutive columns, no pole, no seam
+            const R *bu = wu + (size_t)(r0 - 2) * n + ci;
+            const R *bv = wv + (size_t)(r0 - 2) * n + ci;
 #pragma unroll
-        for (int ra = 0; ra < 6; ++ra) {
-            const int r = r0 - 2 + ra;                 // in [-3, nl + 2]
-            const bool beyond = r < 0 || r >= nl;
-            const int rr = r < 0 ? -1 - r : (r >= nl ? 2 * nl - 1 - r : r);
-            int c0 = i0 - 2 + (beyond ? n / 2 : 0);    // in [-2, 3n/2 - 2)
-            if (c0 < 0) c0 += n;
-            else if (c0 >= n) c0 -= n;
-            R tu, tv;
-            stencil_row(wu + (size_t)rr * n, wv + (size_t)rr * n, c0, n, Lx, tu, tv);
-            const R wy = beyond ? -Ly[ra] : Ly[ra];
-            su = fma(wy, tu, su);
-            sv = fma(wy, tv, sv);
+            for (int ra = 0; ra < 6; ++ra) {
+                R tu = 0, tv = 0;
+#pragma unroll
+                for (int b = 0; b < 6; ++b) {
+                    tu = fma(Lx[b], __ldg(bu + ra * n + b), tu);
+                    tv = fma(Lx[b], __ldg(bv + ra * n + b), tv);
+                }
+                su = fma(Ly[ra], tu, su);
+                sv = fma(Ly[ra], tv, sv);
+            }
+        } else {
+#pragma unroll
+            for (int ra = 0; ra < 6; ++ra) {
+                const int r = r0 - 2 + ra;                 // in [-3, nl + 2]
+                const bool beyond = r < 0 || r >= nl;
+                const int rr = r < 0 ? -1 - r : (r >= nl ? 2 * nl - 1 - r : r);
+                int c0 = i0 - 2 + (beyond ? n / 2 : 0);    // in [-2, 3n/2 - 2)
+                if (c0 < 0) c0 += n;
+                else if (c0 >= n) c0 -= n;
+                R tu, tv;
+                stencil_row(wu + (size_t)rr * n, wv + (size_t)rr * n, c0, n, Lx, tu, tv);
+                const R wy = beyond ? -Ly[ra] : Ly[ra];
+                su = fma(wy, tu, su);
+                sv = fma(wy, tv, sv);
+            }
         }
         R p, q;
         rotation_pq(sA, cA, g, &p, &q);
