@@ -29,8 +29,13 @@ Contents, each following the passage it cites:
   field's parity (Sec. 4), then the plain discrete Fourier sums over the doubled
   torus (Sec. 4, the transforms in phi and theta written out as sums).
 
+Submodules: :mod:`oracle.departure` (departure points of Eq. 2.4 and the
+rotation Q of Sec. 2) and :mod:`oracle.lagrange` (the cubic and quintic
+Lagrange interpolation of the paper's baseline, for the comparator).
+
 Every function here is pinned by the ``-m "not gpu"`` tests against closed
-forms, invariants and library special cases (see tests/test_oracle_pins.py).
+forms, invariants and library special cases (see tests/test_oracle_pins.py,
+tests/test_departure_pins.py and tests/test_lagrange_pins.py).
 """
 from __future__ import annotations
 
