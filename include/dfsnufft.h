@@ -361,6 +361,29 @@ int dfsnufft_rotate_to_arrival(int n_lon, int n_lat, int n_members, int dtype,
                                const void *u_d, const void *v_d, int64_t stride, void *u_a,
                                void *v_a, void *stream);
 
+/* ---- Lagrange interpolation comparator ----------------------------------- */
+
+/* Tensor-product Lagrange interpolation of degree order (3 = cubic, 5 =
+ * quintic) of samples on Grid [0] at arbitrary points: the interpolation of the
+ * paper's baseline model (cubic for the scalar forcing, quintic for the vector
+ * one; Sec. 1-2), for comparison with the spectral path.  Stencil: the
+ * (order + 1)^2 grid nodes around the point in index space x = phi n_lon /
+ * (2 pi), y = theta n_lat / pi - 1/2; rows beyond a pole and points with a
+ * negative colatitude use the doubled sphere, f(phi + pi, -theta) =
+ * parity f(phi, theta).
+ *   parity : host array of n_fields values, +1 scalar, -1 wind component.
+ *   samples: device, n_fields x n_lat x n_lon dtype reals (phi fastest).
+ *   lon, colat: device doubles, n_points each, any real value (coordinates of
+ *            magnitude above about 2^40 give unspecified values, never an
+ *            out-of-bounds read).
+ *   values : device, n_fields x n_points dtype reals.
+ * n_lon even and > order, n_lat >= (order + 1) / 2, 1 <= n_fields <= 32.
+ * Asynchronous on stream; returns DFSNUFFT_ERR_INVALID_ARG or
+ * DFSNUFFT_ERR_CUDA (launch failure). */
+int dfsnufft_lagrange_interp(int n_lon, int n_lat, int n_fields, const int *parity, int order,
+                             int dtype, int64_t n_points, const double *lon, const double *colat,
+                             const void *samples, void *values, void *stream);
+
 /* Host-buffer variants: the same operations with host pointers.  The data are
  * copied to plan-owned device buffers on the plan's stream (pinned host memory
  * makes the copies asynchronous); dfsnufft_execute_host waits for the stream

@@ -43,7 +43,7 @@ EXPORTS = (
     "dfsnufft_choose_params_opts", "dfsnufft_plan_create_opts", "dfsnufft_ensemble_create_opts",
     "dfsnufft_server_create_opts", "dfsnufft_autotune", "dfsnufft_selftest_wait_timeout",
     "dfsnufft_execute_pr", "dfsnufft_grid_to_coeffs", "dfsnufft_interpolate_grid",
-    "dfsnufft_departure_points", "dfsnufft_rotate_to_arrival",
+    "dfsnufft_departure_points", "dfsnufft_rotate_to_arrival", "dfsnufft_lagrange_interp",
 )
 REAL_FIELDS = 1
 KEEP_ORDER = 2
@@ -197,6 +197,8 @@ def lib():
                                                 vp]
         L.dfsnufft_rotate_to_arrival.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, vp, i64, vp,
                                                  vp, vp]
+        L.dfsnufft_lagrange_interp.argtypes = [i32, i32, i32, vp, i32, i32, i64, vp, vp, vp, vp,
+                                               vp]
         for name in EXPORTS:
             if name not in ("dfsnufft_strerror", "dfsnufft_plan_last_error", "dfsnufft_es_kernel",
                             "dfsnufft_version"):
@@ -449,6 +451,28 @@ def rotate_to_arrival(n_lon, n_lat, lon_d, colat_d, u_d, v_d, stride=None, membe
         ctypes.c_void_p(v_d.data_ptr()), int(stride), ctypes.c_void_p(u_a.data_ptr()),
         ctypes.c_void_p(v_a.data_ptr()), _stream_ptr(u_d, stream)))
     return u_a, v_a
+
+
+def lagrange_interp(samples, parity, lon, colat, order, out=None, stream=None):
+    """Cubic (order 3) or quintic (order 5) tensor Lagrange interpolation of
+    Grid [0] samples, CUDA tensor (n_fields, n_lat, n_lon), at the points (lon,
+    colat) (dfsnufft_lagrange_interp); returns (n_fields, n_points)."""
+    import torch
+    if not samples.is_cuda or not samples.is_contiguous() or samples.dim() != 3:
+        raise ValueError("samples must be a contiguous CUDA tensor (n_fields, n_lat, n_lon)")
+    F, n_lat, n_lon = (int(x) for x in samples.shape)
+    par = np.ascontiguousarray(parity, dtype=np.int32)
+    if par.size != F:
+        raise ValueError("one parity per field")
+    P = int(lon.numel())
+    if out is None:
+        out = torch.empty((F, P), dtype=samples.dtype, device=samples.device)
+    _check(lib().dfsnufft_lagrange_interp(
+        n_lon, n_lat, F, par.ctypes.data, int(order), _real_code(samples), P,
+        ctypes.c_void_p(lon.data_ptr()), ctypes.c_void_p(colat.data_ptr()),
+        ctypes.c_void_p(samples.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+        _stream_ptr(samples, stream)))
+    return out
 
 
 def dfsnufft_plan_get_params(h) -> dict:
