@@ -41,6 +41,8 @@ WORKLOADS = {
     "c3pr_2048x1024_f32": ("f32", "c3pr"),
     "c3grid_2048x1024_f32": ("f32", "c3grid"),
     "c3sl_2048x1024_f32": ("f32", "c3sl"),
+    "c3lag_2048x1024_f32": ("f32", "c3lag"),
+    "c3lag_2048x1024_f64": ("f64", "c3lag"),
     "c4_ensemble_f32": ("f32", "c4"),
     "c3_2048x1024_f64": ("f64", "c3"),
     "c2_512x256_f64": ("f64", "c2"),
@@ -87,6 +89,17 @@ def make_workload(name):
                  "dt_over_a": dt / synth.EARTH_RADIUS, "iterations": 3}
         wl.lon, wl.colat = lon_a, colat_a       # arrival points; departures come from the step
         wl.name = "c3sl_%dx%d_%s" % (wl.n_lon, wl.n_lat, dtype)
+        return wl
+    if kind == "c3lag":
+        # the C3 spectra and departure points, the fields given by their samples on
+        # the arrival grid: the spectral step (grid -> coefficients -> NUFFT) timed,
+        # and beside it the cubic and quintic Lagrange interpolation of the same
+        # samples (the paper's baseline), with the error of all three
+        wl = synth.workload_c3(dtype)
+        wl.grid = synth.coeffs_to_grid_samples(wl.coeffs, wl.n_lon, wl.n_lat)
+        wl.parity = [1, -1, -1]
+        wl.lag = (3, 5)
+        wl.name = "c3lag_%dx%d_%s" % (wl.n_lon, wl.n_lat, dtype)
         return wl
     if kind == "c3pr":
         # the C3 points; fields given as partial-regularity coefficients (Sec. 4),
@@ -414,6 +427,31 @@ def run_ours(args):
     d2h = h_out.nbytes
     assert np.array_equal(h_out, out.cpu().numpy()), "host and device paths disagree"
 
+    comparator = None
+    if getattr(wl, "lag", None):
+        # the Lagrange interpolation of the same arrival-grid samples at the same
+        # points, timed the same way (L2 flushed before each run)
+        comparator, lag_vals = {}, {}
+        for order in wl.lag:
+            lo = torch.empty((F, P), dtype=rd, device=dev)
+            for _ in range(3):
+                nufft.lagrange_interp(coeffs, wl.parity, lon, colat, order, out=lo, stream=stream)
+            times = []
+            for i in range(args.steps):
+                flush.fill_(i & 255)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                nufft.lagrange_interp(coeffs, wl.parity, lon, colat, order, out=lo, stream=stream)
+                e1.record(stream)
+                times.append((e0, e1))
+            torch.cuda.synchronize(dev)
+            ms = float(np.mean([a.elapsed_time(b) for a, b in times]))
+            comparator["lagrange%d" % order] = {"ms": ms, "value": F * P / (ms * 1e-3),
+                                                "unit": UNIT}
+            lag_vals["lagrange%d" % order] = lo.cpu().numpy()
+        comparator["spectral"] = {"ms": total_ms / args.steps,
+                                  "value": F * P / (total_ms / args.steps * 1e-3), "unit": UNIT}
+
     if rank != 0:
         plan.destroy()
         if ws > 1:
@@ -519,7 +557,14 @@ def run_ours(args):
                                           np.ascontiguousarray(wl.pr[f].imag.T))
                 cs_.append(oracle.complex_from_cossin(fc, fs, wl.n_lon, wl.n_lat))
             wl.coeffs = np.stack(cs_)
-        line["cpu_baseline"], line["error"] = cpu_baseline(wl, out.cpu().numpy(), args.cpu_seconds)
+        line["cpu_baseline"], line["error"] = cpu_baseline(
+            wl, out.cpu().numpy(), args.cpu_seconds, lag_vals if comparator else None)
+    if comparator:
+        line["comparator"] = comparator
+        line["config"]["input"] = ("samples of the C3 spectra on the arrival grid; the step "
+                                   "computes coefficients and evaluates them at the departure "
+                                   "points; comparator: Lagrange interpolation of the same "
+                                   "samples")
     plan.destroy()
     if ws == 1 and args.serve_seconds > 0:
         line["serving"] = serving_sweep(dev, [100, 500, 1000, 2000, 5000], args.serve_seconds)
@@ -556,9 +601,10 @@ def _oracle_sample_size(wl, seconds):
     return int(max(8, min(wl.sample.size, seconds / max(per_point, 1e-9))))
 
 
-def cpu_baseline(wl, gpu_vals, seconds):
+def cpu_baseline(wl, gpu_vals, seconds, others=None):
     """The oracle as it stands on the host cores, on a bounded sample of the
-    workload's checked points; also the GPU error on that sample."""
+    workload's checked points; also the GPU error on that sample (and that of
+    the other value arrays in ``others``, by name)."""
     import oracle
     n = _oracle_sample_size(wl, seconds)
     s = wl.sample[:n]
@@ -573,8 +619,11 @@ def cpu_baseline(wl, gpu_vals, seconds):
             "sample": "%d of the workload's seeded check points x %d fields, %s"
                       % (n, wl.n_fields, what)}
     bound = 1e-11 if wl.dtype == "f64" else 2e-5
-    return base, {"rel_linf_per_field": err, "bound": bound, "ok": max(err) <= bound,
-                  "points_checked": int(n)}
+    out = {"rel_linf_per_field": err, "bound": bound, "ok": max(err) <= bound,
+           "points_checked": int(n)}
+    for name, vals in (others or {}).items():
+        out[name] = [oracle.rel_linf(vals[f][s], ref[f]) for f in range(wl.n_fields)]
+    return base, out
 
 
 # ------------------------------------------------------------------ ensemble and serving

@@ -373,9 +373,8 @@ int dfsnufft_rotate_to_arrival(int n_lon, int n_lat, int n_members, int dtype,
  * parity f(phi, theta).
  *   parity : host array of n_fields values, +1 scalar, -1 wind component.
  *   samples: device, n_fields x n_lat x n_lon dtype reals (phi fastest).
- *   lon, colat: device doubles, n_points each, any real value (coordinates of
- *            magnitude above about 2^40 give unspecified values, never an
- *            out-of-bounds read).
+ *   lon, colat: device doubles, n_points each, any real value below 2^53 rad
+ *            in magnitude, reduced exactly (others give NaN values).
  *   values : device, n_fields x n_points dtype reals.
  * n_lon even and > order, n_lat >= (order + 1) / 2, 1 <= n_fields <= 32.
  * Asynchronous on stream; returns DFSNUFFT_ERR_INVALID_ARG or

@@ -9,20 +9,28 @@
 // nodes around the point in grid-index space, x = phi n_lon / (2 pi),
 // y = theta n_lat / pi - 1/2; rows beyond a pole come from the same extension
 // (the row mirrored about the pole, half a turn away, times the parity).
-// Positions are reduced in FP64, weights and sums run in the precision R.
+// Positions are reduced exactly in integer arithmetic (fractions of a turn in
+// Q0.64, turns.cuh), so no FP64 arithmetic runs in the FP32 form; weights and
+// sums run in the precision R.  A coordinate that is not finite or of
+// magnitude 2^53 rad or more gives NaN values.
 #include "common.cuh"
+#include "turns.cuh"
 
 namespace {
-
-constexpr double kPi = 3.14159265358979323846;
 
 struct LagArgs {
     int n_lon, n_lat, F;
     long long n_points;
     unsigned vec_mask;        // bit f: field f is a wind component (parity -1)
-    double to_x, to_y;        // n_lon / (2 pi), n_lat / pi
-    double inv_n;             // 1 / n_lon
 };
+
+// A Q0.64 fraction as a value in [0, 1) of precision R.
+__device__ __forceinline__ float q64_unit(unsigned long long q, float) {
+    return (float)(unsigned)(q >> 40) * 0x1p-24f;
+}
+__device__ __forceinline__ double q64_unit(unsigned long long q, double) {
+    return (double)(q >> 11) * 0x1p-53;
+}
 
 // Weights of the Lagrange interpolant through the nodes -H .. ORD - H at t.
 template <typename R, int ORD>
@@ -45,7 +53,7 @@ __device__ __forceinline__ void weights(R t, R *L) {
 // grid ceil(n_points / 256); block 256.  samples: F x n_lat x n_lon; values:
 // F x n_points.
 template <typename R, int ORD>
-__global__ void __launch_bounds__(256) k_lagrange(LagArgs a, const double *__restrict__ lon,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_lagrange(LagArgs a, const double *__restrict__ lon,
                                                   const double *__restrict__ colat,
                                                   const R *__restrict__ samples,
                                                   R *__restrict__ values) {
@@ -53,26 +61,46 @@ __global__ void __launch_bounds__(256) k_lagrange(LagArgs a, const double *__res
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.n_points) return;
     const int n = a.n_lon, nl = a.n_lat;
-    double th = colat[p], ph = lon[p];
-    th -= 2.0 * kPi * floor((th + kPi) * (0.5 / kPi));          // [-pi, pi)
-    const bool neg = th < 0.0;
+    // fractions of a turn: theta in [-1/2, 1/2) read signed; a negative one is
+    // the point (phi + 1/2 turn, -theta)
+    unsigned long long ux = 0, uy = 0;
+    const bool ok = turns_q64(lon[p], ux) & turns_q64(colat[p], uy);
+    const bool neg = (long long)uy < 0;
     if (neg) {
-        th = -th;
-        ph += kPi;
+        uy = 0ULL - uy;                                            // in (0, 2^63]
+        ux += 1ULL << 63;
     }
-    double x = ph * a.to_x;
-    x -= (double)n * floor(x * a.inv_n);                           // [0, n] up to rounding
-    const double y = th * a.to_y - 0.5;                            // [-1/2, nl - 1/2]
-    const double fx = floor(x), fy = floor(y);
+    // x = phi n / (2 pi) = ux n / 2^64: cell i and offset, exactly
+    const int i = (int)__umul64hi(ux, (unsigned long long)n);      // in [0, n)
+    const unsigned long long xf = ux * (unsigned long long)n;
+    // y = theta n_lat / pi - 1/2 = uy 2 n_lat / 2^64 - 1/2
+    const unsigned long long zi = __umul64hi(uy, 2ULL * nl);      // in [0, nl]
+    const unsigned long long zf = uy * (2ULL * nl);
+    const int j = (int)zi - (zf < (1ULL << 63) ? 1 : 0);           // in [-1, nl - 1]
+    const unsigned long long yf = zf ^ (1ULL << 63);
     R Lx[NP], Ly[NP];
-    weights<R, ORD>((R)(x - fx), Lx);
-    weights<R, ORD>((R)(y - fy), Ly);
-    // fx is in [-1, n] for moderate coordinates (rounding at both ends); taken
-    // mod n for any value, so that huge or non-finite input stays in bounds
-    int i = (int)fx % n;
-    if (i < 0) i += n;
-    int j = (int)fy;
-    j = j < -1 ? -1 : (j > nl - 1 ? nl - 1 : j);
+    weights<R, ORD>(q64_unit(xf, R()), Lx);
+    weights<R, ORD>(q64_unit(yf, R()), Ly);
+    const size_t plane = (size_t)nl * n;
+    if (j >= H && j - H + ORD < nl && i >= H && i - H + ORD < n) {
+        // the common case: the stencil lies inside the grid (no pole, no seam),
+        // one address for all its rows
+        const R *base = samples + (size_t)(j - H) * n + (i - H);
+        for (int f = 0; f < a.F; ++f) {
+            const R *s = base + (size_t)f * plane;
+            R acc = 0;
+#pragma unroll
+            for (int r = 0; r < NP; ++r) {
+                R t = 0;
+#pragma unroll
+                for (int b = 0; b < NP; ++b) t = fma(Lx[b], __ldg(s + r * n + b), t);
+                acc = fma(Ly[r], t, acc);
+            }
+            const bool vec = (a.vec_mask >> f) & 1u;
+            values[(size_t)f * a.n_points + p] = !ok ? (R)NAN : ((neg && vec) ? -acc : acc);
+        }
+        return;
+    }
     // row offsets and the first column of each stencil row (mod n)
     int roff[NP], cfirst[NP];
     bool beyond[NP];
@@ -88,7 +116,7 @@ __global__ void __launch_bounds__(256) k_lagrange(LagArgs a, const double *__res
         cfirst[r] = c;
     }
     for (int f = 0; f < a.F; ++f) {
-        const R *s = samples + (size_t)f * nl * n;
+        const R *s = samples + (size_t)f * plane;
         const bool vec = (a.vec_mask >> f) & 1u;
         R acc = 0;
 #pragma unroll
@@ -108,7 +136,7 @@ __global__ void __launch_bounds__(256) k_lagrange(LagArgs a, const double *__res
             }
             acc = fma((beyond[r] && vec) ? -Ly[r] : Ly[r], t, acc);
         }
-        values[(size_t)f * a.n_points + p] = (neg && vec) ? -acc : acc;
+        values[(size_t)f * a.n_points + p] = !ok ? (R)NAN : ((neg && vec) ? -acc : acc);
     }
 }
 
@@ -146,9 +174,6 @@ extern "C" int dfsnufft_lagrange_interp(int n_lon, int n_lat, int n_fields, cons
         if (parity[f] != 1 && parity[f] != -1) return DFSNUFFT_ERR_INVALID_ARG;
         if (parity[f] < 0) a.vec_mask |= 1u << f;
     }
-    a.to_x = n_lon / (2.0 * kPi);
-    a.to_y = n_lat / kPi;
-    a.inv_n = 1.0 / n_lon;
     cudaStream_t st = (cudaStream_t)stream;
     const cudaError_t e = dtype == DFSNUFFT_F64
                               ? launch<double>(a, order, lon, colat, samples, values, st)

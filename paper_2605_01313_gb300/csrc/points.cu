@@ -17,12 +17,9 @@
 // offset t leaves this file in plan precision (FP32 or FP64), so the FP32 form
 // keeps its kernel arguments accurate to ~1e-9 cells at any grid size.
 #include "common.cuh"
+#include "turns.cuh"
 
 namespace {
-
-// 1/(2 pi) as an unsigned Q0.128 number, floor(2^128 / (2 pi)) (Machin's formula).
-#define DFS_INV_2PI_HI 0x28be60db9391054aULL
-#define DFS_INV_2PI_LO 0x7f09d5f47d4d3770ULL
 
 struct FoldParams {
     int L1, L2;         // log2 of the fine sizes
@@ -30,35 +27,6 @@ struct FoldParams {
     int c0, w;
     int ltx, lty, nbx;  // log2 of the bin size (powers of two), bins per bin row
 };
-
-// Fraction of a turn of v in Q0.64.  False for inf/nan and for |v| >= 2^53,
-// where FP64 no longer resolves a position within a turn.
-__device__ __forceinline__ bool turns_q64(double v, unsigned long long &Y) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-    int e = (int)((bits >> 52) & 0x7ff);
-    if (e == 0x7ff) return false;
-    unsigned long long m = bits & 0xfffffffffffffULL;
-    if (e == 0) e = 1;                      // subnormal: m * 2^(1 - 1075)
-    else m |= 1ULL << 52;                   // |v| = m * 2^(e - 1075)
-    const int sh = 1139 - e;                // Y = floor(m * K * 2^-sh), K = 2^128 / (2 pi)
-    if (sh < 64) return false;
-    unsigned long long y = 0;
-    if (sh < 192) {
-        const unsigned long long hi0 = __umul64hi(m, DFS_INV_2PI_LO);
-        const unsigned long long lo1 = m * DFS_INV_2PI_HI;
-        const unsigned long long hi1 = __umul64hi(m, DFS_INV_2PI_HI);
-        const unsigned long long p1 = hi0 + lo1;          // product bits 64..127
-        const unsigned long long p2 = hi1 + (p1 < hi0);   // product bits 128..
-        if (sh >= 128) {
-            y = p2 >> (sh - 128);
-        } else {
-            const int s = sh - 64;
-            y = s ? ((p1 >> s) | (p2 << (64 - s))) : p1;
-        }
-    }
-    Y = (bits >> 63) ? 0ULL - y : y;
-    return true;
-}
 
 // Base cell and offset of one coordinate on a fine grid of 2^L cells.  tq is the
 // offset t in units of 2^-64 cells (signed for odd w).

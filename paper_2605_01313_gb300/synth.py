@@ -185,6 +185,18 @@ def torus_samples_to_coeffs(samples: np.ndarray) -> np.ndarray:
     return f
 
 
+def coeffs_to_grid_samples(c: np.ndarray, n_lon: int, n_lat: int) -> np.ndarray:
+    """Real samples on Grid [0] (n_lat x n_lon) of the fields whose centred
+    coefficients are c (F, N2, N1): the inverse of torus_samples_to_coeffs,
+    rows j < n_lat of the doubled torus.  Used only to draw inputs (arrival-grid
+    fields of a given spectrum)."""
+    n2, n1 = c.shape[-2:]
+    n = np.arange(n2) - n2 // 2
+    f = c * np.exp(1j * n * (math.pi / n2))[:, None]
+    f = np.fft.ifft2(np.fft.ifftshift(f, axes=(-2, -1))) * (n1 * n2)
+    return np.ascontiguousarray(f[..., :n_lat, :].real)
+
+
 def gaussian_bump_coeffs(n_lon: int, n_lat: int, center_lon: float, center_colat: float,
                          width: float, amplitude: float,
                          radius: float = EARTH_RADIUS) -> np.ndarray:
