@@ -78,7 +78,7 @@ typedef struct {
     int dtype;             /* DFSNUFFT_F64 or DFSNUFFT_F32                          */
     int tile_x, tile_y;    /* interpolation bin size in fine cells                 */
     int sigma;             /* oversampling factor (2 or 4)                          */
-    unsigned flags;        /* DFSNUFFT_REAL_FIELDS | DFSNUFFT_KEEP_ORDER, or 0        */
+    unsigned flags;        /* DFSNUFFT_REAL_FIELDS | _KEEP_ORDER | _GAUSS_GRID, or 0 */
 } dfsnufft_params;
 
 /* ---- plan options -------------------------------------------------------- */
@@ -102,9 +102,22 @@ typedef struct {
  * order; any order gives the same values (only slower). */
 #define DFSNUFFT_KEEP_ORDER 2u
 
+/* The arrival grid's latitudes are the n_lat Gauss-Legendre nodes (Sec. 3, the
+ * GL grid; colatitude theta_j = arccos(z_j), increasing from the north pole)
+ * instead of Grid [0].  dfsnufft_grid_to_coeffs and dfsnufft_interpolate_grid
+ * then take samples on that grid: the FFT in longitude and, in latitude, the
+ * inversion of the DFT matrix of the doubled column (Sec. 5, interpolation for
+ * the spherical-harmonic model), split by the field parity into two real
+ * n_lat x n_lat solves whose inverses the plan forms once in FP64 on the host
+ * (plan creation takes O(n_lat^3) host time: about a second at n_lat = 1024)
+ * and applies as GEMMs (cuBLAS).  Same size limits as dfsnufft_grid_to_coeffs.
+ * dfsnufft_plan_latitudes returns the nodes. */
+#define DFSNUFFT_GAUSS_GRID 4u
+
 /* Options of dfsnufft_plan_create_opts.  A zero-filled struct gives the
  * defaults of dfsnufft_plan_create.
- *   flags  : DFSNUFFT_REAL_FIELDS, DFSNUFFT_KEEP_ORDER (either, both or 0).
+ *   flags  : any of DFSNUFFT_REAL_FIELDS, DFSNUFFT_KEEP_ORDER,
+ *            DFSNUFFT_GAUSS_GRID (or 0).
  *   sigma  : oversampling factor, 0 (= 2), 2 or 4.  With 4 the fine grid has
  *            4x the cells of sigma 2 and the kernel may be narrower (the width
  *            rule keeps the kernel's modelled interpolation error at or below
@@ -299,6 +312,10 @@ int dfsnufft_execute_pr(dfsnufft_plan plan, int M, int N, const void *pr, void *
  * execute).  A changed parity array is uploaded with a synchronising copy. */
 int dfsnufft_grid_to_coeffs(dfsnufft_plan plan, const void *samples, const int *parity,
                             void *coeffs);
+
+/* The arrival grid's colatitudes (n_lat doubles, host): the Gauss-Legendre
+ * nodes of a DFSNUFFT_GAUSS_GRID plan, else Grid [0]'s (j + 1/2) pi / n_lat. */
+int dfsnufft_plan_latitudes(dfsnufft_plan plan, double *colat);
 
 /* One semi-Lagrangian interpolation step: samples on the arrival grid (as for
  * dfsnufft_grid_to_coeffs) to values at the plan's points (as for

@@ -70,7 +70,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".%d.tmp" % os.getpid()
-        run([nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"])
+        # cuBLAS serves the Gauss-Legendre latitude solve (plain GEMMs)
+        libdir = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+        run([nvcc(), "-shared", "-o", tmp] + objs + ARCH +
+            ["-Xcompiler", "-fPIC", "-L" + libdir, "-lcublas",
+             "-Xlinker", "-rpath", "-Xlinker", libdir])
         os.replace(tmp, LIB)
     return LIB
 

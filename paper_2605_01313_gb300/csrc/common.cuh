@@ -69,6 +69,12 @@ struct dfsnufft_plan_s {
     int64_t *h_pofs;            // members + 1 point offsets of the current points (host)
     int64_t max_member_points;  // largest member's point count
     int *d_status;              // device status word (DFS_STATUS_*), zero when healthy
+    // Gauss-Legendre latitude grid (DFSNUFFT_GAUSS_GRID, gauss.cu)
+    int gl;
+    void *d_gl_mat;             // C^{-1}, S^{-1} (n_lat x n_lat each, / n_lon), then w
+    double *h_gl_colat;         // the n_lat colatitudes
+    void *blas;                 // cublasHandle_t
+    int gl_emulated;            // FP32 GEMMs on the BF16x9 tensor-core emulation
     int *d_parity;              // fields: +1 scalar / -1 wind component (grid input)
     int h_parity[64];           // the parities last uploaded
     int parity_set;
@@ -127,6 +133,12 @@ cudaError_t dfs_launch_phi_pass(dfsnufft_plan p);
 cudaError_t dfs_launch_interp(dfsnufft_plan p, void *values);
 // forward.cu
 bool dfs_forward_supported(const dfsnufft_params &q);
+// gauss.cu
+int dfs_gl_setup(dfsnufft_plan p);
+void dfs_gl_release(dfsnufft_plan p);
+int dfs_launch_forward_gl(dfsnufft_plan p, const void *samples, const int *d_parity,
+                          void *coeffs, bool full);
+size_t dfs_gl_scratch_bytes(const dfsnufft_params &q, int lines);
 // full = false: of the columns m < 0 only the Nyquist row n = -N2/2 is written
 // (all that a real-field plan's theta pass reads there)
 cudaError_t dfs_launch_forward(dfsnufft_plan p, const void *samples, const int *d_parity,

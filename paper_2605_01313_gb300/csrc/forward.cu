@@ -33,15 +33,22 @@ struct FwdArgs {
     int F;                    // fields per member
     int CB;                   // columns per CTA (theta pass)
     int full;                 // 0: of the columns m < 0 only the Nyquist row is written
+    int K;                    // Gauss-Legendre form: complex slots per line and class
 };
 
 // grid (n_lat / 2, lines); block N1 / E threads.  Rows 2r and 2r + 1 of line f.
 // LOG > 0: length 2^LOG at compile time with the stage-ordered table stw.
-template <typename R, int E, int LOG>
+// GL: the spectra go to the two parity classes of the Gauss-Legendre solve
+// (gauss.cu): mode m of a field of parity s is in class 0 when s (-1)^m = +1
+// (spec), else in class 1 (g1); row j, slot line * K + m / 2 of an n_lat x
+// (lines K) complex matrix.
+template <typename R, int E, int LOG, bool GL>
 __global__ void __launch_bounds__(512) k_fwd_phi(FwdArgs a, const R *__restrict__ samples,
                                                  const typename CxT<R>::type *__restrict__ tw1,
                                                  const typename CxT<R>::type *__restrict__ stw,
-                                                 typename CxT<R>::type *__restrict__ spec) {
+                                                 typename CxT<R>::type *__restrict__ spec,
+                                                 const int *__restrict__ parity,
+                                                 typename CxT<R>::type *__restrict__ g1) {
     typedef typename CxT<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
@@ -58,12 +65,29 @@ __global__ void __launch_bounds__(512) k_fwd_phi(FwdArgs a, const R *__restrict_
     else line_fft<E>(a.log1, tw1, a.tws1, sm, t, ld, st);
     __syncthreads();
     // X_m = (Z_m + conj Z_{-m}) / 2,  Y_m = (Z_m - conj Z_{-m}) / (2i)
-    C *sx = spec + ((size_t)f * a.n_lat + j) * a.N1;
-    C *sy = sx + a.N1;
-    for (int m = t; m <= a.N1 / 2; m += blockDim.x) {          // the theta pass reads m <= N1/2
-        const C zp = z[m], zm = conjc(z[(a.N1 - m) & (a.N1 - 1)]);
-        sx[m] = cmake((R)0.5 * (zp.x + zm.x), (R)0.5 * (zp.y + zm.y));
-        sy[m] = cmake((R)0.5 * (zp.y - zm.y), (R)-0.5 * (zp.x - zm.x));
+    if constexpr (GL) {
+        const int pneg = parity[f % a.F] < 0;
+        const size_t pitch = (size_t)gridDim.y * a.K;             // complex per class row
+        for (int m = t; m <= a.N1 / 2; m += blockDim.x) {
+            const C zp = z[m], zm = conjc(z[(a.N1 - m) & (a.N1 - 1)]);
+            C *g = (pneg == (m & 1)) ? spec : g1;
+            const size_t o = (size_t)j * pitch + (size_t)f * a.K + (m >> 1);
+            g[o] = cmake((R)0.5 * (zp.x + zm.x), (R)0.5 * (zp.y + zm.y));
+            g[o + pitch] = cmake((R)0.5 * (zp.y - zm.y), (R)-0.5 * (zp.x - zm.x));
+            if (m == a.N1 / 2) {           // the other class has no mode in this slot
+                C *h = g == spec ? g1 : spec;
+                h[o] = cmake((R)0, (R)0);
+                h[o + pitch] = cmake((R)0, (R)0);
+            }
+        }
+    } else {
+        C *sx = spec + ((size_t)f * a.n_lat + j) * a.N1;
+        C *sy = sx + a.N1;
+        for (int m = t; m <= a.N1 / 2; m += blockDim.x) {      // the theta pass reads m <= N1/2
+            const C zp = z[m], zm = conjc(z[(a.N1 - m) & (a.N1 - 1)]);
+            sx[m] = cmake((R)0.5 * (zp.x + zm.x), (R)0.5 * (zp.y + zm.y));
+            sy[m] = cmake((R)0.5 * (zp.y - zm.y), (R)-0.5 * (zp.x - zm.x));
+        }
     }
 }
 
@@ -128,15 +152,26 @@ __global__ void __launch_bounds__(512) k_fwd_theta(FwdArgs a,
 
 template <typename R, int LOG>
 cudaError_t run_fwd_phi(dfsnufft_plan p, const FwdArgs &a, const void *samples, void *spec,
-                        int lines) {
+                        int lines, const int *d_parity = nullptr, void *g1 = nullptr) {
     typedef typename CxT<R>::type C;
     constexpr int E = DFS_FFT_E;
     const int threads = a.N1 / E;
     const size_t smem = sizeof(C) * (size_t)(region_len<C>(a.N1) + a.N1);
-    cudaError_t e = allow_smem(k_fwd_phi<R, E, LOG>, smem);
-    if (e) return e;
-    k_fwd_phi<R, E, LOG><<<dim3(a.n_lat / 2, lines), threads, smem, p->stream>>>(
-        a, (const R *)samples, (const C *)p->d_tw1, (const C *)p->d_stw_phi, (C *)spec);
+    const dim3 grid(a.n_lat / 2, lines);
+    cudaError_t e;
+    if (g1) {
+        e = allow_smem(k_fwd_phi<R, E, LOG, true>, smem);
+        if (e) return e;
+        k_fwd_phi<R, E, LOG, true><<<grid, threads, smem, p->stream>>>(
+            a, (const R *)samples, (const C *)p->d_tw1, (const C *)p->d_stw_phi, (C *)spec,
+            d_parity, (C *)g1);
+    } else {
+        e = allow_smem(k_fwd_phi<R, E, LOG, false>, smem);
+        if (e) return e;
+        k_fwd_phi<R, E, LOG, false><<<grid, threads, smem, p->stream>>>(
+            a, (const R *)samples, (const C *)p->d_tw1, (const C *)p->d_stw_phi, (C *)spec,
+            nullptr, nullptr);
+    }
     return cudaGetLastError();
 }
 
@@ -213,4 +248,38 @@ cudaError_t dfs_launch_forward(dfsnufft_plan p, const void *samples, const int *
     return p->prm.dtype == DFSNUFFT_F64
                ? launch_forward<double>(p, samples, d_parity, coeffs, p->d_T, full)
                : launch_forward<float>(p, samples, d_parity, coeffs, p->d_T, full);
+}
+
+// The longitude pass of the Gauss-Legendre form (gauss.cu): the row spectra of
+// every line into the two parity classes g0 and g1 (n_lat x (lines K) complex).
+template <typename R>
+static cudaError_t launch_fwd_phi_gl(dfsnufft_plan p, const void *samples, const int *d_parity,
+                                     void *g0, void *g1, int K) {
+    const dfsnufft_params &q = p->prm;
+    FwdArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n_lat = q.n_lat;
+    a.N1 = q.N1;
+    a.N2 = q.N2;
+    a.log1 = ilog2(q.N1);
+    a.log2 = ilog2(q.N2);
+    a.tws1 = ilog2(q.n1) - a.log1;
+    a.tws2 = ilog2(q.n2) - a.log2;
+    a.F = p->n_fields;
+    a.K = K;
+    const int lines = p->n_members * p->n_fields;
+    const bool ct1 = p->d_stw_phi && q.n1 == 2 * q.N1 && a.log1 >= 9 && a.log1 <= 11;
+    switch (ct1 ? a.log1 : 0) {
+        case 9: return run_fwd_phi<R, 9>(p, a, samples, g0, lines, d_parity, g1);
+        case 10: return run_fwd_phi<R, 10>(p, a, samples, g0, lines, d_parity, g1);
+        case 11: return run_fwd_phi<R, 11>(p, a, samples, g0, lines, d_parity, g1);
+        default: return run_fwd_phi<R, 0>(p, a, samples, g0, lines, d_parity, g1);
+    }
+}
+
+cudaError_t dfs_launch_fwd_phi_gl(dfsnufft_plan p, const void *samples, const int *d_parity,
+                                  void *g0, void *g1, int K) {
+    return p->prm.dtype == DFSNUFFT_F64
+               ? launch_fwd_phi_gl<double>(p, samples, d_parity, g0, g1, K)
+               : launch_fwd_phi_gl<float>(p, samples, d_parity, g0, g1, K);
 }

@@ -241,7 +241,7 @@ extern "C" int dfsnufft_choose_params_opts(int n_lon, int n_lat, double tol, int
     if (n_lon < 4 || (n_lon & 1) || n_lat < 2) return DFSNUFFT_ERR_INVALID_ARG;
     if (dtype != DFSNUFFT_F64 && dtype != DFSNUFFT_F32) return DFSNUFFT_ERR_INVALID_ARG;
     if (!(tol > 0.0) || !(tol < 1.0)) return DFSNUFFT_ERR_INVALID_ARG;
-    if ((o.flags & ~(DFSNUFFT_REAL_FIELDS | DFSNUFFT_KEEP_ORDER)) != 0)
+    if ((o.flags & ~(DFSNUFFT_REAL_FIELDS | DFSNUFFT_KEEP_ORDER | DFSNUFFT_GAUSS_GRID)) != 0)
         return DFSNUFFT_ERR_INVALID_ARG;
     const int sigma = o.sigma == 0 ? 2 : o.sigma;
     if (sigma != 2 && sigma != 4) return DFSNUFFT_ERR_INVALID_ARG;
@@ -315,6 +315,7 @@ extern "C" const char *dfsnufft_version(void) { return DFS_VERSION; }
 // ------------------------------------------------------------------ plan lifetime
 
 static void release(dfsnufft_plan p) {
+    dfs_gl_release(p);
     void **bufs[] = {&p->d_inv1, &p->d_inv2, &p->d_tw1, &p->d_tw2, &p->d_stw_theta, &p->d_stw_phi,
                      &p->d_T, &p->d_G, (void **)&p->d_bin_count, (void **)&p->d_bin_start,
                      (void **)&p->d_task_bin, (void **)&p->d_n_tasks,
@@ -508,6 +509,18 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
     }
     rc = upload_tables(p);
     if (rc == DFSNUFFT_OK) rc = upload_stage_tables(p);
+    if (rc == DFSNUFFT_OK && (prm.flags & DFSNUFFT_GAUSS_GRID)) {
+        // samples on Gauss-Legendre latitudes: the solve matrices, in the theta-pass
+        // buffer's room for the class matrices
+        p->gl = 1;
+        if (!dfs_forward_supported(prm) ||
+            dfs_gl_scratch_bytes(prm, n_members * n_fields) >
+                (dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2)) *
+                    (size_t)n_members * n_fields * prm.n2 * dfs_tpitch(p->herm, prm.N1))
+            rc = DFSNUFFT_ERR_UNSUPPORTED;
+        else
+            rc = dfs_gl_setup(p);
+    }
     if (rc == DFSNUFFT_OK) {
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
@@ -710,6 +723,14 @@ static int grid_to_coeffs(dfsnufft_plan p, const void *samples, const int *parit
     if (!dfs_forward_supported(p->prm)) return DFSNUFFT_ERR_UNSUPPORTED;
     int rc = set_parity(p, parity);
     if (rc) return rc;
+    if (p->gl) {
+        rc = dfs_launch_forward_gl(p, samples, p->d_parity, coeffs, full);
+        if (rc) {
+            p->status = rc;
+            snprintf(p->msg, sizeof(p->msg), "Gauss-Legendre grid to coefficients failed");
+        }
+        return rc;
+    }
     DFS_CK(p, dfs_launch_forward(p, samples, p->d_parity, coeffs, full));
     return DFSNUFFT_OK;
 }
@@ -862,5 +883,13 @@ extern "C" int dfsnufft_plan_point_stats(dfsnufft_plan p, int64_t *rows_needed,
     const int64_t blocks = (rows / M) / DFS_ROW_BLOCK;
     *rows_needed = blocks * DFS_ROW_BLOCK;
     *nonempty_bins = bins;
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_plan_latitudes(dfsnufft_plan p, double *colat) {
+    if (!p || !colat) return DFSNUFFT_ERR_INVALID_ARG;
+    const int N = p->prm.n_lat;
+    for (int j = 0; j < N; ++j)
+        colat[j] = p->gl ? p->h_gl_colat[j] : (j + 0.5) * (3.14159265358979323846 / N);
     return DFSNUFFT_OK;
 }

@@ -44,9 +44,11 @@ EXPORTS = (
     "dfsnufft_server_create_opts", "dfsnufft_autotune", "dfsnufft_selftest_wait_timeout",
     "dfsnufft_execute_pr", "dfsnufft_grid_to_coeffs", "dfsnufft_interpolate_grid",
     "dfsnufft_departure_points", "dfsnufft_rotate_to_arrival", "dfsnufft_lagrange_interp",
+    "dfsnufft_plan_latitudes",
 )
 REAL_FIELDS = 1
 KEEP_ORDER = 2
+GAUSS_GRID = 4
 N_STAGES = 4
 STAGES = ("set_points", "theta_pass", "phi_pass", "interp")
 
@@ -68,9 +70,10 @@ class Options(ctypes.Structure):
                 ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int)]
 
     @classmethod
-    def make(cls, real_fields=False, sigma=0, w=0, tile=None, keep_order=False):
+    def make(cls, real_fields=False, sigma=0, w=0, tile=None, keep_order=False, gauss=False):
         o = cls()
-        o.flags = (REAL_FIELDS if real_fields else 0) | (KEEP_ORDER if keep_order else 0)
+        o.flags = ((REAL_FIELDS if real_fields else 0) | (KEEP_ORDER if keep_order else 0)
+                   | (GAUSS_GRID if gauss else 0))
         o.sigma = int(sigma or 0)
         o.w = int(w or 0)
         if tile:
@@ -197,6 +200,7 @@ def lib():
                                                 vp]
         L.dfsnufft_rotate_to_arrival.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, vp, i64, vp,
                                                  vp, vp]
+        L.dfsnufft_plan_latitudes.argtypes = [vp, vp]
         L.dfsnufft_lagrange_interp.argtypes = [i32, i32, i32, vp, i32, i32, i64, vp, vp, vp, vp,
                                                vp]
         for name in EXPORTS:
@@ -599,6 +603,13 @@ class Plan:
         if par.shape != (self.n_fields,):
             raise ValueError("parity needs one entry (+1 or -1) per field")
         return par
+
+    def latitudes(self):
+        """Colatitudes of the arrival grid's rows (Gauss-Legendre nodes for a
+        DFSNUFFT_GAUSS_GRID plan)."""
+        out = np.empty(self.n_lat, dtype=np.float64)
+        _check(lib().dfsnufft_plan_latitudes(self._h, out.ctypes.data), self._h)
+        return out
 
     def grid_to_coeffs(self, samples, parity, out=None):
         """Coefficients (the execute layout) of fields sampled on the arrival grid

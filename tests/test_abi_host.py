@@ -119,7 +119,7 @@ def test_options_explicit_fields(lib):
 
 @pytest.mark.parametrize("field,value", [("sigma", 3), ("sigma", 1), ("w", 1), ("w", 17),
                                          ("tile_x", 48), ("tile_x", 4), ("tile_y", 256),
-                                         ("flags", 4)])
+                                         ("flags", 8)])
 def test_options_errors(lib, field, value):
     o = nufft.Options()
     setattr(o, field, value)
