@@ -43,6 +43,7 @@ WORKLOADS = {
     "c3sl_2048x1024_f32": ("f32", "c3sl"),
     "c3lag_2048x1024_f32": ("f32", "c3lag"),
     "c3lag_2048x1024_f64": ("f64", "c3lag"),
+    "c3gl_2048x1024_f32": ("f32", "c3gl"),
     "c4_ensemble_f32": ("f32", "c4"),
     "c3_2048x1024_f64": ("f64", "c3"),
     "c2_512x256_f64": ("f64", "c2"),
@@ -89,6 +90,24 @@ def make_workload(name):
                  "dt_over_a": dt / synth.EARTH_RADIUS, "iterations": 3}
         wl.lon, wl.colat = lon_a, colat_a       # arrival points; departures come from the step
         wl.name = "c3sl_%dx%d_%s" % (wl.n_lon, wl.n_lat, dtype)
+        return wl
+    if kind == "c3gl":
+        # the C3 departure points; the fields (h, u, v) of the tilted steady zonal
+        # flow sampled on a Gauss-Legendre latitude grid (the spherical-harmonic
+        # model's grid, Sec. 3 and 5): coefficients by the latitude solve each step
+        wl = synth.workload_c3(dtype)
+        alpha = math.pi / 2 - 0.05
+        wl.parity = [1, -1, -1]
+        wl.coeffs = np.stack(synth.zonal_flow_coeffs(wl.n_lon, wl.n_lat, alpha))
+
+        def sampler(colat, wl=wl, alpha=alpha):
+            cc, ll = np.meshgrid(colat, np.arange(wl.n_lon) * 2 * math.pi / wl.n_lon,
+                                 indexing="ij")
+            h, u, v = synth.zonal_flow_values(ll.ravel(), cc.ravel(), alpha)
+            return np.stack([h, u, v]).reshape(3, wl.n_lat, wl.n_lon)
+        wl.gauss = sampler
+        wl.grid = np.zeros((3, wl.n_lat, wl.n_lon))       # replaced once the plan's nodes exist
+        wl.name = "c3gl_%dx%d_%s" % (wl.n_lon, wl.n_lat, dtype)
         return wl
     if kind == "c3lag":
         # the C3 spectra and departure points, the fields given by their samples on
@@ -317,9 +336,16 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    opts = nufft.Options.make(real_fields=not args.general, keep_order=args.keep_order)
+    gauss = getattr(wl, "gauss", None)
+    opts = nufft.Options.make(real_fields=not args.general, keep_order=args.keep_order,
+                              gauss=gauss is not None)
+    t_plan = time.perf_counter()
     plan = Plan(wl.n_lon, wl.n_lat, wl.tol, wl.dtype, F, stream=stream, options=opts)
+    t_plan = time.perf_counter() - t_plan
     prm = plan.params
+    if gauss is not None:         # samples at the plan's Gauss-Legendre latitudes
+        wl.grid = gauss(plan.latitudes())
+        coeffs = torch.from_numpy(wl.grid).to(rd).to(dev)
 
     def step(evs=None):
         if sl is not None:        # departure points of Eq. 2.4 into the point buffers
@@ -559,6 +585,11 @@ def run_ours(args):
             wl.coeffs = np.stack(cs_)
         line["cpu_baseline"], line["error"] = cpu_baseline(
             wl, out.cpu().numpy(), args.cpu_seconds, lag_vals if comparator else None)
+    if gauss is not None:
+        line["config"]["input"] = ("samples of the tilted steady zonal flow (h, u, v) on the "
+                                   "Gauss-Legendre grid; coefficients by the latitude solve "
+                                   "each step")
+        line["config"]["plan_seconds"] = t_plan
     if comparator:
         line["comparator"] = comparator
         line["config"]["input"] = ("samples of the C3 spectra on the arrival grid; the step "

@@ -34,6 +34,7 @@ struct FwdArgs {
     int CB;                   // columns per CTA (theta pass)
     int full;                 // 0: of the columns m < 0 only the Nyquist row is written
     int K;                    // Gauss-Legendre form: complex slots per line and class
+    long long gpitch;         // and complex per class row (>= lines K)
 };
 
 // grid (n_lat / 2, lines); block N1 / E threads.  Rows 2r and 2r + 1 of line f.
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(512) k_fwd_phi(FwdArgs a, const R *__restrict_
     // X_m = (Z_m + conj Z_{-m}) / 2,  Y_m = (Z_m - conj Z_{-m}) / (2i)
     if constexpr (GL) {
         const int pneg = parity[f % a.F] < 0;
-        const size_t pitch = (size_t)gridDim.y * a.K;             // complex per class row
+        const size_t pitch = (size_t)a.gpitch;                    // complex per class row
         for (int m = t; m <= a.N1 / 2; m += blockDim.x) {
             const C zp = z[m], zm = conjc(z[(a.N1 - m) & (a.N1 - 1)]);
             C *g = (pneg == (m & 1)) ? spec : g1;
@@ -254,7 +255,7 @@ cudaError_t dfs_launch_forward(dfsnufft_plan p, const void *samples, const int *
 // every line into the two parity classes g0 and g1 (n_lat x (lines K) complex).
 template <typename R>
 static cudaError_t launch_fwd_phi_gl(dfsnufft_plan p, const void *samples, const int *d_parity,
-                                     void *g0, void *g1, int K) {
+                                     void *g0, void *g1, int K, long long pitch) {
     const dfsnufft_params &q = p->prm;
     FwdArgs a;
     memset(&a, 0, sizeof(a));
@@ -267,6 +268,7 @@ static cudaError_t launch_fwd_phi_gl(dfsnufft_plan p, const void *samples, const
     a.tws2 = ilog2(q.n2) - a.log2;
     a.F = p->n_fields;
     a.K = K;
+    a.gpitch = pitch;
     const int lines = p->n_members * p->n_fields;
     const bool ct1 = p->d_stw_phi && q.n1 == 2 * q.N1 && a.log1 >= 9 && a.log1 <= 11;
     switch (ct1 ? a.log1 : 0) {
@@ -278,8 +280,8 @@ static cudaError_t launch_fwd_phi_gl(dfsnufft_plan p, const void *samples, const
 }
 
 cudaError_t dfs_launch_fwd_phi_gl(dfsnufft_plan p, const void *samples, const int *d_parity,
-                                  void *g0, void *g1, int K) {
+                                  void *g0, void *g1, int K, long long pitch) {
     return p->prm.dtype == DFSNUFFT_F64
-               ? launch_fwd_phi_gl<double>(p, samples, d_parity, g0, g1, K)
-               : launch_fwd_phi_gl<float>(p, samples, d_parity, g0, g1, K);
+               ? launch_fwd_phi_gl<double>(p, samples, d_parity, g0, g1, K, pitch)
+               : launch_fwd_phi_gl<float>(p, samples, d_parity, g0, g1, K, pitch);
 }

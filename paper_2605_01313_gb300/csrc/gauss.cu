@@ -34,7 +34,7 @@
 #include "common.cuh"
 
 cudaError_t dfs_launch_fwd_phi_gl(dfsnufft_plan p, const void *samples, const int *d_parity,
-                                  void *g0, void *g1, int K);
+                                  void *g0, void *g1, int K, long long pitch);
 
 namespace {
 
@@ -247,8 +247,12 @@ int dfs_gl_setup(dfsnufft_plan p) {
             rc = DFSNUFFT_ERR_CUDA;
         } else {
             p->blas = h;
-            if (!f64) p->gl_emulated = cublasSetMathMode(h, CUBLAS_FP32_EMULATED_BF16X9_MATH) ==
-                                       CUBLAS_STATUS_SUCCESS;
+            // FP32 GEMMs on the tensor cores through the BF16x9 emulation whenever
+            // cuBLAS offers it (checked at the first call)
+            if (!f64)
+                p->gl_emulated =
+                    cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_EAGER) ==
+                    CUBLAS_STATUS_SUCCESS;
         }
     }
     free(th);
@@ -275,7 +279,9 @@ int dfs_launch_forward_gl(dfsnufft_plan p, const void *samples, const int *d_par
     const dfsnufft_params &q = p->prm;
     const int N = q.n_lat, lines = p->n_members * p->n_fields;
     const int K = q.N1 / 4 + 1;
-    const long long pitch = (long long)lines * K;            // complex per class row
+    // complex per class row, rounded up so that every GEMM column starts on 32
+    // bytes (the tensor-core GEMMs need 16-byte aligned leading dimensions)
+    const long long pitch = ((long long)lines * K + 3) / 4 * 4;
     const long long cols = 2 * pitch;                        // reals
     const bool f64 = q.dtype == DFSNUFFT_F64;
     const size_t rs = f64 ? sizeof(double) : sizeof(float);
@@ -283,7 +289,12 @@ int dfs_launch_forward_gl(dfsnufft_plan p, const void *samples, const int *d_par
     char *base = (char *)p->d_T;
     void *g0 = base, *g1 = base + rs * N * cols;
     void *o0 = base + 2 * rs * N * cols;
-    cudaError_t e = dfs_launch_fwd_phi_gl(p, samples, d_parity, g0, g1, K);
+    cudaError_t e = dfs_launch_fwd_phi_gl(p, samples, d_parity, g0, g1, K, pitch);
+    if (!e && pitch > (long long)lines * K) {            // zero the padding columns
+        const size_t cs = 2 * rs, used = cs * lines * K;
+        e = cudaMemset2DAsync((char *)g0 + used, cs * pitch, 0, cs * pitch - used, 2 * N,
+                              p->stream);
+    }
     if (e) return DFSNUFFT_ERR_CUDA;
     cublasHandle_t h = (cublasHandle_t)p->blas;
     if (cublasSetStream(h, p->stream) != CUBLAS_STATUS_SUCCESS) return DFSNUFFT_ERR_CUDA;
@@ -298,10 +309,20 @@ int dfs_launch_forward_gl(dfsnufft_plan p, const void *samples, const int *d_par
                                        (double *)o0, (int)cols, sC, 2);
     } else {
         const float one = 1.f, zero = 0.f;
-        st = cublasSgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)cols, N, N, &one,
-                                       (const float *)g0, (int)cols, sA,
-                                       (const float *)p->d_gl_mat, N, sB, &zero,
-                                       (float *)o0, (int)cols, sC, 2);
+        st = CUBLAS_STATUS_NOT_SUPPORTED;
+        if (p->gl_emulated) {
+            st = cublasGemmStridedBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)cols, N, N, &one,
+                                            g0, CUDA_R_32F, (int)cols, sA, p->d_gl_mat,
+                                            CUDA_R_32F, N, sB, &zero, o0, CUDA_R_32F, (int)cols,
+                                            sC, 2, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+                                            CUBLAS_GEMM_DEFAULT);
+            if (st != CUBLAS_STATUS_SUCCESS) p->gl_emulated = 0;    // plain FP32 from now on
+        }
+        if (st != CUBLAS_STATUS_SUCCESS)
+            st = cublasSgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)cols, N, N, &one,
+                                           (const float *)g0, (int)cols, sA,
+                                           (const float *)p->d_gl_mat, N, sB, &zero,
+                                           (float *)o0, (int)cols, sC, 2);
     }
     if (st != CUBLAS_STATUS_SUCCESS) return DFSNUFFT_ERR_CUDA;
     GlArgs a;
@@ -331,5 +352,6 @@ int dfs_launch_forward_gl(dfsnufft_plan p, const void *samples, const int *d_par
 // Bytes of the theta-pass buffer the Gauss-Legendre form needs.
 size_t dfs_gl_scratch_bytes(const dfsnufft_params &q, int lines) {
     const size_t rs = q.dtype == DFSNUFFT_F64 ? sizeof(double) : sizeof(float);
-    return 4 * rs * (size_t)q.n_lat * 2 * (size_t)lines * (q.N1 / 4 + 1);
+    const size_t pitch = ((size_t)lines * (q.N1 / 4 + 1) + 3) / 4 * 4;
+    return 4 * rs * (size_t)q.n_lat * 2 * pitch;
 }
