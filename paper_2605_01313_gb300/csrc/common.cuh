@@ -45,6 +45,8 @@ struct dfsnufft_plan_s {
     int c0;                 // first tap sits c0 cells left of the point's base cell
     int herm;               // DFSNUFFT_REAL_FIELDS: theta pass on columns m >= 0 only
     int keep_order;         // DFSNUFFT_KEEP_ORDER: points processed unsorted, in caller order
+    int gdf;                // FP64 plan whose fine grid is stored as double-single (hi, lo)
+                            // pairs for the double-single interpolation (df32.cuh)
     int nbx, nby, nbins;    // interpolation bins
     int bstride;            // per-member stride of the bin arrays: >= nbins + 1, multiple of 4
     int cstride;            // per-member stride of d_bin_count: bstride + the scan workspace

@@ -1,0 +1,74 @@
+// Double-single arithmetic for the FP64 plans: a value carried as an unevaluated
+// sum hi + lo of two FP32 numbers (|lo| <= ulp(hi) / 2, 48 significant bits),
+// so that FP64-accurate work runs on the FP32 units, which GB300 has at 64 times
+// its FP64 rate.  Error-free transformations (Knuth's TwoSum, the FMA-based
+// TwoProduct) and the compensated dot product of Ogita, Rump and Oishi (Dot2):
+// a sum of products accumulated this way carries an error of about
+// (n u)^2 sum |x_i y_i| (u = 2^-24) before its final rounding.  The operations
+// use the _rn intrinsics so that no product is contracted into a neighbouring
+// addition, which would break the transformations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace {
+
+struct df32 {
+    float hi, lo;
+};
+
+// s + e = a + b exactly.
+__device__ __forceinline__ df32 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// s + e = a + b exactly, for |a| >= |b| (or a = 0).
+__device__ __forceinline__ df32 quick_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// a * s + c in double-single (one Horner step).
+__device__ __forceinline__ df32 df_mul_add(df32 a, df32 s, df32 c) {
+    const float p = __fmul_rn(a.hi, s.hi);
+    float e = fmaf(a.hi, s.hi, -p);
+    e = fmaf(a.hi, s.lo, e);
+    e = fmaf(a.lo, s.hi, e);
+    df32 t = two_sum(p, c.hi);
+    t.lo = __fadd_rn(t.lo, __fadd_rn(e, c.lo));
+    return quick_two_sum(t.hi, t.lo);
+}
+
+// One term of a compensated dot product: (r, c) += x * y with x, y double-single;
+// r is the running FP32 sum, c collects the rounding errors and the low parts.
+__device__ __forceinline__ void dot2_step(float &r, float &c, df32 x, df32 y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    const float e = fmaf(x.hi, y.hi, -p);
+    const df32 t = two_sum(r, p);
+    r = t.hi;
+    c = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, __fadd_rn(c, __fadd_rn(t.lo, e))));
+}
+
+// A double as hi + lo: hi holds the top 24 bits of the significand (truncated),
+// lo the remaining 29 rounded to 24, by integer operations on the bit pattern
+// (no FP64 arithmetic).  Magnitudes outside [2^-100, 2^100) take the plain
+// conversion.
+__device__ __forceinline__ df32 split_double(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 1023 - 100 || e >= 1023 + 100) return {__double2float_rn(v), 0.f};
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned long long m = b & 0xfffffffffffffULL;
+    const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) |
+                                     (unsigned)(m >> 29));
+    // lo = (m mod 2^29) 2^(e - 1075), scaled in two exact steps
+    const float r = __uint2float_rn((unsigned)(m & 0x1fffffffULL));
+    const float s1 = __uint_as_float((unsigned)(e - 1075 + 64 + 127) << 23);   // 2^(e - 1011)
+    const float lo = __fmul_rn(__fmul_rn(r, 0x1p-64f), s1);     // stays inside FP32's range
+    return {hi, sign ? -lo : lo};
+}
+
+}  // namespace

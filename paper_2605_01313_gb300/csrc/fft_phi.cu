@@ -13,6 +13,7 @@
 // rows inside the plan's needed row range; the row's values are staged in
 // shared memory first, since every one of them enters two Z_k.
 #include "fft_core.cuh"
+#include "df32.cuh"
 
 using namespace dfs_fft;
 
@@ -27,7 +28,9 @@ struct PhiArgs {
 
 // grid (n2 / CB, lines); block CB * M/E threads, thread = (t, c) with t fastest.
 // LOGM > 0 fixes the transform length at compile time; 0 takes it from a.logm.
-template <typename R, int E, int MAXT, int MINB, int LOGM, bool HERM>
+// DF (FP64 plans): each fine-grid value is written as the double-single pair
+// (hi, lo) of df32.cuh, the input of the double-single interpolation.
+template <typename R, int E, int MAXT, int MINB, int LOGM, bool HERM, bool DF = false>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_phi_pass(PhiArgs a, const typename CxT<R>::type *__restrict__ in,
                const typename CxT<R>::type *__restrict__ tw,
@@ -85,7 +88,14 @@ __global__ void __launch_bounds__(MAXT, MINB)
         // (h0 + h1 + i d) / 2
         return cmake((R)0.5 * (h0.x + h1.x - d.y), (R)0.5 * (h0.y + h1.y + d.x));
     };
-    auto st = [&](int j, C z) { reinterpret_cast<C *>(dst)[j] = z; };
+    auto st = [&](int j, C z) {
+        if constexpr (DF) {
+            const df32 h0 = split_double(z.x), h1 = split_double(z.y);
+            reinterpret_cast<float4 *>(dst)[j] = make_float4(h0.hi, h0.lo, h1.hi, h1.lo);
+        } else {
+            reinterpret_cast<C *>(dst)[j] = z;
+        }
+    };
     if constexpr (LOGM > 0) line_fft_ct<LOGM, E>(stw, sm, t, ld, st);
     else line_fft<E>(a.logm, tw, 1, sm, t, ld, st);
 }
@@ -173,16 +183,25 @@ template <> struct PhiCfg<double> {
     static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, MAXTW = 512;
 };
 
-template <typename R, int MAXT, int MINB, int LOGM, bool HERM>
-cudaError_t run_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
+template <typename R, int MAXT, int MINB, int LOGM, bool HERM, bool DF>
+cudaError_t run_phi_df(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
     typedef typename CxT<R>::type C;
     constexpr int E = PhiCfg<R>::E;
-    cudaError_t e = allow_smem(k_phi_pass<R, E, MAXT, MINB, LOGM, HERM>, smem);
+    cudaError_t e = allow_smem(k_phi_pass<R, E, MAXT, MINB, LOGM, HERM, DF>, smem);
     if (e) return e;
-    k_phi_pass<R, E, MAXT, MINB, LOGM, HERM><<<grid, threads, smem, p->stream>>>(
+    k_phi_pass<R, E, MAXT, MINB, LOGM, HERM, DF><<<grid, threads, smem, p->stream>>>(
         a, (const C *)p->d_T, (const C *)p->d_tw1, (const C *)p->d_stw_phi, p->d_rowrange,
         (R *)p->d_G);
     return cudaGetLastError();
+}
+
+// FP64 plans whose interpolation runs in double-single (p->gdf) take the DF form.
+template <typename R, int MAXT, int MINB, int LOGM, bool HERM>
+cudaError_t run_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
+    if constexpr (sizeof(R) == 8) {
+        if (p->gdf) return run_phi_df<R, MAXT, MINB, LOGM, HERM, true>(p, a, smem, grid, threads);
+    }
+    return run_phi_df<R, MAXT, MINB, LOGM, HERM, false>(p, a, smem, grid, threads);
 }
 
 template <typename R, bool HERM>

@@ -23,6 +23,7 @@
 #include <limits.h>
 
 #include "common.cuh"
+#include "df32.cuh"
 #include "tma.cuh"
 
 namespace {
@@ -126,6 +127,119 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const __grid_const
                     }
                     out_all[(size_t)a.F * p0 + (size_t)(f0 + ff) * Pk + dst] = acc;
                 }
+            }
+        }
+    }
+}
+
+// ---- FP64 plans in double-single arithmetic (df32.cuh)
+//
+// The fine grid holds (hi, lo) FP32 pairs (written so by the phi pass), the
+// Horner coefficients are split the same way, the weights are evaluated by
+// double-single Horner steps and every stencil sum is a compensated dot
+// product (Dot2): about 10 FP32 operations a tap instead of one FP64 FMA, on
+// units that run 64 times faster, with an error of about (w u)^2 sum |w g|
+// (u = 2^-24, a few 1e-13 of the value for smooth fields).
+#define DFS_DF_FG 4            // fields a CTA of k_interp_df stages at once, at most
+
+template <int W> struct HornerDF {
+    float hi[W][W + 1], lo[W][W + 1];
+};
+
+template <int W>
+__device__ __forceinline__ void df_weights(double t, const HornerDF<W> &h, df32 *wv) {
+    const df32 s = split_double(t - (W % 2 == 0 ? 0.5 : 0.0));
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        df32 acc = {h.hi[a][W], h.lo[a][W]};
+#pragma unroll
+        for (int k = W - 1; k >= 0; --k) acc = df_mul_add(acc, s, df32{h.hi[a][k], h.lo[a][k]});
+        wv[a] = acc;
+    }
+}
+
+// As k_interp, with the tile of (hi, lo) pairs.
+template <int W>
+__global__ void __launch_bounds__(256) k_interp_df(InterpArgs a,
+                                                   const __grid_constant__ HornerDF<W> hw,
+                                                   const float2 *__restrict__ grid,
+                                                   const int2 *__restrict__ base,
+                                                   const double *__restrict__ frac,
+                                                   const int *__restrict__ idx,
+                                                   const int *__restrict__ bin_start_all,
+                                                   const int *__restrict__ task_all,
+                                                   const int *__restrict__ n_tasks,
+                                                   const int *__restrict__ pofs,
+                                                   double *__restrict__ out_all) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+    const int TH = a.tile_y + W - 1;
+    const int TW = a.tile_x + W - 1;
+    const int tsz = TH * TW;
+    const int k = blockIdx.y;
+    const int p0 = pofs[k];
+    const int Pk = pofs[k + 1] - p0;
+    const int ntask = n_tasks[k];
+    const int *task_bin = task_all + (size_t)k * a.bstride;
+    const int *bin_start = bin_start_all + (size_t)k * a.bstride;
+    for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+        const int bin = task_bin[task];
+        const int by = bin / a.nbx;
+        const int bx = bin - by * a.nbx;
+        const int col0 = bx * a.tile_x - a.c0;
+        const int row0 = by * a.tile_y - a.c0;
+        const int s = p0 + bin_start[bin];
+        const int e = p0 + bin_start[bin + 1];
+        for (int f0 = 0; f0 < a.F; f0 += a.FG) {
+            const int fg = min(a.FG, a.F - f0);
+            __syncthreads();
+            for (int rr = threadIdx.x >> 5; rr < fg * TH; rr += blockDim.x >> 5) {
+                const int ff = rr / TH;
+                const int r = rr - ff * TH;
+                const int gr = (row0 + r) & (a.n2 - 1);
+                const float2 *src = grid + ((size_t)(k * a.F + f0 + ff) * a.n2 + gr) * a.n1;
+                float2 *dst = tile + ff * tsz + r * TW;
+                for (int cc = threadIdx.x & 31; cc < TW; cc += 32)
+                    dst[cc] = src[(col0 + cc) & (a.n1 - 1)];
+            }
+            __syncthreads();
+            for (int pi = s + threadIdx.x; pi < e; pi += blockDim.x) {
+                const int2 b = base[pi];
+                df32 wx[W];
+                df_weights<W>(frac[2 * pi], hw, wx);
+                const df32 sy = split_double(frac[2 * pi + 1] - (W % 2 == 0 ? 0.5 : 0.0));
+                const int ox = b.x - col0;
+                const int oy = b.y - row0;
+                const int dst = idx[pi];
+                // stencil rows one at a time (the y weight of the row evaluated
+                // there), all fields of the group per row: few live registers
+                float r2[DFS_DF_FG], c2[DFS_DF_FG];
+#pragma unroll
+                for (int ff = 0; ff < DFS_DF_FG; ++ff) r2[ff] = c2[ff] = 0.f;
+#pragma unroll 1
+                for (int bb = 0; bb < W; ++bb) {
+                    df32 wyb = {hw.hi[bb][W], hw.lo[bb][W]};
+#pragma unroll
+                    for (int kk = W - 1; kk >= 0; --kk)
+                        wyb = df_mul_add(wyb, sy, df32{hw.hi[bb][kk], hw.lo[bb][kk]});
+#pragma unroll
+                    for (int ff = 0; ff < DFS_DF_FG; ++ff) {
+                        if (ff >= fg) break;
+                        const float2 *tp = tile + ff * tsz + (oy + bb) * TW + ox;
+                        float r = 0.f, c = 0.f;
+#pragma unroll
+                        for (int aa = 0; aa < W; ++aa) {
+                            const float2 g = tp[aa];
+                            dot2_step(r, c, wx[aa], df32{g.x, g.y});
+                        }
+                        dot2_step(r2[ff], c2[ff], wyb, quick_two_sum(r, c));
+                    }
+                }
+#pragma unroll
+                for (int ff = 0; ff < DFS_DF_FG; ++ff)
+                    if (ff < fg)
+                        out_all[(size_t)a.F * p0 + (size_t)(f0 + ff) * Pk + dst] =
+                            (double)r2[ff] + (double)c2[ff];
             }
         }
     }
@@ -706,6 +820,25 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
     int per = (152 * 16 + M - 1) / M;
     if (per > p->nbins) per = p->nbins;
     if (per < 1) per = 1;
+    if constexpr (sizeof(R) == 8) {
+        if (p->gdf) {
+            HornerDF<W> hd;
+            for (int i = 0; i < W; ++i)
+                for (int kk = 0; kk <= W; ++kk) {
+                    const double c = (double)hw.c[i][kk];
+                    hd.hi[i][kk] = (float)c;
+                    hd.lo[i][kk] = (float)(c - (double)hd.hi[i][kk]);
+                }
+            if (a.FG > DFS_DF_FG) a.FG = DFS_DF_FG;
+            const size_t smem_df = per_field * a.FG;
+            cudaError_t e = dfs_allow_smem((const void *)k_interp_df<W>, smem_df);
+            if (e) return e;
+            k_interp_df<W><<<dim3(per, M), 256, smem_df, p->stream>>>(
+                a, hd, (const float2 *)p->d_G, p->d_base, (const double *)p->d_frac, p->d_idx,
+                p->d_bin_start, p->d_task_bin, p->d_n_tasks, p->d_pofs, (double *)values);
+            return cudaGetLastError();
+        }
+    }
     cudaError_t e = dfs_allow_smem((const void *)k_interp<R, W>, smem);
     if (e) return e;
     const int threads = sizeof(R) == 4 ? 128 : 256;

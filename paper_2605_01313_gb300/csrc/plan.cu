@@ -465,6 +465,9 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
     p->stream = (cudaStream_t)stream;
     p->herm = (prm.flags & DFSNUFFT_REAL_FIELDS) ? 1 : 0;
     p->keep_order = (prm.flags & DFSNUFFT_KEEP_ORDER) ? 1 : 0;
+    // FP64 with sorted points: fine grid as double-single pairs, interpolation
+    // on the FP32 units in double-single arithmetic
+    p->gdf = (dtype == DFSNUFFT_F64 && !p->keep_order) ? 1 : 0;
     p->c0 = (prm.w % 2 == 0) ? prm.w / 2 - 1 : (prm.w - 1) / 2;
     p->nbx = prm.n1 / prm.tile_x;    // base cells lie in [0, n): no wrap bin
     p->nby = prm.n2 / prm.tile_y;
