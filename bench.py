@@ -255,6 +255,19 @@ def interp_flops(prm, n_fields, n_points):
     return n_fields * n_points * 2 * w * (w + 1) + n_points * 4 * w * w
 
 
+def fft_flops(prm, n_fields, rows, stage):
+    """Algorithmic flops of one FFT pass, 5 L log2 L a complex transform of
+    length L: the theta pass transforms the coefficient columns (N1/2 + 1 of a
+    real-field plan, else N1) at length n2; the phi pass the needed rows at
+    length n1 / 2 (its complex-to-real form)."""
+    if stage == "theta_pass":
+        cols = prm["N1"] // 2 + 1 if prm["flags"] & 1 else prm["N1"]
+        L = prm["n2"]
+        return n_fields * cols * 5.0 * L * math.log2(L)
+    L = prm["n1"] // 2
+    return n_fields * rows * 5.0 * L * math.log2(L)
+
+
 def profile_traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary of this kernel and
     workload, if the kernel's source is unchanged since the capture."""
@@ -496,9 +509,14 @@ def run_ours(args):
     dom = max(("theta_pass", "phi_pass", "interp", "set_points"),
               key=lambda k: per_stage_ms[k] or 0.0)
     dom_ms = per_stage_ms[dom]
-    if wl.dtype == "f64" and dom == "interp":
+    if wl.dtype == "f64" and dom in ("interp", "theta_pass", "phi_pass"):
+        # FP64 stages are bound by arithmetic: FP64 flops of the stage against the
+        # measured FP64 FMA rate (the interpolation runs them in double-single on
+        # the FP32 units, so its fraction may exceed 1)
         fma = nufft.dfsnufft_probe_fma_rate("f64", 20.0)
-        achieved = interp_flops(prm, F, P) / (dom_ms * 1e-3) / 1e12
+        flops = (interp_flops(prm, F, P) if dom == "interp"
+                 else fft_flops(prm, F, stats["rows_needed"], dom))
+        achieved = flops / (dom_ms * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fma / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / (fma / 1e12),
                 "peak_source": "measured FP64 FMA rate (dfsnufft_probe_fma_rate)",
