@@ -45,8 +45,10 @@ struct dfsnufft_plan_s {
     int c0;                 // first tap sits c0 cells left of the point's base cell
     int herm;               // DFSNUFFT_REAL_FIELDS: theta pass on columns m >= 0 only
     int keep_order;         // DFSNUFFT_KEEP_ORDER: points processed unsorted, in caller order
-    int gdf;                // FP64 plan whose fine grid is stored as double-single (hi, lo)
-                            // pairs for the double-single interpolation (df32.cuh)
+    int gdf;                // FP64 plan run in double-single arithmetic (df32.cuh): theta
+                            // and phi passes, fine grid as (hi, lo) pairs, interpolation
+    void *d_df_tw1, *d_df_tw2;      // double-single twiddles (n1, n2 complex)
+    void *d_df_inv1, *d_df_inv2;    // double-single deconvolution factors (N1, N2)
     int nbx, nby, nbins;    // interpolation bins
     int bstride;            // per-member stride of the bin arrays: >= nbins + 1, multiple of 4
     int cstride;            // per-member stride of d_bin_count: bstride + the scan workspace

@@ -11,10 +11,19 @@
 
 #include <cuda_runtime.h>
 
-namespace {
+#include "common.cuh"
+
+// (global namespace: the complex overloads must join the generic cmake / cmul
+// of common.cuh in the same overload set)
 
 struct df32 {
     float hi, lo;
+    __host__ __device__ constexpr df32() : hi(0.f), lo(0.f) {}
+    __host__ __device__ constexpr df32(float h, float l) : hi(h), lo(l) {}
+    // constants (folded at compile time); not for values computed at run time
+    __host__ __device__ constexpr df32(double d)
+        : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ constexpr df32(int i) : df32((double)i) {}
 };
 
 // s + e = a + b exactly.
@@ -41,6 +50,44 @@ __device__ __forceinline__ df32 df_mul_add(df32 a, df32 s, df32 c) {
     t.lo = __fadd_rn(t.lo, __fadd_rn(e, c.lo));
     return quick_two_sum(t.hi, t.lo);
 }
+
+// Arithmetic on double-single values ("sloppy" addition: the low parts are
+// added without their own error term, which keeps normwise accuracy of about
+// u^2 for the FFT's butterflies), complex numbers of two of them, and the
+// helpers the FFT engine uses (cmake, cmul, twiddle loads).
+__device__ __forceinline__ df32 operator+(df32 a, df32 b) {
+    df32 s = two_sum(a.hi, b.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df32 operator-(df32 a) { return df32(-a.hi, -a.lo); }
+__device__ __forceinline__ df32 operator-(df32 a, df32 b) { return a + (-b); }
+__device__ __forceinline__ df32 operator*(df32 a, df32 b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+
+struct dfc {
+    df32 x, y;
+};
+__device__ __forceinline__ dfc cmake(df32 a, df32 b) { return dfc{a, b}; }
+__device__ __forceinline__ dfc operator+(dfc a, dfc b) { return dfc{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ dfc operator-(dfc a, dfc b) { return dfc{a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ dfc cmul(dfc a, dfc b) {
+    return dfc{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// A complex FP64 value (user data) as double-single.
+__device__ __forceinline__ dfc to_dfc(double2 v);
+// Read-only loads of table entries.
+__device__ __forceinline__ dfc ldt(const dfc *p) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return dfc{df32(v.x, v.y), df32(v.z, v.w)};
+}
+__device__ __forceinline__ float2 ldt(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldt(const double2 *p) { return __ldg(p); }
 
 // One term of a compensated dot product: (r, c) += x * y with x, y double-single;
 // r is the running FP32 sum, c collects the rounding errors and the low parts.
@@ -71,4 +118,8 @@ __device__ __forceinline__ df32 split_double(double v) {
     return {hi, sign ? -lo : lo};
 }
 
-}  // namespace
+__device__ __forceinline__ dfc to_dfc(double2 v) {
+    return dfc{split_double(v.x), split_double(v.y)};
+}
+
+template <> struct CxT<df32> { typedef dfc type; };

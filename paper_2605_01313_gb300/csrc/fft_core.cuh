@@ -6,6 +6,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "df32.cuh"
 #include "tma.cuh"
 
 namespace dfs_fft {
@@ -109,7 +110,7 @@ __device__ __forceinline__ void stockham_butterfly(C *v, int t, int T, int Ns, i
         if (Ns > 1) {
             const int d = jm << tsh;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[K + r * G] = cmul(v[K + r * G], __ldg(&tw[r * d]));
+            for (int r = 1; r < R; ++r) v[K + r * G] = cmul(v[K + r * G], ldt(&tw[r * d]));
         }
         dif_levels<R, K, G, R / 2>(v);
         const int base = (j - jm) * R + jm;
@@ -203,7 +204,7 @@ __device__ __forceinline__ void ct_butterfly(C *v, int t, const C *__restrict__ 
         if constexpr (NS > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r)
-                v[K + r * G] = cmul(v[K + r * G], __ldg(&stw[OFF + (r - 1) * NS + jm]));
+                v[K + r * G] = cmul(v[K + r * G], ldt(&stw[OFF + (r - 1) * NS + jm]));
         }
         dif_levels<R, K, G, R / 2>(v);
         const int base = (j - jm) * R + jm;
@@ -267,7 +268,7 @@ __device__ __forceinline__ void ct_butterfly2(C *v0, C *v1, int t, const C *__re
         if constexpr (NS > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const C w = __ldg(&stw[OFF + (r - 1) * NS + jm]);
+                const C w = ldt(&stw[OFF + (r - 1) * NS + jm]);
                 v0[K + r * G] = cmul(v0[K + r * G], w);
                 v1[K + r * G] = cmul(v1[K + r * G], w);
             }

@@ -12,6 +12,8 @@
 // holds H_k itself for k = 0..N1/2, and H_{-k} = conj H_k.  Each CTA handles CB
 // rows inside the plan's needed row range; the row's values are staged in
 // shared memory first, since every one of them enters two Z_k.
+#include <type_traits>
+
 #include "fft_core.cuh"
 #include "df32.cuh"
 
@@ -77,19 +79,21 @@ __global__ void __launch_bounds__(MAXT, MINB)
     auto ld = [&](int k) -> C {
         if constexpr (HERM) {
             const C h0 = hval(k), h1 = hval(k + M);
-            const C d = cmul(cmake(h0.x - h1.x, h0.y - h1.y), __ldg(&tw[k]));
+            const C d = cmul(cmake(h0.x - h1.x, h0.y - h1.y), ldt(&tw[k]));
             return cmake(h0.x + h1.x - d.y, h0.y + h1.y + d.x);
         }
         const C t0 = tval(k), t1 = tval(-k), t2 = tval(k + M), t3 = tval(M - k);
         // 2 H_k = T_k + conj T_{-k},  2 H_{k+M} = T_{k+M} + conj T_{M-k}
         const C h0 = cmake(t0.x + t1.x, t0.y - t1.y);
         const C h1 = cmake(t2.x + t3.x, t2.y - t3.y);
-        const C d = cmul(cmake(h0.x - h1.x, h0.y - h1.y), __ldg(&tw[k]));
+        const C d = cmul(cmake(h0.x - h1.x, h0.y - h1.y), ldt(&tw[k]));
         // (h0 + h1 + i d) / 2
         return cmake((R)0.5 * (h0.x + h1.x - d.y), (R)0.5 * (h0.y + h1.y + d.x));
     };
     auto st = [&](int j, C z) {
-        if constexpr (DF) {
+        if constexpr (std::is_same<R, df32>::value) {       // already double-single
+            reinterpret_cast<float4 *>(dst)[j] = make_float4(z.x.hi, z.x.lo, z.y.hi, z.y.lo);
+        } else if constexpr (DF) {
             const df32 h0 = split_double(z.x), h1 = split_double(z.y);
             reinterpret_cast<float4 *>(dst)[j] = make_float4(h0.hi, h0.lo, h1.hi, h1.lo);
         } else {
@@ -182,6 +186,9 @@ template <> struct PhiCfg<float> {
 template <> struct PhiCfg<double> {
     static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, MAXTW = 512;
 };
+template <> struct PhiCfg<df32> {
+    static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, MAXTW = 512;
+};
 
 template <typename R, int MAXT, int MINB, int LOGM, bool HERM, bool DF>
 cudaError_t run_phi_df(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
@@ -189,16 +196,17 @@ cudaError_t run_phi_df(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid
     constexpr int E = PhiCfg<R>::E;
     cudaError_t e = allow_smem(k_phi_pass<R, E, MAXT, MINB, LOGM, HERM, DF>, smem);
     if (e) return e;
+    const bool dfr = std::is_same<R, df32>::value;     // double-single tables
     k_phi_pass<R, E, MAXT, MINB, LOGM, HERM, DF><<<grid, threads, smem, p->stream>>>(
-        a, (const C *)p->d_T, (const C *)p->d_tw1, (const C *)p->d_stw_phi, p->d_rowrange,
-        (R *)p->d_G);
+        a, (const C *)p->d_T, (const C *)(dfr ? p->d_df_tw1 : p->d_tw1),
+        (const C *)(dfr ? nullptr : p->d_stw_phi), p->d_rowrange, (R *)p->d_G);
     return cudaGetLastError();
 }
 
 // FP64 plans whose interpolation runs in double-single (p->gdf) take the DF form.
 template <typename R, int MAXT, int MINB, int LOGM, bool HERM>
 cudaError_t run_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
-    if constexpr (sizeof(R) == 8) {
+    if constexpr (std::is_same<R, double>::value) {
         if (p->gdf) return run_phi_df<R, MAXT, MINB, LOGM, HERM, true>(p, a, smem, grid, threads);
     }
     return run_phi_df<R, MAXT, MINB, LOGM, HERM, false>(p, a, smem, grid, threads);
@@ -208,7 +216,9 @@ template <typename R, bool HERM>
 cudaError_t dispatch_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
     constexpr int MAXT = PhiCfg<R>::MAXT, MINB = PhiCfg<R>::MINB, MAXTW = PhiCfg<R>::MAXTW;
     if (threads > MAXT) return run_phi<R, MAXTW, 1, 0, HERM>(p, a, smem, grid, threads);
-    if (!p->d_stw_phi) return run_phi<R, MAXT, MINB, 0, HERM>(p, a, smem, grid, threads);
+    // double-single: the run-time-length transform (no stage-ordered tables)
+    if (!p->d_stw_phi || std::is_same<R, df32>::value)
+        return run_phi<R, MAXT, MINB, 0, HERM>(p, a, smem, grid, threads);
     switch (a.logm) {
         case 9: return run_phi<R, MAXT, MINB, 9, HERM>(p, a, smem, grid, threads);
         case 10: return run_phi<R, MAXT, MINB, 10, HERM>(p, a, smem, grid, threads);
@@ -273,5 +283,6 @@ cudaError_t launch_phi(dfsnufft_plan p) {
 }  // namespace
 
 cudaError_t dfs_launch_phi_pass(dfsnufft_plan p) {
+    if (p->gdf) return launch_phi<df32>(p);           // FP64 plans in double-single
     return p->prm.dtype == DFSNUFFT_F64 ? launch_phi<double>(p) : launch_phi<float>(p);
 }

@@ -27,6 +27,8 @@
 // N2/2 and are added there).  k_theta_pass is the plain-load version for shapes
 // the TMA kernel does not take (unaligned coefficient pointer, CTA or
 // shared-memory limits).
+#include <type_traits>
+
 #include "fft_core.cuh"
 #include "tma.cuh"
 
@@ -35,6 +37,10 @@ using namespace dfs_fft;
 namespace {
 
 template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake(a.x, -a.y); }
+// A coefficient as the pass's complex type: itself, or (double-single passes of
+// FP64 plans) the FP64 value split into double-single parts.
+template <typename C, typename CIn> __device__ __forceinline__ C in_value(CIn v) { return v; }
+template <> __device__ __forceinline__ dfc in_value<dfc, double2>(double2 v) { return to_dfc(v); }
 template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) {
     return cmake(a.x * s, a.y * s);
 }
@@ -67,18 +73,18 @@ __device__ __forceinline__ C herm_coef(int n, int k, int half, int N1, Rd &cf) {
 // Eq. 5.4: c = S/2 (m = 0, n != 0; S for n = 0), conj(S)/2 or /4 (even m), and
 // -sign(n) i conj(S)/4 (odd m).  The stencils are linear with real weights, so
 // they act on the cosine and sine parts at once.
-template <typename C>
-__device__ __forceinline__ C pr_coef(int n, int m, int N, const C *__restrict__ col) {
+template <typename C, typename CIn>
+__device__ __forceinline__ C pr_coef(int n, int m, int N, const CIn *__restrict__ col) {
     typedef decltype(C().x) R;
     const int na = n < 0 ? -n : n;
     // f_{k,m} on the case's index range, zero elsewhere
     auto f = [&](int k, int lo, int hi) -> C {
-        return (k >= lo && k <= hi) ? col[k] : cmake((R)0, (R)0);
+        return (k >= lo && k <= hi) ? in_value<C>(col[k]) : cmake((R)0, (R)0);
     };
     C S;
     if (m == 0) {
         if (na > N) return cmake((R)0, (R)0);
-        const R v = col[na].x;                             // no sine part at m = 0
+        const R v = in_value<C>(col[na]).x;                // no sine part at m = 0
         return cmake(na == 0 ? v : (R)0.5 * v, (R)0);
     } else if (m == 1) {
         if (na == 0) return cmake((R)0, (R)0);
@@ -114,9 +120,10 @@ struct ThetaArgs {
 // grid (ceil(tcols / CB), lines); block CB * n2/E threads, thread = (t, c) with c fastest.
 // PRIN (real-field plans): the input is partial-regularity DFS coefficients,
 // lines x (prM + 1) x (prN + 1) complex, converted on the fly by pr_coef.
-template <typename R, int E, int MAXT, int MINB, bool HERM, bool PRIN = false>
+template <typename R, int E, int MAXT, int MINB, bool HERM, bool PRIN = false,
+          typename CIn = typename CxT<R>::type>
 __global__ void __launch_bounds__(MAXT, MINB)
-    k_theta_pass(ThetaArgs a, const typename CxT<R>::type *__restrict__ coef,
+    k_theta_pass(ThetaArgs a, const CIn *__restrict__ coef,
                  const R *__restrict__ inv1, const R *__restrict__ inv2,
                  const typename CxT<R>::type *__restrict__ tw,
                  const int2 *__restrict__ rowrange, typename CxT<R>::type *__restrict__ out) {
@@ -129,14 +136,15 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int f = blockIdx.y;
     const int2 rr = rowrange[f / a.F];
     const bool col_ok = q < a.tcols;
-    const C *cf0 = coef + (size_t)f * a.N2 * a.N1;
+    const CIn *cf0 = coef + (size_t)f * a.N2 * a.N1;
     C *dst = out + (size_t)f * a.n2 * a.tpitch + q;
     const int half = a.N2 / 2;
     const int qa = HERM ? a.N1 / 2 + q : q;        // array column
     const R sq = col_ok ? inv1[qa < a.N1 ? qa : 0] : (R)0;
     C *sm = smem + (size_t)c * region_len<C>(a.n2);
     auto cf = [&](int r, int col) -> C {
-        return (r < a.N2 && col < a.N1) ? cf0[(size_t)r * a.N1 + col] : cmake((R)0, (R)0);
+        return (r < a.N2 && col < a.N1) ? in_value<C>(cf0[(size_t)r * a.N1 + col])
+                                        : cmake((R)0, (R)0);
     };
     auto ld = [&](int i) -> C {
         if (!col_ok) return cmake((R)0, (R)0);
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
         const R s = sq * inv2[r < a.N2 ? r : 0];
         if constexpr (PRIN) {
             if (q > a.prM || n > a.prN || n < -a.prN) return cmake((R)0, (R)0);
-            const C *col = coef + ((size_t)f * (a.prM + 1) + q) * (a.prN + 1);
+            const CIn *col = coef + ((size_t)f * (a.prM + 1) + q) * (a.prN + 1);
             return cscale(pr_coef<C>(n, q, a.prN, col), s);
         } else if constexpr (HERM) {
             return cscale(herm_coef<C>(n, q, half, a.N1, cf), s);
@@ -302,7 +310,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
             // for n = i - H: one table read a thread, the rest rotations by
             // multiples of pi/8 that are constants once the loop over e unrolls.
             constexpr int TT = (1 << LOGH) / E;
-            const C wt = __ldg(&tw[t]);
+            const C wt = ldt(&tw[t]);
             auto ld2 = [&](int i, C &y0, C &y1) {
                 y0 = y1 = cmake((R)0, (R)0);
                 if (!col_ok) return;
@@ -320,7 +328,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
                 if (HERM && i == half) {
                     const C y = coef_nm(half);
                     y0 = y0 + y;
-                    y1 = y1 + cmul(y, __ldg(&tw[half]));
+                    y1 = y1 + cmul(y, ldt(&tw[half]));
                 }
             };
             auto st2 = [&](int qq, C z0, C z1) {
@@ -338,7 +346,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
             for (int s = 0; s < 2; ++s) {
                 auto term = [&](int n) -> C {
                     C y = coef_nm(n);
-                    if (s) y = cmul(y, __ldg(&tw[n & (a.n2 - 1)]));
+                    if (s) y = cmul(y, ldt(&tw[n & (a.n2 - 1)]));
                     return y;
                 };
                 auto ld = [&](int i) -> C {
@@ -373,6 +381,9 @@ template <> struct ThetaCfg<float> {
 };
 template <> struct ThetaCfg<double> {
     static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, CB = 2, TMAXT = 512, TMINB = 1;
+};
+template <> struct ThetaCfg<df32> {
+    static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, CB = 1, TMAXT = 512, TMINB = 1;
 };
 
 template <typename R, int CB, int LOGH, bool HERM>
@@ -472,21 +483,32 @@ cudaError_t run_theta_plain(dfsnufft_plan p, const ThetaArgs &a, const void *coe
                             dim3 grid, int threads) {
     typedef typename CxT<R>::type C;
     constexpr int MAXT = ThetaCfg<R>::MAXT, MINB = ThetaCfg<R>::MINB;
-    cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM, PRIN>, smem);
-    if (e) return e;
-    k_theta_pass<R, E, MAXT, MINB, HERM, PRIN><<<grid, threads, smem, p->stream>>>(
-        a, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2, (const C *)p->d_tw2,
-        p->d_rowrange, (C *)p->d_T);
+    if constexpr (std::is_same<R, df32>::value) {
+        // FP64 coefficients, double-single factors and twiddles
+        cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM, PRIN, double2>, smem);
+        if (e) return e;
+        k_theta_pass<R, E, MAXT, MINB, HERM, PRIN, double2><<<grid, threads, smem, p->stream>>>(
+            a, (const double2 *)coeffs, (const R *)p->d_df_inv1, (const R *)p->d_df_inv2,
+            (const C *)p->d_df_tw2, p->d_rowrange, (C *)p->d_T);
+    } else {
+        cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM, PRIN>, smem);
+        if (e) return e;
+        k_theta_pass<R, E, MAXT, MINB, HERM, PRIN><<<grid, threads, smem, p->stream>>>(
+            a, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2,
+            (const C *)p->d_tw2, p->d_rowrange, (C *)p->d_T);
+    }
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs, int prM, int prN) {
     typedef typename CxT<R>::type C;
-    if (prM < 0) {
-        cudaError_t e = launch_theta_tma<R>(p, coeffs);
-        if (e != cudaErrorNotSupported) return e;
-        cudaGetLastError();
+    if constexpr (!std::is_same<R, df32>::value) {
+        if (prM < 0) {
+            cudaError_t e = launch_theta_tma<R>(p, coeffs);
+            if (e != cudaErrorNotSupported) return e;
+            cudaGetLastError();
+        }
     }
     constexpr int MAXT = ThetaCfg<R>::MAXT;
     const dfsnufft_params &q = p->prm;
@@ -530,6 +552,7 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs, int prM, int prN) 
 }  // namespace
 
 cudaError_t dfs_launch_theta_pass(dfsnufft_plan p, const void *coeffs, int prM, int prN) {
+    if (p->gdf) return launch_theta<df32>(p, coeffs, prM, prN);   // FP64 in double-single
     return p->prm.dtype == DFSNUFFT_F64 ? launch_theta<double>(p, coeffs, prM, prN)
                                         : launch_theta<float>(p, coeffs, prM, prN);
 }

@@ -322,7 +322,8 @@ static void release(dfsnufft_plan p) {
                      (void **)&p->d_status, (void **)&p->d_parity, (void **)&p->d_rowrange,
                      (void **)&p->d_pofs,
                      (void **)&p->d_rank, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
-                     (void **)&p->d_pts_stage, &p->d_coef_stage, &p->d_val_stage};
+                     (void **)&p->d_pts_stage, &p->d_coef_stage, &p->d_val_stage,
+                     &p->d_df_tw1, &p->d_df_tw2, &p->d_df_inv1, &p->d_df_inv2};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) dfs_free(bufs[i]);
     free(p->h_pofs);
     p->h_pofs = nullptr;
@@ -391,6 +392,52 @@ static int upload_stage_tables(dfsnufft_plan p) {
         if (e) return fail_cuda(p, "upload stage twiddles", e);
     }
     return DFSNUFFT_OK;
+}
+
+// Double-single copies of an FP64 table: each value v as (hi, lo) FP32 with
+// hi = v rounded, lo = v - hi rounded (48 significant bits).
+static void split_table(const double *src, float *dst, size_t n) {
+    for (size_t i = 0; i < n; ++i) {
+        const float hi = (float)src[i];
+        dst[2 * i] = hi;
+        dst[2 * i + 1] = (float)(src[i] - (double)hi);
+    }
+}
+
+// Tables of the double-single passes of an FP64 plan (p->gdf): twiddles of
+// lengths n1 and n2 and the deconvolution factors, in the layout of the
+// df32 / dfc types.
+static int upload_df_tables(dfsnufft_plan p) {
+    const dfsnufft_params &q = p->prm;
+    const size_t nmax = (size_t)(q.n1 > q.n2 ? q.n1 : q.n2);
+    double *d = (double *)malloc(sizeof(double) * 2 * nmax);
+    float *f = (float *)malloc(sizeof(float) * 4 * nmax);
+    int rc = (d && f) ? DFSNUFFT_OK : DFSNUFFT_ERR_OOM;
+    struct { void **ptr; int n; bool tw; } tabs[] = {
+        {&p->d_df_tw1, q.n1, true}, {&p->d_df_tw2, q.n2, true},
+        {&p->d_df_inv1, q.N1, false}, {&p->d_df_inv2, q.N2, false}};
+    for (int k = 0; rc == DFSNUFFT_OK && k < 4; ++k) {
+        const int n = tabs[k].n;
+        size_t vals;
+        if (tabs[k].tw) {
+            fill_twiddles<double2, double>((double2 *)d, n);
+            vals = 2 * (size_t)n;
+        } else {
+            dfsnufft_kernel_ft(q.w, q.beta, k == 2 ? q.n1 : q.n2, n, d);
+            for (int i = 0; i < n; ++i) d[i] = 1.0 / d[i];
+            vals = (size_t)n;
+        }
+        split_table(d, f, vals);
+        rc = dfs_alloc(p, tabs[k].ptr, sizeof(float) * 2 * vals, "double-single tables");
+        if (rc == DFSNUFFT_OK) {
+            const cudaError_t e =
+                cudaMemcpy(*tabs[k].ptr, f, sizeof(float) * 2 * vals, cudaMemcpyHostToDevice);
+            if (e) rc = fail_cuda(p, "upload double-single tables", e);
+        }
+    }
+    free(d);
+    free(f);
+    return rc;
 }
 
 static int upload_tables(dfsnufft_plan p) {
@@ -512,6 +559,7 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
     }
     rc = upload_tables(p);
     if (rc == DFSNUFFT_OK) rc = upload_stage_tables(p);
+    if (rc == DFSNUFFT_OK && p->gdf) rc = upload_df_tables(p);
     if (rc == DFSNUFFT_OK && (prm.flags & DFSNUFFT_GAUSS_GRID)) {
         // samples on Gauss-Legendre latitudes: the solve matrices, in the theta-pass
         // buffer's room for the class matrices
