@@ -146,15 +146,40 @@ template <int W> struct HornerDF {
     float hi[W][W + 1], lo[W][W + 1];
 };
 
+// The kernel is even, so tap W-1-a at s is tap a at -s: with tap a's
+// polynomial split into even and odd parts in u = s^2, P_a(+-s) = E(u) +- s O(u)
+// gives both weights of the mirror pair from two Horner chains of half length.
+template <int W>
+__device__ __forceinline__ void df_pair(const HornerDF<W> &h, int a, df32 s, df32 u, df32 &lo,
+                                        df32 &hi) {
+    constexpr int KE = W - (W & 1);           // highest even power
+    constexpr int KO = W - 1 + (W & 1);       // highest odd power
+    df32 e = {h.hi[a][KE], h.lo[a][KE]};
+#pragma unroll
+    for (int k = KE - 2; k >= 0; k -= 2) e = df_mul_add(e, u, df32{h.hi[a][k], h.lo[a][k]});
+    df32 o = {h.hi[a][KO], h.lo[a][KO]};
+#pragma unroll
+    for (int k = KO - 2; k >= 1; k -= 2) o = df_mul_add(o, u, df32{h.hi[a][k], h.lo[a][k]});
+    const df32 so = s * o;
+    lo = e + so;                               // tap a
+    hi = e - so;                               // tap W-1-a
+}
+
+template <int W>
+__device__ __forceinline__ df32 df_offset(double t) {
+    return split_double(t - (W % 2 == 0 ? 0.5 : 0.0));
+}
+
 template <int W>
 __device__ __forceinline__ void df_weights(double t, const HornerDF<W> &h, df32 *wv) {
-    const df32 s = split_double(t - (W % 2 == 0 ? 0.5 : 0.0));
+    const df32 s = df_offset<W>(t);
+    const df32 u = s * s;
 #pragma unroll
-    for (int a = 0; a < W; ++a) {
-        df32 acc = {h.hi[a][W], h.lo[a][W]};
-#pragma unroll
-        for (int k = W - 1; k >= 0; --k) acc = df_mul_add(acc, s, df32{h.hi[a][k], h.lo[a][k]});
-        wv[a] = acc;
+    for (int a = 0; a < (W + 1) / 2; ++a) {
+        df32 lo, hi;
+        df_pair<W>(h, a, s, u, lo, hi);
+        wv[a] = lo;
+        if (W - 1 - a != a) wv[W - 1 - a] = hi;
     }
 }
 
@@ -207,21 +232,18 @@ __global__ void __launch_bounds__(256) k_interp_df(InterpArgs a,
                 const int2 b = base[pi];
                 df32 wx[W];
                 df_weights<W>(frac[2 * pi], hw, wx);
-                const df32 sy = split_double(frac[2 * pi + 1] - (W % 2 == 0 ? 0.5 : 0.0));
+                const df32 sy = df_offset<W>(frac[2 * pi + 1]);
+                const df32 uy = sy * sy;
                 const int ox = b.x - col0;
                 const int oy = b.y - row0;
                 const int dst = idx[pi];
-                // stencil rows one at a time (the y weight of the row evaluated
-                // there), all fields of the group per row: few live registers
+                // stencil rows by mirror pairs (bb, W-1-bb), whose y weights come
+                // from one pair of Horner chains; all fields of the group per
+                // row: few live registers
                 float r2[DFS_DF_FG], c2[DFS_DF_FG];
 #pragma unroll
                 for (int ff = 0; ff < DFS_DF_FG; ++ff) r2[ff] = c2[ff] = 0.f;
-#pragma unroll 1
-                for (int bb = 0; bb < W; ++bb) {
-                    df32 wyb = {hw.hi[bb][W], hw.lo[bb][W]};
-#pragma unroll
-                    for (int kk = W - 1; kk >= 0; --kk)
-                        wyb = df_mul_add(wyb, sy, df32{hw.hi[bb][kk], hw.lo[bb][kk]});
+                auto row = [&](int bb, df32 wyb) {
 #pragma unroll
                     for (int ff = 0; ff < DFS_DF_FG; ++ff) {
                         if (ff >= fg) break;
@@ -234,6 +256,13 @@ __global__ void __launch_bounds__(256) k_interp_df(InterpArgs a,
                         }
                         dot2_step(r2[ff], c2[ff], wyb, quick_two_sum(r, c));
                     }
+                };
+#pragma unroll 1
+                for (int bb = 0; bb < (W + 1) / 2; ++bb) {
+                    df32 wlo, whi;
+                    df_pair<W>(hw, bb, sy, uy, wlo, whi);
+                    row(bb, wlo);
+                    if (W - 1 - bb != bb) row(W - 1 - bb, whi);
                 }
 #pragma unroll
                 for (int ff = 0; ff < DFS_DF_FG; ++ff)
