@@ -31,7 +31,7 @@ struct FwdArgs {
     int log1, log2;           // log2 N1, log2 N2
     int tws1, tws2;           // twiddle strides: tw1[k << tws1] = e^{2 pi i k / N1}
     int F;                    // fields per member
-    int CB;                   // columns per CTA (theta pass)
+    int CB, lcb;              // columns per CTA (theta pass), a power of two, and its log2
     int full;                 // 0: of the columns m < 0 only the Nyquist row is written
     int K;                    // Gauss-Legendre form: complex slots per line and class
     long long gpitch;         // and complex per class row (>= lines K)
@@ -92,63 +92,106 @@ __global__ void __launch_bounds__(512) k_fwd_phi(FwdArgs a, const R *__restrict_
     }
 }
 
-// grid (ceil((N1/2 + 1) / CB), lines); block CB * N2/E threads, thread = (t, c),
-// c fastest.  The samples are real, so c_{-n,-m} = conj c_{n,m}: only the modes
+// Persistent: grid = min(tasks, resident CTAs); a task is one block of CB
+// adjacent columns of one line (tasks = ceil((N1/2 + 1) / CB) x lines), CTA i
+// takes tasks i, i + gridDim.x, ...  Block CB * N2/E threads, thread = (t, c), c
+// fastest.  The samples are real, so c_{-n,-m} = conj c_{n,m}: only the modes
 // m = 0..N1/2 (DFT index) are transformed, and each column 0 < m < N1/2 also
 // writes its mirror column -m.  LOG > 0: length 2^LOG at compile time.
+// A task's n_lat x CB row spectra are staged in shared memory row by row (the CB
+// columns of a row are one contiguous read of CB * sizeof(C) >= 16 bytes, a whole
+// 32-byte sector for FP32 at CB = 4), by asynchronous 16-byte copies issued one
+// task ahead into the other of two buffers, so that the next block's reads are
+// in flight while this one is transformed; both halves of the doubled column are
+// read from there, so each spectrum value leaves HBM once.  The copies of the
+// block holding m = N1/2 also read the CB - 1 columns after it (inside the row,
+// as N1 >= 16 > CB); their values are never used.
 template <typename R, int E, int LOG>
-__global__ void __launch_bounds__(512) k_fwd_theta(FwdArgs a,
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fwd_theta(FwdArgs a,
                                                    const typename CxT<R>::type *__restrict__ spec,
                                                    const int *__restrict__ parity,
                                                    const typename CxT<R>::type *__restrict__ tw2,
                                                    const typename CxT<R>::type *__restrict__ stw,
-                                                   typename CxT<R>::type *__restrict__ coef) {
+                                                   typename CxT<R>::type *__restrict__ coef,
+                                                   int nblk, int ntask) {
     typedef typename CxT<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *smem = reinterpret_cast<C *>(smem_raw);
-    const int c = threadIdx.x % a.CB;
-    const int t = threadIdx.x / a.CB;
-    const int m = blockIdx.x * a.CB + c;               // DFT index of the phi mode
-    const int f = blockIdx.y;
-    const bool ok = m <= a.N1 / 2;
+    const int c = threadIdx.x & (a.CB - 1);
+    const int t = threadIdx.x >> a.lcb;
     C *sm = smem + (size_t)c * region_len<C>(a.N2);
-    const C *col = spec + (size_t)f * a.n_lat * a.N1 + (ok ? m : 0);
-    // the upper half of the doubled column: parity (-1)^m times the mirrored row
-    const R sgn = (R)(parity[f % a.F] < 0 ? -1 : 1) * ((m & 1) ? (R)-1 : (R)1);
-    auto ld = [&](int i) -> C {
-        if (!ok) return cmake((R)0, (R)0);
-        const C v = i < a.n_lat ? col[(size_t)i * a.N1]
-                                : cscale2(col[(size_t)(a.N2 - 1 - i) * a.N1], sgn);
-        return conjc(v);
+    C *stage = smem + (size_t)a.CB * region_len<C>(a.N2);   // 2 x (n_lat x CB), c fastest
+    const int per_buf = a.n_lat << a.lcb;
+    // 16-byte chunks of a staged row: CB * sizeof(C) / 16, a power of two
+    const int lcpr = a.lcb + (sizeof(C) == 16 ? 0 : -1);
+    auto prefetch = [&](int task, C *buf) {
+        const int f = task / nblk;
+        const int m0 = (task - f * nblk) * a.CB;
+        const char *src = reinterpret_cast<const char *>(spec + (size_t)f * a.n_lat * a.N1 + m0);
+        const size_t pitch = (size_t)a.N1 * sizeof(C);
+        const int total = a.n_lat << lcpr;
+        for (int q = threadIdx.x; q < total; q += blockDim.x) {
+            const int r = q >> lcpr;
+            cp_async_16(reinterpret_cast<char *>(buf) + (size_t)q * 16,
+                        src + (size_t)r * pitch + (size_t)(q - (r << lcpr)) * 16);
+        }
+        cp_async_commit();
     };
     const R scale = (R)1 / ((R)a.N1 * (R)a.N2);
-    const int mc = m < a.N1 / 2 ? m + a.N1 / 2 : m - a.N1 / 2;   // centred column
-    C *out = coef + (size_t)f * a.N2 * a.N1 + mc;
-    C *mirror = coef + (size_t)f * a.N2 * a.N1 + (a.N1 - mc);   // column of -m
-    const bool has_mirror = ok && m > 0 && m < a.N1 / 2;
-    auto st = [&](int k, C v) {
-        if (!ok) return;
-        // mode n = k (k < N2/2) or k - N2; half-cell phase e^{-i pi n / N2}:
-        // tw2 holds e^{+2 pi i k / n2} with n2 = N2 << tws2, so the phase is
-        // conj(tw2[n << (tws2 - 1)]) taken mod n2
-        const int n = k < a.N2 / 2 ? k : k - a.N2;
-        const int n2 = a.N2 << a.tws2;
-        const C ph = conjc(tw2[((n * (1 << (a.tws2 - 1))) % n2 + n2) % n2]);
-        const C cv = cscale2(cmul(conjc(v), ph), scale);
-        out[(size_t)(n + a.N2 / 2) * a.N1] = cv;
-        // c_{-n,-m} = conj c_{n,m}; the half-cell grid makes the sum antiperiodic
-        // in n (c_{n+N2,m} = -c_{n,m}), so the row n = -N2/2 of column -m is
-        // -conj c_{-N2/2,m}
-        if (has_mirror) {
-            if (n > -a.N2 / 2) {
-                if (a.full) mirror[(size_t)(a.N2 / 2 - n) * a.N1] = conjc(cv);
-            } else {
-                mirror[0] = cmake(-cv.x, cv.y);
-            }
+    // n2 = N2 << tws2 is a power of two: indices of tw2 are taken mod n2 by a mask
+    const int tw_mask = (a.N2 << a.tws2) - 1;
+    const int tw_step = 1 << (a.tws2 - 1);
+    if ((int)blockIdx.x < ntask) prefetch(blockIdx.x, stage);
+    int it = 0;
+    for (int task = blockIdx.x; task < ntask; task += gridDim.x, ++it) {
+        C *in = stage + (size_t)(it & 1) * per_buf;
+        const int nxt = task + gridDim.x;
+        if (nxt < ntask) {
+            prefetch(nxt, stage + (size_t)((it + 1) & 1) * per_buf);
+            cp_async_wait_group<1>();              // this task's copies have landed
+        } else {
+            cp_async_wait_group<0>();
         }
-    };
-    if constexpr (LOG > 0) line_fft_ct<LOG, E>(stw, sm, t, ld, st);
-    else line_fft<E>(a.log2, tw2, a.tws2, sm, t, ld, st);
+        __syncthreads();                           // everyone's have
+        const int f = task / nblk;
+        const int m = (task - f * nblk) * a.CB + c;          // DFT index of the phi mode
+        const bool ok = m <= a.N1 / 2;
+        // the upper half of the doubled column: parity (-1)^m times the mirrored row
+        const R sgn = (R)(parity[f % a.F] < 0 ? -1 : 1) * ((m & 1) ? (R)-1 : (R)1);
+        auto ld = [&](int i) -> C {
+            if (!ok) return cmake((R)0, (R)0);
+            const C v = i < a.n_lat ? in[(i << a.lcb) + c]
+                                    : cscale2(in[((a.N2 - 1 - i) << a.lcb) + c], sgn);
+            return conjc(v);
+        };
+        const int mc = m < a.N1 / 2 ? m + a.N1 / 2 : m - a.N1 / 2;   // centred column
+        C *out = coef + (size_t)f * a.N2 * a.N1 + mc;
+        C *mirror = coef + (size_t)f * a.N2 * a.N1 + (a.N1 - mc);   // column of -m
+        const bool has_mirror = ok && m > 0 && m < a.N1 / 2;
+        auto st = [&](int k, C v) {
+            if (!ok) return;
+            // mode n = k (k < N2/2) or k - N2; half-cell phase e^{-i pi n / N2}:
+            // tw2 holds e^{+2 pi i k / n2} with n2 = N2 << tws2, so the phase is
+            // conj(tw2[n << (tws2 - 1)]) taken mod n2
+            const int n = k < a.N2 / 2 ? k : k - a.N2;
+            const C ph = conjc(tw2[(n * tw_step) & tw_mask]);
+            const C cv = cscale2(cmul(conjc(v), ph), scale);
+            out[(size_t)(n + a.N2 / 2) * a.N1] = cv;
+            // c_{-n,-m} = conj c_{n,m}; the half-cell grid makes the sum antiperiodic
+            // in n (c_{n+N2,m} = -c_{n,m}), so the row n = -N2/2 of column -m is
+            // -conj c_{-N2/2,m}
+            if (has_mirror) {
+                if (n > -a.N2 / 2) {
+                    if (a.full) mirror[(size_t)(a.N2 / 2 - n) * a.N1] = conjc(cv);
+                } else {
+                    mirror[0] = cmake(-cv.x, cv.y);
+                }
+            }
+        };
+        if constexpr (LOG > 0) line_fft_ct<LOG, E>(stw, sm, t, ld, st);
+        else line_fft<E>(a.log2, tw2, a.tws2, sm, t, ld, st);
+        __syncthreads();        // reads of this buffer and of sm end before they are refilled
+    }
 }
 
 template <typename R, int LOG>
@@ -182,13 +225,21 @@ cudaError_t run_fwd_theta(dfsnufft_plan p, const FwdArgs &a, const void *spec,
     typedef typename CxT<R>::type C;
     constexpr int E = DFS_FFT_E;
     const int T = a.N2 / E;
-    const size_t smem = sizeof(C) * (size_t)a.CB * region_len<C>(a.N2);
+    const size_t smem = sizeof(C) * (size_t)a.CB * (region_len<C>(a.N2) + 2 * (size_t)a.n_lat);
     cudaError_t e = allow_smem(k_fwd_theta<R, E, LOG>, smem);
     if (e) return e;
-    const int ncol = a.N1 / 2 + 1;
-    k_fwd_theta<R, E, LOG><<<dim3((ncol + a.CB - 1) / a.CB, lines), a.CB * T, smem, p->stream>>>(
+    const int nblk = (a.N1 / 2 + 1 + a.CB - 1) / a.CB;
+    const int ntask = nblk * lines;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fwd_theta<R, E, LOG>, a.CB * T,
+                                                      smem) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    const long long want = (long long)p->num_sms * occ;
+    const int ctas = (int)(want < ntask ? want : ntask);
+    k_fwd_theta<R, E, LOG><<<ctas, a.CB * T, smem, p->stream>>>(
         a, (const C *)spec, d_parity, (const C *)p->d_tw2, (const C *)p->d_stw_theta,
-        (C *)coeffs);
+        (C *)coeffs, nblk, ntask);
     return cudaGetLastError();
 }
 
@@ -198,6 +249,7 @@ cudaError_t launch_forward(dfsnufft_plan p, const void *samples, const int *d_pa
     constexpr int E = DFS_FFT_E;
     const dfsnufft_params &q = p->prm;
     FwdArgs a;
+    memset(&a, 0, sizeof(a));
     a.n_lat = q.n_lat;
     a.N1 = q.N1;
     a.N2 = q.N2;
@@ -207,11 +259,14 @@ cudaError_t launch_forward(dfsnufft_plan p, const void *samples, const int *d_pa
     a.tws2 = ilog2(q.n2) - a.log2;
     a.F = p->n_fields;
     a.full = full ? 1 : 0;
+    // columns per CTA: CTAs of 1024 threads for FP32 (four FP32 columns of a row
+    // fill a 32-byte sector), of 512 for FP64 (two columns do)
     const int T = q.N2 / E;
-    int cb = 512 / T;
+    int cb = (sizeof(R) == 4 ? 1024 : 512) / T;
     if (cb < 1) cb = 1;
     if (cb > 8) cb = 8;
     a.CB = cb;
+    a.lcb = ilog2(cb);
     const int lines = p->n_members * p->n_fields;
     // the plan's stage-ordered tables are for lengths n1/2 and n2/2: they serve
     // the compile-time drivers when the fine grid is twice the modes

@@ -82,6 +82,13 @@ __device__ __forceinline__ void cp_async_8(void *smem_dst, const void *gmem_src)
                  "l"(gmem_src)
                  : "memory");
 }
+// Asynchronous 16-byte copy global -> shared (both 16-byte aligned), cached in
+// L2 only.
+__device__ __forceinline__ void cp_async_16(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
