@@ -462,8 +462,14 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_total = max_over_ranks(sum(e2e_ms), ws, dev)
     e2e_value = weak_scaling_value(ws, F * P, e2e_steps, e2e_total)
-    h2d = (2 * 8 * P if sl is None else h_w.nbytes + h_wa.nbytes) + h_coef.nbytes
-    d2h = h_out.nbytes
+    if not (pr_in or grid_in):
+        # the bytes the host-buffer entry points copy (a real-field plan stages
+        # only the coefficient columns its theta pass reads)
+        cb = nufft.dfsnufft_plan_host_copy_bytes(plan._h)
+        h2d, d2h = cb["points_h2d"] + cb["coeffs_h2d"], cb["values_d2h"]
+    else:
+        h2d = (2 * 8 * P if sl is None else h_w.nbytes + h_wa.nbytes) + h_coef.nbytes
+        d2h = h_out.nbytes
     assert np.array_equal(h_out, out.cpu().numpy()), "host and device paths disagree"
 
     comparator = None

@@ -403,7 +403,10 @@ int dfsnufft_lagrange_interp(int n_lon, int n_lat, int n_fields, const int *pari
 /* Host-buffer variants: the same operations with host pointers.  The data are
  * copied to plan-owned device buffers on the plan's stream (pinned host memory
  * makes the copies asynchronous); dfsnufft_execute_host waits for the stream
- * before it returns, so values are ready on return. */
+ * before it returns, so values are ready on return.  coeffs has the layout of
+ * dfsnufft_execute; a real-field plan (DFSNUFFT_REAL_FIELDS) copies only the part
+ * its theta pass reads: the columns m >= 0, the Nyquist column m = -N1/2 and
+ * the Nyquist row n = -N2/2 of every line (the rest must still be allocated). */
 int dfsnufft_set_points_host(dfsnufft_plan plan, int64_t n_points, const double *lon,
                              const double *colat);
 int dfsnufft_execute_host(dfsnufft_plan plan, const void *coeffs, void *values);
@@ -444,6 +447,14 @@ int dfsnufft_plan_read_timing(dfsnufft_plan plan, double *ms_total, int64_t *cal
  * rows, covering every row the points' stencils touch) and the number of
  * non-empty interpolation bins.  Measurement aid; no paper counterpart. */
 int dfsnufft_plan_point_stats(dfsnufft_plan plan, int64_t *rows_needed, int64_t *nonempty_bins);
+
+/* Bytes the host-buffer variants move per call at the plan's current points:
+ * host to device by dfsnufft_set_points_host (points) and by
+ * dfsnufft_execute_host (coefficients), device to host by dfsnufft_execute_host
+ * (values).  Measurement aid; no paper counterpart.  DFSNUFFT_ERR_INVALID_ARG
+ * for a null pointer. */
+int dfsnufft_plan_host_copy_bytes(dfsnufft_plan plan, int64_t *points_h2d, int64_t *coeffs_h2d,
+                                  int64_t *values_d2h);
 
 /* ---- autotuner -------------------------------------------------------------- */
 

@@ -843,6 +843,45 @@ extern "C" int dfsnufft_set_points_host(dfsnufft_plan p, int64_t n_points, const
     return DFSNUFFT_OK;
 }
 
+// Host coefficients into the staging buffer.  A real-field plan's theta pass
+// reads the columns m >= 0 (array columns N1/2 .. N1-1), the Nyquist column
+// m = -N1/2 (array column 0) and the Nyquist row n = -N2/2 (row 0 of each line),
+// so only those are copied: in row-major order the columns N1/2 .. N1-1 of one
+// row and column 0 of the next are contiguous, one 2-D copy of N1/2 + 1
+// elements a row takes both, and the first row of each line is copied from
+// column 0 to N1/2.  Other plans copy the whole array.
+static cudaError_t stage_coefficients(dfsnufft_plan p, const void *coeffs, size_t cs) {
+    const dfsnufft_params &q = p->prm;
+    const size_t rows = (size_t)p->n_members * p->n_fields * q.N2;
+    const size_t row = cs * q.N1, half = cs * (q.N1 / 2);
+    char *d = static_cast<char *>(p->d_coef_stage);
+    const char *h = static_cast<const char *>(coeffs);
+    if (!p->herm)
+        return cudaMemcpyAsync(d, h, rows * row, cudaMemcpyHostToDevice, p->stream);
+    cudaError_t e = cudaSuccess;
+    if (rows > 1)
+        e = cudaMemcpy2DAsync(d + half, row, h + half, row, half + cs, rows - 1,
+                              cudaMemcpyHostToDevice, p->stream);
+    if (!e)
+        e = cudaMemcpyAsync(d + (rows - 1) * row + half, h + (rows - 1) * row + half, half,
+                            cudaMemcpyHostToDevice, p->stream);
+    if (!e)
+        e = cudaMemcpy2DAsync(d, (size_t)q.N2 * row, h, (size_t)q.N2 * row, half + cs,
+                              (size_t)p->n_members * p->n_fields, cudaMemcpyHostToDevice,
+                              p->stream);
+    return e;
+}
+
+// Bytes stage_coefficients copies.
+static size_t staged_coefficient_bytes(dfsnufft_plan p, size_t cs) {
+    const dfsnufft_params &q = p->prm;
+    const size_t lines = (size_t)p->n_members * p->n_fields;
+    const size_t rows = lines * q.N2;
+    const size_t half = cs * (q.N1 / 2);
+    if (!p->herm) return rows * cs * q.N1;
+    return (rows - 1) * (half + cs) + half + lines * (half + cs);
+}
+
 extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *values) {
     if (!p) return DFSNUFFT_ERR_INVALID_ARG;
     if (p->status) return p->status;
@@ -866,7 +905,7 @@ extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *
         if (rc) return rc;
         p->val_stage_cap = p->cap_points;
     }
-    DFS_CK(p, cudaMemcpyAsync(p->d_coef_stage, coeffs, cb, cudaMemcpyHostToDevice, p->stream));
+    DFS_CK(p, stage_coefficients(p, coeffs, cs));
     rc = dfsnufft_execute(p, p->d_coef_stage, p->d_val_stage);
     if (rc) return rc;
     DFS_CK(p, cudaMemcpyAsync(values, p->d_val_stage, vb, cudaMemcpyDeviceToHost, p->stream));
@@ -874,6 +913,16 @@ extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *
 }
 
 // ------------------------------------------------------------------ measurement aids
+
+extern "C" int dfsnufft_plan_host_copy_bytes(dfsnufft_plan p, int64_t *points_h2d,
+                                             int64_t *coeffs_h2d, int64_t *values_d2h) {
+    if (!p || !points_h2d || !coeffs_h2d || !values_d2h) return DFSNUFFT_ERR_INVALID_ARG;
+    const size_t cs = p->prm.dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
+    *points_h2d = (int64_t)(2 * sizeof(double) * (size_t)p->n_points);
+    *coeffs_h2d = (int64_t)staged_coefficient_bytes(p, cs);
+    *values_d2h = (int64_t)(cs / 2 * (size_t)p->n_fields * (size_t)p->n_points);
+    return DFSNUFFT_OK;
+}
 
 extern "C" int dfsnufft_plan_enable_timing(dfsnufft_plan p, int enable) {
     if (!p) return DFSNUFFT_ERR_INVALID_ARG;

@@ -44,7 +44,7 @@ EXPORTS = (
     "dfsnufft_server_create_opts", "dfsnufft_autotune", "dfsnufft_selftest_wait_timeout",
     "dfsnufft_execute_pr", "dfsnufft_grid_to_coeffs", "dfsnufft_interpolate_grid",
     "dfsnufft_departure_points", "dfsnufft_rotate_to_arrival", "dfsnufft_lagrange_interp",
-    "dfsnufft_plan_latitudes",
+    "dfsnufft_plan_latitudes", "dfsnufft_plan_host_copy_bytes",
 )
 REAL_FIELDS = 1
 KEEP_ORDER = 2
@@ -192,6 +192,8 @@ def lib():
         L.dfsnufft_plan_enable_timing.argtypes = [vp, i32]
         L.dfsnufft_plan_read_timing.argtypes = [vp, vp, vp]
         L.dfsnufft_plan_point_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.dfsnufft_plan_host_copy_bytes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                                    ctypes.POINTER(i64)]
         L.dfsnufft_probe_fma_rate.argtypes = [i32, f64, ctypes.POINTER(f64)]
         L.dfsnufft_selftest_wait_timeout.argtypes = [ctypes.c_longlong, ctypes.POINTER(i32),
                                                      ctypes.POINTER(f64)]
@@ -348,6 +350,13 @@ def dfsnufft_plan_point_stats(h) -> dict:
     bins = ctypes.c_int64()
     _check(lib().dfsnufft_plan_point_stats(h, ctypes.byref(rows), ctypes.byref(bins)), h)
     return {"rows_needed": rows.value, "nonempty_bins": bins.value}
+
+
+def dfsnufft_plan_host_copy_bytes(h) -> dict:
+    pts, cf, vals = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().dfsnufft_plan_host_copy_bytes(h, ctypes.byref(pts), ctypes.byref(cf),
+                                               ctypes.byref(vals)), h)
+    return {"points_h2d": pts.value, "coeffs_h2d": cf.value, "values_d2h": vals.value}
 
 
 def dfsnufft_probe_fma_rate(dtype, target_ms=20.0) -> float:

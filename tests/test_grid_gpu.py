@@ -29,7 +29,10 @@ def plan_for(n_lon, n_lat, dtype, F, real=True, members=1):
                 options=Options.make(real_fields=real))
 
 
-@pytest.mark.parametrize("n_lon,n_lat", [(16, 8), (64, 32), (128, 64), (512, 256), (256, 512)])
+# (32, 1024) and (32, 2048): columns of 2048 and 4096 doubled rows, the longest
+# the theta pass takes (blocks of 2 and 1 columns in FP64, 4 and 2 in FP32)
+@pytest.mark.parametrize("n_lon,n_lat", [(16, 8), (64, 32), (128, 64), (512, 256), (256, 512),
+                                         (32, 1024), (32, 2048)])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_grid_to_coeffs_matches_oracle(torch_cuda, n_lon, n_lat, dtype):
     torch = torch_cuda

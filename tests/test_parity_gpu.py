@@ -283,6 +283,37 @@ def test_host_variants_match_device(torch_cuda):
     assert np.array_equal(dev, host)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_host_execute_real_plan_stages_what_it_reads(torch_cuda, dtype):
+    """A real-field plan's execute_host copies only the columns m >= 0 and the
+    Nyquist row and column: two different coefficient arrays in a row (white
+    noise in every entry, so that a part missed by the copy would come from the
+    first array) give the device path's values for each."""
+    from paper_2605_01313_gb300 import Plan
+    from paper_2605_01313_gb300.nufft import Options, dfsnufft_plan_host_copy_bytes
+    torch = torch_cuda
+    n_lon, n_lat, F = 64, 32, 3
+    rng = np.random.default_rng(41)
+    lon = rng.uniform(0, 2 * math.pi, 3000)
+    colat = np.arccos(rng.uniform(-1, 1, 3000))
+    cd = np.complex128 if dtype == "f64" else np.complex64
+    arrays = [(rng.standard_normal((F, 2 * n_lat, n_lon)) +
+               1j * rng.standard_normal((F, 2 * n_lat, n_lon))).astype(cd) for _ in range(2)]
+    tol = 1e-12 if dtype == "f64" else 1e-6
+    with Plan(n_lon, n_lat, tol, dtype, F, options=Options.make(real_fields=True)) as plan:
+        plan.set_points(torch.from_numpy(lon).cuda(), torch.from_numpy(colat).cuda())
+        dev = [plan.execute(torch.from_numpy(c).cuda()).cpu().numpy() for c in arrays]
+        plan.set_points_host(lon, colat)
+        host = [plan.execute_host(c) for c in arrays]
+        nb = dfsnufft_plan_host_copy_bytes(plan._h)
+    for d, h in zip(dev, host):
+        assert np.array_equal(d, h)
+    cs = 16 if dtype == "f64" else 8
+    rows, half = F * 2 * n_lat, cs * n_lon // 2
+    assert nb["coeffs_h2d"] == (rows - 1) * (half + cs) + half + F * (half + cs)
+    assert nb["points_h2d"] == 16 * 3000 and nb["values_d2h"] == cs // 2 * F * 3000
+
+
 def test_repeatable_and_resettable(torch_cuda):
     from paper_2605_01313_gb300 import Plan
     torch = torch_cuda
