@@ -406,7 +406,12 @@ int dfsnufft_lagrange_interp(int n_lon, int n_lat, int n_fields, const int *pari
  * before it returns, so values are ready on return.  coeffs has the layout of
  * dfsnufft_execute; a real-field plan (DFSNUFFT_REAL_FIELDS) copies only the part
  * its theta pass reads: the columns m >= 0, the Nyquist column m = -N1/2 and
- * the Nyquist row n = -N2/2 of every line (the rest must still be allocated). */
+ * the Nyquist row n = -N2/2 of every line (the rest must still be allocated).
+ * dfsnufft_execute_host copies the coefficients on a stream of the plan's own,
+ * after the plan's earlier reads of its staging buffer but not after the other
+ * work queued on the plan's stream (such as the set_points before it, which
+ * the copy overlaps): the host array must hold its values when the call is
+ * made. */
 int dfsnufft_set_points_host(dfsnufft_plan plan, int64_t n_points, const double *lon,
                              const double *colat);
 int dfsnufft_execute_host(dfsnufft_plan plan, const void *coeffs, void *values);

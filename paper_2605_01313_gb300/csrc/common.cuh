@@ -98,6 +98,12 @@ struct dfsnufft_plan_s {
     void *d_val_stage;      // host-variant staging of values
     int64_t val_stage_cap;
     int64_t pts_stage_cap;
+    // host-variant coefficient copies run on their own stream, so that they
+    // overlap the work queued before them (set_points): stage_free is recorded
+    // on the plan's stream after each read of d_coef_stage, coef_ready on
+    // copy_stream after the copies
+    cudaStream_t copy_stream;
+    cudaEvent_t stage_free, coef_ready;
 
     // stage timing (dfsnufft_plan_enable_timing)
     int timing;

@@ -333,6 +333,14 @@ static void release(dfsnufft_plan p) {
         free(p->ev);
         p->ev = nullptr;
     }
+    if (p->copy_stream) {
+        cudaStreamSynchronize(p->copy_stream);
+        cudaStreamDestroy(p->copy_stream);
+        p->copy_stream = nullptr;
+    }
+    if (p->stage_free) cudaEventDestroy(p->stage_free);
+    if (p->coef_ready) cudaEventDestroy(p->coef_ready);
+    p->stage_free = p->coef_ready = nullptr;
 }
 
 template <typename C, typename R>
@@ -808,7 +816,10 @@ extern "C" int dfsnufft_interpolate_grid(dfsnufft_plan p, const void *samples, c
     // a real-field plan reads the columns m >= 0 and the Nyquist row only
     int rc = grid_to_coeffs(p, samples, parity, p->d_coef_stage, !p->herm);
     if (rc) return rc;
-    return dfsnufft_execute(p, p->d_coef_stage, values);
+    rc = dfsnufft_execute(p, p->d_coef_stage, values);
+    if (rc) return rc;
+    if (p->copy_stream) DFS_CK(p, cudaEventRecord(p->stage_free, p->stream));
+    return DFSNUFFT_OK;
 }
 
 // ------------------------------------------------------------------ host-buffer variants
@@ -850,25 +861,26 @@ extern "C" int dfsnufft_set_points_host(dfsnufft_plan p, int64_t n_points, const
 // row and column 0 of the next are contiguous, one 2-D copy of N1/2 + 1
 // elements a row takes both, and the first row of each line is copied from
 // column 0 to N1/2.  Other plans copy the whole array.
-static cudaError_t stage_coefficients(dfsnufft_plan p, const void *coeffs, size_t cs) {
+static cudaError_t stage_coefficients(dfsnufft_plan p, const void *coeffs, size_t cs,
+                                      cudaStream_t st) {
     const dfsnufft_params &q = p->prm;
     const size_t rows = (size_t)p->n_members * p->n_fields * q.N2;
     const size_t row = cs * q.N1, half = cs * (q.N1 / 2);
     char *d = static_cast<char *>(p->d_coef_stage);
     const char *h = static_cast<const char *>(coeffs);
     if (!p->herm)
-        return cudaMemcpyAsync(d, h, rows * row, cudaMemcpyHostToDevice, p->stream);
+        return cudaMemcpyAsync(d, h, rows * row, cudaMemcpyHostToDevice, st);
     cudaError_t e = cudaSuccess;
     if (rows > 1)
         e = cudaMemcpy2DAsync(d + half, row, h + half, row, half + cs, rows - 1,
-                              cudaMemcpyHostToDevice, p->stream);
+                              cudaMemcpyHostToDevice, st);
     if (!e)
         e = cudaMemcpyAsync(d + (rows - 1) * row + half, h + (rows - 1) * row + half, half,
-                            cudaMemcpyHostToDevice, p->stream);
+                            cudaMemcpyHostToDevice, st);
     if (!e)
         e = cudaMemcpy2DAsync(d, (size_t)q.N2 * row, h, (size_t)q.N2 * row, half + cs,
                               (size_t)p->n_members * p->n_fields, cudaMemcpyHostToDevice,
-                              p->stream);
+                              st);
     return e;
 }
 
@@ -905,9 +917,22 @@ extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *
         if (rc) return rc;
         p->val_stage_cap = p->cap_points;
     }
-    DFS_CK(p, stage_coefficients(p, coeffs, cs));
+    if (!p->copy_stream) {
+        DFS_CK(p, cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        DFS_CK(p, cudaEventCreateWithFlags(&p->stage_free, cudaEventDisableTiming));
+        DFS_CK(p, cudaEventCreateWithFlags(&p->coef_ready, cudaEventDisableTiming));
+        DFS_CK(p, cudaEventRecord(p->stage_free, p->stream));     // every earlier reader
+    }
+    // the copies wait only for the last reader of the staging buffer, not for
+    // the set_points work queued on the plan's stream, and the transform waits
+    // for the copies
+    DFS_CK(p, cudaStreamWaitEvent(p->copy_stream, p->stage_free, 0));
+    DFS_CK(p, stage_coefficients(p, coeffs, cs, p->copy_stream));
+    DFS_CK(p, cudaEventRecord(p->coef_ready, p->copy_stream));
+    DFS_CK(p, cudaStreamWaitEvent(p->stream, p->coef_ready, 0));
     rc = dfsnufft_execute(p, p->d_coef_stage, p->d_val_stage);
     if (rc) return rc;
+    DFS_CK(p, cudaEventRecord(p->stage_free, p->stream));
     DFS_CK(p, cudaMemcpyAsync(values, p->d_val_stage, vb, cudaMemcpyDeviceToHost, p->stream));
     return dfsnufft_plan_check(p);
 }

@@ -306,8 +306,17 @@ def test_host_execute_real_plan_stages_what_it_reads(torch_cuda, dtype):
         plan.set_points_host(lon, colat)
         host = [plan.execute_host(c) for c in arrays]
         nb = dfsnufft_plan_host_copy_bytes(plan._h)
+        # the staging buffer is shared with interpolate_grid, queued without a
+        # wait: the next host copy must not overtake its reads
+        rd = torch.float64 if dtype == "f64" else torch.float32
+        samples = torch.from_numpy(rng.standard_normal((F, n_lat, n_lon))).to(rd).cuda()
+        from_grid = plan.interpolate_grid(samples, [1, -1, -1])
+        again = plan.execute_host(arrays[0])
+        from_grid_dev = plan.interpolate_grid(samples, [1, -1, -1]).cpu().numpy()
+        assert np.array_equal(from_grid.cpu().numpy(), from_grid_dev)
     for d, h in zip(dev, host):
         assert np.array_equal(d, h)
+    assert np.array_equal(again, dev[0])
     cs = 16 if dtype == "f64" else 8
     rows, half = F * 2 * n_lat, cs * n_lon // 2
     assert nb["coeffs_h2d"] == (rows - 1) * (half + cs) + half + F * (half + cs)
