@@ -227,12 +227,16 @@ cudaError_t dispatch_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 gr
     }
 }
 
+// Four CTAs of 256 threads an SM (at most 64 registers a thread; about 51 KB of
+// shared memory each for rows of 2048): the row loads at the start of each CTA
+// are latency-bound, and the fourth CTA hides more of them than the registers
+// a thread gives up cost (2 us of 64 on the 2048 x 1024 rows).
 template <int LOGM, bool HERM>
 cudaError_t run_phi2(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
     constexpr int E = PhiCfg<float>::E;
-    cudaError_t e = allow_smem(k_phi_pass2<E, 256, 3, LOGM, HERM>, smem);
+    cudaError_t e = allow_smem(k_phi_pass2<E, 256, 4, LOGM, HERM>, smem);
     if (e) return e;
-    k_phi_pass2<E, 256, 3, LOGM, HERM><<<grid, threads, smem, p->stream>>>(
+    k_phi_pass2<E, 256, 4, LOGM, HERM><<<grid, threads, smem, p->stream>>>(
         a, (const float2 *)p->d_T, (const float2 *)p->d_tw1, (const float2 *)p->d_stw_phi,
         p->d_rowrange, (float *)p->d_G);
     return cudaGetLastError();
