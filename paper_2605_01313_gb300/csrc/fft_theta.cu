@@ -182,6 +182,7 @@ struct ThetaTmaArgs {
     unsigned tx_bytes;        // bytes delivered per block
     int tcols, tpitch;        // transformed columns, row pitch of T
     int col_base;             // array column of transformed column 0
+    int prM, prN;             // partial-regularity input: truncation (prM < 0: complex input)
 };
 
 // LOGH > 0: half length 2^LOGH fixed at compile time (unrolled transform);
@@ -192,7 +193,12 @@ struct ThetaTmaArgs {
 // thread has read its inputs (after the transforms' first barrier), so they
 // land while this block is transformed.  Otherwise the halves run one after
 // the other and the next block streams into a second buffer when one fits.
-template <typename R, int E, int CB, int MAXT, int MINB, int LOGH, bool HERM>
+// PRIN (real-field plans): the input is partial-regularity DFS coefficients,
+// lines x (prM + 1) x (prN + 1) complex, whose column m is contiguous; a block's
+// CB columns are staged by 8-byte asynchronous copies of every thread instead of
+// TMA boxes (the columns are not 16-byte aligned), completing on the same
+// mbarrier, and converted on the fly by pr_coef.
+template <typename R, int E, int CB, int MAXT, int MINB, int LOGH, bool HERM, bool PRIN = false>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_theta_tma(ThetaTmaArgs a, const __grid_constant__ CUtensorMap tmap,
                 const typename CxT<R>::type *__restrict__ coef,
@@ -220,15 +226,29 @@ __global__ void __launch_bounds__(MAXT, MINB)
     C *sm1 = ex + (size_t)(CB + c) * region_len<C>(H);      // DUAL: the odd-row transform
     for (int i = threadIdx.x; i < a.N2; i += blockDim.x) f2[i] = inv2[i];
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        // PRIN: every thread arrives once a phase, when its copies have landed
+        mbar_init(&bar[0], PRIN ? blockDim.x : 1);
+        mbar_init(&bar[1], PRIN ? blockDim.x : 1);
         fence_mbar_init();
     }
     __syncthreads();
+    const int prs = a.prN + 1;                     // PRIN: staged elements a column
+    // issued by thread 0 (TMA boxes), or by every thread (PRIN)
     auto issue = [&](int blk, int b) {
         const int f = blk / a.nbq;
         const int qb = blk - f * a.nbq;
         C *dst = inb + (size_t)b * a.in_elems;
+        if constexpr (PRIN) {
+            for (int cc = 0; cc < CB; ++cc) {
+                const int q = qb * CB + cc;
+                if (q > a.prM) break;
+                const C *src = coef + ((size_t)f * (a.prM + 1) + q) * prs;
+                for (int k = threadIdx.x; k < prs; k += blockDim.x)
+                    cp_async_8(dst + (size_t)cc * prs + k, src + k);
+            }
+            cp_async_mbar_arrive_noinc(&bar[b]);
+            return;
+        }
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bar[b], a.tx_bytes);
         const int x = (a.col_base + qb * CB) * (int)(sizeof(C) / 8);
@@ -238,13 +258,14 @@ __global__ void __launch_bounds__(MAXT, MINB)
     };
     uint32_t phase0 = 0, phase1 = 0;
     int it = 0;
-    if (threadIdx.x == 0 && (int)blockIdx.x < a.total) issue(blockIdx.x, 0);
+    const bool issuer = PRIN || threadIdx.x == 0;
+    if (issuer && (int)blockIdx.x < a.total) issue(blockIdx.x, 0);
     for (int blk = blockIdx.x; blk < a.total; blk += gridDim.x, ++it) {
         const int cur = a.nbuf == 2 ? (it & 1) : 0;
         const int nxt = blk + gridDim.x;
         const bool pre = a.nbuf == 2 && nxt < a.total;
-        if (pre && threadIdx.x == 0) issue(nxt, cur ^ 1);
-        if (HERM && threadIdx.x < CB) {
+        if (pre && issuer) issue(nxt, cur ^ 1);
+        if (HERM && !PRIN && threadIdx.x < CB) {
             // conj c_{-N2/2,-m} of each column (the mirror of the Nyquist row),
             // fetched while the block's boxes land
             const int f = blk / a.nbq;
@@ -259,7 +280,10 @@ __global__ void __launch_bounds__(MAXT, MINB)
         else phase0 ^= 1;
         if (__syncthreads_or(!ok)) {
             // give up on this launch; let copies still in flight land first
-            if (threadIdx.x == 0) {
+            if constexpr (PRIN) {
+                cp_async_wait_all();
+                if (threadIdx.x == 0) atomicExch(status, DFS_STATUS_TIMEOUT);
+            } else if (threadIdx.x == 0) {
                 atomicExch(status, DFS_STATUS_TIMEOUT);
                 mbar_wait_bounded(&bar[cur], cur ? phase1 ^ 1 : phase0 ^ 1);
                 if (pre) mbar_wait_bounded(&bar[cur ^ 1], cur ? phase0 : phase1);
@@ -282,6 +306,10 @@ __global__ void __launch_bounds__(MAXT, MINB)
         // h_{n,m} (real-field plans, see herm_coef) or c_{n,m}, deconvolved
         auto coef_nm = [&](int n) -> C {
             const int r = n + half;
+            if constexpr (PRIN) {
+                if (q > a.prM || n > a.prN || n < -a.prN) return cmake((R)0, (R)0);
+                return cscale(pr_coef<C>(n, q, a.prN, in + (size_t)c * prs), sq * f2[r]);
+            }
             C v;
             if constexpr (HERM) {
                 if (k_nyq) {                           // one column per line: global loads
@@ -337,7 +365,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
                 if (row_needed(2 * qq + 1)) dst[(size_t)(2 * qq + 1) * a.tpitch] = z1;
             };
             auto refill = [&]() {
-                if (threadIdx.x == 0 && a.nbuf == 1 && nxt < a.total) issue(nxt, 0);
+                if (issuer && a.nbuf == 1 && nxt < a.total) issue(nxt, 0);
             };
             line_fft_ct2<LOGH, E>(stw, sm, sm1, t, ld2, st2, refill);
             __syncthreads();
@@ -365,7 +393,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
                 else line_fft<E>(a.logh, tw, 1, sm, t, ld, st);
                 __syncthreads();
             }
-            if (a.nbuf == 1 && threadIdx.x == 0 && nxt < a.total) issue(nxt, 0);
+            if (a.nbuf == 1 && issuer && nxt < a.total) issue(nxt, 0);
         }
     }
 }
@@ -386,42 +414,48 @@ template <> struct ThetaCfg<df32> {
     static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, CB = 1, TMAXT = 512, TMINB = 1;
 };
 
-template <typename R, int CB, int LOGH, bool HERM>
+template <typename R, int CB, int LOGH, bool HERM, bool PRIN>
 cudaError_t run_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUtensorMap &tmap,
                           const void *coeffs, size_t smem, int grid, int threads) {
     typedef typename CxT<R>::type C;
     constexpr int E = ThetaCfg<R>::E, MAXT = ThetaCfg<R>::TMAXT, MINB = ThetaCfg<R>::TMINB;
-    cudaError_t e = allow_smem(k_theta_tma<R, E, CB, MAXT, MINB, LOGH, HERM>, smem);
+    cudaError_t e = allow_smem(k_theta_tma<R, E, CB, MAXT, MINB, LOGH, HERM, PRIN>, smem);
     if (e) return e;
-    k_theta_tma<R, E, CB, MAXT, MINB, LOGH, HERM><<<grid, threads, smem, p->stream>>>(
+    k_theta_tma<R, E, CB, MAXT, MINB, LOGH, HERM, PRIN><<<grid, threads, smem, p->stream>>>(
         a, tmap, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2,
         (const C *)p->d_tw2, (const C *)p->d_stw_theta, p->d_rowrange, (C *)p->d_T, p->d_status);
     return cudaGetLastError();
 }
 
-template <typename R, int CB, bool HERM>
+template <typename R, int CB, bool HERM, bool PRIN = false>
 cudaError_t dispatch_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUtensorMap &tmap,
                                const void *coeffs, size_t smem, int grid, int threads) {
     if (!p->d_stw_theta)
-        return run_theta_tma<R, CB, 0, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+        return run_theta_tma<R, CB, 0, HERM, PRIN>(p, a, tmap, coeffs, smem, grid, threads);
     switch (a.logh) {
-        case 9: return run_theta_tma<R, CB, 9, HERM>(p, a, tmap, coeffs, smem, grid, threads);
-        case 10: return run_theta_tma<R, CB, 10, HERM>(p, a, tmap, coeffs, smem, grid, threads);
-        case 11: return run_theta_tma<R, CB, 11, HERM>(p, a, tmap, coeffs, smem, grid, threads);
-        default: return run_theta_tma<R, CB, 0, HERM>(p, a, tmap, coeffs, smem, grid, threads);
+        case 9: return run_theta_tma<R, CB, 9, HERM, PRIN>(p, a, tmap, coeffs, smem, grid, threads);
+        case 10:
+            return run_theta_tma<R, CB, 10, HERM, PRIN>(p, a, tmap, coeffs, smem, grid, threads);
+        case 11:
+            return run_theta_tma<R, CB, 11, HERM, PRIN>(p, a, tmap, coeffs, smem, grid, threads);
+        default: return run_theta_tma<R, CB, 0, HERM, PRIN>(p, a, tmap, coeffs, smem, grid, threads);
     }
 }
 
 // Launch the TMA theta pass with CB columns per block; returns
 // cudaErrorNotSupported (without launching) when the shape or the coefficient
-// pointer does not suit it.
+// pointer does not suit it.  prM >= 0: partial-regularity input (real-field
+// plans), staged by asynchronous 8-byte copies (no tensor map).
 template <typename R, int CB>
-cudaError_t launch_theta_tma_cb(dfsnufft_plan p, const void *coeffs) {
+cudaError_t launch_theta_tma_cb(dfsnufft_plan p, const void *coeffs, int prM, int prN) {
     typedef typename CxT<R>::type C;
     constexpr int E = ThetaCfg<R>::E, MAXT = ThetaCfg<R>::TMAXT, MINB = ThetaCfg<R>::TMINB;
     static_assert(CB * sizeof(C) >= 16, "a TMA box row spans at least 16 bytes");
     const dfsnufft_params &q = p->prm;
-    if (((uintptr_t)coeffs & 15) != 0 || !p->d_status) return cudaErrorNotSupported;
+    const bool pr = prM >= 0;
+    if (pr && (!p->herm || ((uintptr_t)coeffs & (sizeof(C) - 1)) != 0))
+        return cudaErrorNotSupported;
+    if ((!pr && ((uintptr_t)coeffs & 15) != 0) || !p->d_status) return cudaErrorNotSupported;
     const int H = q.n2 / 2;
     if (H < E || CB * (H / E) > MAXT) return cudaErrorNotSupported;
     ThetaTmaArgs a;
@@ -432,6 +466,8 @@ cudaError_t launch_theta_tma_cb(dfsnufft_plan p, const void *coeffs) {
     a.tcols = dfs_tcols(p->herm, q.N1);
     a.tpitch = dfs_tpitch(p->herm, q.N1);
     a.col_base = p->herm ? q.N1 / 2 : 0;
+    a.prM = prM;
+    a.prN = prN;
     // the box's first column must sit on a 16-byte boundary
     if ((a.col_base * sizeof(C)) % 16 != 0) return cudaErrorNotSupported;
     a.nbq = (a.tcols + CB - 1) / CB;
@@ -445,6 +481,7 @@ cudaError_t launch_theta_tma_cb(dfsnufft_plan p, const void *coeffs) {
     a.nbox = (q.N2 + a.box_rows - 1) / a.box_rows;
     a.in_elems = a.nbox * a.box_rows * CB;
     a.tx_bytes = (unsigned)(sizeof(C) * a.in_elems);
+    if (pr && (long long)CB * (prN + 1) > a.in_elems) return cudaErrorNotSupported;
     // compile-time lengths in FP32 run both halves at once (see k_theta_tma)
     const bool dual = sizeof(R) == 4 && p->d_stw_theta && a.logh >= 9 && a.logh <= 11;
     const size_t ex_bytes = sizeof(C) * (size_t)(dual ? 2 : 1) * CB * region_len<C>(H);
@@ -455,25 +492,29 @@ cudaError_t launch_theta_tma_cb(dfsnufft_plan p, const void *coeffs) {
     const size_t smem = 256 + a.nbuf * in_bytes + ex_bytes + f2_bytes;
     if (smem > limit) return cudaErrorNotSupported;
     CUtensorMap tmap;
-    cudaError_t e = dfs_encode_tensor_map_2d(&tmap, coeffs, (uint64_t)q.N1 * (sizeof(C) / 8),
-                                             (uint64_t)q.N2 * lines,
-                                             sizeof(C) * (uint64_t)q.N1,
-                                             (uint32_t)(CB * (sizeof(C) / 8)),
-                                             (uint32_t)a.box_rows);
-    if (e) return e;
+    memset(&tmap, 0, sizeof(tmap));             // unused by the partial-regularity form
+    if (!pr) {
+        cudaError_t e = dfs_encode_tensor_map_2d(&tmap, coeffs, (uint64_t)q.N1 * (sizeof(C) / 8),
+                                                 (uint64_t)q.N2 * lines,
+                                                 sizeof(C) * (uint64_t)q.N1,
+                                                 (uint32_t)(CB * (sizeof(C) / 8)),
+                                                 (uint32_t)a.box_rows);
+        if (e) return e;
+    }
     int grid = (p->num_sms > 0 ? p->num_sms : 1) * MINB;
     if (grid > a.total) grid = a.total;
     const int threads = CB * (H / E);
+    if (pr) return dispatch_theta_tma<R, CB, true, true>(p, a, tmap, coeffs, smem, grid, threads);
     if (p->herm) return dispatch_theta_tma<R, CB, true>(p, a, tmap, coeffs, smem, grid, threads);
     return dispatch_theta_tma<R, CB, false>(p, a, tmap, coeffs, smem, grid, threads);
 }
 
 // The configured block width, else (FP64 columns of 8192 fine rows) one column.
 template <typename R>
-cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs) {
-    cudaError_t e = launch_theta_tma_cb<R, ThetaCfg<R>::CB>(p, coeffs);
+cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs, int prM, int prN) {
+    cudaError_t e = launch_theta_tma_cb<R, ThetaCfg<R>::CB>(p, coeffs, prM, prN);
     if constexpr (sizeof(R) == 8) {
-        if (e == cudaErrorNotSupported) e = launch_theta_tma_cb<R, 1>(p, coeffs);
+        if (e == cudaErrorNotSupported) e = launch_theta_tma_cb<R, 1>(p, coeffs, prM, prN);
     }
     return e;
 }
@@ -504,11 +545,9 @@ template <typename R>
 cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs, int prM, int prN) {
     typedef typename CxT<R>::type C;
     if constexpr (!std::is_same<R, df32>::value) {
-        if (prM < 0) {
-            cudaError_t e = launch_theta_tma<R>(p, coeffs);
-            if (e != cudaErrorNotSupported) return e;
-            cudaGetLastError();
-        }
+        cudaError_t e = launch_theta_tma<R>(p, coeffs, prM, prN);
+        if (e != cudaErrorNotSupported) return e;
+        cudaGetLastError();
     }
     constexpr int MAXT = ThetaCfg<R>::MAXT;
     const dfsnufft_params &q = p->prm;

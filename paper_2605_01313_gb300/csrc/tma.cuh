@@ -89,6 +89,16 @@ __device__ __forceinline__ void cp_async_16(void *smem_dst, const void *gmem_src
                  "l"(gmem_src)
                  : "memory");
 }
+// Arrive on an mbarrier once every cp.async this thread issued before has
+// landed; .noinc: the barrier's expected arrival count already includes it.
+__device__ __forceinline__ void cp_async_mbar_arrive_noinc(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// Wait until every cp.async this thread issued has landed (committed or not).
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
