@@ -49,6 +49,8 @@ struct dfsnufft_plan_s {
                             // and phi passes, fine grid as (hi, lo) pairs, interpolation
     void *d_df_tw1, *d_df_tw2;      // double-single twiddles (n1, n2 complex)
     void *d_df_inv1, *d_df_inv2;    // double-single deconvolution factors (N1, N2)
+    void *d_df_stw_phi;             // double-single stage-ordered twiddles (length n1/2)
+    void *d_df_stw_theta;           // and (length n2) for the theta pass
     int nbx, nby, nbins;    // interpolation bins
     int bstride;            // per-member stride of the bin arrays: >= nbins + 1, multiple of 4
     int cstride;            // per-member stride of d_bin_count: bstride + the scan workspace

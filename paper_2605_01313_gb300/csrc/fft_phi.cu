@@ -199,7 +199,7 @@ cudaError_t run_phi_df(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid
     const bool dfr = std::is_same<R, df32>::value;     // double-single tables
     k_phi_pass<R, E, MAXT, MINB, LOGM, HERM, DF><<<grid, threads, smem, p->stream>>>(
         a, (const C *)p->d_T, (const C *)(dfr ? p->d_df_tw1 : p->d_tw1),
-        (const C *)(dfr ? nullptr : p->d_stw_phi), p->d_rowrange, (R *)p->d_G);
+        (const C *)(dfr ? p->d_df_stw_phi : p->d_stw_phi), p->d_rowrange, (R *)p->d_G);
     return cudaGetLastError();
 }
 
@@ -216,8 +216,9 @@ template <typename R, bool HERM>
 cudaError_t dispatch_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
     constexpr int MAXT = PhiCfg<R>::MAXT, MINB = PhiCfg<R>::MINB, MAXTW = PhiCfg<R>::MAXTW;
     if (threads > MAXT) return run_phi<R, MAXTW, 1, 0, HERM>(p, a, smem, grid, threads);
-    // double-single: the run-time-length transform (no stage-ordered tables)
-    if (!p->d_stw_phi || std::is_same<R, df32>::value)
+    // compile-time lengths need the plan's stage-ordered table (double-single
+    // for df32)
+    if (std::is_same<R, df32>::value ? !p->d_df_stw_phi : !p->d_stw_phi)
         return run_phi<R, MAXT, MINB, 0, HERM>(p, a, smem, grid, threads);
     switch (a.logm) {
         case 9: return run_phi<R, MAXT, MINB, 9, HERM>(p, a, smem, grid, threads);

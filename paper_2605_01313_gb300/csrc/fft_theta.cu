@@ -120,12 +120,14 @@ struct ThetaArgs {
 // grid (ceil(tcols / CB), lines); block CB * n2/E threads, thread = (t, c) with c fastest.
 // PRIN (real-field plans): the input is partial-regularity DFS coefficients,
 // lines x (prM + 1) x (prN + 1) complex, converted on the fly by pr_coef.
+// LOGN > 0: length n2 = 2^LOGN at compile time with the stage-ordered table stw.
 template <typename R, int E, int MAXT, int MINB, bool HERM, bool PRIN = false,
-          typename CIn = typename CxT<R>::type>
+          typename CIn = typename CxT<R>::type, int LOGN = 0>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_theta_pass(ThetaArgs a, const CIn *__restrict__ coef,
                  const R *__restrict__ inv1, const R *__restrict__ inv2,
                  const typename CxT<R>::type *__restrict__ tw,
+                 const typename CxT<R>::type *__restrict__ stw,
                  const int2 *__restrict__ rowrange, typename CxT<R>::type *__restrict__ out) {
     typedef typename CxT<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -168,7 +170,8 @@ __global__ void __launch_bounds__(MAXT, MINB)
     auto st = [&](int i, C v) {
         if (col_ok && ((i - rr.x) & (a.n2 - 1)) < rr.y) dst[(size_t)i * a.tpitch] = v;
     };
-    line_fft<E>(a.logn2, tw, 0, sm, t, ld, st);
+    if constexpr (LOGN > 0) line_fft_ct<LOGN, E>(stw, sm, t, ld, st);
+    else line_fft<E>(a.logn2, tw, 0, sm, t, ld, st);
 }
 
 struct ThetaTmaArgs {
@@ -519,24 +522,47 @@ cudaError_t launch_theta_tma(dfsnufft_plan p, const void *coeffs, int prM, int p
     return e;
 }
 
+template <typename R, int E, int MAXT, int MINB, bool HERM, bool PRIN, int LOGN>
+cudaError_t run_theta_df(dfsnufft_plan p, const ThetaArgs &a, const void *coeffs, size_t smem,
+                         dim3 grid, int threads) {
+    typedef typename CxT<R>::type C;
+    cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM, PRIN, double2, LOGN>, smem);
+    if (e) return e;
+    k_theta_pass<R, E, MAXT, MINB, HERM, PRIN, double2, LOGN><<<grid, threads, smem, p->stream>>>(
+        a, (const double2 *)coeffs, (const R *)p->d_df_inv1, (const R *)p->d_df_inv2,
+        (const C *)p->d_df_tw2, (const C *)p->d_df_stw_theta, p->d_rowrange, (C *)p->d_T);
+    return cudaGetLastError();
+}
+
 template <typename R, int E, bool HERM, bool PRIN = false>
 cudaError_t run_theta_plain(dfsnufft_plan p, const ThetaArgs &a, const void *coeffs, size_t smem,
                             dim3 grid, int threads) {
     typedef typename CxT<R>::type C;
     constexpr int MAXT = ThetaCfg<R>::MAXT, MINB = ThetaCfg<R>::MINB;
     if constexpr (std::is_same<R, df32>::value) {
-        // FP64 coefficients, double-single factors and twiddles
-        cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM, PRIN, double2>, smem);
-        if (e) return e;
-        k_theta_pass<R, E, MAXT, MINB, HERM, PRIN, double2><<<grid, threads, smem, p->stream>>>(
-            a, (const double2 *)coeffs, (const R *)p->d_df_inv1, (const R *)p->d_df_inv2,
-            (const C *)p->d_df_tw2, p->d_rowrange, (C *)p->d_T);
+        // FP64 coefficients, double-single factors and twiddles; lengths 2^10 ..
+        // 2^12 at compile time with the double-single stage-ordered table
+        if constexpr (E == DFS_FFT_E) {
+            switch (p->d_df_stw_theta ? a.logn2 : 0) {
+                case 10:
+                    return run_theta_df<R, E, MAXT, MINB, HERM, PRIN, 10>(p, a, coeffs, smem,
+                                                                          grid, threads);
+                case 11:
+                    return run_theta_df<R, E, MAXT, MINB, HERM, PRIN, 11>(p, a, coeffs, smem,
+                                                                          grid, threads);
+                case 12:
+                    return run_theta_df<R, E, MAXT, MINB, HERM, PRIN, 12>(p, a, coeffs, smem,
+                                                                          grid, threads);
+                default: break;
+            }
+        }
+        return run_theta_df<R, E, MAXT, MINB, HERM, PRIN, 0>(p, a, coeffs, smem, grid, threads);
     } else {
         cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM, PRIN>, smem);
         if (e) return e;
         k_theta_pass<R, E, MAXT, MINB, HERM, PRIN><<<grid, threads, smem, p->stream>>>(
             a, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2,
-            (const C *)p->d_tw2, p->d_rowrange, (C *)p->d_T);
+            (const C *)p->d_tw2, nullptr, p->d_rowrange, (C *)p->d_T);
     }
     return cudaGetLastError();
 }

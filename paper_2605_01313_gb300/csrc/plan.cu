@@ -323,7 +323,8 @@ static void release(dfsnufft_plan p) {
                      (void **)&p->d_pofs,
                      (void **)&p->d_rank, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
                      (void **)&p->d_pts_stage, &p->d_coef_stage, &p->d_val_stage,
-                     &p->d_df_tw1, &p->d_df_tw2, &p->d_df_inv1, &p->d_df_inv2};
+                     &p->d_df_tw1, &p->d_df_tw2, &p->d_df_inv1, &p->d_df_inv2,
+                     &p->d_df_stw_phi, &p->d_df_stw_theta};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) dfs_free(bufs[i]);
     free(p->h_pofs);
     p->h_pofs = nullptr;
@@ -445,6 +446,30 @@ static int upload_df_tables(dfsnufft_plan p) {
     }
     free(d);
     free(f);
+    // the stage-ordered twiddles of the phi pass's length-n1/2 transform and of
+    // the theta pass's length-n2 one
+    struct { void **ptr; int n; } stabs[] = {{&p->d_df_stw_phi, q.n1 / 2},
+                                             {&p->d_df_stw_theta, q.n2}};
+    for (int k = 0; rc == DFSNUFFT_OK && k < 2; ++k) {
+        int logn = 0;
+        while ((1 << logn) < stabs[k].n) ++logn;
+        const size_t sz = (size_t)stage_table_len(stabs[k].n);
+        double2 *h = (double2 *)calloc(sz, sizeof(double2));
+        float *hf = (float *)malloc(sizeof(float) * 4 * sz);
+        rc = (h && hf) ? DFSNUFFT_OK : DFSNUFFT_ERR_OOM;
+        if (rc == DFSNUFFT_OK) {
+            fill_stage_twiddles<double2, double>(h, logn, DFS_FFT_E);
+            split_table(reinterpret_cast<const double *>(h), hf, 2 * sz);
+            rc = dfs_alloc(p, stabs[k].ptr, sizeof(float) * 4 * sz, "double-single tables");
+        }
+        if (rc == DFSNUFFT_OK) {
+            const cudaError_t e = cudaMemcpy(*stabs[k].ptr, hf, sizeof(float) * 4 * sz,
+                                             cudaMemcpyHostToDevice);
+            if (e) rc = fail_cuda(p, "upload double-single tables", e);
+        }
+        free(h);
+        free(hf);
+    }
     return rc;
 }
 
