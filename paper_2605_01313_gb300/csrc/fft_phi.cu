@@ -177,17 +177,20 @@ __global__ void __launch_bounds__(MAXT, MINB)
 }
 
 // Per precision: elements per thread E, threads per CTA at most MAXT with MINB
-// resident CTAs; rows longer than E x MAXT complex values (FP32 fine grids of
-// 8192 columns) use the wide form of MAXTW threads.
+// resident CTAs (MINBH for the rows of real-field plans); rows longer than
+// E x MAXT complex values (FP32 fine grids of 8192 columns) use the wide form of
+// MAXTW threads.  Double-single rows of real-field plans fit 64 registers a
+// thread without spills, so two CTAs share an SM (C3 FP64 phi pass 305 -> 256
+// us); the general rows would spill there and keep one.
 template <typename R> struct PhiCfg;
 template <> struct PhiCfg<float> {
-    static const int E = DFS_FFT_E, MAXT = 256, MINB = 3, MAXTW = 512;
+    static const int E = DFS_FFT_E, MAXT = 256, MINB = 3, MINBH = 3, MAXTW = 512;
 };
 template <> struct PhiCfg<double> {
-    static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, MAXTW = 512;
+    static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, MINBH = 1, MAXTW = 512;
 };
 template <> struct PhiCfg<df32> {
-    static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, MAXTW = 512;
+    static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, MINBH = 2, MAXTW = 512;
 };
 
 template <typename R, int MAXT, int MINB, int LOGM, bool HERM, bool DF>
@@ -214,7 +217,8 @@ cudaError_t run_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, i
 
 template <typename R, bool HERM>
 cudaError_t dispatch_phi(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, int threads) {
-    constexpr int MAXT = PhiCfg<R>::MAXT, MINB = PhiCfg<R>::MINB, MAXTW = PhiCfg<R>::MAXTW;
+    constexpr int MAXT = PhiCfg<R>::MAXT, MAXTW = PhiCfg<R>::MAXTW;
+    constexpr int MINB = HERM ? PhiCfg<R>::MINBH : PhiCfg<R>::MINB;
     if (threads > MAXT) return run_phi<R, MAXTW, 1, 0, HERM>(p, a, smem, grid, threads);
     // compile-time lengths need the plan's stage-ordered table (double-single
     // for df32)

@@ -413,8 +413,12 @@ template <> struct ThetaCfg<float> {
 template <> struct ThetaCfg<double> {
     static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, CB = 2, TMAXT = 512, TMINB = 1;
 };
+// Double-single: two CTAs of one column each per SM (64 registers a thread, a
+// few bytes spilled; 70 KB of shared memory each), which hides the latency of
+// the strided coefficient loads better than one CTA at 101 registers (C3 FP64
+// theta pass 413 -> 342 us).
 template <> struct ThetaCfg<df32> {
-    static const int E = DFS_FFT_E, MAXT = 512, MINB = 1, CB = 1, TMAXT = 512, TMINB = 1;
+    static const int E = DFS_FFT_E, MAXT = 512, MINB = 2, CB = 1, TMAXT = 512, TMINB = 1;
 };
 
 template <typename R, int CB, int LOGH, bool HERM, bool PRIN>
