@@ -208,3 +208,15 @@ def test_departure_and_rotation_argument_errors(lib):
                None) == nufft.ERR_INVALID_ARG                       # odd n_lon
     assert rot(8, 4, 1, 1, None, None, dummy, None, dummy, 32, dummy, dummy,
                None) == nufft.ERR_INVALID_ARG                       # no u
+
+
+def test_host_copy_bytes_argument_errors(lib):
+    """A null plan or output pointer is rejected without touching a GPU."""
+    out = [ctypes.c_int64() for _ in range(3)]
+    refs = [ctypes.byref(o) for o in out]
+    assert lib.dfsnufft_plan_host_copy_bytes(None, *refs) == nufft.ERR_INVALID_ARG
+    dummy = ctypes.c_void_p(16)
+    for k in range(3):
+        args = list(refs)
+        args[k] = None
+        assert lib.dfsnufft_plan_host_copy_bytes(dummy, *args) == nufft.ERR_INVALID_ARG
