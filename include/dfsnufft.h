@@ -13,9 +13,13 @@
  * n_lon = 2J) the coefficient array is N2 x N1 = (2 n_lat) x n_lon.
  *
  * Method: exponential-of-semicircle spreading kernel of width w and shape
- * beta (w = ceil(log10(1/tol)) + 1, beta = 2.30 w), oversampling sigma >= 2
- * to power-of-two fine sizes; deconvolve-and-pad, 2-D inverse FFT (sign +1),
- * then a w x w interpolation at each point from the fine grid.
+ * beta = 2.30 w, oversampling sigma >= 2 to power-of-two fine sizes;
+ * deconvolve-and-pad, 2-D inverse FFT (sign +1), then a w x w interpolation
+ * at each point from the fine grid.  w is the narrowest width whose modelled
+ * 1-D interpolation error is at most 2.5 tol (F64) or 5 tol (F32), so that
+ * even a lone mode at the corner of the band (the worst band-limited input)
+ * stays within half of the accepted relative error, 10 tol (F64) or 20 tol
+ * (F32): w = 14 at tol 1e-12, 16 at 1e-14, 7 at 1e-6.
  *
  * Conventions common to every entry point
  *  - Coefficients: n_fields x N2 x N1 complex, C-contiguous, interleaved
@@ -59,7 +63,7 @@ enum { DFSNUFFT_F64 = 0, DFSNUFFT_F32 = 1 };
 enum {
     DFSNUFFT_OK = 0,
     DFSNUFFT_ERR_INVALID_ARG = 1,      /* bad size, dtype, null pointer, odd dims   */
-    DFSNUFFT_ERR_TOL_UNATTAINABLE = 2, /* tol below 1e-15 (F64) or 1e-7 (F32)       */
+    DFSNUFFT_ERR_TOL_UNATTAINABLE = 2, /* tol below 1e-14 (F64) or 1e-7 (F32)       */
     DFSNUFFT_ERR_NO_POINTS = 3,        /* execute before set_points                 */
     DFSNUFFT_ERR_OOM = 4,              /* device allocation failed                  */
     DFSNUFFT_ERR_CUDA = 5,             /* a CUDA call failed (sticky per plan)      */
@@ -140,7 +144,7 @@ int dfsnufft_choose_params_opts(int n_lon, int n_lat, double tol, int dtype,
 
 /* Create a plan for an n_lat x n_lon grid.
  *   n_lon : even, >= 4; N1 = n_lon phi-modes.  n_lat >= 2; N2 = 2 n_lat.
- *   tol   : requested relative accuracy, 1e-15 <= tol < 1 (F64),
+ *   tol   : requested relative accuracy, 1e-14 <= tol < 1 (F64),
  *           1e-7 <= tol < 1 (F32).
  *   dtype : DFSNUFFT_F64 or DFSNUFFT_F32.
  *   n_fields : fields evaluated per execute at the same points (>= 1).
@@ -528,12 +532,13 @@ int dfsnufft_autotune(const dfsnufft_tune_args *args, dfsnufft_tune_result *resu
  *     (cudaGetSymbolAddress, which may load the module); make that first call
  *     before any stream capture on that device.
  *   - Every call on a device shares the same scratch, which keeps the last
- *     call's contents (the kernel tables are reused when the grid, tolerance
- *     and precision repeat; counters are cleared on every call).  Calls that
- *     overlap on the GPU (other streams, other host threads) race on it:
- *     order them on one stream or synchronise between them.
- *   - Kernel tables are uploaded from host memory with cudaMemcpyAsync when
- *     the configuration changes. */
+ *     call's contents.  Each call first rewrites what it reads there (its point
+ *     offsets, deconvolution factors and twiddles, by one small kernel whose
+ *     arguments carry them; counters are cleared before counting), so no
+ *     result depends on an earlier call, and no host memory is read after the
+ *     call returns.  Calls that overlap on the GPU (other streams, other host
+ *     threads) race on the scratch: order them on one stream or synchronise
+ *     between them. */
 int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dtype, int n_fields,
                              int64_t n_points, const double *lon, const double *colat,
                              const void *coeffs, void *values, void *stream);

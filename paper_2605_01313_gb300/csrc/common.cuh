@@ -51,6 +51,7 @@ struct dfsnufft_plan_s {
     void *d_df_inv1, *d_df_inv2;    // double-single deconvolution factors (N1, N2)
     void *d_df_stw_phi;             // double-single stage-ordered twiddles (length n1/2)
     void *d_df_stw_theta;           // and (length n2) for the theta pass
+    int *d_emax;                    // per line: largest coefficient exponent (df32.cuh scaling)
     int nbx, nby, nbins;    // interpolation bins
     int bstride;            // per-member stride of the bin arrays: >= nbins + 1, multiple of 4
     int cstride;            // per-member stride of d_bin_count: bstride + the scan workspace

@@ -122,4 +122,40 @@ __device__ __forceinline__ dfc to_dfc(double2 v) {
     return dfc{split_double(v.x), split_double(v.y)};
 }
 
+// Exponent scaling of the double-single passes.  FP32 covers 2^-126 .. 2^128
+// and split_double keeps a low part only inside [2^-100, 2^100), while a
+// caller's FP64 coefficients may sit anywhere in FP64's range.  So every line
+// (member x field) is carried as c 2^-s, with s = emax - 1023 and emax the
+// largest biased FP64 exponent among the coefficients the theta pass reads:
+// the largest coefficient then lies in [1, 2) whatever the caller's units, and
+// the interpolated values are multiplied back by 2^s.  Both scalings are exact
+// (powers of two), so a field and the same field times 2^k give values that
+// differ by exactly 2^k.  A line of zeros or subnormals (emax = 0), or one
+// holding a non-finite value (emax = 0x7ff), keeps s = 0.
+__device__ __forceinline__ int df_line_shift(int emax) {
+    return (emax <= 0 || emax >= 0x7ff) ? 0 : emax - 1023;
+}
+
+// v 2^-s: the exponent field lowered by integer arithmetic when the result is
+// a normal number (every value within 2^1022 of the line's largest), else a
+// multiplication by the power of two (zeros, subnormals, non-finite values and
+// results below the normal range).  s in [-1022, 1023].
+__device__ __forceinline__ double df_scale_down(double v, int s) {
+    const long long b = __double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e >= 1 && e < 0x7ff && e - s >= 1 && e - s < 0x7ff)
+        return __longlong_as_double(b - ((long long)s << 52));
+    return scalbn(v, -s);
+}
+
+// 2^s as a double, s in [-1022, 1023].
+__device__ __forceinline__ double df_pow2(int s) {
+    return __longlong_as_double((long long)(s + 1023) << 52);
+}
+
+// A complex FP64 coefficient of a line with shift s, as double-single.
+__device__ __forceinline__ dfc to_dfc_scaled(double2 v, int s) {
+    return dfc{split_double(df_scale_down(v.x, s)), split_double(df_scale_down(v.y, s))};
+}
+
 template <> struct CxT<df32> { typedef dfc type; };

@@ -38,9 +38,12 @@ namespace {
 
 template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake(a.x, -a.y); }
 // A coefficient as the pass's complex type: itself, or (double-single passes of
-// FP64 plans) the FP64 value split into double-single parts.
-template <typename C, typename CIn> __device__ __forceinline__ C in_value(CIn v) { return v; }
-template <> __device__ __forceinline__ dfc in_value<dfc, double2>(double2 v) { return to_dfc(v); }
+// FP64 plans) the FP64 value times 2^-sh (the line's exponent shift, df32.cuh)
+// split into double-single parts.
+template <typename C, typename CIn> __device__ __forceinline__ C in_value(CIn v, int) { return v; }
+template <> __device__ __forceinline__ dfc in_value<dfc, double2>(double2 v, int sh) {
+    return to_dfc_scaled(v, sh);
+}
 template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) {
     return cmake(a.x * s, a.y * s);
 }
@@ -74,17 +77,18 @@ __device__ __forceinline__ C herm_coef(int n, int k, int half, int N1, Rd &cf) {
 // -sign(n) i conj(S)/4 (odd m).  The stencils are linear with real weights, so
 // they act on the cosine and sine parts at once.
 template <typename C, typename CIn>
-__device__ __forceinline__ C pr_coef(int n, int m, int N, const CIn *__restrict__ col) {
+__device__ __forceinline__ C pr_coef(int n, int m, int N, const CIn *__restrict__ col,
+                                     int sh = 0) {
     typedef decltype(C().x) R;
     const int na = n < 0 ? -n : n;
     // f_{k,m} on the case's index range, zero elsewhere
     auto f = [&](int k, int lo, int hi) -> C {
-        return (k >= lo && k <= hi) ? in_value<C>(col[k]) : cmake((R)0, (R)0);
+        return (k >= lo && k <= hi) ? in_value<C>(col[k], sh) : cmake((R)0, (R)0);
     };
     C S;
     if (m == 0) {
         if (na > N) return cmake((R)0, (R)0);
-        const R v = in_value<C>(col[na]).x;                // no sine part at m = 0
+        const R v = in_value<C>(col[na], sh).x;            // no sine part at m = 0
         return cmake(na == 0 ? v : (R)0.5 * v, (R)0);
     } else if (m == 1) {
         if (na == 0) return cmake((R)0, (R)0);
@@ -109,6 +113,40 @@ __device__ __forceinline__ C pr_coef(int n, int m, int N, const CIn *__restrict_
     return cmake(-g * cs.y, g * cs.x);
 }
 
+// Largest biased FP64 exponent of each line's coefficients (emax[line], zeroed
+// before the launch; the double-single passes scale the line by it, df32.cuh),
+// over the entries the theta pass reads: the whole N2 x N1 array (general
+// plans), the Nyquist column 0 and the columns m >= 0 (array columns
+// N1/2 .. N1-1) of every row plus the rest of the Nyquist row 0 (real-field
+// plans), or all line_elems entries (partial-regularity input).  grid
+// (blocks, lines).
+__global__ void __launch_bounds__(256) k_coef_maxexp(const double2 *__restrict__ coef,
+                                                     int line_elems, int rows, int N1, int herm,
+                                                     int *__restrict__ emax) {
+    const double2 *c = coef + (size_t)blockIdx.y * line_elems;
+    const int K = N1 / 2 + 1;
+    const int n = herm ? rows * K + (N1 / 2 - 1) : line_elems;
+    unsigned m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int off = i;
+        if (herm) {
+            if (i < rows * K) {
+                const int r = i / K;
+                const int j = i - r * K;
+                off = r * N1 + (j == 0 ? 0 : N1 / 2 - 1 + j);
+            } else {
+                off = i - rows * K + 1;                  // row 0, columns 1 .. N1/2 - 1
+            }
+        }
+        const double2 v = c[off];
+        const unsigned ex = (unsigned)(__double_as_longlong(v.x) >> 52) & 0x7ffu;
+        const unsigned ey = (unsigned)(__double_as_longlong(v.y) >> 52) & 0x7ffu;
+        m = max(m, max(ex, ey));
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&emax[blockIdx.y], (int)m);
+}
+
 struct ThetaArgs {
     int N1, N2, n2, logn2;
     int CB;                   // columns per CTA
@@ -121,6 +159,8 @@ struct ThetaArgs {
 // PRIN (real-field plans): the input is partial-regularity DFS coefficients,
 // lines x (prM + 1) x (prN + 1) complex, converted on the fly by pr_coef.
 // LOGN > 0: length n2 = 2^LOGN at compile time with the stage-ordered table stw.
+// emax (double-single passes): each line's largest coefficient exponent, from
+// k_coef_maxexp; the line is transformed at the scale of df_line_shift.
 template <typename R, int E, int MAXT, int MINB, bool HERM, bool PRIN = false,
           typename CIn = typename CxT<R>::type, int LOGN = 0>
 __global__ void __launch_bounds__(MAXT, MINB)
@@ -128,7 +168,8 @@ __global__ void __launch_bounds__(MAXT, MINB)
                  const R *__restrict__ inv1, const R *__restrict__ inv2,
                  const typename CxT<R>::type *__restrict__ tw,
                  const typename CxT<R>::type *__restrict__ stw,
-                 const int2 *__restrict__ rowrange, typename CxT<R>::type *__restrict__ out) {
+                 const int2 *__restrict__ rowrange, typename CxT<R>::type *__restrict__ out,
+                 const int *__restrict__ emax) {
     typedef typename CxT<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *smem = reinterpret_cast<C *>(smem_raw);
@@ -144,8 +185,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int qa = HERM ? a.N1 / 2 + q : q;        // array column
     const R sq = col_ok ? inv1[qa < a.N1 ? qa : 0] : (R)0;
     C *sm = smem + (size_t)c * region_len<C>(a.n2);
+    const int sh = emax ? df_line_shift(emax[f]) : 0;
     auto cf = [&](int r, int col) -> C {
-        return (r < a.N2 && col < a.N1) ? in_value<C>(cf0[(size_t)r * a.N1 + col])
+        return (r < a.N2 && col < a.N1) ? in_value<C>(cf0[(size_t)r * a.N1 + col], sh)
                                         : cmake((R)0, (R)0);
     };
     auto ld = [&](int i) -> C {
@@ -160,7 +202,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
         if constexpr (PRIN) {
             if (q > a.prM || n > a.prN || n < -a.prN) return cmake((R)0, (R)0);
             const CIn *col = coef + ((size_t)f * (a.prM + 1) + q) * (a.prN + 1);
-            return cscale(pr_coef<C>(n, q, a.prN, col), s);
+            return cscale(pr_coef<C>(n, q, a.prN, col, sh), s);
         } else if constexpr (HERM) {
             return cscale(herm_coef<C>(n, q, half, a.N1, cf), s);
         } else {
@@ -534,7 +576,8 @@ cudaError_t run_theta_df(dfsnufft_plan p, const ThetaArgs &a, const void *coeffs
     if (e) return e;
     k_theta_pass<R, E, MAXT, MINB, HERM, PRIN, double2, LOGN><<<grid, threads, smem, p->stream>>>(
         a, (const double2 *)coeffs, (const R *)p->d_df_inv1, (const R *)p->d_df_inv2,
-        (const C *)p->d_df_tw2, (const C *)p->d_df_stw_theta, p->d_rowrange, (C *)p->d_T);
+        (const C *)p->d_df_tw2, (const C *)p->d_df_stw_theta, p->d_rowrange, (C *)p->d_T,
+        p->d_emax);
     return cudaGetLastError();
 }
 
@@ -566,7 +609,7 @@ cudaError_t run_theta_plain(dfsnufft_plan p, const ThetaArgs &a, const void *coe
         if (e) return e;
         k_theta_pass<R, E, MAXT, MINB, HERM, PRIN><<<grid, threads, smem, p->stream>>>(
             a, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2,
-            (const C *)p->d_tw2, nullptr, p->d_rowrange, (C *)p->d_T);
+            (const C *)p->d_tw2, nullptr, p->d_rowrange, (C *)p->d_T, nullptr);
     }
     return cudaGetLastError();
 }
@@ -620,8 +663,29 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs, int prM, int prN) 
 
 }  // namespace
 
+// Each line's exponent maximum for the double-single passes (k_coef_maxexp).
+static cudaError_t launch_coef_maxexp(dfsnufft_plan p, const void *coeffs, int prM, int prN) {
+    const dfsnufft_params &q = p->prm;
+    const int lines = p->n_members * p->n_fields;
+    cudaError_t e = cudaMemsetAsync(p->d_emax, 0, sizeof(int) * lines, p->stream);
+    if (e) return e;
+    const bool pr = prM >= 0;
+    const int line_elems = pr ? (prM + 1) * (prN + 1) : q.N2 * q.N1;
+    const int herm = (!pr && p->herm) ? 1 : 0;
+    const int n = herm ? q.N2 * (q.N1 / 2 + 1) + q.N1 / 2 - 1 : line_elems;
+    int blocks = (n + 2047) / 2048;
+    if (blocks > 1024) blocks = 1024;
+    k_coef_maxexp<<<dim3(blocks, lines), 256, 0, p->stream>>>(
+        (const double2 *)coeffs, line_elems, q.N2, q.N1, herm, p->d_emax);
+    return cudaGetLastError();
+}
+
 cudaError_t dfs_launch_theta_pass(dfsnufft_plan p, const void *coeffs, int prM, int prN) {
-    if (p->gdf) return launch_theta<df32>(p, coeffs, prM, prN);   // FP64 in double-single
+    if (p->gdf) {                                  // FP64 in double-single
+        cudaError_t e = launch_coef_maxexp(p, coeffs, prM, prN);
+        if (e) return e;
+        return launch_theta<df32>(p, coeffs, prM, prN);
+    }
     return p->prm.dtype == DFSNUFFT_F64 ? launch_theta<double>(p, coeffs, prM, prN)
                                         : launch_theta<float>(p, coeffs, prM, prN);
 }

@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(256) k_interp_df(InterpArgs a,
                                                    const int *__restrict__ task_all,
                                                    const int *__restrict__ n_tasks,
                                                    const int *__restrict__ pofs,
-                                                   double *__restrict__ out_all) {
+                                                   double *__restrict__ out_all,
+                                                   const int *__restrict__ emax) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);
     const int TH = a.tile_y + W - 1;
@@ -264,11 +265,13 @@ __global__ void __launch_bounds__(256) k_interp_df(InterpArgs a,
                     row(bb, wlo);
                     if (W - 1 - bb != bb) row(W - 1 - bb, whi);
                 }
+                // back to the caller's scale: the line was carried as c 2^-s
 #pragma unroll
                 for (int ff = 0; ff < DFS_DF_FG; ++ff)
                     if (ff < fg)
                         out_all[(size_t)a.F * p0 + (size_t)(f0 + ff) * Pk + dst] =
-                            (double)r2[ff] + (double)c2[ff];
+                            ((double)r2[ff] + (double)c2[ff]) *
+                            df_pow2(df_line_shift(emax[k * a.F + f0 + ff]));
             }
         }
     }
@@ -864,7 +867,8 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
             if (e) return e;
             k_interp_df<W><<<dim3(per, M), 256, smem_df, p->stream>>>(
                 a, hd, (const float2 *)p->d_G, p->d_base, (const double *)p->d_frac, p->d_idx,
-                p->d_bin_start, p->d_task_bin, p->d_n_tasks, p->d_pofs, (double *)values);
+                p->d_bin_start, p->d_task_bin, p->d_n_tasks, p->d_pofs, (double *)values,
+                p->d_emax);
             return cudaGetLastError();
         }
     }

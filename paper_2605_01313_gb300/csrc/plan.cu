@@ -146,15 +146,9 @@ extern "C" int dfsnufft_kernel_ft(int w, double beta, int n_fine, int n_modes, d
     //            = w int_0^{pi/2} e^{beta (cos s - 1)} cos(xi (w/2) sin s) cos s ds   (u = sin s)
     // The substitution removes the square-root endpoint singularity, so the
     // Gauss-Legendre rule converges exponentially.
-    const int q = 2 * w + 60;
-    double *x = (double *)malloc(sizeof(double) * q);
-    double *wt = (double *)malloc(sizeof(double) * q);
-    double *fz = (double *)malloc(sizeof(double) * q);
-    double *zz = (double *)malloc(sizeof(double) * q);
-    if (!x || !wt || !fz || !zz) {
-        free(x); free(wt); free(fz); free(zz);
-        return DFSNUFFT_ERR_INVALID_ARG;
-    }
+    // (no allocation: the allocation-free entry point calls this too)
+    const int q = 2 * w + 60;                          // <= 92 nodes
+    double x[92], wt[92], fz[92], zz[92];
     gauss_legendre(q, x, wt);
     for (int i = 0; i < q; ++i) {
         double sv = 0.25 * kPi * (x[i] + 1.0);  // node mapped to [0, pi/2]
@@ -168,7 +162,6 @@ extern "C" int dfsnufft_kernel_ft(int w, double beta, int n_fine, int n_modes, d
         for (int i = 0; i < q; ++i) acc += fz[i] * cos(xi * zz[i]);
         out[qi] = w * acc;
     }
-    free(x); free(wt); free(fz); free(zz);
     return DFSNUFFT_OK;
 }
 
@@ -249,12 +242,17 @@ extern "C" int dfsnufft_choose_params_opts(int n_lon, int n_lat, double tol, int
     if ((o.tile_x != 0 && !pow2_in(o.tile_x, 8, 128)) ||
         (o.tile_y != 0 && !pow2_in(o.tile_y, 8, 128)))
         return DFSNUFFT_ERR_INVALID_ARG;
-    if (dtype == DFSNUFFT_F64 && tol < 1e-15) return DFSNUFFT_ERR_TOL_UNATTAINABLE;
+    if (dtype == DFSNUFFT_F64 && tol < 1e-14) return DFSNUFFT_ERR_TOL_UNATTAINABLE;
     if (dtype == DFSNUFFT_F32 && tol < 1e-7) return DFSNUFFT_ERR_TOL_UNATTAINABLE;
-    // sigma 2: w = ceil(log10(1/tol)) + 1, beta = 2.30 w
-    int w = (int)ceil(-log10(tol) - 1e-9) + 1;
-    if (w < 2) w = 2;
-    if (w > 16) w = 16;
+    // sigma 2, beta = 2.30 w: the narrowest w whose modelled 1-D error kErr2[w]
+    // is at most 2.5 tol (FP64) or 5 tol (FP32).  A lone mode at the corner of
+    // the band carries the 1-D band-edge error in both dimensions, about
+    // 2 kErr2[w], which this keeps at half of the accepted relative error
+    // (10 tol in FP64, 20 tol in FP32).  w = 14 at tol 1e-12 (13 would leave
+    // such a mode at about 1.4e-11), 7 at tol 1e-6.
+    const double wfac = dtype == DFSNUFFT_F64 ? 2.5 : 5.0;
+    int w = 2;
+    while (w < 16 && kErr2[w] > wfac * tol) ++w;
     double beta = 2.30 * w;
     if (sigma == 4) {
         int w4 = 2;
@@ -324,7 +322,7 @@ static void release(dfsnufft_plan p) {
                      (void **)&p->d_rank, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
                      (void **)&p->d_pts_stage, &p->d_coef_stage, &p->d_val_stage,
                      &p->d_df_tw1, &p->d_df_tw2, &p->d_df_inv1, &p->d_df_inv2,
-                     &p->d_df_stw_phi, &p->d_df_stw_theta};
+                     &p->d_df_stw_phi, &p->d_df_stw_theta, (void **)&p->d_emax};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) dfs_free(bufs[i]);
     free(p->h_pofs);
     p->h_pofs = nullptr;
@@ -593,6 +591,8 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
     rc = upload_tables(p);
     if (rc == DFSNUFFT_OK) rc = upload_stage_tables(p);
     if (rc == DFSNUFFT_OK && p->gdf) rc = upload_df_tables(p);
+    if (rc == DFSNUFFT_OK && p->gdf)
+        rc = dfs_alloc(p, (void **)&p->d_emax, sizeof(int) * nf, "line exponents");
     if (rc == DFSNUFFT_OK && (prm.flags & DFSNUFFT_GAUSS_GRID)) {
         // samples on Gauss-Legendre latitudes: the solve matrices, in the theta-pass
         // buffer's room for the class matrices

@@ -53,12 +53,55 @@ def test_strerror_covers_every_code(lib):
     assert lib.dfsnufft_strerror(99).decode() == "unknown status"
 
 
-@pytest.mark.parametrize("tol,w", [(1e-1, 2), (1e-3, 4), (1e-6, 7), (1e-9, 10), (1e-12, 13),
-                                   (1e-14, 15), (1e-15, 16)])
-def test_width_rule(lib, tol, w):
+@pytest.mark.parametrize("tol,w,w32", [(1e-1, 2, 2), (1e-3, 5, 4), (1e-6, 7, 7), (1e-9, 11, None),
+                                       (1e-12, 14, None), (1e-14, 16, None)])
+def test_width_rule(lib, tol, w, w32):
     p = nufft.dfsnufft_choose_params(64, 32, tol, "f64")
     assert p["w"] == w
     assert p["beta"] == pytest.approx(2.30 * w)
+    if w32 is not None:
+        p = nufft.dfsnufft_choose_params(64, 32, tol, "f32")
+        assert p["w"] == w32 and p["beta"] == pytest.approx(2.30 * w32)
+
+
+def test_width_rule_monotone(lib):
+    ws = [nufft.dfsnufft_choose_params(64, 32, 10.0 ** (-k / 4), "f64")["w"]
+          for k in range(4, 57)]
+    assert ws == sorted(ws) and ws[-1] == 16
+
+
+def _es_band_edge_error(w, beta, n_off=201, n_freq=5):
+    """Worst 1-D error of interpolating e^{i omega x} from integer samples with
+    the ES kernel and exact deconvolution, over offsets x in [0, 1] and
+    |omega| <= pi/2 (the band of sigma = 2): the error model of the width rule,
+    computed here independently of the library's tables."""
+    from scipy.integrate import quad
+    def es(z):
+        u = 2.0 * z / w
+        out = np.zeros_like(z)
+        m = np.abs(u) < 1
+        out[m] = np.exp(beta * (np.sqrt(1 - u[m] ** 2) - 1))
+        return out
+    j = np.arange(-w, w + 2)
+    x = np.linspace(0.0, 1.0, n_off)[:, None]
+    worst = 0.0
+    for om in np.linspace(0.0, math.pi / 2, n_freq):
+        ph = 2 * quad(lambda z: math.exp(beta * (math.sqrt(1 - (2 * z / w) ** 2) - 1))
+                      * math.cos(om * z), 0, w / 2, epsabs=1e-16, epsrel=1e-14, limit=400)[0]
+        s = np.sum(es(x - j) * np.exp(1j * om * j), axis=1) / ph
+        worst = max(worst, float(np.max(np.abs(s - np.exp(1j * om * x[:, 0])))))
+    return worst
+
+
+def test_width_rule_meets_corner_mode_bound(lib):
+    """At tol 1e-12 the rule's width leaves a lone corner mode (1-D error in both
+    dimensions) within half of the 1e-11 acceptance bound, and the next
+    narrower width would not."""
+    w = nufft.dfsnufft_choose_params(64, 32, 1e-12, "f64")["w"]
+    e = _es_band_edge_error(w, 2.30 * w)
+    e_narrow = _es_band_edge_error(w - 1, 2.30 * (w - 1))
+    assert 2 * e <= 0.5e-11
+    assert 2 * e_narrow > 0.5e-11
 
 
 @pytest.mark.parametrize("n_lon,n_lat", [(64, 32), (160, 80), (2048, 1024), (8, 4), (24, 12)])
@@ -77,6 +120,7 @@ def test_parameter_errors(lib):
            ((64, 32, 0.0, "f64"), nufft.ERR_INVALID_ARG),
            ((64, 32, 1.5, "f64"), nufft.ERR_INVALID_ARG),
            ((64, 32, 1e-16, "f64"), nufft.ERR_TOL_UNATTAINABLE),
+           ((64, 32, 5e-15, "f64"), nufft.ERR_TOL_UNATTAINABLE),
            ((64, 32, 1e-8, "f32"), nufft.ERR_TOL_UNATTAINABLE),
            ((8192, 32, 1e-6, "f32"), nufft.ERR_UNSUPPORTED),
            ((64, 4096, 1e-6, "f32"), nufft.ERR_UNSUPPORTED)]
@@ -94,8 +138,8 @@ def test_options_defaults_equal_plain_choice(lib):
         assert a["sigma"] == 2 and a["flags"] == 0
 
 
-@pytest.mark.parametrize("tol,w2,w4", [(1e-12, 13, 11), (1e-9, 10, 9), (1e-6, 7, 6),
-                                       (1e-3, 4, 4), (1e-14, 15, 13)])
+@pytest.mark.parametrize("tol,w2,w4", [(1e-12, 14, 12), (1e-9, 11, 9), (1e-6, 7, 6),
+                                       (1e-3, 5, 5), (1e-14, 16, 13)])
 def test_sigma4_width_rule(lib, tol, w2, w4):
     """Oversampling 4: the narrowest width whose modelled error is at most
     that of the sigma-2 width; beta = 0.97 pi (1 - 1/8) w; fine grid 4 N."""

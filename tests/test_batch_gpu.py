@@ -65,11 +65,23 @@ def test_batched_plan_equals_single_plans(torch_cuda, dtype):
             assert oracle.rel_linf(got[f][wl.sample], ref[f].real) <= bound
 
 
+def _check_members_against_oracle(wls, vals, bound=2e-5):
+    off = 0
+    for wl in wls:
+        got = vals[off:off + 3 * wl.n_points].reshape(3, wl.n_points)
+        off += 3 * wl.n_points
+        ref = oracle.evaluate(wl.coeffs, wl.lon[wl.sample], wl.colat[wl.sample])
+        for f in range(3):
+            assert oracle.rel_linf(got[f][wl.sample], ref[f].real) <= bound, (wl.name, f)
+
+
 def test_ensemble_graph_uneven_grids(torch_cuda):
-    """Groups of 128x64, 256x128 and 512x256 members in one graph; replays give
-    the same values, and new points re-record the graph."""
+    """Groups of 128x64, 256x128, 512x256 and 1024x512 members (the ensemble's
+    grid sizes) in one graph: every member within 2e-5 of the oracle at its
+    seeded sample points; replays give the same values, and new points
+    re-record the graph."""
     torch = torch_cuda
-    groups = [(3, 128, 64), (2, 256, 128), (2, 512, 256)]
+    groups = [(3, 128, 64), (2, 256, 128), (2, 512, 256), (1, 1024, 512)]
     ens = nufft.Ensemble(groups, tol=1e-6, dtype="f32", n_fields=3)
     all_wls, pts, cfs, outs = [], [], [], []
     for gi, (m, n_lon, n_lat) in enumerate(groups):
@@ -84,6 +96,8 @@ def test_ensemble_graph_uneven_grids(torch_cuda):
     ens.run(pts, cfs, outs)          # runs, then records
     ens.check()
     first = [o.cpu().numpy().copy() for o in outs]
+    for wls, vals in zip(all_wls, first):
+        _check_members_against_oracle(wls, vals)
     for o in outs:
         o.zero_()
     ens.run(pts, cfs, outs)          # graph replay
@@ -106,6 +120,7 @@ def test_ensemble_graph_uneven_grids(torch_cuda):
     ens.run(pts, cfs, outs)
     ens.check()
     vals = outs[0].cpu().numpy()
+    _check_members_against_oracle(wl2, vals)
     off = 0
     for wl in wl2:
         got = vals[off:off + 3 * wl.n_points].reshape(3, wl.n_points)

@@ -89,6 +89,23 @@ def test_c3_f64_full_size(torch_cuda):
     check_against_oracle(vals, wl, TOL_F64)
 
 
+@pytest.mark.parametrize("shift", [(110, 110, 110), (-110, -110, -110), (110, -110, 0)])
+def test_c3_f64_scaled_coefficients(torch_cuda, shift):
+    """FP64 plans compute in double-single arithmetic (pairs of FP32 numbers),
+    yet keep their accuracy at any magnitude of the coefficients: the C3 fields
+    times 2^k, far outside FP32's exponent range (each field with its own k in
+    the mixed case), give exactly the unscaled values times 2^k, within 1e-11
+    of the oracle."""
+    wl = synth.workload_c3("f64", n_sample=200)
+    base = run_gpu(torch_cuda, wl)
+    s = np.array([math.ldexp(1.0, k) for k in shift])
+    scaled = synth.Workload(wl.name, wl.n_lon, wl.n_lat, wl.coeffs * s[:, None, None], wl.lon,
+                            wl.colat, wl.tol, "f64", sample=wl.sample)
+    vals = run_gpu(torch_cuda, scaled)
+    assert np.array_equal(vals, base * s[:, None])
+    check_against_oracle(vals, scaled, TOL_F64)
+
+
 # ------------------------------------------------------- sizes, fields, tolerances
 
 @pytest.mark.parametrize("n_lon,n_lat", [(8, 4), (16, 8), (24, 12), (64, 32), (96, 48),
@@ -209,17 +226,18 @@ def test_non_finite_point_gives_nan_only_there(torch_cuda):
 def test_single_modes_including_nyquist(torch_cuda, dtype):
     """One unit coefficient at (n0, m0) evaluates to cos(m0 phi + n0 theta).
 
-    A lone mode at the corner of the band is the kernel's worst case: at
-    tol 1e-12 (w = 13) the 1-D band-edge error is 7e-12, so the bound for FP64
-    here is 2e-11; the seeded workloads keep the 1e-11 bound."""
+    A lone mode at the corner of the band is the kernel's worst case (the 1-D
+    band-edge error in both dimensions); the width rule keeps it within the
+    same bound as every other input: 1e-11 at tol 1e-12."""
     n_lon, n_lat = 32, 16
     n2, n1 = synth.coeff_shape(n_lon, n_lat)
     rng = np.random.default_rng(13)
     lon = rng.uniform(-1, 7, 300)
     colat = rng.uniform(-1, 4, 300)
-    bound = 2e-11 if dtype == "f64" else TOL_F32
+    bound = TOL_F64 if dtype == "f64" else TOL_F32
     for n0, m0 in [(0, 0), (3, -5), (n2 // 2 - 1, n1 // 2 - 1), (-(n2 // 2), -(n1 // 2)),
-                   (-(n2 // 2), 4), (7, -(n1 // 2))]:
+                   (-(n2 // 2), 4), (7, -(n1 // 2)), (n2 // 2 - 1, -(n1 // 2) + 1),
+                   (-(n2 // 2) + 1, n1 // 2 - 1)]:
         c = np.zeros((1, n2, n1), np.complex128)
         c[0, n0 + n2 // 2, m0 + n1 // 2] = 1.0
         wl = synth.Workload("mode", n_lon, n_lat, c, lon, colat, 1e-12 if dtype == "f64" else 1e-6,

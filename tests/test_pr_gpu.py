@@ -102,3 +102,22 @@ def test_pr_errors(torch_cuda):
         assert ei.value.status == nufft.ERR_INVALID_ARG
         plan.execute_pr(pr)
         plan.check()
+
+
+def test_pr_f64_scaled_inputs(torch_cuda):
+    """Partial-regularity input of an FP64 plan scaled by 2^-120 and 2^+120 (one
+    field each): the values scale exactly, and stay within 1e-11 of the oracle."""
+    rng = np.random.default_rng(712)
+    M, N = 255, 254
+    pr = synth.random_pr_spectrum(rng, M, N, 2.0)
+    P = 1500
+    lon = rng.uniform(0, 2 * math.pi, P)
+    colat = rng.uniform(0, math.pi, P)
+    base = run_pr(torch_cuda, pr[None], lon, colat, 512, 256, "f64")[0]
+    s = np.array([math.ldexp(1.0, -120), math.ldexp(1.0, 120)])
+    vals = run_pr(torch_cuda, pr[None] * s[:, None, None], lon, colat, 512, 256, "f64")
+    idx = np.arange(0, P, 5)
+    ref = reference(pr, lon[idx], colat[idx], 512, 256)
+    for f in range(2):
+        assert np.array_equal(vals[f], base * s[f])
+        assert oracle.rel_linf(vals[f][idx], ref * s[f]) <= 1e-11
