@@ -4,6 +4,13 @@
 // loop that cannot afford cudaMalloc/cudaFree and the synchronisation they
 // imply).  The kernels are the library's own; only where their working memory
 // comes from differs.
+//
+// Each call writes everything it needs into the scratch from values carried in
+// its own kernel arguments: the point offsets, the deconvolution factors
+// (computed on the host by dfsnufft_kernel_ft, the plan path's routine, and
+// passed by value) and the twiddles (computed on the device).  No host buffer is
+// read after the call returns, and nothing depends on what an earlier call left
+// in the scratch.
 #include <math.h>
 #include <string.h>
 
@@ -18,91 +25,52 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[DFSNUFFT_NOALLO
 
 const int kMaxDevices = 64;
 const int kMaxFine = 2048;                       // fine-grid cells per dimension
-const double kPi = 3.14159265358979323846264338327950288;
+const int kMaxModes = kMaxFine / 2;              // modes per dimension at sigma 2
 
-struct DeviceState {
-    unsigned char *base;                         // device address of the scratch
-    // configuration whose kernel tables are in the scratch now
-    int have_tables, n1, n2, N1, N2, w, dtype;
-    double beta;
-};
-DeviceState g_state[kMaxDevices];
-std::mutex g_mutex;                              // set-up and table uploads
-
-// Host staging for the tables (static: nothing is allocated per call).
-double2 g_tw_stage[2 * kMaxFine];
-double g_ft_stage[kMaxFine];
-int g_pofs_stage[2];
+// Device address of the scratch, resolved once per device.
+unsigned char *g_base[kMaxDevices];
+std::mutex g_mutex;
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// 1 / phihat(k) at the centred modes, phihat(xi) = w int_0^{pi/2}
-// e^{beta (cos s - 1)} cos(xi (w/2) sin s) cos s ds by Gauss-Legendre on
-// [0, pi/2] (nodes by Newton's method on the Legendre recurrence).
-void inverse_kernel_ft(int w, double beta, int n_fine, int n_modes, double *out) {
-    const int q = 2 * w + 60;                    // <= 92
-    double node[96], weight[96];
-    for (int i = 0; i < q; ++i) {
-        double z = cos(kPi * (i + 0.75) / (q + 0.5));
-        double p0 = 1.0, p1 = z;
-        for (int it = 0; it < 100; ++it) {
-            p0 = 1.0;
-            p1 = z;
-            for (int k = 1; k < q; ++k) {
-                double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
-                p0 = p1;
-                p1 = p2;
-            }
-            double dz = p1 / (q * (z * p1 - p0) / (z * z - 1.0));
-            z -= dz;
-            if (fabs(dz) < 1e-16) break;
-        }
-        p0 = 1.0;
-        p1 = z;
-        for (int k = 1; k < q; ++k) {
-            double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
-            p0 = p1;
-            p1 = p2;
-        }
-        double dp = q * (z * p1 - p0) / (z * z - 1.0);
-        node[i] = z;
-        weight[i] = 2.0 / ((1.0 - z * z) * dp * dp);
-    }
-    for (int m = 0; m < n_modes; ++m) {
-        double xi = 2.0 * kPi * (double)(m - n_modes / 2) / (double)n_fine;
-        double acc = 0.0;
-        for (int i = 0; i < q; ++i) {
-            double s = 0.25 * kPi * (node[i] + 1.0);
-            acc += 0.25 * kPi * weight[i] * exp(beta * (cos(s) - 1.0)) * cos(s) *
-                   cos(xi * 0.5 * w * sin(s));
-        }
-        out[m] = 1.0 / (w * acc);
-    }
-}
+// Per-call tables, by value (about 16 KB of kernel arguments).
+struct NoallocTables {
+    int N1, N2, n1, n2;
+    int n_points;
+    int f64;                                     // plan precision of the tables
+    double inv[2 * kMaxModes];                   // 1 / phihat: N1 values, then N2
+};
 
-// Deconvolution factors in plan precision (FP64 values rounded once for FP32).
-cudaError_t upload_factors(const dfsnufft_params &prm, int dtype, int n_fine, int n_modes,
-                           void *dst, cudaStream_t st) {
-    inverse_kernel_ft(prm.w, prm.beta, n_fine, n_modes, g_ft_stage);
-    size_t bytes = sizeof(double) * n_modes;
-    if (dtype == DFSNUFFT_F32) {
-        float *f = reinterpret_cast<float *>(g_ft_stage);
-        for (int i = 0; i < n_modes; ++i) f[i] = (float)g_ft_stage[i];
-        bytes = sizeof(float) * n_modes;
+// Writes the deconvolution factors (plan precision), the twiddles
+// e^{+2 pi i k / n} of both fine lengths and the point offsets {0, P}.
+__global__ void __launch_bounds__(256) k_noalloc_tables(const __grid_constant__ NoallocTables t,
+                                                        void *__restrict__ inv1,
+                                                        void *__restrict__ inv2,
+                                                        void *__restrict__ tw1,
+                                                        void *__restrict__ tw2,
+                                                        int *__restrict__ pofs) {
+    const int total = t.N1 + t.N2 + t.n1 + t.n2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        if (i < t.N1 + t.N2) {
+            void *dst = i < t.N1 ? inv1 : inv2;
+            const int k = i < t.N1 ? i : i - t.N1;
+            if (t.f64) static_cast<double *>(dst)[k] = t.inv[i];
+            else static_cast<float *>(dst)[k] = (float)t.inv[i];
+            continue;
+        }
+        const int j = i - t.N1 - t.N2;
+        const int n = j < t.n1 ? t.n1 : t.n2;
+        const int k = j < t.n1 ? j : j - t.n1;
+        void *dst = j < t.n1 ? tw1 : tw2;
+        double sn, cs;
+        sincospi(2.0 * (double)k / (double)n, &sn, &cs);     // n a power of two: exact ratio
+        if (t.f64) static_cast<double2 *>(dst)[k] = make_double2(cs, sn);
+        else static_cast<float2 *>(dst)[k] = make_float2((float)cs, (float)sn);
     }
-    return cudaMemcpyAsync(dst, g_ft_stage, bytes, cudaMemcpyHostToDevice, st);
-}
-
-template <typename C, typename R>
-cudaError_t upload_twiddles(int n, void *dst, cudaStream_t st) {
-    C *h = reinterpret_cast<C *>(g_tw_stage);
-    for (int k = 0; k < n; ++k) {
-        double a = 2.0 * kPi * (double)k / (double)n;
-        h[k].x = (R)cos(a);
-        h[k].y = (R)sin(a);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        pofs[0] = 0;
+        pofs[1] = t.n_points;
     }
-    // pageable source: the call returns once the staging buffer may be reused
-    return cudaMemcpyAsync(dst, h, sizeof(C) * n, cudaMemcpyHostToDevice, st);
 }
 
 }  // namespace
@@ -117,7 +85,8 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     dfsnufft_params prm;
     int rc = dfsnufft_choose_params(n_lon, n_lat, tol, dtype, &prm);
     if (rc != DFSNUFFT_OK) return rc;
-    if (prm.n1 > kMaxFine || prm.n2 > kMaxFine) return DFSNUFFT_ERR_UNSUPPORTED;
+    if (prm.n1 > kMaxFine || prm.n2 > kMaxFine || prm.N1 > kMaxModes || prm.N2 > kMaxModes)
+        return DFSNUFFT_ERR_UNSUPPORTED;
 
     // the plan-shaped view of the problem, its buffers carved from the scratch
     dfsnufft_plan_s p;
@@ -157,16 +126,18 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return DFSNUFFT_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    DeviceState &ds = g_state[dev];
-    if (!ds.base) {
-        // once per device, with that device current
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) return DFSNUFFT_ERR_CUDA;
-        ds.base = (unsigned char *)ptr;
+    unsigned char *b = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (!g_base[dev]) {
+            // once per device, with that device current
+            void *ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) return DFSNUFFT_ERR_CUDA;
+            g_base[dev] = (unsigned char *)ptr;
+        }
+        b = g_base[dev];
     }
-    unsigned char *b = ds.base;
     p.d_inv1 = b + off[0];
     p.d_inv2 = b + off[1];
     p.d_tw1 = b + off[2];
@@ -184,37 +155,22 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     p.d_pofs = (int *)(b + off[10]);
     p.d_rowrange = (int2 *)(b + off[15]);
 
-    // kernel tables: uploaded only when the configuration differs from the
-    // one whose tables the scratch holds (their offsets depend only on it)
-    const bool same = ds.have_tables && ds.n1 == prm.n1 && ds.n2 == prm.n2 &&
-                      ds.N1 == prm.N1 && ds.N2 == prm.N2 && ds.w == prm.w &&
-                      ds.dtype == dtype && ds.beta == prm.beta;
-    if (!same) {
-        ds.have_tables = 0;
-        const bool ok =
-            !upload_factors(prm, dtype, prm.n1, prm.N1, p.d_inv1, p.stream) &&
-            !upload_factors(prm, dtype, prm.n2, prm.N2, p.d_inv2, p.stream) &&
-            (dtype == DFSNUFFT_F64
-                 ? !upload_twiddles<double2, double>(prm.n1, p.d_tw1, p.stream) &&
-                       !upload_twiddles<double2, double>(prm.n2, p.d_tw2, p.stream)
-                 : !upload_twiddles<float2, float>(prm.n1, p.d_tw1, p.stream) &&
-                       !upload_twiddles<float2, float>(prm.n2, p.d_tw2, p.stream));
-        if (!ok) return DFSNUFFT_ERR_CUDA;
-        ds.have_tables = 1;
-        ds.n1 = prm.n1;
-        ds.n2 = prm.n2;
-        ds.N1 = prm.N1;
-        ds.N2 = prm.N2;
-        ds.w = prm.w;
-        ds.dtype = dtype;
-        ds.beta = prm.beta;
-    }
-    // one member: point offsets {0, P}
-    g_pofs_stage[0] = 0;
-    g_pofs_stage[1] = (int)n_points;
-    if (cudaMemcpyAsync(p.d_pofs, g_pofs_stage, sizeof(g_pofs_stage), cudaMemcpyHostToDevice,
-                        p.stream) != cudaSuccess)
-        return DFSNUFFT_ERR_CUDA;
+    // this call's tables, carried by value into the scratch
+    NoallocTables t;
+    t.N1 = prm.N1;
+    t.N2 = prm.N2;
+    t.n1 = prm.n1;
+    t.n2 = prm.n2;
+    t.n_points = (int)n_points;
+    t.f64 = dtype == DFSNUFFT_F64 ? 1 : 0;
+    if (dfsnufft_kernel_ft(prm.w, prm.beta, prm.n1, prm.N1, t.inv) != DFSNUFFT_OK ||
+        dfsnufft_kernel_ft(prm.w, prm.beta, prm.n2, prm.N2, t.inv + prm.N1) != DFSNUFFT_OK)
+        return DFSNUFFT_ERR_INVALID_ARG;
+    for (int i = 0; i < prm.N1 + prm.N2; ++i) t.inv[i] = 1.0 / t.inv[i];
+    const int items = prm.N1 + prm.N2 + prm.n1 + prm.n2;
+    k_noalloc_tables<<<(items + 255) / 256, 256, 0, p.stream>>>(t, p.d_inv1, p.d_inv2, p.d_tw1,
+                                                              p.d_tw2, p.d_pofs);
+    if (cudaGetLastError() != cudaSuccess) return DFSNUFFT_ERR_CUDA;
     // set_points clears the bin counters before counting
     if (dfs_launch_set_points(&p, lon, colat) != cudaSuccess ||
         dfs_launch_theta_pass(&p, coeffs) != cudaSuccess ||

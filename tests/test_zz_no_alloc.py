@@ -60,7 +60,9 @@ def test_noalloc_matches_plan_on_consecutive_calls(torch_cuda):
     by one call does not leak into the next."""
     first = synth.small_workload(31, 128, 64, n_fields=3, dtype="f64", points="divergent")
     second = synth.small_workload(32, 256, 128, n_fields=2, dtype="f32", points="rotation")
-    for wl, bound in ((first, 1e-11), (second, 2e-5), (first, 1e-11)):
+    # the same configuration as the one before it, with new points and coefficients
+    again = synth.small_workload(33, 128, 64, n_fields=3, dtype="f64", points="rotation")
+    for wl, bound in ((first, 1e-11), (second, 2e-5), (first, 1e-11), (again, 1e-11)):
         got = _noalloc(torch_cuda, wl)
         ref = _with_plan(torch_cuda, wl)
         assert np.all(np.isfinite(got))
