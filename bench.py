@@ -255,6 +255,22 @@ def interp_flops(prm, n_fields, n_points):
     return n_fields * n_points * 2 * w * (w + 1) + n_points * 4 * w * w
 
 
+def df32_interp_ops(prm, n_fields, n_points):
+    """FP32 arithmetic instructions (FADD, FMUL, FFMA: one each) of one
+    double-single interpolation launch (FP64 plans, k_interp_df), counted from
+    its operations: TwoSum 6, TwoProduct 2, a double-single product 7 (with its
+    fast renormalisation), sum 11, Horner step 15, Dot2 step 12.  Per point: the
+    x and y weights, each (w + 1) / 2 mirror pairs of an even and an odd Horner
+    chain (w - 1 steps together), one product s o and the two sums, plus u = s^2
+    for each axis; per point and field, w stencil rows of w Dot2 steps, each row
+    then renormalised (3) and added by one more Dot2 step."""
+    w = prm["w"]
+    pairs = (w + 1) // 2
+    weights = pairs * ((w - 1) * 15 + 7 + 2 * 11) + 7
+    rows = w * (12 * w + 3 + 12)
+    return n_points * (2 * weights + n_fields * rows)
+
+
 def fft_flops(prm, n_fields, rows, stage):
     """Algorithmic flops of one FFT pass, 5 L log2 L a complex transform of
     length L: the theta pass transforms the coefficient columns (N1/2 + 1 of a
@@ -319,7 +335,6 @@ def weak_scaling_value(ws, units_per_rank_step, steps, max_total_ms):
 
 def run_ours(args):
     import torch
-    from paper_2605_01313_gb300 import Plan, nufft
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -327,8 +342,37 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-
     wl = make_workload(args.workload)
+    line = measure(args, args.workload, wl, ws, rank, dev, serving=True)
+    if args.workload == DEFAULT_WORKLOAD and not args.no_fp64:
+        # the same workload with an FP64 plan at tol 1e-12 (the paper's precision)
+        from paper_2605_01313_gb300 import synth
+        wl64 = synth.Workload("c3_2048x1024_f64", wl.n_lon, wl.n_lat, wl.coeffs, wl.lon,
+                              wl.colat, 1e-12, "f64", sample=wl.sample)
+        rec = measure(args, "c3_2048x1024_f64", wl64, ws, rank, dev, serving=False,
+                      cpu_seconds=args.cpu_seconds / 2)
+        if line is not None:
+            line["fp64"] = {k: rec[k] for k in FP64_KEYS if k in rec}
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# keys of the nested FP64 record of the default run
+FP64_KEYS = ("metric", "value", "unit", "ms_per_step", "p50_ms", "p99_ms", "steps", "warmup",
+             "dtype", "config", "roofline", "roofline_step", "stages", "gpu_launches", "e2e",
+             "error", "clocks")
+
+
+def measure(args, name, wl, ws, rank, dev, serving, cpu_seconds=None):
+    """Time one workload (warm-up, K timed steps, stage times, end to end through
+    the host-buffer entry points, roofline, oracle error); returns the JSON
+    line's dict on rank 0, None on the other ranks."""
+    import torch
+    from paper_2605_01313_gb300 import Plan, nufft
+
     pr_in = getattr(wl, "pr", None) is not None
     grid_in = getattr(wl, "grid", None) is not None
     sl = getattr(wl, "sl", None)
@@ -499,10 +543,7 @@ def run_ours(args):
 
     if rank != 0:
         plan.destroy()
-        if ws > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
-        return
+        return None
 
     # ---- roofline of the dominant kernel
     pk, pk_kind = peaks()
@@ -515,24 +556,28 @@ def run_ours(args):
     dom = max(("theta_pass", "phi_pass", "interp", "set_points"),
               key=lambda k: per_stage_ms[k] or 0.0)
     dom_ms = per_stage_ms[dom]
-    if wl.dtype == "f64" and dom in ("interp", "theta_pass", "phi_pass"):
-        # FP64 stages are bound by arithmetic: FP64 flops of the stage against the
-        # measured FP64 FMA rate (the interpolation runs them in double-single on
-        # the FP32 units, so its fraction may exceed 1)
-        fma = nufft.dfsnufft_probe_fma_rate("f64", 20.0)
-        flops = (interp_flops(prm, F, P) if dom == "interp"
-                 else fft_flops(prm, F, stats["rows_needed"], dom))
-        achieved = flops / (dom_ms * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fma / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / (fma / 1e12),
-                "peak_source": "measured FP64 FMA rate (dfsnufft_probe_fma_rate)",
-                "traffic": profile_traffic(dom, args.workload)}
+    if wl.dtype == "f64" and dom == "interp" and not (prm["flags"] & 2):
+        # FP64 plans interpolate in double-single arithmetic on the FP32 units:
+        # the stage's FP32 instructions (df32_interp_ops) against the FP32 pipe's
+        # instruction rate, measured live by the FMA probe (FLOP/s / 2)
+        fma32 = nufft.dfsnufft_probe_fma_rate("f32", 20.0)
+        ops = df32_interp_ops(prm, F, P)
+        achieved = ops / (dom_ms * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fma32 / 2e12,
+                "unit": "T FP32-instructions/s", "frac": achieved / (fma32 / 2e12),
+                "ops_per_launch": ops,
+                "peak_source": "measured FP32 FMA rate / 2 (dfsnufft_probe_fma_rate, "
+                               "one FFMA instruction = 2 FLOP)",
+                "traffic": profile_traffic(dom, name),
+                "hbm": {"achieved": sbytes[dom] / (dom_ms * 1e-3) / 1e9,
+                        "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": sbytes[dom] / (dom_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}}
     else:
         achieved = sbytes[dom] / (dom_ms * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
                 "peak_source": "%s hbm_gbs" % pk_kind,
-                "traffic": profile_traffic(dom, args.workload)}
+                "traffic": profile_traffic(dom, name)}
     stages_out = {}
     for k in per_stage_ms:
         ms = per_stage_ms[k]
@@ -558,7 +603,7 @@ def run_ours(args):
         # FP64 plans compute in double-single (pairs of FP32, 48-bit significands)
         # on the FP32 units, FP64 kept for the folding and the factors' set-up
         "dtype": "df32" if wl.dtype == "f64" else wl.dtype, "data": "synthetic",
-        "config": {"workload": args.workload, "grid": "%dx%d" % (wl.n_lon, wl.n_lat),
+        "config": {"workload": name, "grid": "%dx%d" % (wl.n_lon, wl.n_lat),
                    "modes": "%dx%d" % (2 * wl.n_lat, wl.n_lon), "fields": F, "points": P,
                    "tol": wl.tol, "w": prm["w"], "fine": "%dx%d" % (prm["n2"], prm["n1"]),
                    "rows_needed": stats["rows_needed"], "l2": "flushed between steps (512 MiB write)",
@@ -570,7 +615,9 @@ def run_ours(args):
         "roofline_step": roof_step,
         "stages": stages_out,
         "gpu_launches": ((4 if prm["flags"] & 2 else 7) + (2 if grid_in else 0)
-                         + (2 if sl is not None else 0)) * args.steps,
+                         + (2 if sl is not None else 0)
+                         + (1 if wl.dtype == "f64" and not prm["flags"] & 2 else 0))
+                        * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / e2e_steps},
         "clocks": clocks,
@@ -610,7 +657,8 @@ def run_ours(args):
                 cs_.append(oracle.complex_from_cossin(fc, fs, wl.n_lon, wl.n_lat))
             wl.coeffs = np.stack(cs_)
         line["cpu_baseline"], line["error"] = cpu_baseline(
-            wl, out.cpu().numpy(), args.cpu_seconds, lag_vals if comparator else None)
+            wl, out.cpu().numpy(), cpu_seconds or args.cpu_seconds,
+            lag_vals if comparator else None)
     if gauss is not None:
         line["config"]["input"] = ("samples of the tilted steady zonal flow (h, u, v) on the "
                                    "Gauss-Legendre grid; coefficients by the latitude solve "
@@ -623,12 +671,9 @@ def run_ours(args):
                                    "points; comparator: Lagrange interpolation of the same "
                                    "samples")
     plan.destroy()
-    if ws == 1 and args.serve_seconds > 0:
+    if serving and ws == 1 and args.serve_seconds > 0:
         line["serving"] = serving_sweep(dev, [100, 500, 1000, 2000, 5000], args.serve_seconds)
-    print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    return line
 
 
 def oracle_values(wl, s):
@@ -958,6 +1003,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the nested FP64 record of the default workload")
     ap.add_argument("--keep-order", action="store_true",
                     help="evaluate the points unsorted, in their grid order")
     ap.add_argument("--general", action="store_true",

@@ -27,7 +27,7 @@ def bench():
 P, F, ROWS = 2_097_152, 3, 2096
 C3_F32 = {"N1": 2048, "N2": 2048, "n1": 4096, "n2": 4096, "dtype": 1, "flags": 1, "sigma": 2,
           "w": 7}
-C3_F64 = dict(C3_F32, dtype=0, w=13)
+C3_F64 = dict(C3_F32, dtype=0, w=14)
 
 
 def test_stage_bytes_fp32(bench):
@@ -53,7 +53,17 @@ def test_model_bytes(bench):
 def test_interp_flops_fp64(bench):
     # per point and field 2 w (w + 1) for the taps and row sums, per point 4 w^2
     # for the kernel weights
-    assert bench.interp_flops(C3_F64, F, P) == P * (3 * 2 * 13 * 14 + 4 * 13 * 13)
+    assert bench.interp_flops(C3_F64, F, P) == P * (3 * 2 * 14 * 15 + 4 * 14 * 14)
+
+
+def test_df32_interp_ops(bench):
+    # w = 14: 7 mirror pairs of Horner chains with 13 steps together (15 FP32
+    # instructions each), a product (7) and two sums (11 each): 224 a pair, 7
+    # pairs plus u = s^2 (7) for each of x and y; per field 14 rows of 14 Dot2
+    # steps (12 each), a renormalisation (3) and one more Dot2 step
+    per_point = 2 * (7 * (13 * 15 + 7 + 2 * 11) + 7) + 3 * (14 * (14 * 12 + 3 + 12))
+    assert per_point == 10836
+    assert bench.df32_interp_ops(C3_F64, F, P) == P * per_point
 
 
 def test_fft_flops(bench):
