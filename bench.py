@@ -614,7 +614,9 @@ def measure(args, name, wl, ws, rank, dev, serving, cpu_seconds=None):
         "roofline": roof,
         "roofline_step": roof_step,
         "stages": stages_out,
-        "gpu_launches": ((4 if prm["flags"] & 2 else 7) + (2 if grid_in else 0)
+        # set_points: fold+count, row prefix, two scan passes, scatter (one fold
+        # kernel for unsorted points); theta pass, phi pass, interpolation
+        "gpu_launches": ((4 if prm["flags"] & 2 else 8) + (2 if grid_in else 0)
                          + (2 if sl is not None else 0)
                          + (1 if wl.dtype == "f64" and not prm["flags"] & 2 else 0))
                         * args.steps,

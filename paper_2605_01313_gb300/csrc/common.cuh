@@ -92,7 +92,8 @@ struct dfsnufft_plan_s {
 
     // point data (capacity grows with set_points)
     int64_t n_points, cap_points;   // all members' points
-    int *d_rank;            // rank of each point inside its bin (input order)
+    void *d_urec;           // unsorted folded records (dfs_fold_rec_bytes each): base
+                            // cell, rank inside its bin (input order), offsets
     int2 *d_base;           // sorted: first-tap fine index (i0, j0)
     void *d_frac;           // sorted: offsets (tx, ty) in plan precision
     int *d_idx;             // sorted: original point index
@@ -128,10 +129,21 @@ __host__ __device__ __forceinline__ int dfs_tpitch(int herm, int N1) {
     return herm ? ((N1 / 2 + 1 + 3) & ~3) : N1;
 }
 
+// Bytes of one unsorted point record of set_points (points.cu FoldRec): packed
+// base cell and rank (two ints) and the two offsets in plan precision.
+__host__ __device__ __forceinline__ int dfs_fold_rec_bytes(int dtype) {
+    return dtype == DFSNUFFT_F64 ? 24 : 16;
+}
+
 // Ints per member of the count array: counts (bstride), completion counter (4),
-// bin-row flags (DFS_MAX_ROW_BLOCKS bytes), chunk sums and non-empty counts.
-__host__ __device__ __forceinline__ int dfs_cstride(int bstride) {
+// bin-row flags (DFS_MAX_ROW_BLOCKS bytes), chunk sums and non-empty counts,
+// then from dfs_rowcount_offset the per-row counts of every bin (nbins x
+// tile_y, bin-major), which order the points inside a bin by fine row.
+__host__ __device__ __forceinline__ int dfs_rowcount_offset(int bstride) {
     return bstride + 4 + DFS_MAX_ROW_BLOCKS / 4 + 2 * DFS_SCAN_MAXCH;
+}
+__host__ __device__ __forceinline__ int dfs_cstride(int bstride, int nbins, int tile_y) {
+    return dfs_rowcount_offset(bstride) + ((nbins * tile_y + 3) & ~3);
 }
 
 // ---------------------------------------------------------------- launches

@@ -17,7 +17,8 @@
 // FP32 plans run k_interp_tma: persistent CTAs walk their bins with the next
 // bin's tiles arriving by TMA (one 2-D box per field) while the current bin is
 // evaluated; the few bins whose tile wraps around the torus seam are staged
-// with plain loads instead.  k_interp_f32 (plain loads, the same arithmetic)
+// with plain loads instead.  Inside a bin the points come sorted by fine row
+// (set_points), so a warp's lanes mostly read consecutive words of one row.  k_interp_f32 (plain loads, the same arithmetic)
 // serves plans without a tensor map, and k_interp the FP64 form and wide
 // kernels.
 #include <limits.h>

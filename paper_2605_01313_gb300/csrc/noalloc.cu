@@ -99,7 +99,7 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     p.nby = prm.n2 / prm.tile_y;
     p.nbins = p.nbx * p.nby;
     p.bstride = (p.nbins + 4) & ~3;
-    p.cstride = dfs_cstride(p.bstride);
+    p.cstride = dfs_cstride(p.bstride, p.nbins, prm.tile_y);
     p.nch = (p.nbins + DFS_SCAN_CHUNK - 1) / DFS_SCAN_CHUNK;
     p.n_members = 1;
     p.n_points = n_points;
@@ -114,7 +114,8 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
                             cs * prm.n2, cs * nf * prm.n2 * prm.N1, rs * nf * prm.n2 * prm.n1,
                             sizeof(int) * p.cstride, sizeof(int) * p.bstride,
                             sizeof(int) * p.bstride, sizeof(int), 2 * sizeof(int),
-                            sizeof(int) * P, sizeof(int2) * P, 2 * rs * P, sizeof(int) * P,
+                            (size_t)dfs_fold_rec_bytes(dtype) * P, sizeof(int2) * P, 2 * rs * P,
+                            sizeof(int) * P,
                             sizeof(int2)};
     const int nbuf = (int)(sizeof(sizes) / sizeof(sizes[0]));
     for (int i = 0; i < nbuf; ++i) {
@@ -148,7 +149,7 @@ extern "C" int dfsnufft_execute_noalloc(int n_lon, int n_lat, double tol, int dt
     p.d_bin_start = (int *)(b + off[7]);
     p.d_task_bin = (int *)(b + off[8]);
     p.d_n_tasks = (int *)(b + off[9]);
-    p.d_rank = (int *)(b + off[11]);
+    p.d_urec = b + off[11];
     p.d_base = (int2 *)(b + off[12]);
     p.d_frac = b + off[13];
     p.d_idx = (int *)(b + off[14]);

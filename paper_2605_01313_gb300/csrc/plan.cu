@@ -319,7 +319,7 @@ static void release(dfsnufft_plan p) {
                      (void **)&p->d_task_bin, (void **)&p->d_n_tasks,
                      (void **)&p->d_status, (void **)&p->d_parity, (void **)&p->d_rowrange,
                      (void **)&p->d_pofs,
-                     (void **)&p->d_rank, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
+                     &p->d_urec, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
                      (void **)&p->d_pts_stage, &p->d_coef_stage, &p->d_val_stage,
                      &p->d_df_tw1, &p->d_df_tw2, &p->d_df_inv1, &p->d_df_inv2,
                      &p->d_df_stw_phi, &p->d_df_stw_theta, (void **)&p->d_emax};
@@ -551,7 +551,7 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
     p->nby = prm.n2 / prm.tile_y;
     p->nbins = p->nbx * p->nby;
     p->bstride = (p->nbins + 4) & ~3;     // 16-byte aligned member slices
-    p->cstride = dfs_cstride(p->bstride);
+    p->cstride = dfs_cstride(p->bstride, p->nbins, prm.tile_y);
     p->nch = (p->nbins + DFS_SCAN_CHUNK - 1) / DFS_SCAN_CHUNK;
 
     size_t cs = dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
@@ -673,14 +673,15 @@ static int ensure_point_capacity(dfsnufft_plan p, int64_t n) {
     if (n <= p->cap_points) return DFSNUFFT_OK;
     // the stream may still use the old buffers
     DFS_CK(p, cudaStreamSynchronize(p->stream));
-    dfs_free((void **)&p->d_rank);
+    dfs_free(&p->d_urec);
     dfs_free((void **)&p->d_base);
     dfs_free(&p->d_frac);
     dfs_free((void **)&p->d_idx);
     p->cap_points = 0;
     size_t rs = p->prm.dtype == DFSNUFFT_F64 ? sizeof(double) : sizeof(float);
     int rc;
-    if ((rc = dfs_alloc(p, (void **)&p->d_rank, sizeof(int) * n, "point ranks")) ||
+    if ((rc = dfs_alloc(p, &p->d_urec, (size_t)dfs_fold_rec_bytes(p->prm.dtype) * n,
+                        "unsorted point records")) ||
         (rc = dfs_alloc(p, (void **)&p->d_base, sizeof(int2) * n, "point bases")) ||
         (rc = dfs_alloc(p, &p->d_frac, 2 * rs * n, "point offsets")) ||
         (rc = dfs_alloc(p, (void **)&p->d_idx, sizeof(int) * n, "point order")))

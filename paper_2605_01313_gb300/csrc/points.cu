@@ -67,22 +67,55 @@ __device__ __forceinline__ int bin_of(const FoldParams &f, int bx, int by) {
     return (by >> f.lty) * f.nbx + (bx >> f.ltx);
 }
 
-// grid (ceil(max member points / 256), members): member k = blockIdx.y.
+// Unsorted record of a folded point, written by k_fold_count and moved to its
+// sorted place by k_scatter: base cell (bx | by << 16, both below 2^13), the
+// point's rank inside its bin (input order) and its offsets in plan precision.
+// 16 bytes in FP32 (one vector store and load), 24 in FP64.
+template <typename R> struct FoldRec;
+template <> struct __align__(16) FoldRec<float> {
+    int base, rank;
+    float tx, ty;
+};
+template <> struct __align__(8) FoldRec<double> {
+    int base, rank;
+    double tx, ty;
+};
+static_assert(sizeof(FoldRec<float>) == 16 && sizeof(FoldRec<double>) == 24,
+              "record sizes of dfs_fold_rec_bytes");
+
+// Sort key of a point: its bin, then its base cell's row inside the bin (the
+// rank within a bin follows fine rows, so that the points of one warp share
+// stencil rows and read consecutive shared-memory words).
+__device__ __forceinline__ int rowkey_of(const FoldParams &f, int bx, int by) {
+    return (bin_of(f, bx, by) << f.lty) | (by & ((1 << f.lty) - 1));
+}
+
+// grid (ceil(max member points / 256), members): member k = blockIdx.y.  Folds
+// every point once (kept in its unsorted record) and counts the points of each
+// row of each bin (the row counts at rowoff in the member's count slice); the
+// rank of a point is its position among its row's points, in input order.
+template <typename R>
 __global__ void __launch_bounds__(256) k_fold_count(const double *__restrict__ lon,
                                                     const double *__restrict__ colat,
                                                     FoldParams f, const int *__restrict__ pofs,
-                                                    int cstride, int *__restrict__ bin_count,
-                                                    int *__restrict__ rank) {
+                                                    int cstride, int rowoff,
+                                                    int *__restrict__ bin_count,
+                                                    FoldRec<R> *__restrict__ urec) {
     const int k = blockIdx.y;
     const int p0 = pofs[k];
     const int pl = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = pl < pofs[k + 1] - p0;
-    int bin = -1;
+    int bin = -1;                               // the row key
+    FoldRec<R> rec;
     if (live) {
         int bx, by;
         long long tx, ty;
-        fold_point(f, lon[p0 + pl], colat[p0 + pl], bx, by, tx, ty);
-        bin = bin_of(f, bx, by);
+        const bool ok = fold_point(f, lon[p0 + pl], colat[p0 + pl], bx, by, tx, ty);
+        bin = rowkey_of(f, bx, by);
+        rec.base = bx | (by << 16);
+        rec.tx = offset_value<R>(tx, f.odd_w);
+        rec.ty = offset_value<R>(ty, f.odd_w);
+        if (!ok) rec.tx = rec.ty = (R)__int_as_float(0x7fc00000);
     }
     // warp aggregation over runs of equal bins (points arrive nearly sorted):
     // the first lane of each run takes the run's ranks with one atomicAdd
@@ -97,9 +130,30 @@ __global__ void __launch_bounds__(256) k_fold_count(const double *__restrict__ l
     const unsigned later = heads & ~(0xffffffffu >> (31 - lane));   // heads after this lane
     const int run_end = later ? __ffs(later) - 1 : 32 - __clz(live_mask);
     int base = 0;
-    if (head) base = atomicAdd(&bin_count[(size_t)k * cstride + bin], run_end - lane);
+    if (head) base = atomicAdd(&bin_count[(size_t)k * cstride + rowoff + bin], run_end - lane);
     base = __shfl_sync(0xffffffffu, base, my_head);
-    if (live) rank[p0 + pl] = base + lane - my_head;
+    if (live) {
+        rec.rank = base + lane - my_head;
+        urec[p0 + pl] = rec;
+    }
+}
+
+// grid (ceil(nbins / 256), members): for each bin, the exclusive prefix of its
+// row counts (in place: the offset of each row inside the bin) and the bin's
+// total, which the bin scan takes.
+__global__ void __launch_bounds__(256) k_row_prefix(int nbins, int tile_y, int cstride,
+                                                    int rowoff, int *__restrict__ count_all) {
+    const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+    if (bin >= nbins) return;
+    int *slice = count_all + (size_t)blockIdx.y * cstride;
+    int *rc = slice + rowoff + (size_t)bin * tile_y;
+    int sum = 0;
+    for (int r = 0; r < tile_y; ++r) {
+        const int c = rc[r];
+        rc[r] = sum;
+        sum += c;
+    }
+    slice[bin] = sum;
 }
 
 // Smallest index i in [from, from + nb) (circular over nb bits) whose bit in
@@ -410,30 +464,29 @@ __global__ void __launch_bounds__(256) k_fold_direct(const double *__restrict__ 
     finish_rowrange(sp, rows, s_bits, rowrange + k);
 }
 
-// grid (ceil(max member points / 256), members): member k = blockIdx.y.  Sorted
-// records go to the member's slice [pofs[k], pofs[k+1]); idx holds member-local
-// point indices.
+// grid (ceil(max member points / 256), members): member k = blockIdx.y.  Each
+// point's unsorted record goes to its sorted place in the member's slice
+// [pofs[k], pofs[k+1]): bin start plus rank.  idx holds member-local point
+// indices.
 template <typename R>
-__global__ void __launch_bounds__(256) k_scatter(const double *__restrict__ lon,
-                                                 const double *__restrict__ colat, FoldParams f,
-                                                 const int *__restrict__ pofs, int bstride,
-                                                 const int *__restrict__ start_all,
-                                                 const int *__restrict__ rank,
-                                                 int2 *__restrict__ base, R *__restrict__ frac,
+__global__ void __launch_bounds__(256) k_scatter(const FoldRec<R> *__restrict__ urec,
+                                                 FoldParams f, const int *__restrict__ pofs,
+                                                 int bstride, const int *__restrict__ start_all,
+                                                 int cstride, int rowoff,
+                                                 const int *__restrict__ count_all,
+                                                 int2 *__restrict__ base,
+                                                 typename CxT<R>::type *__restrict__ frac,
                                                  int *__restrict__ idx) {
     const int k = blockIdx.y;
     const int p0 = pofs[k];
     const int pl = blockIdx.x * blockDim.x + threadIdx.x;
     if (pl >= pofs[k + 1] - p0) return;
-    int bx, by;
-    long long tx, ty;
-    const bool ok = fold_point(f, lon[p0 + pl], colat[p0 + pl], bx, by, tx, ty);
-    const int pos = p0 + start_all[(size_t)k * bstride + bin_of(f, bx, by)] + rank[p0 + pl];
+    const FoldRec<R> rec = urec[p0 + pl];
+    const int bx = rec.base & 0xffff, by = rec.base >> 16;
+    const int pos = p0 + start_all[(size_t)k * bstride + bin_of(f, bx, by)] +
+                    count_all[(size_t)k * cstride + rowoff + rowkey_of(f, bx, by)] + rec.rank;
     base[pos] = make_int2(bx - f.c0, by - f.c0);
-    R ox = offset_value<R>(tx, f.odd_w), oy = offset_value<R>(ty, f.odd_w);
-    if (!ok) ox = oy = (R)__int_as_float(0x7fc00000);
-    frac[2 * pos] = ox;
-    frac[2 * pos + 1] = oy;
+    frac[pos] = cmake(rec.tx, rec.ty);
     idx[pos] = pl;
 }
 
@@ -484,20 +537,29 @@ cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const doub
                                                              (float *)p->d_frac, p->d_rowrange);
         return cudaGetLastError();
     }
-    k_fold_count<<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->cstride, p->d_bin_count,
-                                              p->d_rank);
+    const int rowoff = dfs_rowcount_offset(p->bstride);
+    if (q.dtype == DFSNUFFT_F64)
+        k_fold_count<double><<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->cstride,
+                                                          rowoff, p->d_bin_count,
+                                                          (FoldRec<double> *)p->d_urec);
+    else
+        k_fold_count<float><<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->cstride,
+                                                         rowoff, p->d_bin_count,
+                                                         (FoldRec<float> *)p->d_urec);
+    k_row_prefix<<<dim3((p->nbins + 255) / 256, M), 256, 0, p->stream>>>(
+        p->nbins, q.tile_y, p->cstride, rowoff, p->d_bin_count);
     const dim3 sgrid(p->nch, M);
     k_scan_sums<<<sgrid, DFS_SCAN_CHUNK / 16, 0, p->stream>>>(sp, p->d_bin_count);
     k_scan_write<<<sgrid, DFS_SCAN_CHUNK / 16, 0, p->stream>>>(sp, p->d_bin_count, p->d_bin_start,
                                                              p->d_task_bin, p->d_n_tasks,
                                                              p->d_rowrange);
     if (q.dtype == DFSNUFFT_F64)
-        k_scatter<double><<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->bstride,
-                                                      p->d_bin_start, p->d_rank, p->d_base,
-                                                      (double *)p->d_frac, p->d_idx);
+        k_scatter<double><<<grid, tpb, 0, p->stream>>>(
+            (const FoldRec<double> *)p->d_urec, f, p->d_pofs, p->bstride, p->d_bin_start,
+            p->cstride, rowoff, p->d_bin_count, p->d_base, (double2 *)p->d_frac, p->d_idx);
     else
-        k_scatter<float><<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->bstride,
-                                                     p->d_bin_start, p->d_rank, p->d_base,
-                                                     (float *)p->d_frac, p->d_idx);
+        k_scatter<float><<<grid, tpb, 0, p->stream>>>(
+            (const FoldRec<float> *)p->d_urec, f, p->d_pofs, p->bstride, p->d_bin_start,
+            p->cstride, rowoff, p->d_bin_count, p->d_base, (float2 *)p->d_frac, p->d_idx);
     return cudaGetLastError();
 }
