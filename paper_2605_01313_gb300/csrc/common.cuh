@@ -89,6 +89,10 @@ struct dfsnufft_plan_s {
     CUtensorMap tmap_G;         // 2-D map of d_G (8-byte elements), box set by the interpolation
     int tmap_G_ok;              // tmap_G is valid (FP32 plans that own their buffers)
     int interp_ctas_per_sm;     // resident CTAs of the TMA interpolation (0: not yet known)
+    // lines (members x fields) the next theta, phi and interpolation launches
+    // cover: [win0, win0 + nwin), every line when nwin == 0 (the host-buffer
+    // path of one-member plans pipelines its fields this way)
+    int win0, nwin;
 
     // point data (capacity grows with set_points)
     int64_t n_points, cap_points;   // all members' points
@@ -108,6 +112,13 @@ struct dfsnufft_plan_s {
     // copy_stream after the copies
     cudaStream_t copy_stream;
     cudaEvent_t stage_free, coef_ready;
+    // one-member host-buffer path, pipelined per field: for line f, coefficients
+    // staged (line_ev[2 f]) and values ready (line_ev[2 f + 1]); pts_copied marks
+    // the end of set_points_host's point copies (pts_pending: not yet waited for)
+    cudaEvent_t *line_ev;
+    int n_line_ev;
+    cudaEvent_t pts_copied, vals_copied;
+    int pts_pending;
 
     // stage timing (dfsnufft_plan_enable_timing)
     int timing;
@@ -144,6 +155,12 @@ __host__ __device__ __forceinline__ int dfs_rowcount_offset(int bstride) {
 }
 __host__ __device__ __forceinline__ int dfs_cstride(int bstride, int nbins, int tile_y) {
     return dfs_rowcount_offset(bstride) + ((nbins * tile_y + 3) & ~3);
+}
+
+// The line window of the next launches: first line and count.
+__host__ __forceinline__ void dfs_lines(const dfsnufft_plan_s *p, int &line0, int &nlines) {
+    line0 = p->nwin ? p->win0 : 0;
+    nlines = p->nwin ? p->nwin : p->n_members * p->n_fields;
 }
 
 // ---------------------------------------------------------------- launches

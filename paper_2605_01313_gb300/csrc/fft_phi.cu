@@ -26,6 +26,7 @@ struct PhiArgs {
     int CB;                   // rows per CTA (divides DFS_ROW_BLOCK)
     int F;                    // fields per member (line f belongs to member f / F)
     int tcols, tpitch;        // theta-pass columns per row and row pitch
+    int line0;                // first line (blockIdx.y = line - line0)
 };
 
 // grid (n2 / CB, lines); block CB * M/E threads, thread = (t, c) with t fastest.
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
                R *__restrict__ grid) {
     typedef typename CxT<R>::type C;
     const int row0 = blockIdx.x * a.CB;
-    const int2 rr = rowrange[blockIdx.y / a.F];
+    const int2 rr = rowrange[(a.line0 + blockIdx.y) / a.F];
     // whole CTA (within one row block): no stencil touches these rows
     if (((row0 - rr.x) & (a.n2 - 1)) >= rr.y) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int t = threadIdx.x % T;
     const int c = threadIdx.x / T;
     const int row = row0 + c;
-    const int f = blockIdx.y;
+    const int f = a.line0 + blockIdx.y;
     const C *src = in + ((size_t)f * a.n2 + row) * a.tpitch;
     R *dst = grid + ((size_t)f * a.n2 + row) * a.n1;
     const int half = a.N1 / 2;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
                 float *__restrict__ grid) {
     typedef float2 C;
     const int row0 = blockIdx.x * a.CB;
-    const int2 rr = rowrange[blockIdx.y / a.F];
+    const int2 rr = rowrange[(a.line0 + blockIdx.y) / a.F];
     if (((row0 - rr.x) & (a.n2 - 1)) >= rr.y) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *smem = reinterpret_cast<C *>(smem_raw);
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int t = threadIdx.x % T;
     const int c = threadIdx.x / T;                 // row pair
     const int row = row0 + 2 * c;
-    const int f = blockIdx.y;
+    const int f = a.line0 + blockIdx.y;
     const int half = a.N1 / 2;
     const int nmask = a.n1 - 1;
     const C *src = in + ((size_t)f * a.n2 + row) * a.tpitch;
@@ -260,13 +261,15 @@ cudaError_t launch_phi(dfsnufft_plan p) {
     a.F = p->n_fields;
     a.tcols = dfs_tcols(p->herm, q.N1);
     a.tpitch = dfs_tpitch(p->herm, q.N1);
+    int lines;
+    dfs_lines(p, a.line0, lines);
     const int M = q.n1 / 2;
     const int T = M / E;
     if (sizeof(R) == 4 && p->d_stw_phi && a.logm >= 9 && a.logm <= 11) {
         // two rows a thread group, 256 threads a CTA
         a.CB = 2 * (256 / T);
         const size_t smem = sizeof(C) * (size_t)a.CB * (region_len<C>(M) + a.tcols);
-        const dim3 grid(q.n2 / a.CB, p->n_members * p->n_fields);
+        const dim3 grid(q.n2 / a.CB, lines);
         const int threads = (a.CB / 2) * T;
         switch (a.logm) {
             case 9: return p->herm ? run_phi2<9, true>(p, a, smem, grid, threads)
@@ -284,7 +287,7 @@ cudaError_t launch_phi(dfsnufft_plan p) {
     while (cb > 1 && per_row * cb > 160 * 1024) cb >>= 1;
     a.CB = cb;
     const size_t smem = per_row * cb;
-    const dim3 grid(q.n2 / cb, p->n_members * p->n_fields);
+    const dim3 grid(q.n2 / cb, lines);
     if (p->herm) return dispatch_phi<R, true>(p, a, smem, grid, cb * T);
     return dispatch_phi<R, false>(p, a, smem, grid, cb * T);
 }

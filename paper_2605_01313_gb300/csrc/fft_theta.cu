@@ -29,14 +29,15 @@
 // shared-memory limits).
 #include <type_traits>
 
+#include "coef_map.cuh"
 #include "fft_core.cuh"
 #include "tma.cuh"
 
 using namespace dfs_fft;
+using namespace dfs_coef;
 
 namespace {
 
-template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake(a.x, -a.y); }
 // A coefficient as the pass's complex type: itself, or (double-single passes of
 // FP64 plans) the FP64 value times 2^-sh (the line's exponent shift, df32.cuh)
 // split into double-single parts.
@@ -44,30 +45,6 @@ template <typename C, typename CIn> __device__ __forceinline__ C in_value(CIn v,
 template <> __device__ __forceinline__ dfc in_value<dfc, double2>(double2 v, int sh) {
     return to_dfc_scaled(v, sh);
 }
-template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) {
-    return cmake(a.x * s, a.y * s);
-}
-
-// h_{n,k} of a real-field plan (see above) for -half <= n <= half and
-// 0 <= k <= N1/2, from a reader cf(row, col) of the coefficient array that
-// returns zero outside it.  half = N2/2.
-template <typename C, class Rd>
-__device__ __forceinline__ C herm_coef(int n, int k, int half, int N1, Rd &cf) {
-    typedef decltype(C().x) R;
-    const int N1h = N1 / 2;
-    const int qa = N1h + k;                        // array column of m = k (N1 if k = N1/2)
-    if (k == N1h)                                  // mirror of the Nyquist column
-        return n == -half ? cmake((R)0, (R)0) : cscale(cconj(cf(half - n, 0)), (R)0.5);
-    if (n == half) return cscale(cconj(cf(0, N1 - qa)), (R)0.5);   // mirror of the Nyquist row
-    const C c = cf(n + half, qa);
-    if (n == -half) return cscale(c, (R)0.5);
-    if (k == 0) {
-        const C mirror = cf(half - n, qa);
-        return cscale(cmake(c.x + mirror.x, c.y - mirror.y), (R)0.5);
-    }
-    return c;
-}
-
 // Complex coefficient c_{n,m} (m >= 0, |n| <= N) of a field given by its
 // partial-regularity DFS coefficients (Sec. 4): col[k] = f^c_{k,m} + i f^s_{k,m},
 // k = 0..N, for this m.  First the standard coefficient S = f~^c + i f~^s at |n|
@@ -153,6 +130,7 @@ struct ThetaArgs {
     int F;                    // fields per member (line f belongs to member f / F)
     int tcols, tpitch;        // transformed columns, row pitch of T
     int prM, prN;             // partial-regularity input: truncation (prM < 0: complex input)
+    int line0;                // first line (blockIdx.y = line - line0)
 };
 
 // grid (ceil(tcols / CB), lines); block CB * n2/E threads, thread = (t, c) with c fastest.
@@ -176,7 +154,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int c = threadIdx.x % a.CB;
     const int t = threadIdx.x / a.CB;
     const int q = blockIdx.x * a.CB + c;           // column of T
-    const int f = blockIdx.y;
+    const int f = a.line0 + blockIdx.y;
     const int2 rr = rowrange[f / a.F];
     const bool col_ok = q < a.tcols;
     const CIn *cf0 = coef + (size_t)f * a.N2 * a.N1;
@@ -228,6 +206,7 @@ struct ThetaTmaArgs {
     int tcols, tpitch;        // transformed columns, row pitch of T
     int col_base;             // array column of transformed column 0
     int prM, prN;             // partial-regularity input: truncation (prM < 0: complex input)
+    int line0;                // first line of the launch (blocks cover lines line0 ..)
 };
 
 // LOGH > 0: half length 2^LOGH fixed at compile time (unrolled transform);
@@ -280,8 +259,8 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int prs = a.prN + 1;                     // PRIN: staged elements a column
     // issued by thread 0 (TMA boxes), or by every thread (PRIN)
     auto issue = [&](int blk, int b) {
-        const int f = blk / a.nbq;
-        const int qb = blk - f * a.nbq;
+        const int f = a.line0 + blk / a.nbq;
+        const int qb = blk - (f - a.line0) * a.nbq;
         C *dst = inb + (size_t)b * a.in_elems;
         if constexpr (PRIN) {
             for (int cc = 0; cc < CB; ++cc) {
@@ -313,8 +292,8 @@ __global__ void __launch_bounds__(MAXT, MINB)
         if (HERM && !PRIN && threadIdx.x < CB) {
             // conj c_{-N2/2,-m} of each column (the mirror of the Nyquist row),
             // fetched while the block's boxes land
-            const int f = blk / a.nbq;
-            const int q = (blk - f * a.nbq) * CB + threadIdx.x;
+            const int f = a.line0 + blk / a.nbq;
+            const int q = (blk - (f - a.line0) * a.nbq) * CB + threadIdx.x;
             const int qa = a.col_base + q;
             C v = cmake((R)0, (R)0);
             if (q < a.tcols) v = coef[(size_t)f * a.N2 * a.N1 + (a.N1 - qa)];
@@ -336,9 +315,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
             __syncthreads();
             return;
         }
-        const int f = blk / a.nbq;
+        const int f = a.line0 + blk / a.nbq;
         const int2 rr = rowrange[f / a.F];
-        const int q = (blk - f * a.nbq) * CB + c;      // column of T
+        const int q = (blk - (f - a.line0) * a.nbq) * CB + c;      // column of T
         const int qa = a.col_base + q;                 // array column
         const bool col_ok = q < a.tcols;
         const R sq = col_ok ? inv1[qa < a.N1 ? qa : 0] : (R)0;
@@ -520,7 +499,9 @@ cudaError_t launch_theta_tma_cb(dfsnufft_plan p, const void *coeffs, int prM, in
     // the box's first column must sit on a 16-byte boundary
     if ((a.col_base * sizeof(C)) % 16 != 0) return cudaErrorNotSupported;
     a.nbq = (a.tcols + CB - 1) / CB;
-    const int lines = p->n_members * p->n_fields;
+    int line0, lines;
+    dfs_lines(p, line0, lines);
+    a.line0 = line0;
     a.total = a.nbq * lines;
     a.F = p->n_fields;
     // boxes of CB columns x box_rows rows, each a multiple of 128 bytes (box
@@ -544,7 +525,7 @@ cudaError_t launch_theta_tma_cb(dfsnufft_plan p, const void *coeffs, int prM, in
     memset(&tmap, 0, sizeof(tmap));             // unused by the partial-regularity form
     if (!pr) {
         cudaError_t e = dfs_encode_tensor_map_2d(&tmap, coeffs, (uint64_t)q.N1 * (sizeof(C) / 8),
-                                                 (uint64_t)q.N2 * lines,
+                                                 (uint64_t)q.N2 * (line0 + lines),
                                                  sizeof(C) * (uint64_t)q.N1,
                                                  (uint32_t)(CB * (sizeof(C) / 8)),
                                                  (uint32_t)a.box_rows);
@@ -637,6 +618,9 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs, int prM, int prN) 
     a.tpitch = dfs_tpitch(p->herm, q.N1);
     a.prM = prM;
     a.prN = prN;
+    int line0, lines;
+    dfs_lines(p, line0, lines);
+    a.line0 = line0;
     const int T = q.n2 / E;
     int cb = MAXT / T;
     if (cb < 1) cb = 1;
@@ -647,7 +631,7 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs, int prM, int prN) 
     while (cb > 1 && per_col * cb > 160 * 1024) cb >>= 1;
     a.CB = cb;
     const size_t smem = per_col * cb;
-    const dim3 grid((a.tcols + cb - 1) / cb, p->n_members * p->n_fields);
+    const dim3 grid((a.tcols + cb - 1) / cb, lines);
     if (prM >= 0) {
         if (!p->herm) return cudaErrorInvalidValue;
         if (wide) return run_theta_plain<R, 16, true, true>(p, a, coeffs, smem, grid, cb * T);
@@ -666,8 +650,9 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs, int prM, int prN) 
 // Each line's exponent maximum for the double-single passes (k_coef_maxexp).
 static cudaError_t launch_coef_maxexp(dfsnufft_plan p, const void *coeffs, int prM, int prN) {
     const dfsnufft_params &q = p->prm;
-    const int lines = p->n_members * p->n_fields;
-    cudaError_t e = cudaMemsetAsync(p->d_emax, 0, sizeof(int) * lines, p->stream);
+    int line0, lines;
+    dfs_lines(p, line0, lines);
+    cudaError_t e = cudaMemsetAsync(p->d_emax + line0, 0, sizeof(int) * lines, p->stream);
     if (e) return e;
     const bool pr = prM >= 0;
     const int line_elems = pr ? (prM + 1) * (prN + 1) : q.N2 * q.N1;
@@ -676,7 +661,8 @@ static cudaError_t launch_coef_maxexp(dfsnufft_plan p, const void *coeffs, int p
     int blocks = (n + 2047) / 2048;
     if (blocks > 1024) blocks = 1024;
     k_coef_maxexp<<<dim3(blocks, lines), 256, 0, p->stream>>>(
-        (const double2 *)coeffs, line_elems, q.N2, q.N1, herm, p->d_emax);
+        (const double2 *)coeffs + (size_t)line0 * line_elems, line_elems, q.N2, q.N1, herm,
+        p->d_emax + line0);
     return cudaGetLastError();
 }
 

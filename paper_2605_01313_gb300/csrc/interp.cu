@@ -37,6 +37,7 @@ struct InterpArgs {
     int NG;               // field groups per bin, ceil(F / FG)
     int BW, box_f;        // TMA box width (cells, multiple of 4), floats per staged box
     int bstride;          // per-member stride of the bin arrays
+    int fa, fn;           // fields evaluated: fa .. fa + fn - 1 of each member
 };
 
 // Kernel weights by Horner's rule: for tap a the weight phi((a - c0) - t) is a
@@ -94,8 +95,8 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const __grid_const
         const int row0 = by * a.tile_y - a.c0;
         const int s = p0 + bin_start[bin];
         const int e = p0 + bin_start[bin + 1];
-        for (int f0 = 0; f0 < a.F; f0 += a.FG) {
-            const int fg = min(a.FG, a.F - f0);
+        for (int f0 = a.fa; f0 < a.fa + a.fn; f0 += a.FG) {
+            const int fg = min(a.FG, a.fa + a.fn - f0);
             __syncthreads();
             // one warp per tile row: coalesced reads of TW consecutive cells
             for (int rr = threadIdx.x >> 5; rr < fg * TH; rr += blockDim.x >> 5) {
@@ -217,8 +218,8 @@ __global__ void __launch_bounds__(256) k_interp_df(InterpArgs a,
         const int row0 = by * a.tile_y - a.c0;
         const int s = p0 + bin_start[bin];
         const int e = p0 + bin_start[bin + 1];
-        for (int f0 = 0; f0 < a.F; f0 += a.FG) {
-            const int fg = min(a.FG, a.F - f0);
+        for (int f0 = a.fa; f0 < a.fa + a.fn; f0 += a.FG) {
+            const int fg = min(a.FG, a.fa + a.fn - f0);
             __syncthreads();
             for (int rr = threadIdx.x >> 5; rr < fg * TH; rr += blockDim.x >> 5) {
                 const int ff = rr / TH;
@@ -337,8 +338,8 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a,
         const int row0 = by * a.tile_y - a.c0;
         const int s = p0 + bin_start[bin];
         const int e = p0 + bin_start[bin + 1];
-        for (int f0 = 0; f0 < a.F; f0 += a.FG) {
-            const int fg = min(a.FG, a.F - f0);
+        for (int f0 = a.fa; f0 < a.fa + a.fn; f0 += a.FG) {
+            const int fg = min(a.FG, a.fa + a.fn - f0);
             __syncthreads();
             // one warp per tile row, a lane per pair of cells (Q <= 32); each warp
             // issues the loads of 4 rows before storing any, to keep them in flight
@@ -451,8 +452,8 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
     };
     auto issue = [&](int sub, int b) {
         const int task = sub / a.NG;
-        const int f0 = (sub - task * a.NG) * a.FG;
-        const int fg = min(a.FG, a.F - f0);
+        const int f0 = a.fa + (sub - task * a.NG) * a.FG;
+        const int fg = min(a.FG, a.fa + a.fn - f0);
         const int bin = task_bin[task];
         const int by = bin / a.nbx;
         const int bx = bin - by * a.nbx;
@@ -478,8 +479,8 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
         if (threadIdx.x == 0 && nxt < total) issue(nxt, cur ^ 1);
         // geometry and the first point's record, fetched while the boxes land
         const int task = sub / a.NG;
-        const int f0 = (sub - task * a.NG) * a.FG;
-        const int fg = min(a.FG, a.F - f0);
+        const int f0 = a.fa + (sub - task * a.NG) * a.FG;
+        const int fg = min(a.FG, a.fa + a.fn - f0);
         const int bin = task_bin[task];
         const int by = bin / a.nbx;
         const int bx = bin - by * a.nbx;
@@ -586,7 +587,7 @@ __global__ void __launch_bounds__(256) k_interp_direct(InterpArgs a,
             const int cx = b.x - odd;                  // even: pairs never straddle a row end
             float w8[WP], wy[W];
             paired_weights<W>(tx, ty, odd, hw, w8, wy);
-            for (int f = 0; f < a.F; ++f) {
+            for (int f = a.fa; f < a.fa + a.fn; ++f) {
                 const float *g = grid + (size_t)(k * a.F + f) * a.n2 * a.n1;
                 float acc = 0.f;
 #pragma unroll
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(256) k_interp_direct(InterpArgs a,
             R wx[W], wy[W];
             es_weights<R, W>(tx, hw, wx);
             es_weights<R, W>(ty, hw, wy);
-            for (int f = 0; f < a.F; ++f) {
+            for (int f = a.fa; f < a.fa + a.fn; ++f) {
                 const R *g = grid + (size_t)(k * a.F + f) * a.n2 * a.n1;
                 R acc = 0;
 #pragma unroll
@@ -690,12 +691,12 @@ __global__ void __launch_bounds__(256) k_interp_wtile(InterpArgs a,
             cp_async_commit();
         };
         __syncwarp();                                      // the previous chunk's boxes are consumed
-        if (fits) stage(0);
-        for (int f = 0; f < a.F; ++f) {
+        if (fits) stage(a.fa);
+        for (int f = a.fa; f < a.fa + a.fn; ++f) {
             const float *g = grid + (size_t)(k * a.F + f) * a.n2 * a.n1;
             float acc = 0.f;
             if (fits) {
-                if (f + 1 < a.F) {
+                if (f + 1 < a.fa + a.fn) {
                     __syncwarp();                          // half (f + 1) & 1 was read at f - 1
                     stage(f + 1);
                     cp_async_wait_group<1>();
@@ -747,6 +748,9 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
     a.c0 = p->c0;
     a.F = p->n_fields;
     a.bstride = p->bstride;
+    // a line window (one-member plans) selects fields
+    a.fa = p->nwin ? p->win0 : 0;
+    a.fn = p->nwin ? p->nwin : a.F;
     a.NG = 1;
     a.BW = 0;
     a.box_f = 0;
@@ -798,7 +802,7 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
                 if (fg < 1) fg = 1;
                 if (fg > a.F) fg = a.F;
                 a.FG = fg;
-                a.NG = (a.F + fg - 1) / fg;
+                a.NG = (a.fn + fg - 1) / fg;
                 const size_t smem = 128 + 128 + 2 * (size_t)fg * a.box_f * sizeof(float);
                 cudaError_t e = dfs_allow_smem((const void *)k_interp_tma<W>, smem);
                 if (e) return e;

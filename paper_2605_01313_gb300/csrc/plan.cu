@@ -340,6 +340,14 @@ static void release(dfsnufft_plan p) {
     if (p->stage_free) cudaEventDestroy(p->stage_free);
     if (p->coef_ready) cudaEventDestroy(p->coef_ready);
     p->stage_free = p->coef_ready = nullptr;
+    for (int i = 0; i < p->n_line_ev; ++i)
+        if (p->line_ev[i]) cudaEventDestroy(p->line_ev[i]);
+    free(p->line_ev);
+    p->line_ev = nullptr;
+    p->n_line_ev = 0;
+    if (p->pts_copied) cudaEventDestroy(p->pts_copied);
+    if (p->vals_copied) cudaEventDestroy(p->vals_copied);
+    p->pts_copied = p->vals_copied = nullptr;
 }
 
 template <typename C, typename R>
@@ -872,6 +880,11 @@ extern "C" int dfsnufft_set_points_host(dfsnufft_plan p, int64_t n_points, const
     DFS_CK(p, cudaMemcpyAsync(p->d_pts_stage, lon, b, cudaMemcpyHostToDevice, p->stream));
     DFS_CK(p, cudaMemcpyAsync(p->d_pts_stage + p->pts_stage_cap, colat, b,
                               cudaMemcpyHostToDevice, p->stream));
+    // the next execute_host's coefficient copies queue behind these on the link
+    if (!p->pts_copied)
+        DFS_CK(p, cudaEventCreateWithFlags(&p->pts_copied, cudaEventDisableTiming));
+    DFS_CK(p, cudaEventRecord(p->pts_copied, p->stream));
+    p->pts_pending = 1;
     p->has_points = 0;
     DFS_CK(p, timing_begin(p, 0));
     DFS_CK(p, dfs_launch_set_points(p, p->d_pts_stage, p->d_pts_stage + p->pts_stage_cap));
@@ -887,13 +900,15 @@ extern "C" int dfsnufft_set_points_host(dfsnufft_plan p, int64_t n_points, const
 // row and column 0 of the next are contiguous, one 2-D copy of N1/2 + 1
 // elements a row takes both, and the first row of each line is copied from
 // column 0 to N1/2.  Other plans copy the whole array.
+// Lines l0 .. l0 + nl - 1 of the coefficients (all lines: nl = members x fields).
 static cudaError_t stage_coefficients(dfsnufft_plan p, const void *coeffs, size_t cs,
-                                      cudaStream_t st) {
+                                      cudaStream_t st, int l0, int nl) {
     const dfsnufft_params &q = p->prm;
-    const size_t rows = (size_t)p->n_members * p->n_fields * q.N2;
+    const size_t rows = (size_t)nl * q.N2;
     const size_t row = cs * q.N1, half = cs * (q.N1 / 2);
-    char *d = static_cast<char *>(p->d_coef_stage);
-    const char *h = static_cast<const char *>(coeffs);
+    const size_t off = (size_t)l0 * q.N2 * row;
+    char *d = static_cast<char *>(p->d_coef_stage) + off;
+    const char *h = static_cast<const char *>(coeffs) + off;
     if (!p->herm)
         return cudaMemcpyAsync(d, h, rows * row, cudaMemcpyHostToDevice, st);
     cudaError_t e = cudaSuccess;
@@ -905,8 +920,7 @@ static cudaError_t stage_coefficients(dfsnufft_plan p, const void *coeffs, size_
                             cudaMemcpyHostToDevice, st);
     if (!e)
         e = cudaMemcpy2DAsync(d, (size_t)q.N2 * row, h, (size_t)q.N2 * row, half + cs,
-                              (size_t)p->n_members * p->n_fields, cudaMemcpyHostToDevice,
-                              st);
+                              (size_t)nl, cudaMemcpyHostToDevice, st);
     return e;
 }
 
@@ -918,6 +932,21 @@ static size_t staged_coefficient_bytes(dfsnufft_plan p, size_t cs) {
     const size_t half = cs * (q.N1 / 2);
     if (!p->herm) return rows * cs * q.N1;
     return (rows - 1) * (half + cs) + half + lines * (half + cs);
+}
+
+// At least 2 n events for the per-field pipeline of execute_host.
+static int ensure_line_events(dfsnufft_plan p, int n) {
+    if (p->n_line_ev >= 2 * n) return DFSNUFFT_OK;
+    cudaEvent_t *ev = (cudaEvent_t *)realloc(p->line_ev, sizeof(cudaEvent_t) * 2 * n);
+    if (!ev) return DFSNUFFT_ERR_OOM;
+    p->line_ev = ev;
+    for (int i = p->n_line_ev; i < 2 * n; ++i) {
+        DFS_CK(p, cudaEventCreateWithFlags(&p->line_ev[i], cudaEventDisableTiming));
+        p->n_line_ev = i + 1;
+    }
+    if (!p->vals_copied)
+        DFS_CK(p, cudaEventCreateWithFlags(&p->vals_copied, cudaEventDisableTiming));
+    return DFSNUFFT_OK;
 }
 
 extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *values) {
@@ -949,11 +978,47 @@ extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *
         DFS_CK(p, cudaEventCreateWithFlags(&p->coef_ready, cudaEventDisableTiming));
         DFS_CK(p, cudaEventRecord(p->stage_free, p->stream));     // every earlier reader
     }
-    // the copies wait only for the last reader of the staging buffer, not for
-    // the set_points work queued on the plan's stream, and the transform waits
-    // for the copies
+    // the copies wait only for the last reader of the staging buffer (and for
+    // set_points_host's point copies, which use the same link), not for the
+    // set_points kernels queued on the plan's stream
     DFS_CK(p, cudaStreamWaitEvent(p->copy_stream, p->stage_free, 0));
-    DFS_CK(p, stage_coefficients(p, coeffs, cs, p->copy_stream));
+    if (p->pts_pending) {
+        DFS_CK(p, cudaStreamWaitEvent(p->copy_stream, p->pts_copied, 0));
+        p->pts_pending = 0;
+    }
+    const int F = p->n_fields;
+    if (p->n_members == 1 && F > 1 && q.dtype == DFSNUFFT_F32) {
+        // FP32 (bound by the host link): pipelined per field, so that field f's
+        // transform and interpolation start once its coefficients have landed,
+        // and its values travel back while later fields are still being copied
+        // in or computed.  FP64 plans are bound by arithmetic and take one
+        // transform of all fields.
+        rc = ensure_line_events(p, F);
+        if (rc) return rc;
+        for (int f = 0; f < F; ++f) {
+            DFS_CK(p, stage_coefficients(p, coeffs, cs, p->copy_stream, f, 1));
+            DFS_CK(p, cudaEventRecord(p->line_ev[2 * f], p->copy_stream));
+        }
+        const size_t fb = rs * (size_t)p->n_points;
+        for (int f = 0; f < F; ++f) {
+            DFS_CK(p, cudaStreamWaitEvent(p->stream, p->line_ev[2 * f], 0));
+            p->win0 = f;
+            p->nwin = 1;
+            rc = dfsnufft_execute(p, p->d_coef_stage, p->d_val_stage);
+            p->win0 = p->nwin = 0;
+            if (rc) return rc;
+            DFS_CK(p, cudaEventRecord(p->line_ev[2 * f + 1], p->stream));
+            DFS_CK(p, cudaStreamWaitEvent(p->copy_stream, p->line_ev[2 * f + 1], 0));
+            DFS_CK(p, cudaMemcpyAsync(static_cast<char *>(values) + f * fb,
+                                      static_cast<const char *>(p->d_val_stage) + f * fb, fb,
+                                      cudaMemcpyDeviceToHost, p->copy_stream));
+        }
+        DFS_CK(p, cudaEventRecord(p->stage_free, p->stream));
+        DFS_CK(p, cudaEventRecord(p->vals_copied, p->copy_stream));
+        DFS_CK(p, cudaStreamWaitEvent(p->stream, p->vals_copied, 0));
+        return dfsnufft_plan_check(p);
+    }
+    DFS_CK(p, stage_coefficients(p, coeffs, cs, p->copy_stream, 0, p->n_members * F));
     DFS_CK(p, cudaEventRecord(p->coef_ready, p->copy_stream));
     DFS_CK(p, cudaStreamWaitEvent(p->stream, p->coef_ready, 0));
     rc = dfsnufft_execute(p, p->d_coef_stage, p->d_val_stage);

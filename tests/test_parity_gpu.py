@@ -291,14 +291,20 @@ def test_zonal_flow_analytic(torch_cuda):
 
 # ------------------------------------------------------------------ API behaviour
 
-def test_host_variants_match_device(torch_cuda):
+@pytest.mark.parametrize("n_fields", [1, 3, 5])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_host_variants_match_device(torch_cuda, n_fields, dtype):
+    """The host-buffer calls (one field: one transform; several fields:
+    pipelined field by field) give the device path's values bit for bit."""
     from paper_2605_01313_gb300 import Plan
-    wl = synth.small_workload(16, 128, 64, n_fields=3, dtype="f32")
+    wl = synth.small_workload(16, 128, 64, n_fields=n_fields, dtype=dtype)
     dev = run_gpu(torch_cuda, wl)
-    with Plan(wl.n_lon, wl.n_lat, wl.tol, "f32", 3) as plan:
-        plan.set_points_host(wl.lon, wl.colat)
-        host = plan.execute_host(wl.coeffs.astype(np.complex64))
-    assert np.array_equal(dev, host)
+    cd = np.complex128 if dtype == "f64" else np.complex64
+    with Plan(wl.n_lon, wl.n_lat, wl.tol, dtype, n_fields) as plan:
+        for _ in range(2):
+            plan.set_points_host(wl.lon, wl.colat)
+            host = plan.execute_host(wl.coeffs.astype(cd))
+            assert np.array_equal(dev, host)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
