@@ -220,6 +220,23 @@ int dfsnufft_ensemble_check(dfsnufft_ensemble ens);
 /* The batched plan of group g (owned by the ensemble). */
 int dfsnufft_ensemble_plan(dfsnufft_ensemble ens, int group, dfsnufft_plan *out);
 
+/* Persistent mode (on = 1) or the fork/join graph (on = 0, the default) for the
+ * next steps.  In persistent mode each group's set_points still runs as a branch
+ * of the step's graph, and the theta pass, phi pass and interpolation of every
+ * member of every group then run as ONE persistent launch, recorded in the same
+ * graph: its CTAs drain a device work queue that lists all groups' theta tasks
+ * (column blocks), then their phi tasks (row blocks), then their interpolation
+ * tasks (bins); a phi task waits until its group's theta tasks are done and an
+ * interpolation task until its group's phi tasks are done (Sec. 5, the NUFFT of
+ * Eq. 5.3 for many fields and members of uneven grids at once).  Each wait is
+ * bounded (about a second); one that runs out ends the launch early and
+ * dfsnufft_ensemble_check then returns DFSNUFFT_ERR_TIMEOUT.  Supported for
+ * FP32 ensembles of at most 16 groups whose plans keep points sorted, have
+ * kernel width 6 or 7 and fine grids from 256 to 4096 cells a side; otherwise
+ * DFSNUFFT_ERR_UNSUPPORTED and the mode is unchanged.  The step is recorded
+ * again on the next run. */
+int dfsnufft_ensemble_set_persistent(dfsnufft_ensemble ens, int on);
+
 int dfsnufft_ensemble_destroy(dfsnufft_ensemble ens);
 
 /* ---- serving: continuous batching under an HBM budget ------------------- */

@@ -28,6 +28,19 @@ int dfsnufft_probe_fma_rate(int dtype, double target_ms, double *flops_per_s);
  * of this library's failure detection that needs no GPU fault. */
 int dfsnufft_selftest_wait_timeout(long long cycles, int *device_status, double *elapsed_ms);
 
+/* Self-test of the persistent ensemble step's queue waits: the last step of an
+ * ensemble in persistent mode is launched once more, uncaptured and
+ * synchronously, with group 0's count of theta tasks one higher than it can
+ * ever reach, so that its phi tasks wait for a completion that never comes.
+ * Each wait gives up after `cycles` SM clock cycles (1 <= cycles <= 4e9); the
+ * first that does raises the step's abort flag and timeout status, the other
+ * CTAs skip their remaining tasks and the launch ends.  Returns
+ * DFSNUFFT_ERR_TIMEOUT (the expected outcome) or DFSNUFFT_OK, without making
+ * the failure sticky: the values of that launch are incomplete, and the next
+ * dfsnufft_ensemble_run computes normally.  DFSNUFFT_ERR_NO_POINTS if the
+ * ensemble is not in persistent mode or has not run a step yet. */
+int dfsnufft_ensemble_selftest_queue_timeout(struct dfsnufft_ensemble_s *ens, long long cycles);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,6 +5,11 @@
 // replayed with one graph launch while the caller's pointers and point counts
 // stay the same; when they change, the step runs once uncaptured (it may
 // allocate or upload offsets) and is recorded again.
+//
+// In persistent mode (dfsnufft_ensemble_set_persistent) the groups' set_points
+// still run as the graph's fork/join branches, and the transform and
+// interpolation of every group then run as one persistent launch that drains a
+// device work queue (ensemble_persistent.cu), recorded in the same graph.
 #include <stdlib.h>
 #include <string.h>
 
@@ -12,6 +17,8 @@
 #include <vector>
 
 #include "common.cuh"
+#include "ensemble_persistent.cuh"
+#include "tma.cuh"
 
 struct dfsnufft_ensemble_s {
     int n_groups;
@@ -27,6 +34,13 @@ struct dfsnufft_ensemble_s {
     std::vector<const void *> sig_ptr;
     std::vector<int64_t> sig_counts;
     int status;
+    // persistent mode
+    int persistent;
+    int *d_ctl;                          // the step's control words (ENS_CTL_INTS)
+    EnsArgs *args;                       // the groups' views; per-step pointers filled by the step
+    int args_ready;                      // args hold a complete step (for the self-test)
+    int num_sms;
+    int resident;                        // CTAs per SM of the persistent step (0: unknown)
 };
 
 namespace {
@@ -37,7 +51,8 @@ int ens_fail(dfsnufft_ensemble e, int code) {
 }
 
 // The step, enqueued on the group streams after a fork from `main` and joined
-// back into it.
+// back into it; in persistent mode the groups' branches only set their points,
+// and one launch on `main` does the rest.
 int enqueue_step(dfsnufft_ensemble e, cudaStream_t main, const int64_t *const *counts,
                  const double *const *lon, const double *const *colat, const void *const *coeffs,
                  void *const *values) {
@@ -46,11 +61,27 @@ int enqueue_step(dfsnufft_ensemble e, cudaStream_t main, const int64_t *const *c
         if (cudaStreamWaitEvent(e->streams[g], e->fork, 0)) return DFSNUFFT_ERR_CUDA;
         int rc = dfsnufft_set_points_batch(e->plans[g], counts[g], lon[g], colat[g]);
         if (rc) return rc;
-        rc = dfsnufft_execute(e->plans[g], coeffs[g], values[g]);
-        if (rc) return rc;
+        if (!e->persistent) {
+            rc = dfsnufft_execute(e->plans[g], coeffs[g], values[g]);
+            if (rc) return rc;
+        }
         if (cudaEventRecord(e->done[g], e->streams[g])) return DFSNUFFT_ERR_CUDA;
         if (cudaStreamWaitEvent(main, e->done[g], 0)) return DFSNUFFT_ERR_CUDA;
     }
+    if (!e->persistent) return DFSNUFFT_OK;
+    EnsArgs &a = *e->args;
+    a.total = 0;
+    for (int g = 0; g < e->n_groups; ++g) {
+        dfs_ensemble_group_points(e->plans[g], a.g[g]);     // set_points may reallocate
+        a.g[g].coef = static_cast<const float2 *>(coeffs[g]);
+        a.g[g].values = static_cast<float *>(values[g]);
+        a.total += a.g[g].ntask[0] + a.g[g].ntask[1] + a.g[g].ntask[2];
+    }
+    a.budget = DFS_WAIT_CYCLES;
+    a.poison_group = -1;
+    e->args_ready = 1;
+    if (dfs_ensemble_step_launch(a, e->d_ctl, e->num_sms, main, &e->resident))
+        return DFSNUFFT_ERR_CUDA;
     return DFSNUFFT_OK;
 }
 
@@ -64,6 +95,8 @@ void release(dfsnufft_ensemble e) {
         if (v) cudaEventDestroy(v);
     if (e->fork) cudaEventDestroy(e->fork);
     if (e->origin) cudaStreamDestroy(e->origin);
+    if (e->d_ctl) cudaFree(e->d_ctl);
+    delete e->args;
 }
 
 }  // namespace
@@ -92,6 +125,12 @@ extern "C" int dfsnufft_ensemble_create_opts(int n_groups, const int *n_members,
     e->fork = nullptr;
     e->origin = nullptr;
     e->status = 0;
+    e->persistent = 0;
+    e->d_ctl = nullptr;
+    e->args = nullptr;
+    e->args_ready = 0;
+    e->num_sms = 0;
+    e->resident = 0;
     e->plans.assign(n_groups, nullptr);
     e->streams.assign(n_groups, nullptr);
     e->done.assign(n_groups, nullptr);
@@ -170,6 +209,15 @@ extern "C" int dfsnufft_ensemble_run(dfsnufft_ensemble e, const int64_t *const *
     return DFSNUFFT_OK;
 }
 
+// The persistent step's status word, after synchronising the ensemble's stream.
+static int read_ctl_status(dfsnufft_ensemble e) {
+    int st = 0;
+    if (cudaStreamSynchronize(e->stream) ||
+        cudaMemcpy(&st, e->d_ctl + ENS_STATUS, sizeof(int), cudaMemcpyDeviceToHost))
+        return DFSNUFFT_ERR_CUDA;
+    return st ? DFSNUFFT_ERR_TIMEOUT : DFSNUFFT_OK;
+}
+
 extern "C" int dfsnufft_ensemble_check(dfsnufft_ensemble e) {
     if (!e) return DFSNUFFT_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(e->stream)) return ens_fail(e, DFSNUFFT_ERR_CUDA);
@@ -177,7 +225,60 @@ extern "C" int dfsnufft_ensemble_check(dfsnufft_ensemble e) {
         int rc = dfsnufft_plan_check(p);
         if (rc) return ens_fail(e, rc);
     }
+    if (e->persistent && e->d_ctl) {
+        int rc = read_ctl_status(e);
+        if (rc) return ens_fail(e, rc);
+    }
     return e->status;
+}
+
+extern "C" int dfsnufft_ensemble_set_persistent(dfsnufft_ensemble e, int on) {
+    if (!e) return DFSNUFFT_ERR_INVALID_ARG;
+    if (e->status) return e->status;
+    if (on) {
+        if (e->n_groups > ENS_MAXG) return DFSNUFFT_ERR_UNSUPPORTED;
+        EnsArgs *a = e->args ? e->args : new (std::nothrow) EnsArgs();
+        if (!a) return DFSNUFFT_ERR_OOM;
+        e->args = a;
+        memset(a, 0, sizeof(*a));
+        a->ngroups = e->n_groups;
+        for (int g = 0; g < e->n_groups; ++g)
+            if (!dfs_ensemble_group(e->plans[g], a->g[g])) return DFSNUFFT_ERR_UNSUPPORTED;
+        if (!e->d_ctl) {
+            if (cudaMalloc(&e->d_ctl, sizeof(int) * ENS_CTL_INTS)) {
+                cudaGetLastError();
+                e->d_ctl = nullptr;
+                return DFSNUFFT_ERR_OOM;
+            }
+            if (cudaMemset(e->d_ctl, 0, sizeof(int) * ENS_CTL_INTS))
+                return ens_fail(e, DFSNUFFT_ERR_CUDA);
+        }
+        e->num_sms = e->plans[0]->num_sms > 0 ? e->plans[0]->num_sms : 1;
+    }
+    e->persistent = on ? 1 : 0;
+    e->args_ready = 0;
+    // the next run records the step again
+    if (e->exec) {
+        cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+    }
+    e->sig_ptr.clear();
+    e->sig_counts.clear();
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_ensemble_selftest_queue_timeout(dfsnufft_ensemble e,
+                                                        long long cycles) {
+    if (!e || cycles < 1 || cycles > 4000000000LL) return DFSNUFFT_ERR_INVALID_ARG;
+    if (!e->persistent || !e->args_ready) return DFSNUFFT_ERR_NO_POINTS;
+    if (e->status) return e->status;
+    EnsArgs a = *e->args;
+    a.budget = cycles;
+    a.poison_group = 0;
+    if (cudaStreamSynchronize(e->stream) ||
+        dfs_ensemble_step_launch(a, e->d_ctl, e->num_sms, e->stream, &e->resident))
+        return ens_fail(e, DFSNUFFT_ERR_CUDA);
+    return read_ctl_status(e);
 }
 
 extern "C" int dfsnufft_ensemble_plan(dfsnufft_ensemble e, int group, dfsnufft_plan *out) {

@@ -45,6 +45,7 @@ EXPORTS = (
     "dfsnufft_execute_pr", "dfsnufft_grid_to_coeffs", "dfsnufft_interpolate_grid",
     "dfsnufft_departure_points", "dfsnufft_rotate_to_arrival", "dfsnufft_lagrange_interp",
     "dfsnufft_plan_latitudes", "dfsnufft_plan_host_copy_bytes",
+    "dfsnufft_ensemble_set_persistent", "dfsnufft_ensemble_selftest_queue_timeout",
 )
 REAL_FIELDS = 1
 KEEP_ORDER = 2
@@ -160,6 +161,8 @@ def lib():
         L.dfsnufft_ensemble_check.argtypes = [vp]
         L.dfsnufft_ensemble_plan.argtypes = [vp, i32, ctypes.POINTER(vp)]
         L.dfsnufft_ensemble_destroy.argtypes = [vp]
+        L.dfsnufft_ensemble_set_persistent.argtypes = [vp, i32]
+        L.dfsnufft_ensemble_selftest_queue_timeout.argtypes = [vp, ctypes.c_longlong]
         L.dfsnufft_server_create.argtypes = [f64, i32, i32, i64, i32, ctypes.POINTER(vp)]
         L.dfsnufft_autotune.argtypes = [ctypes.POINTER(TuneArgs), ctypes.POINTER(TuneResult), i32,
                                         ctypes.POINTER(i32), ctypes.POINTER(Options)]
@@ -700,7 +703,8 @@ class Ensemble:
     float64 tensors/list, a (members, F, 2 n_lat, n_lon) complex tensor and an
     output tensor of F x sum(counts) reals; the whole step is one CUDA graph."""
 
-    def __init__(self, groups, tol=1e-6, dtype="f32", n_fields=3, stream=None, options=None):
+    def __init__(self, groups, tol=1e-6, dtype="f32", n_fields=3, stream=None, options=None,
+                 persistent=False):
         import torch
         self.groups = [tuple(int(x) for x in g) for g in groups]
         self.dtype = "f64" if _dtype_code(dtype) == F64 else "f32"
@@ -723,6 +727,18 @@ class Ensemble:
             opts, ctypes.c_void_p(int(handle)), ctypes.byref(h)))
         self._h = h
         self._keep = None
+        if persistent:
+            self.set_persistent(True)
+
+    def set_persistent(self, on):
+        """One persistent launch per step for the transform and interpolation
+        of all groups (on), or the fork/join graph of per-group plans (off)."""
+        _check(lib().dfsnufft_ensemble_set_persistent(self._h, 1 if on else 0))
+
+    def selftest_queue_timeout(self, cycles):
+        """Status of the last persistent step relaunched with a queue wait that
+        cannot complete (ERR_TIMEOUT is the expected outcome)."""
+        return lib().dfsnufft_ensemble_selftest_queue_timeout(self._h, int(cycles))
 
     def plan_handle(self, g):
         h = ctypes.c_void_p()

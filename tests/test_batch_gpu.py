@@ -127,3 +127,80 @@ def test_ensemble_graph_uneven_grids(torch_cuda):
         off += 3 * wl.n_points
         assert np.array_equal(got, _single(torch, wl))
     ens.destroy()
+
+
+def _ensemble_inputs(torch, groups, seed0, real=False):
+    all_wls, pts, cfs, outs = [], [], [], []
+    for gi, (m, n_lon, n_lat) in enumerate(groups):
+        wls = _members(m, n_lon, n_lat, "f32", seed0 + 10 * gi)
+        all_wls.append(wls)
+        pts.append((torch.from_numpy(np.concatenate([w.lon for w in wls])).cuda(),
+                    torch.from_numpy(np.concatenate([w.colat for w in wls])).cuda(),
+                    [w.n_points for w in wls]))
+        cfs.append(torch.from_numpy(np.stack([w.coeffs for w in wls])).to(torch.complex64).cuda())
+        outs.append(torch.zeros(3 * sum(w.n_points for w in wls), dtype=torch.float32,
+                                device="cuda"))
+    return all_wls, pts, cfs, outs
+
+
+@pytest.mark.parametrize("real", [False, True])
+def test_ensemble_persistent_launch(torch_cuda, real):
+    """The persistent step (one launch draining every group's theta, phi and
+    interpolation tasks) gives every member within 2e-5 of the oracle and of
+    the fork/join graph, and the same values on a graph replay."""
+    torch = torch_cuda
+    groups = [(3, 128, 64), (2, 256, 128), (2, 512, 256), (1, 1024, 512)]
+    opts = [nufft.Options.make(real_fields=real) for _ in groups]
+    all_wls, pts, cfs, outs = _ensemble_inputs(torch, groups, 1100)
+    ref_outs = [torch.zeros_like(o) for o in outs]
+    forkjoin = nufft.Ensemble(groups, tol=1e-6, dtype="f32", n_fields=3, options=opts)
+    forkjoin.run(pts, cfs, ref_outs)
+    forkjoin.check()
+    ens = nufft.Ensemble(groups, tol=1e-6, dtype="f32", n_fields=3, options=opts,
+                         persistent=True)
+    ens.run(pts, cfs, outs)            # runs, then records
+    ens.check()
+    first = [o.cpu().numpy().copy() for o in outs]
+    for wls, vals, ref in zip(all_wls, first, ref_outs):
+        _check_members_against_oracle(wls, vals)
+        r = ref.cpu().numpy()
+        assert np.max(np.abs(vals - r)) <= 2e-5 * np.max(np.abs(r))
+    for o in outs:
+        o.zero_()
+    ens.run(pts, cfs, outs)            # graph replay
+    ens.check()
+    for a, o in zip(first, outs):
+        assert np.array_equal(a, o.cpu().numpy())
+    ens.destroy()
+    forkjoin.destroy()
+
+
+def test_ensemble_persistent_queue_wait_times_out(torch_cuda):
+    """A queue wait that can never complete gives up after its cycle budget,
+    the step reports DFSNUFFT_ERR_TIMEOUT, and the next step computes
+    correctly (failure detection without a GPU fault)."""
+    torch = torch_cuda
+    groups = [(2, 128, 64), (1, 256, 128)]
+    all_wls, pts, cfs, outs = _ensemble_inputs(torch, groups, 1200)
+    ens = nufft.Ensemble(groups, tol=1e-6, dtype="f32", n_fields=3, persistent=True)
+    ens.run(pts, cfs, outs)
+    ens.check()
+    assert ens.selftest_queue_timeout(2_000_000) == nufft.ERR_TIMEOUT   # ~1 ms of SM cycles
+    for o in outs:
+        o.zero_()
+    ens.run(pts, cfs, outs)
+    ens.check()
+    for wls, o in zip(all_wls, outs):
+        _check_members_against_oracle(wls, o.cpu().numpy())
+    ens.destroy()
+
+
+def test_ensemble_persistent_unsupported_kinds(torch_cuda):
+    """FP64 ensembles and unsorted points keep the fork/join form."""
+    with pytest.raises(nufft.DfsError) as ei:
+        nufft.Ensemble([(1, 128, 64)], tol=1e-12, dtype="f64", n_fields=3, persistent=True)
+    assert ei.value.status == nufft.ERR_UNSUPPORTED
+    with pytest.raises(nufft.DfsError) as ei:
+        nufft.Ensemble([(1, 128, 64)], tol=1e-6, dtype="f32", n_fields=3, persistent=True,
+                       options=[nufft.Options.make(keep_order=True)])
+    assert ei.value.status == nufft.ERR_UNSUPPORTED
