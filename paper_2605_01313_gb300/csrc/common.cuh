@@ -51,6 +51,7 @@ struct dfsnufft_plan_s {
     void *d_df_inv1, *d_df_inv2;    // double-single deconvolution factors (N1, N2)
     void *d_df_stw_phi;             // double-single stage-ordered twiddles (length n1/2)
     void *d_df_stw_theta;           // and (length n2) for the theta pass
+    void *d_df_stw_half;            // and (length n2/2) for the forward column pass
     int *d_emax;                    // per line: largest coefficient exponent (df32.cuh scaling)
     int nbx, nby, nbins;    // interpolation bins
     int bstride;            // per-member stride of the bin arrays: >= nbins + 1, multiple of 4
@@ -171,6 +172,12 @@ cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const doub
 cudaError_t dfs_launch_theta_pass(dfsnufft_plan p, const void *coeffs, int prM = -1,
                                   int prN = -1);
 cudaError_t dfs_launch_phi_pass(dfsnufft_plan p);
+// Largest FP64 exponent of each of lines line0 .. line0 + lines - 1 into
+// p->d_emax (the double-single scaling of df32.cuh): every one of the
+// line_elems complex values of a line, or (herm) those a real-field theta pass
+// reads of a rows x N1 array.
+cudaError_t dfs_launch_line_maxexp(dfsnufft_plan p, const void *data, int line_elems, int rows,
+                                   int herm, int line0, int lines);
 // interp.cu
 cudaError_t dfs_launch_interp(dfsnufft_plan p, void *values);
 // forward.cu

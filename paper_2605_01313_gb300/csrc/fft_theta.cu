@@ -647,23 +647,29 @@ cudaError_t launch_theta(dfsnufft_plan p, const void *coeffs, int prM, int prN) 
 
 }  // namespace
 
+cudaError_t dfs_launch_line_maxexp(dfsnufft_plan p, const void *data, int line_elems, int rows,
+                                   int herm, int line0, int lines) {
+    const dfsnufft_params &q = p->prm;
+    cudaError_t e = cudaMemsetAsync(p->d_emax + line0, 0, sizeof(int) * lines, p->stream);
+    if (e) return e;
+    const int n = herm ? rows * (q.N1 / 2 + 1) + q.N1 / 2 - 1 : line_elems;
+    int blocks = (n + 2047) / 2048;
+    if (blocks > 1024) blocks = 1024;
+    k_coef_maxexp<<<dim3(blocks, lines), 256, 0, p->stream>>>(
+        (const double2 *)data + (size_t)line0 * line_elems, line_elems, rows, q.N1, herm,
+        p->d_emax + line0);
+    return cudaGetLastError();
+}
+
 // Each line's exponent maximum for the double-single passes (k_coef_maxexp).
 static cudaError_t launch_coef_maxexp(dfsnufft_plan p, const void *coeffs, int prM, int prN) {
     const dfsnufft_params &q = p->prm;
     int line0, lines;
     dfs_lines(p, line0, lines);
-    cudaError_t e = cudaMemsetAsync(p->d_emax + line0, 0, sizeof(int) * lines, p->stream);
-    if (e) return e;
     const bool pr = prM >= 0;
     const int line_elems = pr ? (prM + 1) * (prN + 1) : q.N2 * q.N1;
-    const int herm = (!pr && p->herm) ? 1 : 0;
-    const int n = herm ? q.N2 * (q.N1 / 2 + 1) + q.N1 / 2 - 1 : line_elems;
-    int blocks = (n + 2047) / 2048;
-    if (blocks > 1024) blocks = 1024;
-    k_coef_maxexp<<<dim3(blocks, lines), 256, 0, p->stream>>>(
-        (const double2 *)coeffs + (size_t)line0 * line_elems, line_elems, q.N2, q.N1, herm,
-        p->d_emax + line0);
-    return cudaGetLastError();
+    return dfs_launch_line_maxexp(p, coeffs, line_elems, q.N2, (!pr && p->herm) ? 1 : 0, line0,
+                                  lines);
 }
 
 cudaError_t dfs_launch_theta_pass(dfsnufft_plan p, const void *coeffs, int prM, int prN) {

@@ -15,6 +15,14 @@
 //              factor (-1)^m), its transform, the half-cell phase e^{-i pi n / N2}
 //              and the 1 / (N1 N2) scale, written in the centred layout of
 //              dfsnufft_execute.
+//
+// FP64 plans run both passes in double-single arithmetic (df32.cuh), as their
+// inverse passes do: each line's samples are scaled by the power of two that
+// brings its largest into [1, 2) on load, and the coefficients, written in
+// FP64, are scaled back.
+#include <type_traits>
+
+#include "df32.cuh"
 #include "fft_core.cuh"
 
 using namespace dfs_fft;
@@ -24,6 +32,29 @@ namespace {
 template <typename C> __device__ __forceinline__ C conjc(C a) { return cmake(a.x, -a.y); }
 template <typename C, typename R> __device__ __forceinline__ C cscale2(C a, R s) {
     return cmake(a.x * s, a.y * s);
+}
+
+// Storage types of a pass in arithmetic type R: samples In, coefficients Out.
+template <typename R> struct FwdIO {
+    typedef R In;
+    typedef typename CxT<R>::type Out;
+};
+template <> struct FwdIO<df32> {
+    typedef double In;
+    typedef double2 Out;
+};
+// A sample as the pass's real type R (double-single: times 2^-sh, split).
+template <typename R>
+__device__ __forceinline__ R fwd_in(typename FwdIO<R>::In v, int) { return v; }
+template <> __device__ __forceinline__ df32 fwd_in<df32>(double v, int sh) {
+    return split_double(df_scale_down(v, sh));
+}
+// A coefficient to its storage (double-single: hi + lo in FP64, times 2^sh).
+template <typename C> __device__ __forceinline__ C fwd_out(C v, int) { return v; }
+__device__ __forceinline__ double2 fwd_out(dfc v, int sh) {
+    const double s = df_pow2(sh);
+    return make_double2(((double)v.x.hi + (double)v.x.lo) * s,
+                        ((double)v.y.hi + (double)v.y.lo) * s);
 }
 
 struct FwdArgs {
@@ -43,24 +74,29 @@ struct FwdArgs {
 // (gauss.cu): mode m of a field of parity s is in class 0 when s (-1)^m = +1
 // (spec), else in class 1 (g1); row j, slot line * K + m / 2 of an n_lat x
 // (lines K) complex matrix.
+// emax (double-single passes): each line's largest sample exponent.
 template <typename R, int E, int LOG, bool GL>
-__global__ void __launch_bounds__(512) k_fwd_phi(FwdArgs a, const R *__restrict__ samples,
+__global__ void __launch_bounds__(512) k_fwd_phi(FwdArgs a,
+                                                 const typename FwdIO<R>::In *__restrict__ samples,
                                                  const typename CxT<R>::type *__restrict__ tw1,
                                                  const typename CxT<R>::type *__restrict__ stw,
                                                  typename CxT<R>::type *__restrict__ spec,
                                                  const int *__restrict__ parity,
-                                                 typename CxT<R>::type *__restrict__ g1) {
+                                                 typename CxT<R>::type *__restrict__ g1,
+                                                 const int *__restrict__ emax) {
     typedef typename CxT<R>::type C;
+    typedef typename FwdIO<R>::In In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     C *z = sm + region_len<C>(a.N1);                   // the pair's transform
     const int f = blockIdx.y;
     const int j = 2 * blockIdx.x;
     const int t = threadIdx.x;
-    const R *x = samples + ((size_t)f * a.n_lat + j) * a.N1;
-    const R *y = x + a.N1;
+    const In *x = samples + ((size_t)f * a.n_lat + j) * a.N1;
+    const In *y = x + a.N1;
+    const int sh = emax ? df_line_shift(emax[f]) : 0;
     // DFT_-(x + i y) = conj(DFT_+(conj(x + i y)))
-    auto ld = [&](int i) -> C { return cmake(x[i], -y[i]); };
+    auto ld = [&](int i) -> C { return cmake(fwd_in<R>(x[i], sh), -fwd_in<R>(y[i], sh)); };
     auto st = [&](int k, C v) { z[k] = conjc(v); };
     if constexpr (LOG > 0) line_fft_ct<LOG, E>(stw, sm, t, ld, st);
     else line_fft<E>(a.log1, tw1, a.tws1, sm, t, ld, st);
@@ -112,9 +148,11 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fwd_theta(FwdAr
                                                    const int *__restrict__ parity,
                                                    const typename CxT<R>::type *__restrict__ tw2,
                                                    const typename CxT<R>::type *__restrict__ stw,
-                                                   typename CxT<R>::type *__restrict__ coef,
-                                                   int nblk, int ntask) {
+                                                   typename FwdIO<R>::Out *__restrict__ coef,
+                                                   int nblk, int ntask,
+                                                   const int *__restrict__ emax) {
     typedef typename CxT<R>::type C;
+    typedef typename FwdIO<R>::Out CO;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *smem = reinterpret_cast<C *>(smem_raw);
     const int c = threadIdx.x & (a.CB - 1);
@@ -137,7 +175,8 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fwd_theta(FwdAr
         }
         cp_async_commit();
     };
-    const R scale = (R)1 / ((R)a.N1 * (R)a.N2);
+    // 1 / (N1 N2), a power of two
+    const R scale = R(ldexpf(1.f, -(a.log1 + a.log2)));
     // n2 = N2 << tws2 is a power of two: indices of tw2 are taken mod n2 by a mask
     const int tw_mask = (a.N2 << a.tws2) - 1;
     const int tw_step = 1 << (a.tws2 - 1);
@@ -165,8 +204,9 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fwd_theta(FwdAr
             return conjc(v);
         };
         const int mc = m < a.N1 / 2 ? m + a.N1 / 2 : m - a.N1 / 2;   // centred column
-        C *out = coef + (size_t)f * a.N2 * a.N1 + mc;
-        C *mirror = coef + (size_t)f * a.N2 * a.N1 + (a.N1 - mc);   // column of -m
+        CO *out = coef + (size_t)f * a.N2 * a.N1 + mc;
+        CO *mirror = coef + (size_t)f * a.N2 * a.N1 + (a.N1 - mc);   // column of -m
+        const int sh = emax ? df_line_shift(emax[f]) : 0;
         const bool has_mirror = ok && m > 0 && m < a.N1 / 2;
         auto st = [&](int k, C v) {
             if (!ok) return;
@@ -176,15 +216,15 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fwd_theta(FwdAr
             const int n = k < a.N2 / 2 ? k : k - a.N2;
             const C ph = conjc(tw2[(n * tw_step) & tw_mask]);
             const C cv = cscale2(cmul(conjc(v), ph), scale);
-            out[(size_t)(n + a.N2 / 2) * a.N1] = cv;
+            out[(size_t)(n + a.N2 / 2) * a.N1] = fwd_out(cv, sh);
             // c_{-n,-m} = conj c_{n,m}; the half-cell grid makes the sum antiperiodic
             // in n (c_{n+N2,m} = -c_{n,m}), so the row n = -N2/2 of column -m is
             // -conj c_{-N2/2,m}
             if (has_mirror) {
                 if (n > -a.N2 / 2) {
-                    if (a.full) mirror[(size_t)(a.N2 / 2 - n) * a.N1] = conjc(cv);
+                    if (a.full) mirror[(size_t)(a.N2 / 2 - n) * a.N1] = fwd_out(conjc(cv), sh);
                 } else {
-                    mirror[0] = cmake(-cv.x, cv.y);
+                    mirror[0] = fwd_out(cmake(-cv.x, cv.y), sh);
                 }
             }
         };
@@ -194,11 +234,27 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fwd_theta(FwdAr
     }
 }
 
+// The plan's tables for the pass's arithmetic: twiddles of lengths n1 and n2
+// and the stage-ordered table of length n1/2 (double-single copies for df32).
+template <typename R> struct FwdTables {
+    const void *tw1, *tw2, *stw_phi, *stw_half;
+    explicit FwdTables(dfsnufft_plan p) {
+        const bool df = std::is_same<R, df32>::value;
+        tw1 = df ? p->d_df_tw1 : p->d_tw1;
+        tw2 = df ? p->d_df_tw2 : p->d_tw2;
+        stw_phi = df ? p->d_df_stw_phi : p->d_stw_phi;
+        stw_half = df ? p->d_df_stw_half : p->d_stw_theta;     // length n2 / 2
+    }
+};
+
 template <typename R, int LOG>
 cudaError_t run_fwd_phi(dfsnufft_plan p, const FwdArgs &a, const void *samples, void *spec,
-                        int lines, const int *d_parity = nullptr, void *g1 = nullptr) {
+                        int lines, const int *d_parity = nullptr, void *g1 = nullptr,
+                        const int *emax = nullptr) {
     typedef typename CxT<R>::type C;
+    typedef typename FwdIO<R>::In In;
     constexpr int E = DFS_FFT_E;
+    const FwdTables<R> tb(p);
     const int threads = a.N1 / E;
     const size_t smem = sizeof(C) * (size_t)(region_len<C>(a.N1) + a.N1);
     const dim3 grid(a.n_lat / 2, lines);
@@ -207,23 +263,26 @@ cudaError_t run_fwd_phi(dfsnufft_plan p, const FwdArgs &a, const void *samples, 
         e = allow_smem(k_fwd_phi<R, E, LOG, true>, smem);
         if (e) return e;
         k_fwd_phi<R, E, LOG, true><<<grid, threads, smem, p->stream>>>(
-            a, (const R *)samples, (const C *)p->d_tw1, (const C *)p->d_stw_phi, (C *)spec,
-            d_parity, (C *)g1);
+            a, (const In *)samples, (const C *)tb.tw1, (const C *)tb.stw_phi, (C *)spec,
+            d_parity, (C *)g1, emax);
     } else {
         e = allow_smem(k_fwd_phi<R, E, LOG, false>, smem);
         if (e) return e;
         k_fwd_phi<R, E, LOG, false><<<grid, threads, smem, p->stream>>>(
-            a, (const R *)samples, (const C *)p->d_tw1, (const C *)p->d_stw_phi, (C *)spec,
-            nullptr, nullptr);
+            a, (const In *)samples, (const C *)tb.tw1, (const C *)tb.stw_phi, (C *)spec,
+            nullptr, nullptr, emax);
     }
     return cudaGetLastError();
 }
 
 template <typename R, int LOG>
 cudaError_t run_fwd_theta(dfsnufft_plan p, const FwdArgs &a, const void *spec,
-                          const int *d_parity, void *coeffs, int lines) {
+                          const int *d_parity, void *coeffs, int lines,
+                          const int *emax = nullptr) {
     typedef typename CxT<R>::type C;
+    typedef typename FwdIO<R>::Out CO;
     constexpr int E = DFS_FFT_E;
+    const FwdTables<R> tb(p);
     const int T = a.N2 / E;
     const size_t smem = sizeof(C) * (size_t)a.CB * (region_len<C>(a.N2) + 2 * (size_t)a.n_lat);
     cudaError_t e = allow_smem(k_fwd_theta<R, E, LOG>, smem);
@@ -238,8 +297,8 @@ cudaError_t run_fwd_theta(dfsnufft_plan p, const FwdArgs &a, const void *spec,
     const long long want = (long long)p->num_sms * occ;
     const int ctas = (int)(want < ntask ? want : ntask);
     k_fwd_theta<R, E, LOG><<<ctas, a.CB * T, smem, p->stream>>>(
-        a, (const C *)spec, d_parity, (const C *)p->d_tw2, (const C *)p->d_stw_theta,
-        (C *)coeffs, nblk, ntask);
+        a, (const C *)spec, d_parity, (const C *)tb.tw2, (const C *)tb.stw_half,
+        (CO *)coeffs, nblk, ntask, emax);
     return cudaGetLastError();
 }
 
@@ -268,23 +327,32 @@ cudaError_t launch_forward(dfsnufft_plan p, const void *samples, const int *d_pa
     a.CB = cb;
     a.lcb = ilog2(cb);
     const int lines = p->n_members * p->n_fields;
+    constexpr bool df = std::is_same<R, df32>::value;
+    const FwdTables<R> tb(p);
     // the plan's stage-ordered tables are for lengths n1/2 and n2/2: they serve
     // the compile-time drivers when the fine grid is twice the modes
-    const bool ct1 = p->d_stw_phi && q.n1 == 2 * q.N1 && a.log1 >= 9 && a.log1 <= 11;
-    const bool ct2 = p->d_stw_theta && q.n2 == 2 * q.N2 && a.log2 >= 9 && a.log2 <= 11;
+    const bool ct1 = tb.stw_phi && q.n1 == 2 * q.N1 && a.log1 >= 9 && a.log1 <= 11;
+    const bool ct2 = tb.stw_half && q.n2 == 2 * q.N2 && a.log2 >= 9 && a.log2 <= 11;
     cudaError_t e;
+    const int *emax = nullptr;
+    if (df) {
+        // each line's largest sample (n_lat x N1 reals, read as pairs)
+        e = dfs_launch_line_maxexp(p, samples, q.n_lat * q.N1 / 2, q.n_lat, 0, 0, lines);
+        if (e) return e;
+        emax = p->d_emax;
+    }
     switch (ct1 ? a.log1 : 0) {
-        case 9: e = run_fwd_phi<R, 9>(p, a, samples, spec, lines); break;
-        case 10: e = run_fwd_phi<R, 10>(p, a, samples, spec, lines); break;
-        case 11: e = run_fwd_phi<R, 11>(p, a, samples, spec, lines); break;
-        default: e = run_fwd_phi<R, 0>(p, a, samples, spec, lines); break;
+        case 9: e = run_fwd_phi<R, 9>(p, a, samples, spec, lines, nullptr, nullptr, emax); break;
+        case 10: e = run_fwd_phi<R, 10>(p, a, samples, spec, lines, nullptr, nullptr, emax); break;
+        case 11: e = run_fwd_phi<R, 11>(p, a, samples, spec, lines, nullptr, nullptr, emax); break;
+        default: e = run_fwd_phi<R, 0>(p, a, samples, spec, lines, nullptr, nullptr, emax); break;
     }
     if (e) return e;
     switch (ct2 ? a.log2 : 0) {
-        case 9: return run_fwd_theta<R, 9>(p, a, spec, d_parity, coeffs, lines);
-        case 10: return run_fwd_theta<R, 10>(p, a, spec, d_parity, coeffs, lines);
-        case 11: return run_fwd_theta<R, 11>(p, a, spec, d_parity, coeffs, lines);
-        default: return run_fwd_theta<R, 0>(p, a, spec, d_parity, coeffs, lines);
+        case 9: return run_fwd_theta<R, 9>(p, a, spec, d_parity, coeffs, lines, emax);
+        case 10: return run_fwd_theta<R, 10>(p, a, spec, d_parity, coeffs, lines, emax);
+        case 11: return run_fwd_theta<R, 11>(p, a, spec, d_parity, coeffs, lines, emax);
+        default: return run_fwd_theta<R, 0>(p, a, spec, d_parity, coeffs, lines, emax);
     }
 }
 
@@ -301,6 +369,8 @@ cudaError_t dfs_launch_forward(dfsnufft_plan p, const void *samples, const int *
                                void *coeffs, bool full) {
     // the row spectra (lines x n_lat x N1 complex) fit in the theta-pass buffer,
     // which the execute that follows overwrites only later in stream order
+    // FP64 plans whose inverse passes run in double-single run these too
+    if (p->gdf) return launch_forward<df32>(p, samples, d_parity, coeffs, p->d_T, full);
     return p->prm.dtype == DFSNUFFT_F64
                ? launch_forward<double>(p, samples, d_parity, coeffs, p->d_T, full)
                : launch_forward<float>(p, samples, d_parity, coeffs, p->d_T, full);

@@ -322,7 +322,8 @@ static void release(dfsnufft_plan p) {
                      &p->d_urec, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
                      (void **)&p->d_pts_stage, &p->d_coef_stage, &p->d_val_stage,
                      &p->d_df_tw1, &p->d_df_tw2, &p->d_df_inv1, &p->d_df_inv2,
-                     &p->d_df_stw_phi, &p->d_df_stw_theta, (void **)&p->d_emax};
+                     &p->d_df_stw_phi, &p->d_df_stw_theta, &p->d_df_stw_half,
+                     (void **)&p->d_emax};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) dfs_free(bufs[i]);
     free(p->h_pofs);
     p->h_pofs = nullptr;
@@ -455,8 +456,9 @@ static int upload_df_tables(dfsnufft_plan p) {
     // the stage-ordered twiddles of the phi pass's length-n1/2 transform and of
     // the theta pass's length-n2 one
     struct { void **ptr; int n; } stabs[] = {{&p->d_df_stw_phi, q.n1 / 2},
-                                             {&p->d_df_stw_theta, q.n2}};
-    for (int k = 0; rc == DFSNUFFT_OK && k < 2; ++k) {
+                                             {&p->d_df_stw_theta, q.n2},
+                                             {&p->d_df_stw_half, q.n2 / 2}};
+    for (int k = 0; rc == DFSNUFFT_OK && k < 3; ++k) {
         int logn = 0;
         while ((1 << logn) < stabs[k].n) ++logn;
         const size_t sz = (size_t)stage_table_len(stabs[k].n);

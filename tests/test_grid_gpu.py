@@ -104,3 +104,23 @@ def test_grid_batched_members_and_errors(torch_cuda):
             plan.grid_to_coeffs(torch.zeros((1, 12, 24), dtype=torch.float64, device="cuda"),
                                 [1])
         assert ei.value.status == nufft.ERR_UNSUPPORTED
+
+
+def test_grid_to_coeffs_f64_scaled_samples(torch_cuda):
+    """FP64 plans transform in double-single arithmetic: samples times 2^-110
+    and 2^+110 (one field each, far outside FP32's exponent range) give exactly
+    the unscaled coefficients times the same powers of two, within the FP64
+    bound of the oracle."""
+    torch = torch_cuda
+    n_lon, n_lat = 512, 256
+    rng = np.random.default_rng(840)
+    s = rng.standard_normal((n_lat, n_lon))
+    k = np.array([math.ldexp(1.0, -110), math.ldexp(1.0, 110)])
+    with plan_for(n_lon, n_lat, "f64", 2) as plan:
+        base = plan.grid_to_coeffs(torch.from_numpy(np.stack([s, s])).cuda(), [1, -1]).cpu().numpy()
+        c = plan.grid_to_coeffs(torch.from_numpy(np.stack([s * k[0], s * k[1]])).cuda(),
+                                [1, -1]).cpu().numpy()
+    for f in range(2):
+        assert np.array_equal(c[f], base[f] * k[f])
+        ref = oracle.grid_to_coeffs(s[None], [(1, -1)[f]])[0]
+        assert np.max(np.abs(base[f] - ref)) <= 1e-12 * np.max(np.abs(ref))
