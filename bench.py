@@ -616,9 +616,16 @@ def measure(args, name, wl, ws, rank, dev, serving, cpu_seconds=None):
         "stages": stages_out,
         # set_points: fold+count, row prefix, two scan passes, scatter (one fold
         # kernel for unsorted points); theta pass, phi pass, interpolation
-        "gpu_launches": ((4 if prm["flags"] & 2 else 8) + (2 if grid_in else 0)
+        # grid input: the two forward passes (Gauss-Legendre: longitude pass,
+        # latitude solve, coefficient mapping; the FP32 solve is our tcgen05
+        # kernel, the FP64 one cuBLAS DGEMM, not counted); FP64 plans in
+        # double-single: the exponent reductions of the coefficients (and samples)
+        "gpu_launches": ((4 if prm["flags"] & 2 else 8)
+                         + ((3 if gauss is not None and wl.dtype == "f32" else 2)
+                            if grid_in else 0)
                          + (2 if sl is not None else 0)
-                         + (1 if wl.dtype == "f64" and not prm["flags"] & 2 else 0))
+                         + ((1 + (1 if grid_in and gauss is None else 0))
+                            if wl.dtype == "f64" and not prm["flags"] & 2 else 0))
                         * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / e2e_steps},

@@ -81,8 +81,9 @@ struct dfsnufft_plan_s {
     int gl;
     void *d_gl_mat;             // C^{-1}, S^{-1} (n_lat x n_lat each, / n_lon), then w
     double *h_gl_colat;         // the n_lat colatitudes
-    void *blas;                 // cublasHandle_t
-    int gl_emulated;            // FP32 GEMMs on the BF16x9 tensor-core emulation
+    void *blas;                 // cublasHandle_t (FP64 plans)
+    void *d_gl_tc;              // FP32 plans: M_hi, M_lo (2 classes each) of the tcgen05 solve
+    CUtensorMap tmap_gl_hi, tmap_gl_lo;
     int *d_parity;              // fields: +1 scalar / -1 wind component (grid input)
     int h_parity[64];           // the parities last uploaded
     int parity_set;
@@ -188,6 +189,9 @@ void dfs_gl_release(dfsnufft_plan p);
 int dfs_launch_forward_gl(dfsnufft_plan p, const void *samples, const int *d_parity,
                           void *coeffs, bool full);
 size_t dfs_gl_scratch_bytes(const dfsnufft_params &q, int lines);
+// gl_gemm.cu: the FP32 latitude solve on the tensor cores
+int dfs_gl_tc_setup(dfsnufft_plan p, const double *cm, const double *sm, int N);
+cudaError_t dfs_gl_tc_gemm(dfsnufft_plan p, const float *g, float *out, int N, int cols);
 // full = false: of the columns m < 0 only the Nyquist row n = -N2/2 is written
 // (all that a real-field plan's theta pass reads there)
 cudaError_t dfs_launch_forward(dfsnufft_plan p, const void *samples, const int *d_parity,

@@ -16,12 +16,14 @@
 //            c_{+-n} += a_n / 2.
 // The inverse matrices C^{-1} (cos) and S^{-1} (sin) are formed once in FP64 on
 // the host (Gauss-Jordan), scaled by 1 / n_lon (the FFT's normalisation) and
-// applied to all modes of all fields as two real GEMMs (cuBLAS; FP32 through
-// its BF16x9 tensor-core emulation where available).  The column of mode -m is
-// the solve of the conjugate data, (a, b, beta) -> conjugates.  For a
-// real-field plan's staging only the Hermitian part matters (Re v): in the
-// columns 0 < m < N1/2 the beta w terms cancel and are left out (of m < 0 only
-// the Nyquist row is written); the columns m = 0 and N1/2 keep their values.
+// applied to all modes of all fields as two real GEMMs: FP32 plans on the
+// tensor cores by the library's own tcgen05 kernel (gl_gemm.cu, TF32 with a
+// three-term split for FP32 accuracy), FP64 plans by cuBLAS DGEMM.  The
+// column of mode -m is the solve of the conjugate data, (a, b, beta) ->
+// conjugates.  For a real-field plan's staging only the Hermitian part
+// matters (Re v): in the columns 0 < m < N1/2 the beta w terms cancel and are
+// left out (of m < 0 only the Nyquist row is written); the columns m = 0 and
+// N1/2 keep their values.
 //
 // Kernels: the longitude pass k_fwd_phi (GL form, forward.cu) writes the row
 // spectra into the two classes; k_gl_coeffs maps the GEMM results to the
@@ -220,6 +222,18 @@ int dfs_gl_setup(dfsnufft_plan p) {
         }
         const double sc = 1.0 / q.N1;
         const size_t nn = (size_t)N * N;
+        if (!f64) {
+            // the tensor-core solve's split matrices, from the scaled FP64 inverses
+            for (size_t i = 0; i < nn; ++i) {
+                cm[i] *= sc;
+                sm[i] *= sc;
+            }
+            rc = dfs_gl_tc_setup(p, cm, sm, N);
+            for (size_t i = 0; i < nn; ++i) {
+                cm[i] /= sc;
+                sm[i] /= sc;
+            }
+        }
         if (f64) {
             convert(cm, (double *)hbuf, nn, sc);
             convert(sm, (double *)hbuf + nn, nn, sc);
@@ -242,17 +256,10 @@ int dfs_gl_setup(dfsnufft_plan p) {
     if (rc == DFSNUFFT_OK) {
         p->h_gl_colat = th;
         th = nullptr;
-        cublasHandle_t h = nullptr;
-        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) {
-            rc = DFSNUFFT_ERR_CUDA;
-        } else {
-            p->blas = h;
-            // FP32 GEMMs on the tensor cores through the BF16x9 emulation whenever
-            // cuBLAS offers it (checked at the first call)
-            if (!f64)
-                p->gl_emulated =
-                    cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_EAGER) ==
-                    CUBLAS_STATUS_SUCCESS;
+        if (f64) {
+            cublasHandle_t h = nullptr;
+            if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) rc = DFSNUFFT_ERR_CUDA;
+            else p->blas = h;
         }
     }
     free(th);
@@ -270,6 +277,8 @@ void dfs_gl_release(dfsnufft_plan p) {
     p->h_gl_colat = nullptr;
     if (p->d_gl_mat) cudaFree(p->d_gl_mat);
     p->d_gl_mat = nullptr;
+    if (p->d_gl_tc) cudaFree(p->d_gl_tc);
+    p->d_gl_tc = nullptr;
 }
 
 // Samples on the Gauss-Legendre grid to coefficients (the layout of
@@ -296,35 +305,20 @@ int dfs_launch_forward_gl(dfsnufft_plan p, const void *samples, const int *d_par
                               p->stream);
     }
     if (e) return DFSNUFFT_ERR_CUDA;
-    cublasHandle_t h = (cublasHandle_t)p->blas;
-    if (cublasSetStream(h, p->stream) != CUBLAS_STATUS_SUCCESS) return DFSNUFFT_ERR_CUDA;
-    // out_c (col-major cols x N) = g_c (cols x N) * M_c^T, M_c row-major N x N
-    cublasStatus_t st;
-    const long long sA = (long long)N * cols, sB = (long long)N * N, sC = sA;
     if (f64) {
+        cublasHandle_t h = (cublasHandle_t)p->blas;
+        if (cublasSetStream(h, p->stream) != CUBLAS_STATUS_SUCCESS) return DFSNUFFT_ERR_CUDA;
+        // out_c (col-major cols x N) = g_c (cols x N) * M_c^T, M_c row-major N x N
+        const long long sA = (long long)N * cols, sB = (long long)N * N, sC = sA;
         const double one = 1.0, zero = 0.0;
-        st = cublasDgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)cols, N, N, &one,
-                                       (const double *)g0, (int)cols, sA,
-                                       (const double *)p->d_gl_mat, N, sB, &zero,
-                                       (double *)o0, (int)cols, sC, 2);
-    } else {
-        const float one = 1.f, zero = 0.f;
-        st = CUBLAS_STATUS_NOT_SUPPORTED;
-        if (p->gl_emulated) {
-            st = cublasGemmStridedBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)cols, N, N, &one,
-                                            g0, CUDA_R_32F, (int)cols, sA, p->d_gl_mat,
-                                            CUDA_R_32F, N, sB, &zero, o0, CUDA_R_32F, (int)cols,
-                                            sC, 2, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-                                            CUBLAS_GEMM_DEFAULT);
-            if (st != CUBLAS_STATUS_SUCCESS) p->gl_emulated = 0;    // plain FP32 from now on
-        }
-        if (st != CUBLAS_STATUS_SUCCESS)
-            st = cublasSgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)cols, N, N, &one,
-                                           (const float *)g0, (int)cols, sA,
-                                           (const float *)p->d_gl_mat, N, sB, &zero,
-                                           (float *)o0, (int)cols, sC, 2);
+        if (cublasDgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)cols, N, N, &one,
+                                      (const double *)g0, (int)cols, sA,
+                                      (const double *)p->d_gl_mat, N, sB, &zero, (double *)o0,
+                                      (int)cols, sC, 2) != CUBLAS_STATUS_SUCCESS)
+            return DFSNUFFT_ERR_CUDA;
+    } else if (dfs_gl_tc_gemm(p, (const float *)g0, (float *)o0, N, (int)cols)) {
+        return DFSNUFFT_ERR_CUDA;
     }
-    if (st != CUBLAS_STATUS_SUCCESS) return DFSNUFFT_ERR_CUDA;
     GlArgs a;
     a.N = N;
     a.N1 = q.N1;

@@ -124,3 +124,21 @@ cudaError_t dfs_allow_smem(const void *kernel, size_t bytes);
 cudaError_t dfs_encode_tensor_map_2d(CUtensorMap *map, const void *base, uint64_t width,
                                      uint64_t height, uint64_t pitch_bytes, uint32_t box_w,
                                      uint32_t box_h);
+
+// Host: encode a 3-D tensor map of FP32 elements (dims[0] innermost; strides of
+// dims 1 and 2 in bytes), box box[0] x box[1] x box[2], optionally with the
+// 128-byte swizzle (box[0] x 4 must then be at most 128 bytes).  Elements
+// outside the dims read as zero.
+cudaError_t dfs_encode_tensor_map_3d_f32(CUtensorMap *map, const void *base, const uint64_t dims[3],
+                                         const uint64_t strides_bytes[2], const uint32_t box[3],
+                                         int swizzle128);
+
+// 3-D tiled TMA load of one box, completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
