@@ -67,8 +67,8 @@ __device__ void theta_task(const EnsGroup &g, int line, int qb, unsigned char *s
     constexpr int CB = kThreads / TT > 0 ? kThreads / TT : 1;
     const int c = threadIdx.x % CB;
     const int t = threadIdx.x / CB;
-    C *sm0 = reinterpret_cast<C *>(smem) + (size_t)c * region_len<C>(H);
-    C *sm1 = reinterpret_cast<C *>(smem) + (size_t)(CB + c) * region_len<C>(H);
+    C *sm0 = reinterpret_cast<C *>(smem) + (size_t)c * region_stride<C>(H, CB);
+    C *sm1 = reinterpret_cast<C *>(smem) + (size_t)(CB + c) * region_stride<C>(H, CB);
     const int half = g.N2 / 2;
     const int q = qb * CB + c;
     const bool col_ok = q < g.tcols;

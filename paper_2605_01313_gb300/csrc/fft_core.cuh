@@ -79,18 +79,27 @@ __host__ __device__ constexpr int bitrev(int r, int R) {
     return out;
 }
 
-// Shared-memory exchange layout: one padding element after every 128 bytes of
-// elements, so that strided Stockham writes spread over the banks; regions of
-// FP32 lines placed side by side are skewed by 32 bytes (stride = 32 mod 128
-// bytes) so that the lines of one warp fall on different banks too.
+// Shared-memory exchange layout.  FP32 lines (8-byte elements, a bank pair
+// each, 16 pairs a row of banks): element i sits at i ^ ((i >> 3) & 15), a
+// permutation of [0, n) for every power of two n that XORs the bank pair with
+// the 8-element group, so that neither the unit-stride reads nor the
+// Ns-strided Stockham writes of a half-warp meet twice on one pair.  When the
+// lanes of a warp interleave cb lines (lane = t cb + c), line c's region starts
+// c region_stride(n, cb) elements in, n + 16 / cb apart, which puts the lines'
+// pairs evenly apart; region_len(n) = n + 16 bounds every stride, for sizing.
+// 16-byte elements: one padding element after every 128 bytes.
 template <typename C> __host__ __device__ constexpr int pad_shift() {
     return sizeof(C) == 8 ? 4 : 3;
 }
 template <typename C> __device__ __forceinline__ int spad(int i) {
-    return i + (i >> pad_shift<C>());
+    if constexpr (sizeof(C) == 8) return i ^ ((i >> 3) & 15);
+    else return i + (i >> pad_shift<C>());
 }
 template <typename C> __host__ __device__ constexpr int region_len(int n) {
-    return n + (n >> pad_shift<C>()) + (sizeof(C) == 8 ? 4 : 0);
+    return sizeof(C) == 8 ? n + 16 : n + (n >> pad_shift<C>());
+}
+template <typename C> __host__ __device__ constexpr int region_stride(int n, int cb) {
+    return sizeof(C) == 8 ? n + (cb >= 16 ? 1 : 16 / cb) : region_len<C>(n);
 }
 
 // One radix-R Stockham stage over the E register elements of thread t.  Thread

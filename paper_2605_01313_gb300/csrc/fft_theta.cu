@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int half = a.N2 / 2;
     const int qa = HERM ? a.N1 / 2 + q : q;        // array column
     const R sq = col_ok ? inv1[qa < a.N1 ? qa : 0] : (R)0;
-    C *sm = smem + (size_t)c * region_len<C>(a.n2);
+    C *sm = smem + (size_t)c * region_stride<C>(a.n2, a.CB);
     const int sh = emax ? df_line_shift(emax[f]) : 0;
     auto cf = [&](int r, int col) -> C {
         return (r < a.N2 && col < a.N1) ? in_value<C>(cf0[(size_t)r * a.N1 + col], sh)
@@ -246,8 +246,10 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int c = threadIdx.x % CB;
     const int t = threadIdx.x / CB;
     const int half = a.N2 / 2;
-    C *sm = ex + (size_t)c * region_len<C>(H);
-    C *sm1 = ex + (size_t)(CB + c) * region_len<C>(H);      // DUAL: the odd-row transform
+    // column c's regions c and (DUAL: its odd-row transform) CB + c, region_stride
+    // apart (the columns of a warp on different bank pairs)
+    C *sm = ex + (size_t)c * region_stride<C>(H, CB);
+    C *sm1 = ex + (size_t)(CB + c) * region_stride<C>(H, CB);
     for (int i = threadIdx.x; i < a.N2; i += blockDim.x) f2[i] = inv2[i];
     if (threadIdx.x == 0) {
         // PRIN: every thread arrives once a phase, when its copies have landed

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fwd_theta(FwdAr
     C *smem = reinterpret_cast<C *>(smem_raw);
     const int c = threadIdx.x & (a.CB - 1);
     const int t = threadIdx.x >> a.lcb;
-    C *sm = smem + (size_t)c * region_len<C>(a.N2);
+    C *sm = smem + (size_t)c * region_stride<C>(a.N2, a.CB);
     C *stage = smem + (size_t)a.CB * region_len<C>(a.N2);   // 2 x (n_lat x CB), c fastest
     const int per_buf = a.n_lat << a.lcb;
     // 16-byte chunks of a staged row: CB * sizeof(C) / 16, a power of two
