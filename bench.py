@@ -313,6 +313,13 @@ def profile_traffic(kernel, workload):
     return None
 
 
+def set_points_launches(prm):
+    """Kernels one set_points launches: one fold for unsorted points; else
+    fold+count, the in-bin row prefix, the two bin-scan passes and the
+    scatter."""
+    return 1 if prm["flags"] & 2 else 5
+
+
 def max_over_ranks(x, ws, device="cpu"):
     """Largest value of x over the ranks of the default process group (x itself
     for one rank).  NCCL needs a CUDA device; gloo runs on the CPU."""
@@ -614,13 +621,12 @@ def measure(args, name, wl, ws, rank, dev, serving, cpu_seconds=None):
         "roofline": roof,
         "roofline_step": roof_step,
         "stages": stages_out,
-        # set_points: fold+count, row prefix, two scan passes, scatter (one fold
-        # kernel for unsorted points); theta pass, phi pass, interpolation
+        # set_points (set_points_launches); theta pass, phi pass, interpolation;
         # grid input: the two forward passes (Gauss-Legendre: longitude pass,
         # latitude solve, coefficient mapping; the FP32 solve is our tcgen05
         # kernel, the FP64 one cuBLAS DGEMM, not counted); FP64 plans in
         # double-single: the exponent reductions of the coefficients (and samples)
-        "gpu_launches": ((4 if prm["flags"] & 2 else 8)
+        "gpu_launches": (set_points_launches(prm) + 3
                          + ((3 if gauss is not None and wl.dtype == "f32" else 2)
                             if grid_in else 0)
                          + (2 if sl is not None else 0)
@@ -834,7 +840,10 @@ def run_ensemble(args):
     p_total = max_over_ranks(sum(p_ms), ws, dev)
     persistent = {"ms_per_step": p_total / args.steps,
                   "value": weak_scaling_value(ws, total_pf, args.steps, p_total), "unit": UNIT,
-                  "options": pers_note, "gpu_launches_per_step": 5 * len(groups) + 1,
+                  "options": pers_note,
+                  "gpu_launches_per_step": sum(
+                      set_points_launches(nufft.dfsnufft_plan_get_params(pens.plan_handle(gi)))
+                      for gi in range(len(groups))) + 1,
                   "error": {"rel_linf_first_member_32_points": p_err, "bound": 2e-5,
                             "ok": max(p_err.values()) <= 2e-5}}
     pens.destroy()
@@ -861,8 +870,10 @@ def run_ensemble(args):
     d2h = sum(t.numel() * t.element_size() for t in host_out)
     # algorithmic bytes of every stage of every group, one step
     step_bytes = 0
+    sp_launches = []
     for gi, (m, n_lon, n_lat) in enumerate(groups):
         prm = nufft.dfsnufft_plan_get_params(ens.plan_handle(gi))
+        sp_launches.append(set_points_launches(prm))
         st = nufft.dfsnufft_plan_point_stats(ens.plan_handle(gi))
         step_bytes += sum(stage_bytes(prm, 3 * m, sum(pts[gi][2]), st["rows_needed"]).values())
     pk, pk_kind = peaks()
@@ -902,8 +913,8 @@ def run_ensemble(args):
                      "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "peak_source": "%s hbm_gbs" % pk_kind,
                      "traffic": None},
-        # per group: set_points (5 kernels), theta, phi, interpolation
-        "gpu_launches": 8 * len(groups) * args.steps,
+        # per group: set_points (set_points_launches), theta, phi, interpolation
+        "gpu_launches": sum(sp_launches[gi] + 3 for gi in range(len(groups))) * args.steps,
         "persistent": persistent,
         "e2e": {"value": total_pf / (np.mean(e2e_ms) * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
