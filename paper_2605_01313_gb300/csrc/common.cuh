@@ -7,6 +7,34 @@
 
 #include "dfsnufft.h"
 
+// ---------------------------------------------------------------- dependent launches
+// A kernel of the hot path launched by dfs_launch_dependent may start
+// launching while the kernel before it in the stream drains (programmatic
+// stream serialization): its CTAs are placed as soon as the previous grid's
+// CTAs have all exited, without a fresh launch in between.  Such a kernel's
+// first statement is dfs_grid_wait(), which returns once the previous grid
+// has completed and its writes are visible, so that nothing it reads or writes
+// runs ahead of the work it depends on.
+__device__ __forceinline__ void dfs_grid_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t dfs_launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 // ---------------------------------------------------------------- complex helpers
 template <typename R> struct CxT;
 template <> struct CxT<float> { typedef float2 type; };

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
     k_phi_pass2(PhiArgs a, const float2 *__restrict__ in, const float2 *__restrict__ tw,
                 const float2 *__restrict__ stw, const int2 *__restrict__ rowrange,
                 float *__restrict__ grid) {
+    dfs_grid_wait();
     typedef float2 C;
     const int row0 = blockIdx.x * a.CB;
     const int2 rr = rowrange[(a.line0 + blockIdx.y) / a.F];
@@ -242,10 +243,10 @@ cudaError_t run_phi2(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid, 
     constexpr int E = PhiCfg<float>::E;
     cudaError_t e = allow_smem(k_phi_pass2<E, 256, 4, LOGM, HERM>, smem);
     if (e) return e;
-    k_phi_pass2<E, 256, 4, LOGM, HERM><<<grid, threads, smem, p->stream>>>(
-        a, (const float2 *)p->d_T, (const float2 *)p->d_tw1, (const float2 *)p->d_stw_phi,
-        p->d_rowrange, (float *)p->d_G);
-    return cudaGetLastError();
+    return dfs_launch_dependent(k_phi_pass2<E, 256, 4, LOGM, HERM>, grid, dim3(threads), smem,
+                                p->stream, a, (const float2 *)p->d_T, (const float2 *)p->d_tw1,
+                                (const float2 *)p->d_stw_phi, (const int2 *)p->d_rowrange,
+                                (float *)p->d_G);
 }
 
 template <typename R>

@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
                 const typename CxT<R>::type *__restrict__ tw,
                 const typename CxT<R>::type *__restrict__ stw, const int2 *__restrict__ rowrange,
                 typename CxT<R>::type *__restrict__ out, int *__restrict__ status) {
+    dfs_grid_wait();
     typedef typename CxT<R>::type C;
     constexpr bool DUAL = LOGH > 0 && sizeof(R) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -451,10 +452,11 @@ cudaError_t run_theta_tma(dfsnufft_plan p, const ThetaTmaArgs &a, const CUtensor
     constexpr int E = ThetaCfg<R>::E, MAXT = ThetaCfg<R>::TMAXT, MINB = ThetaCfg<R>::TMINB;
     cudaError_t e = allow_smem(k_theta_tma<R, E, CB, MAXT, MINB, LOGH, HERM, PRIN>, smem);
     if (e) return e;
-    k_theta_tma<R, E, CB, MAXT, MINB, LOGH, HERM, PRIN><<<grid, threads, smem, p->stream>>>(
-        a, tmap, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2,
-        (const C *)p->d_tw2, (const C *)p->d_stw_theta, p->d_rowrange, (C *)p->d_T, p->d_status);
-    return cudaGetLastError();
+    return dfs_launch_dependent(
+        k_theta_tma<R, E, CB, MAXT, MINB, LOGH, HERM, PRIN>, dim3(grid), dim3(threads), smem,
+        p->stream, a, tmap, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2,
+        (const C *)p->d_tw2, (const C *)p->d_stw_theta, (const int2 *)p->d_rowrange, (C *)p->d_T,
+        p->d_status);
 }
 
 template <typename R, int CB, bool HERM, bool PRIN = false>

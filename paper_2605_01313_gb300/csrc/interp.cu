@@ -427,6 +427,7 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
                                                     const int *__restrict__ pofs,
                                                     float *__restrict__ out_all,
                                                     int *__restrict__ status) {
+    dfs_grid_wait();
     constexpr int WP = (W + 2) & ~1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *sb = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
@@ -818,12 +819,13 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
                 const int64_t cap = (int64_t)p->nbins * a.NG;
                 if (want > cap) want = cap;
                 if (want < 1) want = 1;
-                k_interp_tma<W><<<dim3((unsigned)want, M), 128, smem, p->stream>>>(
-                    a, hf, p->tmap_G, (const float *)p->d_G, p->d_base,
-                    (const float *)p->d_frac, p->d_idx,
-                    p->d_bin_start, p->d_task_bin, p->d_n_tasks, p->d_pofs, (float *)values,
+                return dfs_launch_dependent(
+                    k_interp_tma<W>, dim3((unsigned)want, M), dim3(128), smem, p->stream, a, hf,
+                    p->tmap_G, (const float *)p->d_G, (const int2 *)p->d_base,
+                    (const float *)p->d_frac, (const int *)p->d_idx,
+                    (const int *)p->d_bin_start, (const int *)p->d_task_bin,
+                    (const int *)p->d_n_tasks, (const int *)p->d_pofs, (float *)values,
                     p->d_status);
-                return cudaGetLastError();
             }
         }
         // plain loads: tile rows of at most 32 pairs

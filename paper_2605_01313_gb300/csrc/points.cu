@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(256) k_fold_count(const double *__restrict__ l
 // total, which the bin scan takes.
 __global__ void __launch_bounds__(256) k_row_prefix(int nbins, int tile_y, int cstride,
                                                     int rowoff, int *__restrict__ count_all) {
+    dfs_grid_wait();
     const int bin = blockIdx.x * blockDim.x + threadIdx.x;
     if (bin >= nbins) return;
     int *slice = count_all + (size_t)blockIdx.y * cstride;
@@ -313,6 +314,7 @@ __device__ void finish_rowrange(const ScanParams &sp, const unsigned char *rows,
 // sum and number of non-empty bins of each chunk of DFS_SCAN_CHUNK bins.
 __global__ void __launch_bounds__(DFS_SCAN_CHUNK / 16) k_scan_sums(ScanParams sp,
                                                                    int *__restrict__ count_all) {
+    dfs_grid_wait();
     int *slice = count_all + (size_t)blockIdx.y * sp.cstride;
     int c[16];
     load16(slice, blockIdx.x * DFS_SCAN_CHUNK + 16 * threadIdx.x, sp.nbins, c);
@@ -344,6 +346,7 @@ __global__ void __launch_bounds__(DFS_SCAN_CHUNK / 16) k_scan_write(ScanParams s
                                                                     int *__restrict__ task_all,
                                                                     int *__restrict__ n_tasks,
                                                                     int2 *__restrict__ rowrange) {
+    dfs_grid_wait();
     const int member = blockIdx.y, chunk = blockIdx.x;
     int *slice = count_all + (size_t)member * sp.cstride;
     int *start = start_all + (size_t)member * sp.bstride;
@@ -477,6 +480,7 @@ __global__ void __launch_bounds__(256) k_scatter(const FoldRec<R> *__restrict__ 
                                                  int2 *__restrict__ base,
                                                  typename CxT<R>::type *__restrict__ frac,
                                                  int *__restrict__ idx) {
+    dfs_grid_wait();
     const int k = blockIdx.y;
     const int p0 = pofs[k];
     const int pl = blockIdx.x * blockDim.x + threadIdx.x;
@@ -546,20 +550,28 @@ cudaError_t dfs_launch_set_points(dfsnufft_plan p, const double *lon, const doub
         k_fold_count<float><<<grid, tpb, 0, p->stream>>>(lon, colat, f, p->d_pofs, p->cstride,
                                                          rowoff, p->d_bin_count,
                                                          (FoldRec<float> *)p->d_urec);
-    k_row_prefix<<<dim3((p->nbins + 255) / 256, M), 256, 0, p->stream>>>(
-        p->nbins, q.tile_y, p->cstride, rowoff, p->d_bin_count);
+    // the kernels after the fold start launching while their predecessor drains
+    if ((e = dfs_launch_dependent(k_row_prefix, dim3((p->nbins + 255) / 256, M), dim3(256), 0,
+                                  p->stream, p->nbins, q.tile_y, p->cstride, rowoff,
+                                  p->d_bin_count)))
+        return e;
     const dim3 sgrid(p->nch, M);
-    k_scan_sums<<<sgrid, DFS_SCAN_CHUNK / 16, 0, p->stream>>>(sp, p->d_bin_count);
-    k_scan_write<<<sgrid, DFS_SCAN_CHUNK / 16, 0, p->stream>>>(sp, p->d_bin_count, p->d_bin_start,
-                                                             p->d_task_bin, p->d_n_tasks,
-                                                             p->d_rowrange);
+    if ((e = dfs_launch_dependent(k_scan_sums, sgrid, dim3(DFS_SCAN_CHUNK / 16), 0, p->stream, sp,
+                                  p->d_bin_count)))
+        return e;
+    if ((e = dfs_launch_dependent(k_scan_write, sgrid, dim3(DFS_SCAN_CHUNK / 16), 0, p->stream, sp,
+                                  p->d_bin_count, p->d_bin_start, p->d_task_bin, p->d_n_tasks,
+                                  p->d_rowrange)))
+        return e;
     if (q.dtype == DFSNUFFT_F64)
-        k_scatter<double><<<grid, tpb, 0, p->stream>>>(
-            (const FoldRec<double> *)p->d_urec, f, p->d_pofs, p->bstride, p->d_bin_start,
-            p->cstride, rowoff, p->d_bin_count, p->d_base, (double2 *)p->d_frac, p->d_idx);
-    else
-        k_scatter<float><<<grid, tpb, 0, p->stream>>>(
-            (const FoldRec<float> *)p->d_urec, f, p->d_pofs, p->bstride, p->d_bin_start,
-            p->cstride, rowoff, p->d_bin_count, p->d_base, (float2 *)p->d_frac, p->d_idx);
-    return cudaGetLastError();
+        return dfs_launch_dependent(k_scatter<double>, grid, dim3(tpb), 0, p->stream,
+                                    (const FoldRec<double> *)p->d_urec, f, p->d_pofs, p->bstride,
+                                    (const int *)p->d_bin_start, p->cstride, rowoff,
+                                    (const int *)p->d_bin_count, p->d_base, (double2 *)p->d_frac,
+                                    p->d_idx);
+    return dfs_launch_dependent(k_scatter<float>, grid, dim3(tpb), 0, p->stream,
+                                (const FoldRec<float> *)p->d_urec, f, p->d_pofs, p->bstride,
+                                (const int *)p->d_bin_start, p->cstride, rowoff,
+                                (const int *)p->d_bin_count, p->d_base, (float2 *)p->d_frac,
+                                p->d_idx);
 }
