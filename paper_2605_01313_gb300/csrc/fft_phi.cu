@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
                const typename CxT<R>::type *__restrict__ tw,
                const typename CxT<R>::type *__restrict__ stw, const int2 *__restrict__ rowrange,
                R *__restrict__ grid) {
+    dfs_grid_wait();
     typedef typename CxT<R>::type C;
     const int row0 = blockIdx.x * a.CB;
     const int2 rr = rowrange[(a.line0 + blockIdx.y) / a.F];
@@ -202,10 +203,11 @@ cudaError_t run_phi_df(dfsnufft_plan p, const PhiArgs &a, size_t smem, dim3 grid
     cudaError_t e = allow_smem(k_phi_pass<R, E, MAXT, MINB, LOGM, HERM, DF>, smem);
     if (e) return e;
     const bool dfr = std::is_same<R, df32>::value;     // double-single tables
-    k_phi_pass<R, E, MAXT, MINB, LOGM, HERM, DF><<<grid, threads, smem, p->stream>>>(
-        a, (const C *)p->d_T, (const C *)(dfr ? p->d_df_tw1 : p->d_tw1),
-        (const C *)(dfr ? p->d_df_stw_phi : p->d_stw_phi), p->d_rowrange, (R *)p->d_G);
-    return cudaGetLastError();
+    return dfs_launch_dependent(k_phi_pass<R, E, MAXT, MINB, LOGM, HERM, DF>, grid,
+                                dim3(threads), smem, p->stream, a, (const C *)p->d_T,
+                                (const C *)(dfr ? p->d_df_tw1 : p->d_tw1),
+                                (const C *)(dfr ? p->d_df_stw_phi : p->d_stw_phi),
+                                (const int2 *)p->d_rowrange, (R *)p->d_G);
 }
 
 // FP64 plans whose interpolation runs in double-single (p->gdf) take the DF form.

@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
                  const typename CxT<R>::type *__restrict__ stw,
                  const int2 *__restrict__ rowrange, typename CxT<R>::type *__restrict__ out,
                  const int *__restrict__ emax) {
+    dfs_grid_wait();
     typedef typename CxT<R>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *smem = reinterpret_cast<C *>(smem_raw);
@@ -559,11 +560,11 @@ cudaError_t run_theta_df(dfsnufft_plan p, const ThetaArgs &a, const void *coeffs
     typedef typename CxT<R>::type C;
     cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM, PRIN, double2, LOGN>, smem);
     if (e) return e;
-    k_theta_pass<R, E, MAXT, MINB, HERM, PRIN, double2, LOGN><<<grid, threads, smem, p->stream>>>(
-        a, (const double2 *)coeffs, (const R *)p->d_df_inv1, (const R *)p->d_df_inv2,
-        (const C *)p->d_df_tw2, (const C *)p->d_df_stw_theta, p->d_rowrange, (C *)p->d_T,
-        p->d_emax);
-    return cudaGetLastError();
+    return dfs_launch_dependent(
+        k_theta_pass<R, E, MAXT, MINB, HERM, PRIN, double2, LOGN>, grid, dim3(threads), smem,
+        p->stream, a, (const double2 *)coeffs, (const R *)p->d_df_inv1,
+        (const R *)p->d_df_inv2, (const C *)p->d_df_tw2, (const C *)p->d_df_stw_theta,
+        (const int2 *)p->d_rowrange, (C *)p->d_T, (const int *)p->d_emax);
 }
 
 template <typename R, int E, bool HERM, bool PRIN = false>
@@ -592,11 +593,11 @@ cudaError_t run_theta_plain(dfsnufft_plan p, const ThetaArgs &a, const void *coe
     } else {
         cudaError_t e = allow_smem(k_theta_pass<R, E, MAXT, MINB, HERM, PRIN>, smem);
         if (e) return e;
-        k_theta_pass<R, E, MAXT, MINB, HERM, PRIN><<<grid, threads, smem, p->stream>>>(
-            a, (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2,
-            (const C *)p->d_tw2, nullptr, p->d_rowrange, (C *)p->d_T, nullptr);
+        return dfs_launch_dependent(
+            k_theta_pass<R, E, MAXT, MINB, HERM, PRIN>, grid, dim3(threads), smem, p->stream, a,
+            (const C *)coeffs, (const R *)p->d_inv1, (const R *)p->d_inv2, (const C *)p->d_tw2,
+            (const C *)nullptr, (const int2 *)p->d_rowrange, (C *)p->d_T, (const int *)nullptr);
     }
-    return cudaGetLastError();
 }
 
 template <typename R>

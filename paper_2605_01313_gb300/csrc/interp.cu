@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const __grid_const
                                                 const int *__restrict__ n_tasks,
                                                 const int *__restrict__ pofs,
                                                 R *__restrict__ out_all) {
+    dfs_grid_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *tile = reinterpret_cast<R *>(smem_raw);
     const int TH = a.tile_y + W - 1;
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(256) k_interp_df(InterpArgs a,
                                                    const int *__restrict__ pofs,
                                                    double *__restrict__ out_all,
                                                    const int *__restrict__ emax) {
+    dfs_grid_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);
     const int TH = a.tile_y + W - 1;
@@ -872,20 +874,22 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
             const size_t smem_df = per_field * a.FG;
             cudaError_t e = dfs_allow_smem((const void *)k_interp_df<W>, smem_df);
             if (e) return e;
-            k_interp_df<W><<<dim3(per, M), 256, smem_df, p->stream>>>(
-                a, hd, (const float2 *)p->d_G, p->d_base, (const double *)p->d_frac, p->d_idx,
-                p->d_bin_start, p->d_task_bin, p->d_n_tasks, p->d_pofs, (double *)values,
-                p->d_emax);
-            return cudaGetLastError();
+            return dfs_launch_dependent(
+                k_interp_df<W>, dim3(per, M), dim3(256), smem_df, p->stream, a, hd,
+                (const float2 *)p->d_G, (const int2 *)p->d_base, (const double *)p->d_frac,
+                (const int *)p->d_idx, (const int *)p->d_bin_start, (const int *)p->d_task_bin,
+                (const int *)p->d_n_tasks, (const int *)p->d_pofs, (double *)values,
+                (const int *)p->d_emax);
         }
     }
     cudaError_t e = dfs_allow_smem((const void *)k_interp<R, W>, smem);
     if (e) return e;
     const int threads = sizeof(R) == 4 ? 128 : 256;
-    k_interp<R, W><<<dim3(per, M), threads, smem, p->stream>>>(
-        a, hw, (const R *)p->d_G, p->d_base, (const R *)p->d_frac, p->d_idx, p->d_bin_start,
-        p->d_task_bin, p->d_n_tasks, p->d_pofs, (R *)values);
-    return cudaGetLastError();
+    return dfs_launch_dependent(k_interp<R, W>, dim3(per, M), dim3(threads), smem, p->stream, a,
+                                hw, (const R *)p->d_G, (const int2 *)p->d_base,
+                                (const R *)p->d_frac, (const int *)p->d_idx,
+                                (const int *)p->d_bin_start, (const int *)p->d_task_bin,
+                                (const int *)p->d_n_tasks, (const int *)p->d_pofs, (R *)values);
 }
 
 template <typename R, int W>
