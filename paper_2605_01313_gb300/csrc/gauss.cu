@@ -125,68 +125,111 @@ struct GlArgs {
     int full;                 // 0: real-field staging (Hermitian part, see above)
 };
 
-// grid (ceil((N1/2 + 1) / 128), 2N rows, lines); block 128 threads over the
-// modes m = 0..N1/2 (DFT index).  out0/out1: the GEMM results of the two
-// classes, N x pitch complex; w: N reals.
+// Coefficients c_{n,m} and c_{n,-m} of one centred row n (an = |n|) and one
+// mode m of a line, from the class results: v0 = out0[an] (class 0, an < N),
+// v1 = out1[an - 1] (class 1, an >= 1) and beta = out1[N - 1] of the line's
+// slot of m; wn the Nyquist weight of row an.
+template <typename C, typename R>
+__device__ __forceinline__ void gl_coef(const GlArgs &a, bool cls0, int n, int m, C v0, C v1,
+                                        C beta, R wn, C &cm, C &cneg) {
+    const int N = a.N;
+    const int an = n < 0 ? -n : n;
+    if (cls0) {
+        // c_0 = a_0, c_{+-n} = a_n / 2, c_{-N} = 0; mode -m: conjugate data
+        C v = cmake((R)0, (R)0);
+        if (an < N) v = an ? cmake(v0.x * (R)0.5, v0.y * (R)0.5) : v0;
+        cm = v;
+        cneg = cmake(v.x, -v.y);
+    } else if (an == N) {                             // c_{-N} = i beta
+        cm = cmake(-beta.y, beta.x);
+        cneg = cmake(beta.y, beta.x);                 // i conj(beta)
+    } else {
+        // -+ i b_n / 2 (zero at n = 0), then - i beta w_n (/ 2 off n = 0)
+        C bi = cmake((R)0, (R)0);
+        cneg = cmake((R)0, (R)0);
+        if (an) {
+            const R sg = n > 0 ? (R)0.5 : (R)-0.5;
+            bi = cmake(v1.y * sg, -v1.x * sg);        // -i b sg
+            cneg = cmake(-v1.y * sg, -v1.x * sg);     // -i conj(b) sg
+        }
+        cm = bi;
+        // literal values for full output and in the columns m = 0 and N1/2,
+        // which a real-field plan evaluates as they are (its own mirror, the
+        // Nyquist column)
+        if (a.full || m == 0 || m == a.N1 / 2) {
+            cm = cmake(cm.x + beta.y * wn, cm.y - beta.x * wn);          // - i beta wn
+            cneg = cmake(cneg.x - beta.y * wn, cneg.y - beta.x * wn);    // - i conj(beta) wn
+        }
+    }
+}
+
+template <typename C> __device__ __forceinline__ void store_pair(C *p, C x, C y, bool vec) {
+    if constexpr (sizeof(C) == 8) {
+        if (vec) {
+            *reinterpret_cast<float4 *>(p) = make_float4(x.x, x.y, y.x, y.y);
+            return;
+        }
+    }
+    p[0] = x;
+    p[1] = y;
+}
+
+// grid (ceil((N1/4 + 1) / 128), N + 1, lines); block 128 threads over the
+// mode pairs q (modes m = 2q, 2q + 1 <= N1/2, one slot of both classes), blockIdx.y
+// the row pair an (rows n = +an <= N - 1 and n = -an >= -N).  Each class value
+// is read once for both rows; the two modes of a row go out as one 16-byte
+// store when vec (FP32, 16-byte aligned coefficients).  out0/out1: the GEMM
+// results of the two classes, N x pitch complex; w: N reals.
 template <typename R>
 __global__ void __launch_bounds__(128) k_gl_coeffs(GlArgs a, const typename CxT<R>::type *out0,
                                                    const typename CxT<R>::type *out1,
                                                    const R *__restrict__ w,
                                                    const int *__restrict__ parity,
-                                                   typename CxT<R>::type *__restrict__ coef) {
+                                                   typename CxT<R>::type *__restrict__ coef,
+                                                   int vec) {
+    dfs_grid_wait();
     typedef typename CxT<R>::type C;
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m > a.N1 / 2) return;
-    const int row = blockIdx.y;                       // centred row: n = row - N
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int h1 = a.N1 / 2;
+    if (2 * q > h1) return;
+    const int an = blockIdx.y;
     const int l = blockIdx.z;
     const int N = a.N;
-    const int n = row - N;
-    const int an = n < 0 ? -n : n;
     const int pneg = parity[l % a.F] < 0;
-    const bool cls0 = pneg == (m & 1);
-    const size_t slot = (size_t)l * a.K + (m >> 1);
-    C cm, cneg;                                       // c_{n,m} and c_{n,-m}
-    if (cls0) {
-        // c_0 = a_0, c_{+-n} = a_n / 2, c_{-N} = 0; mode -m: conjugate data
-        C v = cmake((R)0, (R)0);
-        if (an < N) {
-            v = out0[(size_t)an * a.pitch + slot];
-            if (an) v = cmake(v.x * (R)0.5, v.y * (R)0.5);
+    const size_t slot = (size_t)l * a.K + q;
+    const C zero = cmake((R)0, (R)0);
+    const C v0 = an < N ? out0[(size_t)an * a.pitch + slot] : zero;
+    const C v1 = an >= 1 && an <= N ? out1[(size_t)(an - 1) * a.pitch + slot] : zero;
+    const C beta = out1[(size_t)(N - 1) * a.pitch + slot];
+    const R wn = an < N ? (an ? (R)0.5 * w[an] : w[0]) : (R)0;
+    const int m0 = 2 * q;
+    const bool two = m0 + 1 <= h1;                    // mode 2q + 1 exists
+    for (int sgn = 0; sgn < 2; ++sgn) {
+        const int n = sgn ? -an : an;
+        if (sgn && an == 0) break;                    // n = 0 once
+        if (!sgn && an == N) continue;                // n = +N is not a row
+        C *col = coef + (size_t)l * 2 * N * a.N1 + (size_t)(n + N) * a.N1;
+        C cm[2], cn[2];
+        for (int k = 0; k < 2; ++k) {
+            const int m = m0 + k;
+            if (k == 1 && !two) break;
+            gl_coef<C, R>(a, pneg == (m & 1), n, m, v0, v1, beta, wn, cm[k], cn[k]);
         }
-        cm = v;
-        cneg = cmake(v.x, -v.y);
-    } else {
-        const C beta = out1[(size_t)(N - 1) * a.pitch + slot];
-        if (an == N) {                                // c_{-N} = i beta
-            cm = cmake(-beta.y, beta.x);
-            cneg = cmake(beta.y, beta.x);             // i conj(beta)
+        if (two && m0 + 1 < h1) {
+            // modes m0, m0 + 1 < N1/2: centred columns m + N1/2, adjacent
+            store_pair(col + m0 + h1, cm[0], cm[1], vec != 0);
         } else {
-            // -+ i b_n / 2 (zero at n = 0), then - i beta w_n (/ 2 off n = 0)
-            C bi = cmake((R)0, (R)0);
-            if (an) {
-                const C b = out1[(size_t)(an - 1) * a.pitch + slot];
-                const R sg = n > 0 ? (R)0.5 : (R)-0.5;
-                bi = cmake(b.y * sg, -b.x * sg);      // -i b sg
-                cneg = cmake(-b.y * sg, -b.x * sg);   // -i conj(b) sg
-            } else {
-                cneg = cmake((R)0, (R)0);
-            }
-            cm = bi;
-            // literal values for full output and in the columns m = 0 and N1/2,
-            // which a real-field plan evaluates as they are (its own mirror, the
-            // Nyquist column)
-            if (a.full || m == 0 || m == a.N1 / 2) {
-                const R wn = an ? (R)0.5 * w[an] : w[0];
-                cm = cmake(cm.x + beta.y * wn, cm.y - beta.x * wn);          // - i beta wn
-                cneg = cmake(cneg.x - beta.y * wn, cneg.y - beta.x * wn);    // - i conj(beta) wn
+            col[m0 < h1 ? m0 + h1 : 0] = cm[0];
+            if (two) col[m0 + 1 < h1 ? m0 + 1 + h1 : 0] = cm[1];
+        }
+        if (a.full || an == N) {                      // the mirrors of 0 < m < N1/2
+            for (int k = 0; k < 2; ++k) {
+                const int m = m0 + k;
+                if (k == 1 && !two) break;
+                if (m > 0 && m < h1) col[h1 - m] = cn[k];
             }
         }
     }
-    const int h1 = a.N1 / 2;
-    C *col = coef + (size_t)l * 2 * N * a.N1 + (size_t)row * a.N1;
-    const int mc = m < h1 ? m + h1 : 0;               // centred column of m
-    col[mc] = cm;
-    if (m > 0 && m < h1 && (a.full || an == N)) col[a.N1 - mc] = cneg;
 }
 
 }  // namespace
@@ -326,21 +369,26 @@ int dfs_launch_forward_gl(dfsnufft_plan p, const void *samples, const int *d_par
     a.K = K;
     a.pitch = pitch;
     a.full = full ? 1 : 0;
-    const dim3 grid((q.N1 / 2 + 1 + 127) / 128, 2 * N, lines);
+    const dim3 grid((q.N1 / 4 + 1 + 127) / 128, N + 1, lines);
+    // 16-byte stores of mode pairs: rows of N1 complex from a 16-byte aligned
+    // base, pairs starting at the even centred column m + N1/2
+    const int vec = ((uintptr_t)coeffs & 15) == 0 && (q.N1 / 2) % 2 == 0;
     if (f64) {
         typedef double2 C;
         const C *r0 = (const C *)o0;
-        k_gl_coeffs<double><<<grid, 128, 0, p->stream>>>(
-            a, r0, r0 + (size_t)N * pitch, (const double *)p->d_gl_mat + 2 * (size_t)N * N,
-            d_parity, (C *)coeffs);
+        e = dfs_launch_dependent(k_gl_coeffs<double>, grid, dim3(128), 0, p->stream, a, r0,
+                                 r0 + (size_t)N * pitch,
+                                 (const double *)p->d_gl_mat + 2 * (size_t)N * N,
+                                 (const int *)d_parity, (C *)coeffs, vec);
     } else {
         typedef float2 C;
         const C *r0 = (const C *)o0;
-        k_gl_coeffs<float><<<grid, 128, 0, p->stream>>>(
-            a, r0, r0 + (size_t)N * pitch, (const float *)p->d_gl_mat + 2 * (size_t)N * N,
-            d_parity, (C *)coeffs);
+        e = dfs_launch_dependent(k_gl_coeffs<float>, grid, dim3(128), 0, p->stream, a, r0,
+                                 r0 + (size_t)N * pitch,
+                                 (const float *)p->d_gl_mat + 2 * (size_t)N * N,
+                                 (const int *)d_parity, (C *)coeffs, vec);
     }
-    return cudaGetLastError() ? DFSNUFFT_ERR_CUDA : DFSNUFFT_OK;
+    return e ? DFSNUFFT_ERR_CUDA : DFSNUFFT_OK;
 }
 
 // Bytes of the theta-pass buffer the Gauss-Legendre form needs.
