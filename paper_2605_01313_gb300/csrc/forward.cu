@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fwd_theta(FwdAr
                                                    typename FwdIO<R>::Out *__restrict__ coef,
                                                    int nblk, int ntask,
                                                    const int *__restrict__ emax) {
+    dfs_grid_wait();
     typedef typename CxT<R>::type C;
     typedef typename FwdIO<R>::Out CO;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -296,10 +297,9 @@ cudaError_t run_fwd_theta(dfsnufft_plan p, const FwdArgs &a, const void *spec,
         occ = 1;
     const long long want = (long long)p->num_sms * occ;
     const int ctas = (int)(want < ntask ? want : ntask);
-    k_fwd_theta<R, E, LOG><<<ctas, a.CB * T, smem, p->stream>>>(
-        a, (const C *)spec, d_parity, (const C *)tb.tw2, (const C *)tb.stw_half,
-        (CO *)coeffs, nblk, ntask, emax);
-    return cudaGetLastError();
+    return dfs_launch_dependent(k_fwd_theta<R, E, LOG>, dim3(ctas), dim3(a.CB * T), smem,
+                                p->stream, a, (const C *)spec, d_parity, (const C *)tb.tw2,
+                                (const C *)tb.stw_half, (CO *)coeffs, nblk, ntask, emax);
 }
 
 template <typename R>

@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_gl_gemm(const __grid_constant__ 
                                                          const __grid_constant__ CUtensorMap mapG,
                                                          float *__restrict__ out, int N, int cols,
                                                          int *__restrict__ status) {
+    dfs_grid_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     Bars &B = *reinterpret_cast<Bars *>(base + MBYTES + RBYTES);
@@ -453,7 +454,6 @@ cudaError_t dfs_gl_tc_gemm(dfsnufft_plan p, const float *g, float *out, int N, i
     if (dfs_encode_tensor_map_3d_f32(&mapG, g, dims, str, box, 0)) return cudaErrorInvalidValue;
     const int ntiles = 2 * ((N + BM - 1) / BM) * ((cols + BN - 1) / BN);
     const int grid = ntiles < p->num_sms ? ntiles : p->num_sms;
-    k_gl_gemm<<<grid, THREADS, SMEM, p->stream>>>(p->tmap_gl_hi, p->tmap_gl_lo, mapG, out, N, cols,
-                                                 p->d_status);
-    return cudaGetLastError();
+    return dfs_launch_dependent(k_gl_gemm, dim3(grid), dim3(THREADS), SMEM, p->stream,
+                                p->tmap_gl_hi, p->tmap_gl_lo, mapG, out, N, cols, p->d_status);
 }
