@@ -3,10 +3,10 @@ against the FP64 oracle (oracle/gauss.py) through the C ABI.
 
 Tolerances.  The latitude solve's matrices have condition numbers below 5 at
 these sizes (cos and sin bases at the Gauss nodes), so the coefficients carry a
-few units of rounding of the GEMM's precision: FP64 1e-12 and FP32 (BF16x9
-tensor-core emulation or plain FP32) 1e-5 of the largest coefficient; values at
-departure points are then bounded as the interpolation tests bound them
-(1e-11 FP64, 2e-5 FP32, relative l-inf)."""
+few units of rounding of the GEMM's precision: FP64 1e-12 and FP32 (the
+tensor-core solve with TF32 operands split into two parts, FP32-level) 1e-5 of
+the largest coefficient; values at departure points are then bounded as the
+interpolation tests bound them (1e-11 FP64, 2e-5 FP32, relative l-inf)."""
 import math
 
 import numpy as np
@@ -132,3 +132,24 @@ def test_members_and_unsupported_sizes(torch_cuda):
     with pytest.raises(nufft.DfsError) as ei:
         Plan(24, 12, 1e-6, "f32", 1, options=Options.make(gauss=True))
     assert ei.value.status == nufft.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("real", [True, False])
+def test_unaligned_output_gives_the_same_coefficients(torch_cuda, real):
+    """The coefficient mapping writes two modes of a row as one 16-byte store
+    when the output is 16-byte aligned and one at a time otherwise: an output
+    that starts one complex element into a buffer must get the same bits."""
+    torch = torch_cuda
+    n_lon, n_lat = 256, 128
+    rng = np.random.default_rng(4242)
+    s = torch.from_numpy(rng.standard_normal((3, n_lat, n_lon))).to(torch.float32).cuda()
+    par = [1, -1, -1]
+    with gl_plan(n_lon, n_lat, "f32", 3, real=real) as plan:
+        aligned = plan.grid_to_coeffs(s, par).cpu()
+        n = aligned.numel()
+        buf = torch.zeros(n + 1, dtype=aligned.dtype, device="cuda")
+        out = buf[1:].view(aligned.shape)
+        assert out.data_ptr() % 16 == 8
+        shifted = plan.grid_to_coeffs(s, par, out=out).cpu()
+    assert torch.equal(torch.view_as_real(aligned), torch.view_as_real(shifted))
+
