@@ -486,8 +486,9 @@ def measure(args, name, wl, ws, rank, dev, serving, cpu_seconds=None):
 
     def e2e_step():
         if not (pr_in or grid_in):
-            plan.set_points_host(h_lon, h_colat)
-            plan.execute_host(h_coef, h_out)
+            # new points and coefficients from host arrays, values back: the
+            # library's joint call (copies and passes scheduled together)
+            plan.execute_points_host(h_lon, h_colat, h_coef, h_out)
             return
         # the host-buffer entry points take complex coefficients: partial-
         # regularity and grid input go through pinned copies around the call

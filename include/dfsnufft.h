@@ -437,6 +437,24 @@ int dfsnufft_set_points_host(dfsnufft_plan plan, int64_t n_points, const double 
                              const double *colat);
 int dfsnufft_execute_host(dfsnufft_plan plan, const void *coeffs, void *values);
 
+/* dfsnufft_set_points_host followed by dfsnufft_execute_host (Sec. 5, Eq. 5.3:
+ * the values of the fields' series at new points), the two scheduled together:
+ * one step of the semi-Lagrangian scheme from host arrays.  Arguments, layouts
+ * and results as for those two calls (lon, colat: n_points FP64 each; coeffs,
+ * values: the layouts of dfsnufft_execute, plan precision), and as they do it
+ * leaves the points set for later execute calls.  For a one-member FP32 plan of
+ * two or more fields the copies to the device run in the order field 0's
+ * coefficients, points, the other fields' coefficients, so that field 0's theta
+ * and phi passes (over every fine row: the range the points need is not known
+ * before they are sorted) overlap the copy of the points; each field's values
+ * go back as soon as it is done.  Other plans run the two calls in turn.  The
+ * copies start after all work queued on the plan's stream before the call; the
+ * call waits for the stream before it returns, so the host arrays are free again
+ * on return.  Errors: DFSNUFFT_ERR_INVALID_ARG (null pointer, n_points outside
+ * [1, 2^31 - 1], a batched plan), DFSNUFFT_ERR_OOM, CUDA failures (sticky). */
+int dfsnufft_execute_points_host(dfsnufft_plan plan, int64_t n_points, const double *lon,
+                                 const double *colat, const void *coeffs, void *values);
+
 /* Release every device buffer of the plan (synchronises its stream first). */
 int dfsnufft_destroy(dfsnufft_plan plan);
 

@@ -142,6 +142,10 @@ struct dfsnufft_plan_s {
     // copy_stream after the copies
     cudaStream_t copy_stream;
     cudaEvent_t stage_free, coef_ready;
+    // the per-field pipeline's value copies back to the host: a stream of their
+    // own, so that a field's values leave as soon as it is done instead of
+    // queueing behind the later fields' coefficient copies
+    cudaStream_t back_stream;
     // one-member host-buffer path, pipelined per field: for line f, coefficients
     // staged (line_ev[2 f]) and values ready (line_ev[2 f + 1]); pts_copied marks
     // the end of set_points_host's point copies (pts_pending: not yet waited for)

@@ -338,6 +338,11 @@ static void release(dfsnufft_plan p) {
         cudaStreamDestroy(p->copy_stream);
         p->copy_stream = nullptr;
     }
+    if (p->back_stream) {
+        cudaStreamSynchronize(p->back_stream);
+        cudaStreamDestroy(p->back_stream);
+        p->back_stream = nullptr;
+    }
     if (p->stage_free) cudaEventDestroy(p->stage_free);
     if (p->coef_ready) cudaEventDestroy(p->coef_ready);
     p->stage_free = p->coef_ready = nullptr;
@@ -860,6 +865,19 @@ extern "C" int dfsnufft_interpolate_grid(dfsnufft_plan p, const void *samples, c
 
 // ------------------------------------------------------------------ host-buffer variants
 
+// Device staging of the host points, sized to the point capacity.
+static int ensure_point_staging(dfsnufft_plan p) {
+    if (p->pts_stage_cap >= p->cap_points) return DFSNUFFT_OK;
+    DFS_CK(p, cudaStreamSynchronize(p->stream));
+    dfs_free((void **)&p->d_pts_stage);
+    p->pts_stage_cap = 0;
+    const int rc = dfs_alloc(p, (void **)&p->d_pts_stage, 2 * sizeof(double) * p->cap_points,
+                             "point staging");
+    if (rc) return rc;
+    p->pts_stage_cap = p->cap_points;
+    return DFSNUFFT_OK;
+}
+
 extern "C" int dfsnufft_set_points_host(dfsnufft_plan p, int64_t n_points, const double *lon,
                                         const double *colat) {
     if (!p) return DFSNUFFT_ERR_INVALID_ARG;
@@ -868,16 +886,8 @@ extern "C" int dfsnufft_set_points_host(dfsnufft_plan p, int64_t n_points, const
         return DFSNUFFT_ERR_INVALID_ARG;
     int rc = update_counts(p, &n_points);
     if (rc) return rc;
-    if (p->pts_stage_cap < p->cap_points) {
-        // staging sized to the point capacity
-        DFS_CK(p, cudaStreamSynchronize(p->stream));
-        dfs_free((void **)&p->d_pts_stage);
-        p->pts_stage_cap = 0;
-        rc = dfs_alloc(p, (void **)&p->d_pts_stage, 2 * sizeof(double) * p->cap_points,
-                       "point staging");
-        if (rc) return rc;
-        p->pts_stage_cap = p->cap_points;
-    }
+    rc = ensure_point_staging(p);
+    if (rc) return rc;
     size_t b = sizeof(double) * (size_t)n_points;
     DFS_CK(p, cudaMemcpyAsync(p->d_pts_stage, lon, b, cudaMemcpyHostToDevice, p->stream));
     DFS_CK(p, cudaMemcpyAsync(p->d_pts_stage + p->pts_stage_cap, colat, b,
@@ -951,19 +961,15 @@ static int ensure_line_events(dfsnufft_plan p, int n) {
     return DFSNUFFT_OK;
 }
 
-extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *values) {
-    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
-    if (p->status) return p->status;
-    if (!p->has_points) return DFSNUFFT_ERR_NO_POINTS;
-    if (!coeffs || !values) return DFSNUFFT_ERR_INVALID_ARG;
+// Device staging of host coefficients and values, the copy stream and its
+// events (cs: bytes of one complex coefficient).
+static int ensure_host_staging(dfsnufft_plan p, size_t cs) {
     const dfsnufft_params &q = p->prm;
-    size_t cs = q.dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
-    size_t rs = cs / 2;
-    size_t cb = cs * (size_t)p->n_members * p->n_fields * q.N2 * q.N1;
-    size_t vb = rs * (size_t)p->n_fields * (size_t)p->n_points;
+    const size_t rs = cs / 2;
     int rc;
     if (!p->d_coef_stage) {
-        rc = dfs_alloc(p, &p->d_coef_stage, cb, "coefficient staging");
+        rc = dfs_alloc(p, &p->d_coef_stage, cs * (size_t)p->n_members * p->n_fields * q.N2 * q.N1,
+                       "coefficient staging");
         if (rc) return rc;
     }
     if (p->val_stage_cap < p->n_points) {
@@ -980,6 +986,20 @@ extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *
         DFS_CK(p, cudaEventCreateWithFlags(&p->coef_ready, cudaEventDisableTiming));
         DFS_CK(p, cudaEventRecord(p->stage_free, p->stream));     // every earlier reader
     }
+    return DFSNUFFT_OK;
+}
+
+extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *values) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    if (!p->has_points) return DFSNUFFT_ERR_NO_POINTS;
+    if (!coeffs || !values) return DFSNUFFT_ERR_INVALID_ARG;
+    const dfsnufft_params &q = p->prm;
+    size_t cs = q.dtype == DFSNUFFT_F64 ? sizeof(double2) : sizeof(float2);
+    size_t rs = cs / 2;
+    size_t vb = rs * (size_t)p->n_fields * (size_t)p->n_points;
+    int rc = ensure_host_staging(p, cs);
+    if (rc) return rc;
     // the copies wait only for the last reader of the staging buffer (and for
     // set_points_host's point copies, which use the same link), not for the
     // set_points kernels queued on the plan's stream
@@ -997,6 +1017,8 @@ extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *
         // transform of all fields.
         rc = ensure_line_events(p, F);
         if (rc) return rc;
+        if (!p->back_stream)
+            DFS_CK(p, cudaStreamCreateWithFlags(&p->back_stream, cudaStreamNonBlocking));
         for (int f = 0; f < F; ++f) {
             DFS_CK(p, stage_coefficients(p, coeffs, cs, p->copy_stream, f, 1));
             DFS_CK(p, cudaEventRecord(p->line_ev[2 * f], p->copy_stream));
@@ -1010,13 +1032,13 @@ extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *
             p->win0 = p->nwin = 0;
             if (rc) return rc;
             DFS_CK(p, cudaEventRecord(p->line_ev[2 * f + 1], p->stream));
-            DFS_CK(p, cudaStreamWaitEvent(p->copy_stream, p->line_ev[2 * f + 1], 0));
+            DFS_CK(p, cudaStreamWaitEvent(p->back_stream, p->line_ev[2 * f + 1], 0));
             DFS_CK(p, cudaMemcpyAsync(static_cast<char *>(values) + f * fb,
                                       static_cast<const char *>(p->d_val_stage) + f * fb, fb,
-                                      cudaMemcpyDeviceToHost, p->copy_stream));
+                                      cudaMemcpyDeviceToHost, p->back_stream));
         }
         DFS_CK(p, cudaEventRecord(p->stage_free, p->stream));
-        DFS_CK(p, cudaEventRecord(p->vals_copied, p->copy_stream));
+        DFS_CK(p, cudaEventRecord(p->vals_copied, p->back_stream));
         DFS_CK(p, cudaStreamWaitEvent(p->stream, p->vals_copied, 0));
         return dfsnufft_plan_check(p);
     }
@@ -1027,6 +1049,109 @@ extern "C" int dfsnufft_execute_host(dfsnufft_plan p, const void *coeffs, void *
     if (rc) return rc;
     DFS_CK(p, cudaEventRecord(p->stage_free, p->stream));
     DFS_CK(p, cudaMemcpyAsync(values, p->d_val_stage, vb, cudaMemcpyDeviceToHost, p->stream));
+    return dfsnufft_plan_check(p);
+}
+
+namespace {
+// Every fine row of every member needed: the theta and phi passes of a field
+// transformed before the points are sorted compute all rows.
+__global__ void k_rowrange_all(int2 *rowrange, int members, int n2) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < members) rowrange[k] = make_int2(0, n2);
+}
+}  // namespace
+
+// set_points_host then execute_host, scheduled together.  For a one-member FP32
+// plan of several fields the host link carries field 0's coefficients first,
+// then the points, then the other fields' coefficients; field 0's theta and phi
+// passes (over every fine row, the needed range being unknown until the points
+// are sorted) run while the points travel, and each field's values go back as
+// soon as it is done.  Other plans run the two calls one after the other.
+extern "C" int dfsnufft_execute_points_host(dfsnufft_plan p, int64_t n_points, const double *lon,
+                                            const double *colat, const void *coeffs,
+                                            void *values) {
+    if (!p) return DFSNUFFT_ERR_INVALID_ARG;
+    if (p->status) return p->status;
+    const dfsnufft_params &q = p->prm;
+    const int F = p->n_fields;
+    if (p->n_members != 1 || F < 2 || q.dtype != DFSNUFFT_F32) {
+        const int rc = dfsnufft_set_points_host(p, n_points, lon, colat);
+        return rc ? rc : dfsnufft_execute_host(p, coeffs, values);
+    }
+    if (n_points < 1 || n_points > 0x7fffffffLL || !lon || !colat || !coeffs || !values)
+        return DFSNUFFT_ERR_INVALID_ARG;
+    int rc = update_counts(p, &n_points);
+    if (rc) return rc;
+    const size_t cs = sizeof(float2), rs = sizeof(float);
+    if ((rc = ensure_point_staging(p)) || (rc = ensure_host_staging(p, cs)) ||
+        (rc = ensure_line_events(p, F)))
+        return rc;
+    if (!p->back_stream)
+        DFS_CK(p, cudaStreamCreateWithFlags(&p->back_stream, cudaStreamNonBlocking));
+    if (!p->pts_copied)
+        DFS_CK(p, cudaEventCreateWithFlags(&p->pts_copied, cudaEventDisableTiming));
+    // the copies wait for everything queued before the call (the last readers
+    // of the point and coefficient staging among it)
+    DFS_CK(p, cudaEventRecord(p->stage_free, p->stream));
+    DFS_CK(p, cudaStreamWaitEvent(p->copy_stream, p->stage_free, 0));
+    p->pts_pending = 0;
+    p->has_points = 0;
+    DFS_CK(p, stage_coefficients(p, coeffs, cs, p->copy_stream, 0, 1));
+    DFS_CK(p, cudaEventRecord(p->line_ev[0], p->copy_stream));
+    const size_t b = sizeof(double) * (size_t)n_points;
+    DFS_CK(p, cudaMemcpyAsync(p->d_pts_stage, lon, b, cudaMemcpyHostToDevice, p->copy_stream));
+    DFS_CK(p, cudaMemcpyAsync(p->d_pts_stage + p->pts_stage_cap, colat, b,
+                              cudaMemcpyHostToDevice, p->copy_stream));
+    DFS_CK(p, cudaEventRecord(p->pts_copied, p->copy_stream));
+    for (int f = 1; f < F; ++f) {
+        DFS_CK(p, stage_coefficients(p, coeffs, cs, p->copy_stream, f, 1));
+        DFS_CK(p, cudaEventRecord(p->line_ev[2 * f], p->copy_stream));
+    }
+    // field 0's transform over every row while the points travel
+    DFS_CK(p, cudaStreamWaitEvent(p->stream, p->line_ev[0], 0));
+    k_rowrange_all<<<1, 32, 0, p->stream>>>(p->d_rowrange, p->n_members, q.n2);
+    DFS_CK(p, cudaGetLastError());
+    p->win0 = 0;
+    p->nwin = 1;
+    DFS_CK(p, timing_begin(p, 1));
+    DFS_CK(p, dfs_launch_theta_pass(p, p->d_coef_stage));
+    DFS_CK(p, timing_end(p, 1));
+    DFS_CK(p, timing_begin(p, 2));
+    DFS_CK(p, dfs_launch_phi_pass(p));
+    DFS_CK(p, timing_end(p, 2));
+    p->win0 = p->nwin = 0;
+    // the points sorted (this also sets the needed row range of the later fields)
+    DFS_CK(p, cudaStreamWaitEvent(p->stream, p->pts_copied, 0));
+    DFS_CK(p, timing_begin(p, 0));
+    DFS_CK(p, dfs_launch_set_points(p, p->d_pts_stage, p->d_pts_stage + p->pts_stage_cap));
+    DFS_CK(p, timing_end(p, 0));
+    p->has_points = 1;
+    const size_t fb = rs * (size_t)n_points;
+    for (int f = 0; f < F; ++f) {
+        p->win0 = f;
+        p->nwin = 1;
+        if (f > 0) {
+            DFS_CK(p, cudaStreamWaitEvent(p->stream, p->line_ev[2 * f], 0));
+            DFS_CK(p, timing_begin(p, 1));
+            DFS_CK(p, dfs_launch_theta_pass(p, p->d_coef_stage));
+            DFS_CK(p, timing_end(p, 1));
+            DFS_CK(p, timing_begin(p, 2));
+            DFS_CK(p, dfs_launch_phi_pass(p));
+            DFS_CK(p, timing_end(p, 2));
+        }
+        DFS_CK(p, timing_begin(p, 3));
+        DFS_CK(p, dfs_launch_interp(p, p->d_val_stage));
+        DFS_CK(p, timing_end(p, 3));
+        p->win0 = p->nwin = 0;
+        DFS_CK(p, cudaEventRecord(p->line_ev[2 * f + 1], p->stream));
+        DFS_CK(p, cudaStreamWaitEvent(p->back_stream, p->line_ev[2 * f + 1], 0));
+        DFS_CK(p, cudaMemcpyAsync(static_cast<char *>(values) + f * fb,
+                                  static_cast<const char *>(p->d_val_stage) + f * fb, fb,
+                                  cudaMemcpyDeviceToHost, p->back_stream));
+    }
+    DFS_CK(p, cudaEventRecord(p->stage_free, p->stream));
+    DFS_CK(p, cudaEventRecord(p->vals_copied, p->back_stream));
+    DFS_CK(p, cudaStreamWaitEvent(p->stream, p->vals_copied, 0));
     return dfsnufft_plan_check(p);
 }
 

@@ -30,7 +30,8 @@ ERR_TIMEOUT = 7
 # Every symbol include/dfsnufft.h declares.
 EXPORTS = (
     "dfsnufft_plan_create", "dfsnufft_set_points", "dfsnufft_execute",
-    "dfsnufft_set_points_host", "dfsnufft_execute_host", "dfsnufft_destroy",
+    "dfsnufft_set_points_host", "dfsnufft_execute_host", "dfsnufft_execute_points_host",
+    "dfsnufft_destroy",
     "dfsnufft_strerror", "dfsnufft_plan_last_error", "dfsnufft_plan_get_params",
     "dfsnufft_choose_params", "dfsnufft_es_kernel", "dfsnufft_kernel_ft", "dfsnufft_version",
     "dfsnufft_plan_enable_timing", "dfsnufft_plan_read_timing", "dfsnufft_plan_point_stats",
@@ -179,6 +180,7 @@ def lib():
         L.dfsnufft_grid_to_coeffs.argtypes = [vp, vp, vp, vp]
         L.dfsnufft_interpolate_grid.argtypes = [vp, vp, vp, vp]
         L.dfsnufft_execute_host.argtypes = [vp, vp, vp]
+        L.dfsnufft_execute_points_host.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp]
         L.dfsnufft_destroy.argtypes = [vp]
         L.dfsnufft_strerror.argtypes = [i32]
         L.dfsnufft_strerror.restype = ctypes.c_char_p
@@ -325,6 +327,13 @@ def dfsnufft_set_points_host(h, n_points, lon_ptr, colat_ptr):
 def dfsnufft_execute_host(h, coeffs_ptr, values_ptr):
     _check(lib().dfsnufft_execute_host(h, ctypes.c_void_p(coeffs_ptr),
                                        ctypes.c_void_p(values_ptr)), h)
+
+
+def dfsnufft_execute_points_host(h, n_points, lon_ptr, colat_ptr, coeffs_ptr, values_ptr):
+    _check(lib().dfsnufft_execute_points_host(h, ctypes.c_int64(n_points), ctypes.c_void_p(lon_ptr),
+                                              ctypes.c_void_p(colat_ptr),
+                                              ctypes.c_void_p(coeffs_ptr),
+                                              ctypes.c_void_p(values_ptr)), h)
 
 
 def dfsnufft_destroy(h):
@@ -673,6 +682,25 @@ class Plan:
         if out is None:
             out = np.empty((self.n_fields, self.n_points), dtype=rd)
         dfsnufft_execute_host(self._h, c.ctypes.data, out.ctypes.data)
+        return out
+
+    def execute_points_host(self, lon, colat, coeffs, out=None):
+        """set_points_host then execute_host as one call (host arrays in and out),
+        the copies and passes scheduled together."""
+        lon = np.ascontiguousarray(lon, dtype=np.float64)
+        colat = np.ascontiguousarray(colat, dtype=np.float64)
+        if lon.shape != colat.shape or lon.ndim != 1:
+            raise ValueError("points must be 1-D float64 arrays of equal length")
+        cd = np.complex128 if self.dtype == "f64" else np.complex64
+        rd = np.float64 if self.dtype == "f64" else np.float32
+        c = np.ascontiguousarray(coeffs, dtype=cd)
+        if c.shape != self.coeff_shape:
+            raise ValueError("coeffs must have shape %s" % (self.coeff_shape,))
+        if out is None:
+            out = np.empty((self.n_fields, lon.size), dtype=rd)
+        dfsnufft_execute_points_host(self._h, lon.size, lon.ctypes.data, colat.ctypes.data,
+                                     c.ctypes.data, out.ctypes.data)
+        self.n_points = lon.size
         return out
 
     def check(self):

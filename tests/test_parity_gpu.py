@@ -307,6 +307,38 @@ def test_host_variants_match_device(torch_cuda, n_fields, dtype):
             assert np.array_equal(dev, host)
 
 
+@pytest.mark.parametrize("real", [True, False])
+@pytest.mark.parametrize("n_fields", [1, 3])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_execute_points_host_matches_the_two_calls(torch_cuda, n_fields, dtype, real):
+    """execute_points_host (points and coefficients from the host in one call;
+    for FP32 plans of several fields field 0's transform runs over every fine
+    row before the points are sorted) gives the values of set_points_host
+    followed by execute_host bit for bit, leaves the points set for a later
+    execute, and agrees with the oracle; the points change between calls."""
+    from paper_2605_01313_gb300 import Plan
+    from paper_2605_01313_gb300.nufft import Options
+    torch = torch_cuda
+    cd = np.complex128 if dtype == "f64" else np.complex64
+    tol = 1e-12 if dtype == "f64" else 1e-6
+    bound = 1e-11 if dtype == "f64" else 2e-5
+    wls = [synth.small_workload(seed, 128, 64, n_fields=n_fields, dtype=dtype) for seed in (5, 6)]
+    with Plan(128, 64, tol, dtype, n_fields, options=Options.make(real_fields=real)) as plan:
+        for wl in wls:
+            c = wl.coeffs.astype(cd)
+            joint = plan.execute_points_host(wl.lon, wl.colat, c)
+            plan.set_points_host(wl.lon, wl.colat)
+            apart = plan.execute_host(c)
+            assert np.array_equal(joint, apart)
+            plan.execute_points_host(wl.lon, wl.colat, c)
+            dev = plan.execute(torch.from_numpy(c).cuda()).cpu().numpy()
+            assert np.array_equal(dev, joint)
+            s_ = wl.sample[:64]
+            ref = oracle.evaluate(wl.coeffs, wl.lon[s_], wl.colat[s_])
+            for f in range(n_fields):
+                assert oracle.rel_linf(joint[f][s_], ref[f].real) <= bound
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_host_execute_real_plan_stages_what_it_reads(torch_cuda, dtype):
     """A real-field plan's execute_host copies only the columns m >= 0 and the
