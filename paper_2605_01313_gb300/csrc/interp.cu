@@ -281,6 +281,30 @@ __global__ void __launch_bounds__(256) k_interp_df(InterpArgs a,
     }
 }
 
+// FP32 weights by mirror pairs.  The kernel is even and the fit is made on
+// nodes symmetric about the centre, so tap W-1-a at s is tap a at -s: with tap
+// a's polynomial split into even and odd parts in u = s^2, P_a(+-s) = E(u) +-
+// s O(u) gives both weights of the pair from two Horner chains of half length
+// (about 36 FMAs instead of 49 for w = 7).
+template <int W>
+__device__ __forceinline__ void es_weights_mirror(float t, const Horner<float, W> &h, float *wv) {
+    constexpr int KE = W - (W & 1);           // highest even power
+    constexpr int KO = W - 1 + (W & 1);       // highest odd power
+    const float s = t - (W % 2 == 0 ? 0.5f : 0.f);
+    const float u = s * s;
+#pragma unroll
+    for (int a = 0; a < (W + 1) / 2; ++a) {
+        float e = h.c[a][KE];
+#pragma unroll
+        for (int k = KE - 2; k >= 0; k -= 2) e = fmaf(e, u, h.c[a][k]);
+        float o = h.c[a][KO];
+#pragma unroll
+        for (int k = KO - 2; k >= 1; k -= 2) o = fmaf(o, u, h.c[a][k]);
+        wv[a] = fmaf(s, o, e);
+        if (W - 1 - a != a) wv[W - 1 - a] = fmaf(-s, o, e);
+    }
+}
+
 // Weights of one FP32 point for the paired reads: wy[W] and the x weights
 // shifted by the parity of the first tap into a zero-padded vector w8[WP].
 template <int W>
@@ -289,8 +313,8 @@ __device__ __forceinline__ void paired_weights(float tx, float ty, int odd,
                                                float *wy) {
     constexpr int WP = (W + 2) & ~1;
     float wx[W];
-    es_weights<float, W>(tx, hw, wx);
-    es_weights<float, W>(ty, hw, wy);
+    es_weights_mirror<W>(tx, hw, wx);
+    es_weights_mirror<W>(ty, hw, wy);
 #pragma unroll
     for (int k = 0; k < WP; ++k) {
         const float lo = k < W ? wx[k] : 0.f;
