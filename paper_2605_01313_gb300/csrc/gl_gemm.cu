@@ -17,20 +17,20 @@
 // group runs.  M_hi and M_lo are formed on the host (the matrices are the
 // plan's); G is split on the fly.
 //
-// The tensor core computes the transpose, O^T = G^T M^T, in 128 x 128 tiles: the
-// A operand is the split G tile (128 columns of G x 32 k), held
-// in tensor memory, where the threads that split it store it directly (no
-// shared-memory traffic); the B operand is the M tile (128 rows of M x 32 k,
-// K-major, 128-byte swizzle), loaded by TMA.  Accumulator lane n is then column
-// j0 + n of O, so that the stores of a warp are coalesced.  The kernel is
-// persistent: one CTA per multiprocessor takes output tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ..., and its rings and accumulators run on across the
-// tiles, so that one tile's last sums are stored while the next one's products
-// run.  K runs in tiles of 32 through three rings, deep enough to cover the
-// latency of the L2: NM stages
-// of M_hi, M_lo (shared memory), NR stages of raw G tiles (32 k x 128 columns,
-// shared memory) and NT stages of G_hi, G_lo (tensor memory).  The warps have
-// one job each:
+// The tensor core computes the transpose, O^T = G^T M^T, in 128 x 128 tiles:
+// the A operand is the split G tile (128 columns of G x 32 k), held in tensor
+// memory, where the threads that split it store it directly (no shared-memory
+// traffic); the B operand is the M tile (128 rows of M x 32 k, K-major,
+// 128-byte swizzle), loaded by TMA.  Accumulator lane n is then column j0 + n
+// of O, so that the stores of a warp are coalesced.  The kernel is persistent
+// (launched as a dependent of the longitude pass, which it waits for first):
+// one CTA per multiprocessor takes output tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ..., and its rings and accumulators run on across the tiles, so
+// that one tile's last sums are stored while the next one's products run.  K
+// runs in tiles of 32 through three rings, deep enough to cover the latency of
+// the L2: NM stages of M_hi, M_lo (shared memory), NR stages of raw G tiles
+// (32 k x 128 columns, shared memory) and NT stages of G_hi, G_lo (tensor
+// memory).  The warps have one job each:
 //   warps 0-3   (drain) add each finished accumulator group into registers
 //               (`accfull` -> `accempty`) and at the end store the sums;
 //   warps 4-7   (producers) read their column of the raw G tile (`rawfull` ->
