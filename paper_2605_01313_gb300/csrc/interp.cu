@@ -18,9 +18,10 @@
 // bin's tiles arriving by TMA (one 2-D box per field) while the current bin is
 // evaluated; the few bins whose tile wraps around the torus seam are staged
 // with plain loads instead.  Inside a bin the points come sorted by fine row
-// (set_points), so a warp's lanes mostly read consecutive words of one row.  k_interp_f32 (plain loads, the same arithmetic)
-// serves plans without a tensor map, and k_interp the FP64 form and wide
-// kernels.
+// (set_points), so a warp's lanes mostly read consecutive words of one row;
+// each stencil row is read with loads as wide as its alignment allows (see
+// "Stencil reads" below).  k_interp_f32 (plain loads, paired reads) serves
+// plans without a tensor map, and k_interp the FP64 form and wide kernels.
 #include <limits.h>
 
 #include "common.cuh"
@@ -323,6 +324,132 @@ __device__ __forceinline__ void paired_weights(float tx, float ty, int odd,
     }
 }
 
+// Stencil reads of the FP32 TMA kernel.  A tile row holds BW cells (a multiple
+// of 4) and starts on a 16-byte boundary; the point's W taps start at column
+// ox of its row.  Three read patterns, chosen by W:
+//
+// Exact-width reads, W = 4q + 3 (w = 7 on 32-cell bins, whose row stride is a
+// compile-time constant): the row's W cells are one 8-byte pair, one single
+// cell and q aligned 16-byte quads, in an order fixed by m = ox mod 4.
+// Offsets from the first tap:
+//   m = 0: quads at 0,  pair at 4q,     single at 4q + 2
+//   m = 1: single at 0, pair at 1,      quads at 3
+//   m = 2: pair at 0,   quads at 2,     single at 4q + 2
+//   m = 3: single at 0, quads at 1,     pair at 4q + 1
+// Every access is aligned to its width and no cell outside the stencil is
+// read: 2 + q loads a row instead of (W + 1) / 2 pairs, and fewer bank
+// conflicts, since a quarter-warp's 16-byte loads of neighbouring points of
+// one row fall on distinct banks.  For 2.1M points and three fields on a
+// 2048 x 1024 grid (w = 7) this took the kernel from 86 to 77 us.
+//
+// Split reads, other odd W (and w = 7 on other bin widths): (W - 1) / 2
+// aligned pairs and one single cell (first when ox is odd, last when it is
+// even); 80 us on the same case.  Launches of one field (the host-buffer
+// pipeline) would run faster in this form (fewer registers, and the per-point
+// set-up of the exact-width weights is not shared by several fields), but the
+// two forms add a row's products in different orders, and every launch of a
+// plan keeps one form so that all its entry points give the same bits.
+//
+// Paired reads, even W: WP / 2 aligned pairs from the even column at or
+// below ox, the point's weights shifted by the parity of ox (paired_weights).
+template <int W> struct ExactRow {
+    static constexpr int Q4 = W / 4;          // 16-byte quads a row
+    int o4, o2, o1;                           // offsets of the quads, the pair, the single cell
+    float w4[Q4 > 0 ? 4 * Q4 : 1], w2[2], w1; // the x weights in that order
+};
+
+template <int W>
+__device__ __forceinline__ void exact_weights(float tx, float ty, int m,
+                                              const Horner<float, W> &hw, ExactRow<W> &er,
+                                              float *wy) {
+    static_assert(W % 4 == 3, "exact-width reads need W = 4q + 3");
+    constexpr int Q4 = ExactRow<W>::Q4;
+    float wx[W];
+    es_weights_mirror<W>(tx, hw, wx);
+    es_weights_mirror<W>(ty, hw, wy);
+    er.o4 = (4 - m) & 3;
+    er.o2 = m == 0 ? 4 * Q4 : m == 1 ? 1 : m == 2 ? 0 : 4 * Q4 + 1;
+    er.o1 = (m & 1) ? 0 : W - 1;
+#pragma unroll
+    for (int i = 0; i < 4 * Q4; ++i)
+        er.w4[i] = m == 0 ? wx[i] : m == 1 ? wx[3 + i] : m == 2 ? wx[2 + i] : wx[1 + i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        er.w2[i] = m == 0 ? wx[4 * Q4 + i] : m == 1 ? wx[1 + i] : m == 2 ? wx[i]
+                                                                        : wx[4 * Q4 + 1 + i];
+    er.w1 = (m & 1) ? wx[0] : wx[W - 1];
+}
+
+// The w x w stencil sum of one field by exact-width reads: tp points at the
+// first tap's cell in the tile, rows BWC floats apart (bw_rt when BWC is 0).
+template <int W, int BWC>
+__device__ __forceinline__ float exact_sum(const float *tp, int bw_rt, const ExactRow<W> &er,
+                                           const float *wy) {
+    const int bw = BWC ? BWC : bw_rt;
+    const float *p1 = tp + er.o1;
+    const float2 *p2 = reinterpret_cast<const float2 *>(tp + er.o2);
+    const float4 *p4 = reinterpret_cast<const float4 *>(tp + er.o4);
+    float acc = 0.f;
+#pragma unroll
+    for (int bb = 0; bb < W; ++bb) {
+        const float2 g2 = p2[bb * (bw / 2)];
+        float rr = er.w1 * p1[bb * bw];
+        rr = fmaf(er.w2[0], g2.x, rr);
+        rr = fmaf(er.w2[1], g2.y, rr);
+#pragma unroll
+        for (int c = 0; c < ExactRow<W>::Q4; ++c) {
+            const float4 g = p4[bb * (bw / 4) + c];
+            rr = fmaf(er.w4[4 * c], g.x, rr);
+            rr = fmaf(er.w4[4 * c + 1], g.y, rr);
+            rr = fmaf(er.w4[4 * c + 2], g.z, rr);
+            rr = fmaf(er.w4[4 * c + 3], g.w, rr);
+        }
+        acc = fmaf(wy[bb], rr, acc);
+    }
+    return acc;
+}
+
+// Split reads (odd W): the x weights in read order, the single cell's last.
+template <int W> struct SplitRow {
+    int o2, o1;
+    float w2[W - 1], w1;
+};
+
+template <int W>
+__device__ __forceinline__ void split_weights(float tx, float ty, int odd,
+                                              const Horner<float, W> &hw, SplitRow<W> &sr,
+                                              float *wy) {
+    static_assert(W % 2 == 1, "split reads need odd W");
+    float wx[W];
+    es_weights_mirror<W>(tx, hw, wx);
+    es_weights_mirror<W>(ty, hw, wy);
+    sr.o2 = odd;
+    sr.o1 = odd ? 0 : W - 1;
+#pragma unroll
+    for (int i = 0; i < W - 1; ++i) sr.w2[i] = odd ? wx[1 + i] : wx[i];
+    sr.w1 = odd ? wx[0] : wx[W - 1];
+}
+
+template <int W>
+__device__ __forceinline__ float split_sum(const float *tp, int bw, const SplitRow<W> &sr,
+                                           const float *wy) {
+    const float *p1 = tp + sr.o1;
+    const float2 *p2 = reinterpret_cast<const float2 *>(tp + sr.o2);
+    float acc = 0.f;
+#pragma unroll
+    for (int bb = 0; bb < W; ++bb) {
+        float rr = sr.w1 * p1[bb * bw];
+#pragma unroll
+        for (int k = 0; k < (W - 1) / 2; ++k) {
+            const float2 g = p2[bb * (bw / 2) + k];
+            rr = fmaf(sr.w2[2 * k], g.x, rr);
+            rr = fmaf(sr.w2[2 * k + 1], g.y, rr);
+        }
+        acc = fmaf(wy[bb], rr, acc);
+    }
+    return acc;
+}
+
 // FP32 form: the tile starts at an even column and each stencil row is read as
 // WP/2 aligned pairs of cells (8-byte shared loads).  Neighbouring points of
 // the departure grid sit about two cells apart, so a warp's loads fall on
@@ -433,13 +560,14 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a,
 // other stage (issued by thread 0 after the barrier that ends sub-task j - 1's
 // reads of it).  A box starts at the bin's first stencil column rounded down
 // to 4 cells (16 bytes, the TMA alignment rule), so a point's first tap sits
-// at column ox in [0, tile_x + 2] of the box and its paired reads end below
-// tile_x + 2 + WP <= BW.  A box that would leave [0, n1) x [0, n2) (a bin at
+// at column ox in [0, tile_x + 2] of the box and its reads end below
+// tile_x + 2 + WP <= BW.  BWC, when nonzero, is BW as a compile-time constant
+// (the exact-width reads).  A box that would leave [0, n1) x [0, n2) (a bin at
 // the torus seam) is not copied by TMA: its barrier phase completes on the
 // issuing thread's arrival alone, and the CTA stages the tile with wrapped
 // plain loads.  A wait that runs out (about a second) sets the status word to
 // DFS_STATUS_TIMEOUT and ends the CTA after its copies land.
-template <int W>
+template <int W, int BWC>
 __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
                                                     const __grid_constant__ Horner<float, W> hw,
                                                     const __grid_constant__ CUtensorMap gmap,
@@ -460,7 +588,8 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
     uint64_t *bar = reinterpret_cast<uint64_t *>(sb);
     float *stage = reinterpret_cast<float *>(sb + 128);
     const int TH = a.tile_y + W - 1;
-    const int Q = a.BW / 2;                   // pairs per box row
+    const int BWr = BWC ? BWC : a.BW;         // floats per box row
+    const int Q = BWr / 2;                    // pairs per box row
     const int k = blockIdx.y;
     const int p0 = pofs[k];
     const int Pk = pofs[k + 1] - p0;
@@ -547,7 +676,7 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
                 const int r = rr - ff * TH;
                 const int gr = (row0 + r) & (a.n2 - 1);
                 const int gc = (col0 + 2 * qq) & (a.n1 - 1);
-                *reinterpret_cast<float2 *>(tile + (size_t)ff * a.box_f + r * a.BW + 2 * qq) =
+                *reinterpret_cast<float2 *>(tile + (size_t)ff * a.box_f + r * BWr + 2 * qq) =
                     *reinterpret_cast<const float2 *>(
                         grid + ((size_t)(k * a.F + f0 + ff) * a.n2 + gr) * a.n1 + gc);
             }
@@ -555,11 +684,45 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
         }
         while (pi < e) {
             const int ox = b.x - col0;
+            const int oy = b.y - row0;
+            const int d = dst;
+            if constexpr (BWC != 0 && W % 4 == 3) {
+                ExactRow<W> er;
+                float wy[W];
+                exact_weights<W>(t.x, t.y, ox & 3, hw, er, wy);
+                pi += blockDim.x;
+                if (pi < e) {                  // next record in flight during the sums
+                    b = base[pi];
+                    t = reinterpret_cast<const float2 *>(frac)[pi];
+                    dst = idx[pi];
+                }
+                for (int ff = 0; ff < fg; ++ff) {
+                    const float *tp = tile + (size_t)ff * a.box_f + oy * BWr + ox;
+                    out_all[(size_t)a.F * p0 + (size_t)(f0 + ff) * Pk + d] =
+                        exact_sum<W, BWC>(tp, BWr, er, wy);
+                }
+                continue;
+            }
+            if constexpr (W % 2 == 1) {
+                SplitRow<W> sr;
+                float wy[W];
+                split_weights<W>(t.x, t.y, ox & 1, hw, sr, wy);
+                pi += blockDim.x;
+                if (pi < e) {                  // next record in flight during the sums
+                    b = base[pi];
+                    t = reinterpret_cast<const float2 *>(frac)[pi];
+                    dst = idx[pi];
+                }
+                for (int ff = 0; ff < fg; ++ff) {
+                    const float *tp = tile + (size_t)ff * a.box_f + oy * BWr + ox;
+                    out_all[(size_t)a.F * p0 + (size_t)(f0 + ff) * Pk + d] =
+                        split_sum<W>(tp, BWr, sr, wy);
+                }
+                continue;
+            }
             const int odd = ox & 1;
             float w8[WP], wy[W];
             paired_weights<W>(t.x, t.y, odd, hw, w8, wy);
-            const int oy = b.y - row0;
-            const int d = dst;
             pi += blockDim.x;
             if (pi < e) {                      // next record in flight during the sums
                 b = base[pi];
@@ -568,7 +731,7 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
             }
             for (int ff = 0; ff < fg; ++ff) {
                 const float2 *tp = reinterpret_cast<const float2 *>(
-                    tile + (size_t)ff * a.box_f + oy * a.BW + (ox - odd));
+                    tile + (size_t)ff * a.box_f + oy * BWr + (ox - odd));
                 float acc = 0.f;
 #pragma unroll
                 for (int bb = 0; bb < W; ++bb) {
@@ -831,11 +994,17 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
                 a.FG = fg;
                 a.NG = (a.fn + fg - 1) / fg;
                 const size_t smem = 128 + 128 + 2 * (size_t)fg * a.box_f * sizeof(float);
-                cudaError_t e = dfs_allow_smem((const void *)k_interp_tma<W>, smem);
+                // w = 7 on 32-cell bins (BW = 44): the exact-width reads, in
+                // every launch of the plan, so that launches of one field (the
+                // host-buffer pipeline) and of all fields give the same bits
+                auto kern = k_interp_tma<W, 0>;
+                if constexpr (W == 7)
+                    if (BW == 44) kern = k_interp_tma<W, 44>;
+                cudaError_t e = dfs_allow_smem((const void *)kern, smem);
                 if (e) return e;
                 if (p->interp_ctas_per_sm <= 0) {
                     int occ = 0;
-                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_interp_tma<W>, 128,
+                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128,
                                                                       smem) != cudaSuccess ||
                         occ < 1)
                         occ = 1;
@@ -846,7 +1015,7 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
                 if (want > cap) want = cap;
                 if (want < 1) want = 1;
                 return dfs_launch_dependent(
-                    k_interp_tma<W>, dim3((unsigned)want, M), dim3(128), smem, p->stream, a, hf,
+                    kern, dim3((unsigned)want, M), dim3(128), smem, p->stream, a, hf,
                     p->tmap_G, (const float *)p->d_G, (const int2 *)p->d_base,
                     (const float *)p->d_frac, (const int *)p->d_idx,
                     (const int *)p->d_bin_start, (const int *)p->d_task_bin,
