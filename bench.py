@@ -360,12 +360,23 @@ def run_ours(args):
                       cpu_seconds=args.cpu_seconds / 2)
         if line is not None:
             line["fp64"] = {k: rec[k] for k in FP64_KEYS if k in rec}
+    if args.workload == DEFAULT_WORKLOAD and not args.no_ensemble:
+        # the batched form: 64 members of four grid sizes in one graph launch a step
+        rec = measure_ensemble(args, "c4_ensemble_f32", ws, rank, dev,
+                               cpu_seconds=args.cpu_seconds / 4)
+        if line is not None:
+            line["ensemble"] = {k: rec[k] for k in ENSEMBLE_KEYS if k in rec}
     if line is not None:
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
+
+# keys of the nested ensemble record of the default run
+ENSEMBLE_KEYS = ("metric", "value", "unit", "ms_per_step", "p50_ms", "p99_ms", "steps", "warmup",
+                 "dtype", "config", "roofline", "gpu_launches", "persistent", "e2e", "error",
+                 "clocks")
 
 # keys of the nested FP64 record of the default run
 FP64_KEYS = ("metric", "value", "unit", "ms_per_step", "p50_ms", "p99_ms", "steps", "warmup",
@@ -749,7 +760,6 @@ def cpu_baseline(wl, gpu_vals, seconds, others=None):
 def run_ensemble(args):
     """64 members on four grids, three FP32 fields each: one CUDA graph per step."""
     import torch
-    from paper_2605_01313_gb300 import nufft
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -757,7 +767,21 @@ def run_ensemble(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    members = make_workload(args.workload)
+    line = measure_ensemble(args, args.workload, ws, rank, dev, args.cpu_seconds)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def measure_ensemble(args, name, ws, rank, dev, cpu_seconds):
+    """The ensemble step of workload ``name`` (the fork/join graph and the
+    persistent launch), timed on every rank; the line on rank 0, else None."""
+    import torch
+    from paper_2605_01313_gb300 import nufft
+
+    members = make_workload(name)
     groups, pts, cfs, outs, host_in, host_out = [], [], [], [], [], []
     by_size = {}
     for wl in members:
@@ -881,14 +905,14 @@ def run_ensemble(args):
     achieved = step_bytes / (total_ms / args.steps * 1e-3) / 1e9
     if rank != 0:
         ens.destroy()
-        return
+        return None
     # accuracy: the first member of every group against the oracle on its
     # seeded check points (and the oracle's own rate on them)
     errs, o_pf, o_s = {}, 0, 0.0
     for gi, (m, n_lon, n_lat) in enumerate(groups):
         wl = by_size[(n_lon, n_lat)][0]
         vals = outs[gi][:3 * wl.n_points].view(3, wl.n_points).cpu().numpy()
-        n = min(wl.sample.size, _oracle_sample_size(wl, args.cpu_seconds / len(groups)))
+        n = min(wl.sample.size, _oracle_sample_size(wl, cpu_seconds / len(groups)))
         s_ = wl.sample[:n]
         t0 = time.perf_counter()
         ref = oracle.evaluate(wl.coeffs, wl.lon[s_], wl.colat[s_])
@@ -902,7 +926,7 @@ def run_ensemble(args):
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": args.workload,
+        "config": {"workload": name,
                    "groups": ["%dx(%dx%d)" % g for g in groups], "fields": 3,
                    "members": sum(g[0] for g in groups), "point_fields": total_pf, "tol": 1e-6,
                    "graph": "one CUDA graph launch per step (fork/join over group streams)",
@@ -929,7 +953,7 @@ def run_ensemble(args):
                                    "3 fields, FP64 direct sum (%d point-fields)" % o_pf},
     }
     ens.destroy()
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def serving_sweep(dev, rates, seconds, budget_gb=120):
@@ -958,13 +982,19 @@ def serving_sweep(dev, rates, seconds, budget_gb=120):
     from paper_2605_01313_gb300.nufft import Options
     srv = Server(tol=1e-6, dtype="f32", n_fields=3, hbm_budget=int(budget_gb) << 30, max_batch=8,
                  options=Options.make(real_fields=True))
-    poisson_run(srv, reqs, 200, 0.5, seed=1)        # warm: slots created, plans resident
     out = []
     for k, rate in enumerate(rates):
+        # warm-up at this rate: the server creates a slot (a batched plan and its
+        # buffers) the first time the concurrency calls for one, a one-time
+        # cost kept out of the steady-state latencies; the slot counts before
+        # and after the measured run show whether one was still created in it
+        poisson_run(srv, reqs, rate, max(0.5, seconds / 2), seed=100 + k)
+        slots0 = srv.stats()["slots"]
         lat, pf, wall, n = poisson_run(srv, reqs, rate, seconds, seed=10 + k)
         out.append({"rate": rate, "requests": n, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                     "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                    "value": pf / wall})
+                    "max_ms": float(np.max(lat) * 1e3),
+                    "value": pf / wall, "slots": [slots0, srv.stats()["slots"]]})
     stats = srv.stats()
     srv.close()
     # FP64, one request at a time (plans cached per grid)
@@ -1060,6 +1090,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="leave the 64-member ensemble record out of the default run")
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the nested FP64 record of the default workload")
     ap.add_argument("--keep-order", action="store_true",

@@ -149,6 +149,28 @@ __global__ void __launch_bounds__(256) k_row_prefix(int nbins, int tile_y, int c
     int *slice = count_all + (size_t)blockIdx.y * cstride;
     int *rc = slice + rowoff + (size_t)bin * tile_y;
     int sum = 0;
+    if ((tile_y & 3) == 0 && tile_y <= 32 && (reinterpret_cast<uintptr_t>(rc) & 15) == 0) {
+        // all of the bin's row counts in flight at once (16-byte loads), then
+        // the offsets stored over them
+        const int nq = tile_y >> 2;
+        int4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < nq) v[q] = reinterpret_cast<const int4 *>(rc)[q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < nq) {
+                int4 o;
+                o.x = sum;
+                o.y = o.x + v[q].x;
+                o.z = o.y + v[q].y;
+                o.w = o.z + v[q].z;
+                sum = o.w + v[q].w;
+                reinterpret_cast<int4 *>(rc)[q] = o;
+            }
+        slice[bin] = sum;
+        return;
+    }
     for (int r = 0; r < tile_y; ++r) {
         const int c = rc[r];
         rc[r] = sum;
