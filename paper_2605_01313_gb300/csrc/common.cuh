@@ -105,6 +105,8 @@ struct dfsnufft_plan_s {
     int64_t *h_pofs;            // members + 1 point offsets of the current points (host)
     int64_t max_member_points;  // largest member's point count
     int *d_status;              // device status word (DFS_STATUS_*), zero when healthy
+    int *d_work;                // per member: the interpolation's next sub-task and
+                                // finished-CTA counters (zero between launches)
     // Gauss-Legendre latitude grid (DFSNUFFT_GAUSS_GRID, gauss.cu)
     int gl;
     void *d_gl_mat;             // C^{-1}, S^{-1} (n_lat x n_lat each, / n_lon), then w

@@ -553,12 +553,19 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a,
     }
 }
 
-// FP32 with TMA staging.  grid (CTAs per member, members); CTA i of member k
-// takes sub-tasks i, i + gridDim.x, ... of the member, a sub-task being one
-// non-empty bin and one group of FG fields.  Two stages: while sub-task j is
-// evaluated from stage j & 1, the boxes of sub-task j + gridDim.x land in the
-// other stage (issued by thread 0 after the barrier that ends sub-task j - 1's
-// reads of it).  A box starts at the bin's first stencil column rounded down
+// FP32 with TMA staging.  grid (CTAs per member, members); the CTAs of member
+// k claim its sub-tasks from the member's counter work[2k] (one atomic a
+// claim), a sub-task being one non-empty bin and one group of FG fields, so
+// that SMs whose bins hold fewer points take more of them and all finish
+// together.  Claims take the sub-tasks from both ends of the bin list inward
+// (claim i: sub-task total - 1 - i/2 for even i, i/2 for odd i): the bins of
+// the first and last bin rows, where departure points near the poles crowd
+// (up to six times a bin's median count on a 2048 x 1024 grid), start first
+// instead of one of them holding up the end of the launch.  Two stages: while a CTA evaluates its sub-task from stage j & 1,
+// the boxes of the next one it claimed land in the other stage (claimed and
+// issued by thread 0 after the barrier that ends the reads of that stage).
+// The last CTA of the member to finish (counter work[2k + 1]) sets both
+// counters back to zero for the next launch.  A box starts at the bin's first stencil column rounded down
 // to 4 cells (16 bytes, the TMA alignment rule), so a point's first tap sits
 // at column ox in [0, tile_x + 2] of the box and its reads end below
 // tile_x + 2 + WP <= BW.  BWC, when nonzero, is BW as a compile-time constant
@@ -580,12 +587,14 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
                                                     const int *__restrict__ n_tasks,
                                                     const int *__restrict__ pofs,
                                                     float *__restrict__ out_all,
-                                                    int *__restrict__ status) {
+                                                    int *__restrict__ status,
+                                                    int *__restrict__ work) {
     dfs_grid_wait();
     constexpr int WP = (W + 2) & ~1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *sb = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sb);
+    int *s_sub = reinterpret_cast<int *>(sb + 16);   // the sub-task staged in each stage
     float *stage = reinterpret_cast<float *>(sb + 128);
     const int TH = a.tile_y + W - 1;
     const int BWr = BWC ? BWC : a.BW;         // floats per box row
@@ -596,6 +605,7 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
     const int total = n_tasks[k] * a.NG;
     const int *task_bin = task_all + (size_t)k * a.bstride;
     const int *bin_start = bin_start_all + (size_t)k * a.bstride;
+    int *wk = work + 2 * k;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -627,12 +637,26 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
                         (k * a.F + f0 + ff) * a.n2 + row0, &bar[b]);
     };
     uint32_t ph0 = 0, ph1 = 0;
-    int it = 0;
-    if (threadIdx.x == 0 && (int)blockIdx.x < total) issue(blockIdx.x, 0);
-    for (int sub = blockIdx.x; sub < total; sub += gridDim.x, ++it) {
+    auto claim = [&]() {
+        const int i = atomicAdd(&wk[0], 1);
+        return i >= total ? total : (i & 1) ? i >> 1 : total - 1 - (i >> 1);
+    };
+    if (threadIdx.x == 0) {
+        const int first = claim();
+        s_sub[0] = first;
+        if (first < total) issue(first, 0);
+    }
+    __syncthreads();
+    for (int it = 0;; ++it) {
         const int cur = it & 1;
-        const int nxt = sub + gridDim.x;
-        if (threadIdx.x == 0 && nxt < total) issue(nxt, cur ^ 1);
+        const int sub = s_sub[cur];
+        if (sub >= total) break;
+        int nxt = total;
+        if (threadIdx.x == 0) {
+            nxt = claim();
+            s_sub[cur ^ 1] = nxt;
+            if (nxt < total) issue(nxt, cur ^ 1);
+        }
         // geometry and the first point's record, fetched while the boxes land
         const int task = sub / a.NG;
         const int f0 = a.fa + (sub - task * a.NG) * a.FG;
@@ -663,7 +687,7 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
                 if (nxt < total) mbar_wait_bounded(&bar[cur ^ 1], cur ? ph0 : ph1);
             }
             __syncthreads();
-            return;
+            break;
         }
         float *tile = stage + (size_t)cur * a.FG * a.box_f;
         if (wraps(col0, row0)) {
@@ -746,7 +770,16 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
                 out_all[(size_t)a.F * p0 + (size_t)(f0 + ff) * Pk + d] = acc;
             }
         }
-        __syncthreads();                       // stage cur is free for sub-task + 2 gridDim.x
+        __syncthreads();                       // stage cur is free for the claim after next
+    }
+    // the member's last CTA to finish resets its counters for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&wk[1], 1) == (int)gridDim.x - 1) {
+            wk[0] = 0;
+            wk[1] = 0;
+            __threadfence();
+        }
     }
 }
 
@@ -976,7 +1009,7 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
         // TMA form: plans that own their buffers (status word, fixed d_G)
         const int TH = q.tile_y + W - 1;
         const int BW = (q.tile_x + WP + 2 + 3) & ~3;
-        if (p->d_status && BW / 2 <= 256 && TH <= 256) {
+        if (p->d_status && p->d_work && BW / 2 <= 256 && TH <= 256) {
             if (!p->tmap_G_ok) {
                 if (dfs_encode_tensor_map_2d(&p->tmap_G, p->d_G, (uint64_t)(q.n1 / 2),
                                              (uint64_t)M * a.F * q.n2,
@@ -1020,7 +1053,7 @@ cudaError_t launch_w(dfsnufft_plan p, void *values) {
                     (const float *)p->d_frac, (const int *)p->d_idx,
                     (const int *)p->d_bin_start, (const int *)p->d_task_bin,
                     (const int *)p->d_n_tasks, (const int *)p->d_pofs, (float *)values,
-                    p->d_status);
+                    p->d_status, p->d_work);
             }
         }
         // plain loads: tile rows of at most 32 pairs

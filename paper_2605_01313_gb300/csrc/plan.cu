@@ -318,7 +318,7 @@ static void release(dfsnufft_plan p) {
                      &p->d_T, &p->d_G, (void **)&p->d_bin_count, (void **)&p->d_bin_start,
                      (void **)&p->d_task_bin, (void **)&p->d_n_tasks,
                      (void **)&p->d_status, (void **)&p->d_parity, (void **)&p->d_rowrange,
-                     (void **)&p->d_pofs,
+                     (void **)&p->d_pofs, (void **)&p->d_work,
                      &p->d_urec, (void **)&p->d_base, &p->d_frac, (void **)&p->d_idx,
                      (void **)&p->d_pts_stage, &p->d_coef_stage, &p->d_val_stage,
                      &p->d_df_tw1, &p->d_df_tw2, &p->d_df_inv1, &p->d_df_inv2,
@@ -589,6 +589,7 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
         {(void **)&p->d_parity, sizeof(int) * 64, "field parities"},
         {(void **)&p->d_rowrange, sizeof(int2) * nm, "row ranges"},
         {(void **)&p->d_pofs, sizeof(int) * (nm + 1), "point offsets"},
+        {(void **)&p->d_work, sizeof(int) * 2 * nm, "interpolation work counters"},
     };
     p->h_pofs = (int64_t *)calloc(nm + 1, sizeof(int64_t));
     if (!p->h_pofs) {
@@ -625,6 +626,7 @@ static int plan_create_impl(int n_members, int n_lon, int n_lat, double tol, int
         cudaError_t e = cudaGetDevice(&dev);
         if (!e) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (!e) e = cudaMemset(p->d_status, 0, sizeof(int));
+        if (!e) e = cudaMemset(p->d_work, 0, sizeof(int) * 2 * nm);
         if (e) rc = fail_cuda(p, "device query", e);
     }
     if (rc != DFSNUFFT_OK) {
