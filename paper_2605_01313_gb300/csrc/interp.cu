@@ -64,6 +64,17 @@ __device__ __forceinline__ void es_weights(R t, const Horner<R, W> &h, R *wv) {
     }
 }
 
+// The i-th of n claims of the TMA kernel's counter, as a position in the bin
+// list: from both ends inward (n - 1 - i/2 for even i, i/2 for odd i, a
+// permutation of [0, n)).  The densest bins are those of the first and last
+// bin rows, where departure points near the poles crowd, so they start first
+// rather than one of them holding up the end of the launch.  (The kernels
+// that walk the list with a fixed stride keep the plain order: on the
+// wave-scheduled FP64 grid this order measured 1179 against 1140 us.)
+__device__ __forceinline__ int ends_inward(int i, int n) {
+    return (i & 1) ? i >> 1 : n - 1 - (i >> 1);
+}
+
 template <typename R, int W>
 __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const __grid_constant__ Horner<R, W> hw,
                                                 const R *__restrict__ grid,
@@ -639,7 +650,7 @@ __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
     uint32_t ph0 = 0, ph1 = 0;
     auto claim = [&]() {
         const int i = atomicAdd(&wk[0], 1);
-        return i >= total ? total : (i & 1) ? i >> 1 : total - 1 - (i >> 1);
+        return i >= total ? total : ends_inward(i, total);
     };
     if (threadIdx.x == 0) {
         const int first = claim();
