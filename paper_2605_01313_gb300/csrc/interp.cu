@@ -569,22 +569,24 @@ __global__ void __launch_bounds__(128) k_interp_f32(InterpArgs a,
 // claim), a sub-task being one non-empty bin and one group of FG fields, so
 // that SMs whose bins hold fewer points take more of them and all finish
 // together.  Claims take the sub-tasks from both ends of the bin list inward
-// (claim i: sub-task total - 1 - i/2 for even i, i/2 for odd i): the bins of
-// the first and last bin rows, where departure points near the poles crowd
-// (up to six times a bin's median count on a 2048 x 1024 grid), start first
-// instead of one of them holding up the end of the launch.  Two stages: while a CTA evaluates its sub-task from stage j & 1,
-// the boxes of the next one it claimed land in the other stage (claimed and
-// issued by thread 0 after the barrier that ends the reads of that stage).
-// The last CTA of the member to finish (counter work[2k + 1]) sets both
-// counters back to zero for the next launch.  A box starts at the bin's first stencil column rounded down
-// to 4 cells (16 bytes, the TMA alignment rule), so a point's first tap sits
-// at column ox in [0, tile_x + 2] of the box and its reads end below
-// tile_x + 2 + WP <= BW.  BWC, when nonzero, is BW as a compile-time constant
-// (the exact-width reads).  A box that would leave [0, n1) x [0, n2) (a bin at
-// the torus seam) is not copied by TMA: its barrier phase completes on the
-// issuing thread's arrival alone, and the CTA stages the tile with wrapped
-// plain loads.  A wait that runs out (about a second) sets the status word to
-// DFS_STATUS_TIMEOUT and ends the CTA after its copies land.
+// (ends_inward): the bins of the first and last bin rows, where departure
+// points near the poles crowd (up to six times a bin's median count on a
+// 2048 x 1024 grid), start first instead of one of them holding up the end of
+// the launch.  The last CTA of the member to finish (counter work[2k + 1])
+// sets both counters back to zero for the next launch.
+//
+// Two stages: while a CTA evaluates its sub-task from stage j & 1, the boxes
+// of the next one it claimed land in the other stage (claimed and issued by
+// thread 0 after the barrier that ends the reads of that stage).  A box starts
+// at the bin's first stencil column rounded down to 4 cells (16 bytes, the TMA
+// alignment rule), so a point's first tap sits at column ox in [0, tile_x + 2]
+// of the box and its reads end below tile_x + 2 + WP <= BW.  BWC, when
+// nonzero, is BW as a compile-time constant (the exact-width reads).  A box
+// that would leave [0, n1) x [0, n2) (a bin at the torus seam) is not copied
+// by TMA: its barrier phase completes on the issuing thread's arrival alone,
+// and the CTA stages the tile with wrapped plain loads.  A wait that runs out
+// (about a second) sets the status word to DFS_STATUS_TIMEOUT and ends the
+// CTA's loop after its copies land.
 template <int W, int BWC>
 __global__ void __launch_bounds__(128) k_interp_tma(InterpArgs a,
                                                     const __grid_constant__ Horner<float, W> hw,
